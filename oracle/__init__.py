@@ -1,0 +1,268 @@
+"""CPU FP64 oracle for the space-time heat BEM operators and the pFMM matvec.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` / ``--impl reference`` legs may import this package.  It shares no code with
+the CUDA path in ``paper_2106_15911_gb300``; its arithmetic lives in ``pfmm_oracle.c`` (plain
+C, FP64) and ``solve.py`` (plain numpy), each function citing the passage of arXiv 2106.15911
+it follows.
+
+Parity unpinned: the accuracy of the chosen nearfield quadrature rule against the paper's
+semi-analytic scheme (not reproduced); it is pinned by self-convergence and by closed-form
+Laplace potentials only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pfmm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, IEEE semantics, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("nv", ctypes.c_int), ("nt", ctypes.c_int),
+        ("V", ctypes.POINTER(ctypes.c_double)), ("T", ctypes.POINTER(ctypes.c_int)),
+        ("Tend", ctypes.c_double), ("Et", ctypes.c_int), ("alpha", ctypes.c_double),
+        ("m_t", ctypes.c_int), ("m_x", ctypes.c_int), ("c_st", ctypes.c_double),
+        ("n_tr", ctypes.c_int), ("eps_tr", ctypes.c_double),
+        ("leaf_steps", ctypes.c_int), ("leaf_tris", ctypes.c_int),
+        ("n_r", ctypes.c_int), ("n_s", ctypes.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            d, i, pd, pi = ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+            for name in ("orc_G", "orc_G1", "orc_G2", "orc_G2t", "orc_DL2", "orc_DL2t"):
+                getattr(L, name).restype = d
+                getattr(L, name).argtypes = [d, d, d]
+            for name in ("orc_time_V", "orc_time_K"):
+                getattr(L, name).restype = d
+                getattr(L, name).argtypes = [d, i, d, d]
+            L.orc_gauss_legendre01.argtypes = [i, pd, pd]
+            L.orc_pair_integral.argtypes = [pd, pi, pi, i, i, d, d, pd, i, i, pd]
+            L.orc_assemble_V.argtypes = [i, pd, i, pi, d, d, i, i, i, i, pd, i]
+            L.orc_assemble_K.argtypes = [i, pd, i, pi, d, d, i, i, i, i, pd, i]
+            L.orc_assemble_M.argtypes = [i, pd, i, pi, d, pd]
+            L.orc_tree_info.argtypes = [ctypes.POINTER(Problem), pi, pi, pi, pd, pi, pi, pd]
+            L.orc_pfmm_apply.argtypes = [ctypes.POINTER(Problem), i, pd, pd, pi, i, i, i]
+            L.orc_E1.restype = d
+            L.orc_E1.argtypes = [i, i, d, d, i]
+            L.orc_qt.restype = d
+            L.orc_qt.argtypes = [i, i, i, i]
+            L.orc_qx.restype = d
+            L.orc_qx.argtypes = [i, i, d, d, d, d, i]
+            L.orc_lagrange.restype = d
+            L.orc_lagrange.argtypes = [i, i, d, d, d]
+            L.orc_cheb_node.restype = d
+            L.orc_cheb_node.argtypes = [i, i]
+            L.orc_interaction_list.argtypes = [i, pi]
+            L.orc_nearfield_list.argtypes = [i, pi]
+            L.orc_sizeof_problem.restype = i
+            assert L.orc_sizeof_problem() == ctypes.sizeof(Problem)
+            _lib = L
+    return _lib
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _pi(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+# ---- scalar kernels (Section 2) ------------------------------------------------------------
+def G(r, s, alpha=1.0):
+    return lib().orc_G(r, s, alpha)
+
+
+def G1(r, s, alpha=1.0):
+    return lib().orc_G1(r, s, alpha)
+
+
+def G2(r, s, alpha=1.0):
+    return lib().orc_G2(r, s, alpha)
+
+
+def G2t(r, s, alpha=1.0):
+    return lib().orc_G2t(r, s, alpha)
+
+
+def DL2(r, s, alpha=1.0):
+    return lib().orc_DL2(r, s, alpha)
+
+
+def DL2t(r, s, alpha=1.0):
+    return lib().orc_DL2t(r, s, alpha)
+
+
+def time_V(r, d, h, alpha=1.0):
+    return lib().orc_time_V(r, d, h, alpha)
+
+
+def time_K(r, d, h, alpha=1.0):
+    return lib().orc_time_K(r, d, h, alpha)
+
+
+def gauss_legendre01(n):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().orc_gauss_legendre01(n, _pd(x), _pd(w))
+    return x, w
+
+
+KIND_V, KIND_K, KIND_LAPSL, KIND_LAPDL, KIND_POLY = 0, 1, 2, 3, 4
+
+
+def pair_integral(V, tx, ty, kind, n, use_ss=True, d=0, h=1.0, alpha=1.0, poly=(0, 0, 0, 0)):
+    """Integral over gamma_tx x gamma_ty of the chosen kernel (see pfmm_oracle.c, Sec. 3)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    tx = np.ascontiguousarray(tx, dtype=np.int32)
+    ty = np.ascontiguousarray(ty, dtype=np.int32)
+    pc = np.ascontiguousarray(poly, dtype=np.float64)
+    out = np.zeros(3)
+    nc = lib().orc_pair_integral(_pd(V), _pi(tx), _pi(ty), kind, d, h, alpha, _pd(pc), n, 1 if use_ss else 0, _pd(out))
+    return out[:nc] if nc > 1 else float(out[0])
+
+
+# ---- dense Galerkin blocks (Section 2) -----------------------------------------------------
+def assemble_V(V, T, h, alpha=1.0, d0=0, nd=1, n_r=3, n_s=6, nthreads=0):
+    """Toeplitz blocks A_d[x][y] = V[(k,x),(k-d,y)], d = d0 .. d0+nd-1, shape [nd, nt, nt]."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    out = np.zeros((nd, T.shape[0], T.shape[0]))
+    rc = lib().orc_assemble_V(V.shape[0], _pd(V), T.shape[0], _pi(T), h, alpha, d0, nd, n_r, n_s, _pd(out), nthreads)
+    assert rc == 0
+    return out
+
+
+def assemble_K(V, T, h, alpha=1.0, d0=0, nd=1, n_r=3, n_s=6, nthreads=0):
+    """Toeplitz blocks B_d[x][i] = K[(k,x),(k-d,i)] (node columns), shape [nd, nt, nv]."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    out = np.zeros((nd, T.shape[0], V.shape[0]))
+    rc = lib().orc_assemble_K(V.shape[0], _pd(V), T.shape[0], _pi(T), h, alpha, d0, nd, n_r, n_s, _pd(out), nthreads)
+    assert rc == 0
+    return out
+
+
+def assemble_M(V, T, h):
+    """Mass block M[(k,x),(k,i)] = h |gamma_x| / 3 for i a vertex of gamma_x, shape [nt, nv]."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    out = np.zeros((T.shape[0], V.shape[0]))
+    lib().orc_assemble_M(V.shape[0], _pd(V), T.shape[0], _pi(T), h, _pd(out))
+    return out
+
+
+def toeplitz_apply(blocks, x):
+    """f[k] = sum_{d=0}^{k} A_d x[k-d] for blocks [nd,nt,ncol] and x [Et,ncol] (block lower
+    triangular Toeplitz product of Section 2; blocks beyond nd are taken as zero)."""
+    Et = x.shape[0]
+    f = np.zeros((Et, blocks.shape[1]))
+    for k in range(Et):
+        for d in range(min(k + 1, blocks.shape[0])):
+            f[k] += blocks[d] @ x[k - d]
+    return f
+
+
+# ---- tree and pFMM (Sections 3.2 - 3.4) ----------------------------------------------------
+def make_problem(V, T, Tend, Et, alpha=1.0, m_t=4, m_x=4, c_st=1.0, n_tr=-1, eps_tr=1e-12, leaf_steps=2,
+                 leaf_tris=16, n_r=3, n_s=6):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    P = Problem(V.shape[0], T.shape[0], _pd(V), _pi(T), Tend, Et, alpha, m_t, m_x, c_st, n_tr, eps_tr, leaf_steps,
+                leaf_tris, n_r, n_s)
+    P._keep = (V, T)
+    return P
+
+
+def tree_info(P):
+    p = ctypes.c_int()
+    lx = np.zeros(32, np.int32)
+    nbox = np.zeros(32, np.int32)
+    pad = np.zeros(32)
+    ntr = np.zeros(32, np.int32)
+    ntn = ctypes.c_int()
+    root = np.zeros(4)
+    rc = lib().orc_tree_info(ctypes.byref(P), ctypes.byref(p), _pi(lx), _pi(nbox), _pd(pad), _pi(ntr),
+                             ctypes.byref(ntn), _pd(root))
+    if rc:
+        raise ValueError("tree build failed")
+    n = p.value + 1
+    return dict(p=p.value, lx=lx[:n].tolist(), nbox=nbox[:n].tolist(), pad=pad[:n].tolist(),
+                ntr_far=ntr[:n].tolist(), ntr_near=ntn.value, corner=root[:3].tolist(), H=float(root[3]))
+
+
+def pfmm_apply(P, op, x, targets=None, parts=3, nthreads=0):
+    """Oracle pFMM (Alg. 2): op 0 -> V_h w (x [Et,nt]), op 1 -> K_h g (x [Et,nv]).
+    Returns f [Et, nt]; rows of triangles outside ``targets`` are zero."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    f = np.zeros((P.Et, P.nt))
+    if targets is None:
+        tg, nt = None, -1
+    else:
+        tg = np.ascontiguousarray(targets, dtype=np.int32)
+        nt = tg.shape[0]
+    rc = lib().orc_pfmm_apply(ctypes.byref(P), op, _pd(x), _pd(f), _pi(tg) if tg is not None else None, nt, parts,
+                              nthreads)
+    if rc:
+        raise ValueError("oracle pfmm failed")
+    return f
+
+
+def interaction_list(k):
+    """Temporal interaction list of interval k (Eq. 03:ILtemp), same-level indices."""
+    js = np.zeros(2, np.int32)
+    n = lib().orc_interaction_list(k, _pi(js))
+    return js[:n].tolist()
+
+
+def nearfield_list(k):
+    """Temporal nearfield of interval k on a uniform-depth tree (Eq. 03:ILtemp)."""
+    js = np.zeros(2, np.int32)
+    n = lib().orc_nearfield_list(k, _pi(js))
+    return js[:n].tolist()
+
+
+def E1(k, l, r, dab, mx):
+    return lib().orc_E1(k, l, r, dab, mx)
+
+
+def qt(c, ac, ap, m):
+    return lib().orc_qt(c, ac, ap, m)
+
+
+def qx(kap, nu, cc, hc, cp, hp, m):
+    return lib().orc_qx(kap, nu, cc, hc, cp, hp, m)
+
+
+def lagrange(b, m, lo, hi, t):
+    return lib().orc_lagrange(b, m, lo, hi, t)
+
+
+def cheb_node(k, m):
+    return lib().orc_cheb_node(k, m)
