@@ -1,0 +1,268 @@
+"""Benchmark: pFMM V_h matvec throughput (space-time DOF/s) on one GB300.
+
+Workload (the single large problem): surface of the unit cube, 32 x 32 squares per face cut
+into 12288 flat triangles, 256 uniform steps on [0, 1] (3,145,728 space-time DOFs), Chebyshev
+degree 6 in space, Lagrange degree 4 in time, c_st = 1, temporal leaves of 2 steps.  A step is
+one f = V_h w (the product every GMRES iteration applies), w ~ N(0,1) seeded.  The nearfield
+blocks and tables are built before the timed region (assembly).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) each rank runs its own replica of the problem
+(the matvec does not shard on one box: replicas only), timing is the max over ranks and value
+is the whole-job DOF/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pFMM matvec space-time DOF/s"
+N_A, ET, M_X, M_T, C_ST = 32, 256, 6, 4, 1.0
+
+
+def _clock_sampler(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-i",
+           os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"]
+    while not stop.is_set():
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
+            if r.returncode == 0:
+                out.append(r.stdout.strip().splitlines()[0])
+        except Exception:
+            pass
+        stop.wait(0.2)
+
+
+def _clocks_summary(samples):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for s in samples:
+        f = [x.strip() for x in s.split(",")]
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except (ValueError, IndexError):
+            continue
+        for n, v in zip(names, f[3:7]):
+            if v.lower() in ("active", "1"):
+                reasons.add(n)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _oracle_sample(n_targets=16, nthreads=0):
+    """Time the CPU oracle (plain FP64 pFMM of Alg. 2) on a bounded sample: the rows of
+    ``n_targets`` triangles (all 256 steps) of the same workload."""
+    import oracle as O
+    from paper_2106_15911_gb300.inputs import cube_mesh, random_density, sample_triangles
+
+    V, T = cube_mesh(N_A)
+    P = O.make_problem(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST)
+    w = random_density(ET, T.shape[0], 1, seed=1234)[0]
+    tg = sample_triangles(T.shape[0], n_targets, seed=7)
+    t0 = time.perf_counter()
+    O.pfmm_apply(P, 0, w, targets=tg, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    cores = nthreads if nthreads > 0 else (os.cpu_count() or 1)
+    return dict(value=n_targets * ET / dt, unit="space-time DOF/s", cores=cores, kind="oracle",
+                sample=f"rows of {n_targets} seeded target triangles x {ET} steps of V_h w (full S2M/M2M, "
+                       f"M2L/L2L/L2T on their box chains, their nearfield rows); {dt:.1f} s"), dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    vals, tot = [], 0.0
+    for _ in range(args.warmup):
+        _oracle_sample()
+    for _ in range(args.steps):
+        cb, dt = _oracle_sample()
+        vals.append(cb["value"])
+        tot += dt
+    v = statistics.mean(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "space-time DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"cube {N_A}x{N_A} faces ({12 * N_A * N_A} tri) x {ET} steps",
+                                             "m_x": M_X, "m_t": M_T, "c_st": C_ST},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "space-time DOF/s", "h2d_bytes_per_step": 0,
+                                          "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_mesh, random_density
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    V, T = cube_mesh(N_A)
+    nt, nv = T.shape[0], V.shape[0]
+    dof = nt * ET
+    stream = torch.cuda.current_stream()
+    prec = P.PFMM_MIXED if args.precision == "mixed" else P.PFMM_FP64
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t_build = time.perf_counter()
+    op = P.Operator(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST, precision=prec)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    info = op.info()
+    w = torch.tensor(random_density(ET, nt, 1, seed=1234 + rank), device=dev)
+    f = torch.empty_like(w)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def run_device_timed(steps, warm, opx, prof):
+        P.pfmm_set_profiling(opx.h, False)
+        for _ in range(warm):
+            P.pfmm_apply_V(opx.h, w, f, 1, stream)
+        P.pfmm_phase_times(opx.h)
+        P.pfmm_set_profiling(opx.h, prof)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            P.pfmm_apply_V(opx.h, w, f, 1, stream)
+            ev[i][1].record(stream)
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        phases, n = P.pfmm_phase_times(opx.h)
+        P.pfmm_set_profiling(opx.h, False)
+        return ms, {k: v / max(n, 1) for k, v in phases.items()}
+
+    # ---- timed region (device), with live clock sampling
+    stop, samples = threading.Event(), []
+    th = threading.Thread(target=_clock_sampler, args=(stop, samples), daemon=True)
+    th.start()
+    ms, phases = run_device_timed(args.steps, args.warmup, op, prof=True)
+    stop.set()
+    th.join(timeout=5)
+    ms_step = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * dof / (ms_step * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    wh = torch.tensor(random_density(ET, nt, 1, seed=99 + rank)).pin_memory()
+    fh = torch.empty_like(wh).pin_memory()
+    wd, fd = torch.empty_like(w), torch.empty_like(f)
+    for _ in range(args.warmup):
+        wd.copy_(wh, non_blocking=True)
+        P.pfmm_apply_V(op.h, wd, fd, 1, stream)
+        fh.copy_(fd, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        wd.copy_(wh, non_blocking=True)
+        P.pfmm_apply_V(op.h, wd, fd, 1, stream)
+        fh.copy_(fd, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e = {"value": world * dof / (e2e_ms * 1e-3), "unit": "space-time DOF/s", "h2d_bytes_per_step": 8 * dof,
+           "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_ms}
+
+    # ---- roofline of the dominant kernel (nearfield apply): algorithmic flops per launch
+    ls = 2
+    nint = ET // ls
+    flops_nf = 2.0 * nt * nt * nint * sum(ls + s + 1 for s in range(ls))  # 2 * E_x^2 * sum_t |D(t)|
+    nf_ms = phases["nearfield"]
+    fp64 = prec == P.PFMM_FP64
+    peak_meas = P.pfmm_probe_fma_rate(fp64, stream)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_nominal = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
+    roofline = {"bound": "alu", "kernel": "k_nf_apply", "achieved": flops_nf / (nf_ms * 1e-3) / 1e12,
+                "peak": peak_meas, "unit": "TFLOP/s", "frac": flops_nf / (nf_ms * 1e-3) / 1e12 / peak_meas,
+                "traffic": None, "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA probe "
+                                                f"(nominal FP32 {peak_nominal:.1f} at 2070 MHz)",
+                "flops_per_launch": flops_nf, "ms_per_launch": nf_ms}
+
+    # ---- FP64 mode of the same workload (context; the other half of the workload's comparison)
+    fp64_line = None
+    if not fp64 and args.fp64_steps > 0:
+        op64 = P.Operator(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST, precision=P.PFMM_FP64)
+        ms64, ph64 = run_device_timed(args.fp64_steps, 1, op64, prof=True)
+        with torch.no_grad():
+            P.pfmm_apply_V(op64.h, w, fd, 1, stream)
+            P.pfmm_apply_V(op.h, w, f, 1, stream)
+            torch.cuda.synchronize()
+            rel = float((f - fd).abs().max() / fd.abs().max())
+        fp64_line = {"value": dof / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
+                     "phases_ms": ph64, "mixed_vs_fp64_rel_maxnorm": rel,
+                     "fp64_fma_tflops": P.pfmm_probe_fma_rate(True, stream)}
+        op64.close()
+
+    launches = 3 * info["p"]  # permute in/out, nearfield, S2M, L2T, (p-2) M2M, (p-1) M2L, (p-2) L2L
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu, _ = _oracle_sample()
+        except Exception as e:  # the baseline is context; the line still prints
+            cpu = {"value": None, "error": str(e)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "space-time DOF/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if not fp64 else "f64", "data": "synthetic",
+                "config": {"workload": f"cube {N_A}x{N_A} faces ({nt} tri) x {ET} steps, V_h matvec",
+                           "dofs": dof, "m_x": M_X, "m_t": M_T, "c_st": C_ST, "precision": args.precision,
+                           "l2": "flushed (256 MB write) between timed steps; nearfield blocks "
+                                 f"{info['nearfield_bytes'] / 1e9:.2f} GB > L2",
+                           "parallelism": f"replicas x{world}", "build_s": t_build},
+                "phases_ms": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * args.steps, "clocks": _clocks_summary(samples), "fp64": fp64_line}
+        print(json.dumps(line), flush=True)
+    op.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,154 @@
+/*
+ * pfmm.h -- C ABI of the GB300 (sm_103a) parabolic FMM for the space-time Galerkin boundary
+ * element method of the heat equation (arXiv 2106.15911).
+ *
+ * Problem (Section 2): Dirichlet problem of the heat equation u_t - alpha Laplace u = 0 in
+ * Omega x (0, T), zero initial condition, u = g on Gamma x (0, T).  The Neumann datum
+ * w = alpha du/dn solves V w = (1/2 I + K) g (Section 2, boundary integral equation).  With a
+ * fixed triangulation {gamma_x} of Gamma and E_t uniform steps of length h = T / E_t:
+ *
+ *   V_h[(k,x),(j,y)] = int_{I_k} int_{gamma_x} int_{I_j} int_{gamma_y} G_alpha(x - y, t - tau)
+ *   K_h[(k,x),(j,i)] = same with alpha dG_alpha/dn_y times the p1 hat function phi_i(y)
+ *   M_h[(k,x),(k,i)] = int_{I_k} int_{gamma_x} phi_i = h |gamma_x| / 3 for i a vertex of gamma_x
+ *
+ * (Section 2, the matrix entries after Eq. 02:linear:system.)  V_h and K_h are applied by the
+ * space-time FMM of Section 3 (Alg. 2): nearfield blocks (Eq. eval_sl_nf_block) plus S2M
+ * (Eq. s2m), M2M (Eq. temp_m2m, st_m2m), M2L (Eq. m2l with Eq. exp_coeffs_3d/1d), L2L and
+ * L2T (Eq. l2t) over the box cluster tree of Alg. 1.
+ *
+ * Vector layouts (all FP64, all DEVICE pointers, caller-owned):
+ *   w, f        [nrhs][E_t][E_x]  p0 coefficients, index (k-1) E_x + x of Section 2 per rhs
+ *   g           [nrhs][E_t][N_v]  p0-in-time, p1-in-space coefficients (node order of the mesh)
+ * Triangles and nodes are in the caller's order; any reordering is internal.
+ *
+ * Errors: every entry point returns PFMM_OK (0) or a negative code; pfmm_last_error() then
+ * returns a message for the calling thread.  No C++ exception crosses this interface.  On an
+ * error the output vectors are unspecified.  A handle is not thread-safe: calls on one handle
+ * must not overlap (they share the handle's workspaces); different handles are independent.
+ */
+#ifndef PFMM_H
+#define PFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define PFMM_OK 0
+#define PFMM_ERR_INVALID_ARG (-1)  /* a pointer is NULL, a size is out of range, ... */
+#define PFMM_ERR_OOM (-2)          /* device allocation failed or the memory cap is exceeded */
+#define PFMM_ERR_CUDA (-3)         /* a CUDA runtime call or kernel launch failed */
+#define PFMM_ERR_NONFINITE (-4)    /* an input holds NaN or Inf */
+#define PFMM_ERR_TIMEOUT (-5)      /* a bounded device wait gave up */
+#define PFMM_ERR_NOT_CONVERGED (-6)/* the solver stopped before its tolerance */
+#define PFMM_ERR_UNSUPPORTED (-7)  /* a valid request this build does not implement */
+
+/* precision modes */
+#define PFMM_FP64 0   /* every phase in FP64 */
+#define PFMM_MIXED 1  /* FP32 storage and FP32 arithmetic for the nearfield apply and the FMM
+                         passes; FP64 singular quadrature, FP64 output accumulation */
+
+/* nearfield modes */
+#define PFMM_NEARFIELD_STORED 0  /* nearfield blocks assembled once at build time */
+
+/* apply parts (bit mask) */
+#define PFMM_PART_NEAR 1  /* inadmissible (nearfield) blocks, Alg. 2 last loop */
+#define PFMM_PART_FAR 2   /* S2M, M2M, M2L, L2L, L2T, Alg. 2 first four phases */
+#define PFMM_PART_ALL 3
+
+/* The tensor space-time mesh (Section 2).  Arrays are HOST pointers, read during
+ * pfmm_build_trees only (copied). */
+typedef struct pfmm_mesh {
+    int32_t n_vertices;      /* N_v */
+    int32_t n_triangles;     /* E_x */
+    const double *vertices;  /* [N_v][3] */
+    const int32_t *triangles;/* [E_x][3] vertex indices, counter-clockwise seen from outside */
+    double T;                /* end time */
+    int32_t n_steps;         /* E_t, uniform steps h = T / E_t */
+    double alpha;            /* heat capacity constant alpha > 0 */
+} pfmm_mesh;
+
+/* FMM parameters (Section 3; Alg. 2 line 1 names n_max, c_st, n_tr, m_t, m_x). */
+typedef struct pfmm_params {
+    int32_t m_t;        /* Lagrange degree in time (Section 3.1), >= 0 */
+    int32_t m_x;        /* Chebyshev degree in space (total degree), 0 <= m_x <= 12 */
+    double c_st;        /* box-shape constant of Eq. rel_h_t_h_x */
+    int32_t n_tr;       /* interaction-area radius of Eq. 03:Iarea; < 0: derived from eps_tr */
+    double eps_tr;      /* neglected kernel size when n_tr < 0 */
+    int32_t leaf_steps; /* time steps per temporal leaf (E_t / leaf_steps a power of two) */
+    int32_t leaf_tris;  /* no spatial refinement once no box holds more triangles */
+    int32_t precision;  /* PFMM_FP64 or PFMM_MIXED */
+    int32_t nearfield;  /* PFMM_NEARFIELD_STORED */
+    int32_t quad_regular;  /* Gauss points per direction of the collapsed triangle rule */
+    int32_t quad_singular; /* Gauss points per direction of the Sauter-Schwab rule */
+} pfmm_params;
+
+typedef struct pfmm_handle pfmm_handle;
+
+/* Tree statistics of a handle (for tests and logs). */
+typedef struct pfmm_info {
+    int32_t p;              /* leaf level */
+    int32_t lx[32];         /* spatial refinements per level */
+    int32_t nbox[32];       /* non-empty spatial boxes per level */
+    double pad[32];         /* padding per level */
+    int32_t n_m2l_pairs;    /* space-time box pairs in all interaction lists */
+    int64_t nearfield_bytes;/* device bytes of the stored nearfield blocks (V and K) */
+    int64_t device_bytes;   /* all device bytes held by the handle */
+} pfmm_info;
+
+/* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,
+ * leaf_steps = 2, leaf_tris = 16, FP64, stored nearfield, quad_regular = 3,
+ * quad_singular = 6.  Returns PFMM_OK or PFMM_ERR_INVALID_ARG (p NULL). */
+int pfmm_default_params(pfmm_params *p);
+
+/* Build the box cluster tree (Section 3.2, Alg. 1), the nearfield and interaction lists
+ * (Section 3.3), the expansion tables (Section 3.1, 3.4) and, in stored mode, the nearfield
+ * blocks of V_h and K_h (Eq. eval_sl_nf_block).  `stream` is a cudaStream_t (NULL = legacy
+ * default stream); the call synchronises it before returning.  On success *out owns device
+ * memory until pfmm_destroy. */
+int pfmm_build_trees(const pfmm_mesh *mesh, const pfmm_params *params, void *stream, pfmm_handle **out);
+
+/* f = V_h w (Alg. 2), f overwritten.  w, f: device [nrhs][E_t][E_x] FP64, must not overlap.
+ * Enqueued on `stream`; returns without synchronising.  nrhs >= 1. */
+int pfmm_apply_V(pfmm_handle *h, const double *w, double *f, int32_t nrhs, void *stream);
+
+/* f = K_h g (Alg. 2 with the double-layer moments, Section 3 "slight modifications").
+ * g: device [nrhs][E_t][N_v], f: device [nrhs][E_t][E_x], f overwritten. */
+int pfmm_apply_K(pfmm_handle *h, const double *g, double *f, int32_t nrhs, void *stream);
+
+/* f = M_h g (p0-p1 mass matrix, Section 2).  g: [nrhs][E_t][N_v], f: [nrhs][E_t][E_x]. */
+int pfmm_apply_M(pfmm_handle *h, const double *g, double *f, int32_t nrhs, void *stream);
+
+/* Like pfmm_apply_V / pfmm_apply_K (op 0 / 1) but computing only the parts in `parts`
+ * (PFMM_PART_NEAR, PFMM_PART_FAR or both); f is overwritten with that part. */
+int pfmm_apply_parts(pfmm_handle *h, int32_t op, const double *x, double *f, int32_t nrhs, int32_t parts,
+                     void *stream);
+
+/* Per-phase device times.  When enabled, every apply records CUDA events around its phases on
+ * its stream; pfmm_phase_times synchronises the last apply's stream, writes the accumulated
+ * milliseconds of the phases (0 permute in, 1 nearfield, 2 S2M, 3 M2M, 4 M2L, 5 L2L, 6 L2T,
+ * 7 permute out) and the number of applies measured, then resets the accumulators. */
+int pfmm_set_profiling(pfmm_handle *h, int32_t on);
+int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies);
+
+int pfmm_get_info(const pfmm_handle *h, pfmm_info *info);
+
+/* Measurement utility (not part of the paper's method): the sustained FMA throughput of the
+ * current device in TFLOP/s (2 flops per FMA), FP64 (fp64 != 0) or FP32, timed with CUDA
+ * events over five launches of independent FMA chains on `stream`.  Synchronises the stream.
+ * The FP32 / FP64 pipe rooflines of the nearfield and M2L kernels are quoted against it. */
+int pfmm_probe_fma_rate(int32_t fp64, double *tflops, void *stream);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void pfmm_destroy(pfmm_handle *h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *pfmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFMM_H */

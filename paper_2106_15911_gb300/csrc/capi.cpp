@@ -1,0 +1,672 @@
+// capi.cpp -- the C ABI of include/pfmm.h: handle life cycle, one-time set-up and the apply
+// sequence of Alg. 2 (Section 3.4) on the caller's CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pfmm_internal.h"
+
+using namespace pfmm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? PFMM_ERR_OOM : PFMM_ERR_CUDA,                \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Gauss-Legendre nodes and weights on [0, 1] (Newton iteration on P_n)
+void gauss01(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), pp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p1 = 1.0, p2 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                double p3 = p2;
+                p2 = p1;
+                p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+            }
+            pp = n * (z * p1 - p2) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p1 = 1.0, p2 = 0.0;
+        for (int k = 1; k <= n; ++k) {
+            double p3 = p2;
+            p2 = p1;
+            p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+        }
+        pp = n * (z * p1 - p2) / (z * z - 1.0);
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+// collapsed (Duffy) rule on {0 <= s2 <= s1 <= 1}: s1 = u, s2 = u v, weight w_u w_v u
+std::vector<double> collapsed_rule(int n)
+{
+    std::vector<double> x, w, r(3 * (size_t)n * n);
+    gauss01(n, x, w);
+    int q = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j, ++q) {
+            r[q] = x[i];
+            r[n * n + q] = x[i] * x[j];
+            r[2 * n * n + q] = w[i] * w[j] * x[i];
+        }
+    return r;
+}
+
+double cheb_node(int k, int m) { return std::cos((2.0 * k + 1.0) * kPi / (2.0 * m + 2.0)); }
+
+double cheb_T(int k, double x)
+{
+    double t0 = 1.0, t1 = x;
+    if (k == 0) return 1.0;
+    for (int i = 2; i <= k; ++i) {
+        double t2 = 2.0 * x * t1 - t0;
+        t0 = t1;
+        t1 = t2;
+    }
+    return t1;
+}
+
+double lagrange(int b, int m, double lo, double hi, double t)
+{
+    double c = 0.5 * (lo + hi), hw = 0.5 * (hi - lo), xb = c + hw * cheb_node(b, m), v = 1.0;
+    for (int k = 0; k <= m; ++k)
+        if (k != b) {
+            double xk = c + hw * cheb_node(k, m);
+            v *= (t - xk) / (xb - xk);
+        }
+    return v;
+}
+
+struct EvSet {
+    cudaEvent_t ev[9];
+};
+
+}  // namespace
+
+struct pfmm_handle {
+    int nv = 0, nt = 0, Et = 0;
+    double T = 0, alpha = 0, h = 0;
+    pfmm_params prm{};
+    Tree tree;
+    bool mixed = false;
+    int ls = 2, nd = 4, na = 0, nk = 0, mx = 0, p = 0;
+    size_t es = 8;  // bytes of R
+    std::vector<void *> allocs;
+    int64_t dev_bytes = 0;
+
+    double *d_verts = nullptr, *d_area = nullptr;
+    int *d_tri_int = nullptr, *d_tri_user = nullptr, *d_perm = nullptr, *d_tri_leaf = nullptr, *d_leaf_start = nullptr,
+        *d_leaf_grid = nullptr, *d_kidx = nullptr, *d_kinv = nullptr;
+    void *d_Sx = nullptr, *d_SK = nullptr, *d_St = nullptr, *d_qt = nullptr;
+    std::vector<DevLevel> dl;
+    void *d_AV = nullptr, *d_AK = nullptr;
+    int *d_colV = nullptr, *d_colK = nullptr, *d_kmap = nullptr, *d_tiles = nullptr;
+    PanelGPU *d_panels = nullptr;
+    int ntiles = 0;
+    int64_t mom_per_rhs = 0;
+
+    int ws_nrhs = 0;
+    void *d_xint = nullptr, *d_gf = nullptr, *d_mu = nullptr, *d_lam = nullptr;
+    double *d_fint = nullptr;
+
+    bool prof = false;
+    std::vector<EvSet> evs;
+    int ev_head = 0, ev_pending = 0;
+    double acc_ms[8] = {0};
+    int n_prof = 0;
+
+    ~pfmm_handle()
+    {
+        for (void *p : allocs) cudaFree(p);
+        for (auto &e : evs)
+            for (int i = 0; i < 9; ++i) cudaEventDestroy(e.ev[i]);
+    }
+
+    template <typename T_>
+    int alloc(T_ **p, size_t n_elems, size_t elem = sizeof(T_))
+    {
+        void *q = nullptr;
+        size_t bytes = std::max<size_t>(n_elems * elem, 16);
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? PFMM_ERR_OOM : PFMM_ERR_CUDA,
+                        "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        dev_bytes += (int64_t)bytes;
+        *p = (T_ *)q;
+        return PFMM_OK;
+    }
+
+    void release(void *p)
+    {
+        if (!p) return;
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) {
+            cudaFree(p);
+            allocs.erase(it);
+        }
+    }
+};
+
+namespace {
+
+template <typename T_>
+int upload(pfmm_handle *H, T_ **dst, const std::vector<T_> &src, cudaStream_t st)
+{
+    int rc = H->alloc(dst, src.size());
+    if (rc) return rc;
+    if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T_), cudaMemcpyHostToDevice, st));
+    return PFMM_OK;
+}
+
+// upload a host FP64 table in the handle's arithmetic type R
+int upload_R(pfmm_handle *H, void **dst, const std::vector<double> &src, cudaStream_t st)
+{
+    if (!H->mixed) return upload(H, (double **)dst, src, st);
+    std::vector<float> f(src.begin(), src.end());
+    return upload(H, (float **)dst, f, st);
+}
+
+// convert a device FP64 table to the handle's type (in place of a new buffer)
+int device_to_R(pfmm_handle *H, void **dst, double *src, size_t n, cudaStream_t st)
+{
+    if (!H->mixed) {
+        *dst = src;
+        return PFMM_OK;
+    }
+    float *f = nullptr;
+    int rc = H->alloc(&f, n);
+    if (rc) return rc;
+    launch_cast_to_float(src, f, n, st);
+    *dst = f;
+    return PFMM_OK;
+}
+
+int ensure_workspace(pfmm_handle *H, int nrhs)
+{
+    if (nrhs <= H->ws_nrhs) return PFMM_OK;
+    H->release(H->d_xint);
+    H->release(H->d_gf);
+    H->release(H->d_mu);
+    H->release(H->d_lam);
+    H->release(H->d_fint);
+    H->d_xint = H->d_gf = H->d_mu = H->d_lam = nullptr;
+    H->d_fint = nullptr;
+    H->ws_nrhs = 0;
+    size_t n_in = (size_t)nrhs * H->Et * H->nt, n_g = (size_t)nrhs * H->Et * H->nv;
+    int rc;
+    if ((rc = H->alloc((char **)&H->d_xint, n_in * H->es, 1))) return rc;
+    if (H->mixed && (rc = H->alloc((float **)&H->d_gf, n_g))) return rc;
+    if ((rc = H->alloc(&H->d_fint, n_in))) return rc;
+    size_t nm = (size_t)nrhs * std::max<int64_t>(H->mom_per_rhs, 1);
+    if ((rc = H->alloc((char **)&H->d_mu, nm * H->es, 1))) return rc;
+    if ((rc = H->alloc((char **)&H->d_lam, nm * H->es, 1))) return rc;
+    H->ws_nrhs = nrhs;
+    return PFMM_OK;
+}
+
+void prof_collect(pfmm_handle *H, int upto_pending)
+{
+    while (H->ev_pending > upto_pending) {
+        int idx = (H->ev_head - H->ev_pending + (int)H->evs.size()) % (int)H->evs.size();
+        EvSet &e = H->evs[idx];
+        cudaEventSynchronize(e.ev[8]);
+        for (int i = 0; i < 8; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e.ev[i], e.ev[i + 1]);
+            H->acc_ms[i] += ms;
+        }
+        H->n_prof++;
+        H->ev_pending--;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pfmm_last_error(void) { return g_err.c_str(); }
+
+int pfmm_default_params(pfmm_params *p)
+{
+    if (!p) return fail(PFMM_ERR_INVALID_ARG, "params is NULL");
+    p->m_t = 4;
+    p->m_x = 4;
+    p->c_st = 1.0;
+    p->n_tr = -1;
+    p->eps_tr = 1e-12;
+    p->leaf_steps = 2;
+    p->leaf_tris = 16;
+    p->precision = PFMM_FP64;
+    p->nearfield = PFMM_NEARFIELD_STORED;
+    p->quad_regular = 3;
+    p->quad_singular = 6;
+    return PFMM_OK;
+}
+
+static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_t st, pfmm_handle *H)
+{
+    H->nv = mesh->n_vertices;
+    H->nt = mesh->n_triangles;
+    H->Et = mesh->n_steps;
+    H->T = mesh->T;
+    H->alpha = mesh->alpha;
+    H->h = mesh->T / mesh->n_steps;
+    H->prm = *prm;
+    if (prm->precision != PFMM_FP64 && prm->precision != PFMM_MIXED)
+        return fail(PFMM_ERR_INVALID_ARG, "precision must be PFMM_FP64 or PFMM_MIXED");
+    if (prm->nearfield != PFMM_NEARFIELD_STORED)
+        return fail(PFMM_ERR_UNSUPPORTED, "only the stored nearfield mode is implemented");
+    H->mixed = prm->precision == PFMM_MIXED;
+    H->es = H->mixed ? 4 : 8;
+    std::string err;
+    int rc = build_tree(*mesh, *prm, H->tree, err);
+    if (rc) return fail(rc, err);
+    Tree &t = H->tree;
+    H->ls = prm->leaf_steps;
+    H->nd = 2 * H->ls;
+    if (H->nd > 8) return fail(PFMM_ERR_UNSUPPORTED, "leaf_steps > 4 is not supported");
+    H->na = prm->m_t + 1;
+    H->mx = prm->m_x;
+    H->p = t.p;
+    const int mx = H->mx, m1 = mx + 1, na = H->na;
+    // graded multi-indices: all kappa with |kappa| = s, for s = 0 .. m_x
+    std::vector<int> kidx, kinv((size_t)m1 * m1 * m1, -1);
+    for (int s = 0; s <= mx; ++s)
+        for (int a = s; a >= 0; --a)
+            for (int b = s - a; b >= 0; --b) {
+                int c = s - a - b;
+                kinv[((size_t)a * m1 + b) * m1 + c] = (int)kidx.size() / 3;
+                kidx.push_back(a);
+                kidx.push_back(b);
+                kidx.push_back(c);
+            }
+    H->nk = (int)kidx.size() / 3;
+    if (H->ls * H->nk > 2048) return fail(PFMM_ERR_UNSUPPORTED, "leaf_steps * C(m_x+3,3) > 2048");
+    if (H->na * H->nk > 4096) return fail(PFMM_ERR_UNSUPPORTED, "(m_t+1) * C(m_x+3,3) > 4096");
+
+    // ---- geometry in internal order
+    const int nt = H->nt, nv = H->nv, p = t.p;
+    std::vector<double> verts(mesh->vertices, mesh->vertices + 3 * (size_t)nv);
+    std::vector<int> tri_user(mesh->triangles, mesh->triangles + 3 * (size_t)nt), tri_int(3 * (size_t)nt);
+    std::vector<double> area(nt);
+    for (int i = 0; i < nt; ++i)
+        for (int v = 0; v < 3; ++v) tri_int[3 * i + v] = tri_user[3 * t.perm[i] + v];
+    for (int x = 0; x < nt; ++x) {
+        const double *A = &verts[3 * tri_user[3 * x]], *B = &verts[3 * tri_user[3 * x + 1]], *C = &verts[3 * tri_user[3 * x + 2]];
+        double a[3], b[3];
+        for (int c = 0; c < 3; ++c) { a[c] = B[c] - A[c]; b[c] = C[c] - A[c]; }
+        double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+        area[x] = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    if ((rc = upload(H, &H->d_verts, verts, st)) || (rc = upload(H, &H->d_tri_int, tri_int, st)) ||
+        (rc = upload(H, &H->d_tri_user, tri_user, st)) || (rc = upload(H, &H->d_area, area, st)) ||
+        (rc = upload(H, &H->d_perm, t.perm, st)) || (rc = upload(H, &H->d_tri_leaf, t.tri_leaf, st)) ||
+        (rc = upload(H, &H->d_leaf_start, t.leaf_start, st)) || (rc = upload(H, &H->d_leaf_grid, t.lv[p].grid, st)) ||
+        (rc = upload(H, &H->d_kidx, kidx, st)) || (rc = upload(H, &H->d_kinv, kinv, st)))
+        return rc;
+
+    // ---- S2M / L2T tables (Eq. s2m, l2t)
+    {
+        std::vector<double> rule = collapsed_rule(mx / 2 + 2);
+        double *rule_d = nullptr, *Sx = nullptr, *SK = nullptr;
+        if ((rc = upload(H, &rule_d, rule, st)) || (rc = H->alloc(&Sx, (size_t)nt * H->nk)) ||
+            (rc = H->alloc(&SK, (size_t)nt * 3 * H->nk)))
+            return rc;
+        SetupArgs a{};
+        a.verts = H->d_verts;
+        a.tri = H->d_tri_int;
+        a.tri_leaf = H->d_tri_leaf;
+        a.leaf_grid = H->d_leaf_grid;
+        for (int c = 0; c < 3; ++c) a.corner[c] = t.corner[c];
+        a.hx_leaf = t.lv[p].hx;
+        a.hxp_leaf = t.lv[p].hxp;
+        a.alpha = H->alpha;
+        a.nt = nt;
+        a.mx = mx;
+        a.nk = H->nk;
+        a.kidx = H->d_kidx;
+        a.rule_tab = rule_d;
+        a.nq_tab = (mx / 2 + 2) * (mx / 2 + 2);
+        a.Sx = Sx;
+        a.SK = SK;
+        launch_space_tables(a, st);
+        CK(cudaGetLastError());
+        if ((rc = device_to_R(H, &H->d_Sx, Sx, (size_t)nt * H->nk, st)) ||
+            (rc = device_to_R(H, &H->d_SK, SK, (size_t)nt * 3 * H->nk, st)))
+            return rc;
+        // St[s][a] = int over step s of a leaf interval of L_{J,a} (exact Gauss-Legendre)
+        std::vector<double> gx, gw, St((size_t)H->ls * na), qt(2 * (size_t)na * na);
+        gauss01(na, gx, gw);
+        double Lleaf = H->ls * H->h;
+        for (int s = 0; s < H->ls; ++s)
+            for (int aa = 0; aa < na; ++aa) {
+                double v = 0.0;
+                for (int i = 0; i < na; ++i) v += gw[i] * H->h * lagrange(aa, prm->m_t, 0.0, Lleaf, (s + gx[i]) * H->h);
+                St[s * na + aa] = v;
+            }
+        // q^(t)[c][ac][ap] = L_{I_p,ap}(xi_{I_c,ac})  (Eq. temp_m2m)
+        for (int c = 0; c < 2; ++c)
+            for (int ac = 0; ac < na; ++ac)
+                for (int ap = 0; ap < na; ++ap) {
+                    double clo = c == 0 ? -1.0 : 0.0, chi = c == 0 ? 0.0 : 1.0;
+                    double xc = 0.5 * (clo + chi) + 0.5 * (chi - clo) * cheb_node(ac, prm->m_t);
+                    qt[(c * na + ac) * na + ap] = lagrange(ap, prm->m_t, -1.0, 1.0, xc);
+                }
+        if ((rc = upload_R(H, &H->d_St, St, st)) || (rc = upload_R(H, &H->d_qt, qt, st))) return rc;
+    }
+
+    // ---- levels: lists, q^(x) (Eq. st_m2m) and E tables (Eq. exp_coeffs_3d / 1d)
+    H->dl.assign(p + 1, DevLevel{});
+    H->mom_per_rhs = 0;
+    for (int l = 0; l <= p; ++l) {
+        const Level &L = t.lv[l];
+        DevLevel &D = H->dl[l];
+        D.G = L.G;
+        D.nint = L.nint;
+        D.nbox = L.nbox;
+        D.st = L.st ? 1 : 0;
+        D.hxp = L.hxp;
+        D.mom_off = H->mom_per_rhs;
+        if (l >= 2) H->mom_per_rhs += (int64_t)L.nint * L.nbox * na * H->nk;
+        if ((rc = upload(H, &D.grid, L.grid, st))) return rc;
+        if (l > 0 && ((rc = upload(H, &D.parent, L.parent, st)) || (rc = upload(H, &D.octant, L.octant, st)))) return rc;
+        if (l < p && ((rc = upload(H, &D.ch_ptr, L.ch_ptr, st)) || (rc = upload(H, &D.ch_idx, L.ch_idx, st)))) return rc;
+        if (l >= 2 && ((rc = upload(H, &D.m2l_ptr, L.m2l_ptr, st)) || (rc = upload(H, &D.m2l_src, L.m2l_src, st)) ||
+                       (rc = upload(H, &D.m2l_off, L.m2l_off, st))))
+            return rc;
+        if (l > 0 && L.st) {
+            // q^(x)_{kap,nu}(X_c, X_p) per direction for a child in the lower (bit 0) or upper half
+            const Level &P = t.lv[l - 1];
+            std::vector<double> q1(2 * (size_t)m1 * m1);
+            for (int bit = 0; bit < 2; ++bit) {
+                double dc = (2.0 * bit - 1.0) * L.hx;  // child centre - parent centre
+                for (int ka = 0; ka <= mx; ++ka)
+                    for (int nu = 0; nu <= mx; ++nu) {
+                        double s = 0.0;
+                        for (int n = 0; n <= mx; ++n) {
+                            double xn = cheb_node(n, mx);
+                            s += cheb_T(nu, (dc + L.hxp * xn) / P.hxp) * cheb_T(ka, xn);
+                        }
+                        q1[(bit * m1 + ka) * m1 + nu] = (ka == 0 ? 1.0 : 2.0) / (mx + 1.0) * s;
+                    }
+            }
+            if ((rc = upload_R(H, &D.qx, q1, st))) return rc;
+        }
+        if (l >= 2) {
+            size_t ne = 2 * (size_t)na * na * (2 * L.G - 1) * m1 * m1;
+            double *E1 = nullptr, *pref = nullptr;
+            if ((rc = H->alloc(&E1, ne)) || (rc = H->alloc(&pref, 2 * (size_t)na * na))) return rc;
+            launch_e1_table(na, prm->m_t, mx, L.G, L.hx, L.hxp, L.ht, H->alpha, E1, pref, st);
+            CK(cudaGetLastError());
+            if ((rc = device_to_R(H, &D.E1, E1, ne, st)) || (rc = device_to_R(H, &D.pref, pref, 2 * (size_t)na * na, st)))
+                return rc;
+        }
+    }
+
+    // ---- nearfield blocks (Eq. eval_sl_nf_block)
+    {
+        std::vector<PanelGPU> pg(t.panels.size());
+        std::vector<int> tiles;
+        for (size_t i = 0; i < t.panels.size(); ++i) {
+            const Panel &P = t.panels[i];
+            pg[i] = PanelGPU{(int)i, P.row0, P.nrows, P.rows_pad, P.ncolV, P.colsV_pad, P.ncolK, P.colsK_pad,
+                             (long long)P.offV, (long long)P.offK, P.colV_at, P.colK_at};
+            for (int r0 = 0; r0 < P.nrows; r0 += kRowTile) {
+                tiles.push_back((int)i);
+                tiles.push_back(r0);
+            }
+        }
+        H->ntiles = (int)tiles.size() / 2;
+        std::vector<int> sing(12 * t.sing.size(), 0);
+        for (size_t i = 0; i < t.sing.size(); ++i) {
+            const SingularPair &s = t.sing[i];
+            int *o = &sing[12 * i];
+            o[0] = s.x; o[1] = s.y; o[2] = s.panel; o[3] = s.row; o[4] = s.colV; o[5] = s.code;
+            o[6] = s.colK[0]; o[7] = s.colK[1]; o[8] = s.colK[2];
+        }
+        int *d_sing = nullptr;
+        if ((rc = upload(H, &H->d_panels, pg, st)) || (rc = upload(H, &H->d_tiles, tiles, st)) ||
+            (rc = upload(H, &H->d_colV, t.colV, st)) || (rc = upload(H, &H->d_colK, t.colK, st)) ||
+            (rc = upload(H, &H->d_kmap, t.kmap, st)) || (rc = upload(H, &d_sing, sing, st)))
+            return rc;
+        if ((rc = H->alloc((char **)&H->d_AV, (size_t)t.sizeV * H->es, 1)) ||
+            (rc = H->alloc((char **)&H->d_AK, (size_t)t.sizeK * H->es, 1)))
+            return rc;
+        CK(cudaMemsetAsync(H->d_AV, 0, (size_t)t.sizeV * H->es, st));
+        CK(cudaMemsetAsync(H->d_AK, 0, (size_t)t.sizeK * H->es, st));
+        std::vector<double> rreg = collapsed_rule(prm->quad_regular), gx, gw;
+        gauss01(prm->quad_singular, gx, gw);
+        std::vector<double> gls(gx);
+        gls.insert(gls.end(), gw.begin(), gw.end());
+        double *d_rreg = nullptr, *d_gls = nullptr;
+        if ((rc = upload(H, &d_rreg, rreg, st)) || (rc = upload(H, &d_gls, gls, st))) return rc;
+        NfQuadArgs a{};
+        a.verts = H->d_verts;
+        a.tri = H->d_tri_int;
+        a.nv = nv;
+        a.nd = H->nd;
+        a.h = H->h;
+        a.alpha = H->alpha;
+        a.rule_reg = d_rreg;
+        a.nq_reg = prm->quad_regular * prm->quad_regular;
+        a.gl_sing = d_gls;
+        a.nq_sing = prm->quad_singular;
+        a.colV = H->d_colV;
+        a.kmap = H->d_kmap;
+        for (size_t i = 0; i < t.panels.size(); ++i) {
+            launch_nf_regular(a, pg[i], H->d_AV, H->d_AK, H->mixed, st);
+            CK(cudaGetLastError());
+        }
+        launch_nf_singular(a, d_sing, (int)t.sing.size(), H->d_panels, H->d_AV, H->d_AK, H->mixed, st);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(st));
+    return PFMM_OK;
+}
+
+int pfmm_build_trees(const pfmm_mesh *mesh, const pfmm_params *params, void *stream, pfmm_handle **out)
+{
+    if (!mesh || !params || !out) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    pfmm_handle *H = new (std::nothrow) pfmm_handle();
+    if (!H) return fail(PFMM_ERR_OOM, "host allocation failed");
+    int rc;
+    try {
+        rc = build_impl(mesh, params, (cudaStream_t)stream, H);
+    } catch (const std::bad_alloc &) {
+        rc = fail(PFMM_ERR_OOM, "host allocation failed");
+    } catch (...) {
+        rc = fail(PFMM_ERR_CUDA, "unexpected exception during build");
+    }
+    if (rc) {
+        delete H;
+        return rc;
+    }
+    *out = H;
+    return PFMM_OK;
+}
+
+static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nrhs, int parts, cudaStream_t st)
+{
+    if (!H || !x || !f || nrhs < 1 || (op != 0 && op != 1) || parts < 1 || parts > 3)
+        return fail(PFMM_ERR_INVALID_ARG, "invalid apply arguments");
+    int rc = ensure_workspace(H, nrhs);
+    if (rc) return rc;
+    const Tree &t = H->tree;
+    ApplyGeo g{};
+    g.nt = H->nt;
+    g.nv = H->nv;
+    g.Et = H->Et;
+    g.ls = H->ls;
+    g.nd = H->nd;
+    g.na = H->na;
+    g.nk = H->nk;
+    g.mx = H->mx;
+    g.p = H->p;
+    g.perm = H->d_perm;
+    g.tri = H->d_tri_int;
+    g.leaf_start = H->d_leaf_start;
+    g.nbox_leaf = t.lv[H->p].nbox;
+    g.kidx = H->d_kidx;
+    g.kinv = H->d_kinv;
+    EvSet *ev = nullptr;
+    if (H->prof) {
+        if (H->evs.empty()) {
+            H->evs.resize(256);
+            for (auto &e : H->evs)
+                for (int i = 0; i < 9; ++i) CK(cudaEventCreate(&e.ev[i]));
+        }
+        if (H->ev_pending == (int)H->evs.size()) prof_collect(H, H->ev_pending - 1);
+        ev = &H->evs[H->ev_head];
+        H->ev_head = (H->ev_head + 1) % (int)H->evs.size();
+        H->ev_pending++;
+    }
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev->ev[i], st);
+    };
+    mark(0);
+    const void *xin;  // input in the arithmetic type, and its column count
+    int ncolg;
+    if (op == 0) {
+        launch_permute_in(x, H->d_xint, H->mixed, nrhs, g, st);
+        xin = H->d_xint;
+        ncolg = H->nt;
+    } else if (H->mixed) {
+        launch_cast_to_float(x, (float *)H->d_gf, (size_t)nrhs * H->Et * H->nv, st);
+        xin = H->d_gf;
+        ncolg = H->nv;
+    } else {
+        xin = x;
+        ncolg = H->nv;
+    }
+    mark(1);
+    if (parts & PFMM_PART_NEAR)
+        launch_nf_apply(H->mixed, op == 1, op == 0 ? H->d_AV : H->d_AK, op == 0 ? H->d_colV : H->d_colK, H->d_tiles,
+                        H->ntiles, H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st);
+    else
+        CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
+    mark(2);
+    const int p = H->p;
+    bool far = (parts & PFMM_PART_FAR) && p >= 2;
+    char *mu = (char *)H->d_mu, *lam = (char *)H->d_lam;
+    if (far) {
+        launch_s2m(H->mixed, op == 1, xin, ncolg, op == 0 ? H->d_Sx : H->d_SK, H->d_St,
+                   mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st);
+    }
+    mark(3);
+    if (far)
+        for (int l = p - 1; l >= 2; --l) launch_m2m(H->mixed, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
+    mark(4);
+    if (far)
+        for (int l = 2; l <= p; ++l) launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, 0, st);
+    mark(5);
+    if (far)
+        for (int l = 3; l <= p; ++l) launch_l2l(H->mixed, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
+    mark(6);
+    if (far) launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, H->d_fint, nrhs, g, 0, st);
+    mark(7);
+    launch_permute_out(H->d_fint, f, nrhs, g, st);
+    mark(8);
+    CK(cudaGetLastError());
+    return PFMM_OK;
+}
+
+int pfmm_apply_parts(pfmm_handle *h, int32_t op, const double *x, double *f, int32_t nrhs, int32_t parts, void *stream)
+{
+    return apply_impl(h, op, x, f, nrhs, parts, (cudaStream_t)stream);
+}
+
+int pfmm_apply_V(pfmm_handle *h, const double *w, double *f, int32_t nrhs, void *stream)
+{
+    return apply_impl(h, 0, w, f, nrhs, PFMM_PART_ALL, (cudaStream_t)stream);
+}
+
+int pfmm_apply_K(pfmm_handle *h, const double *g, double *f, int32_t nrhs, void *stream)
+{
+    return apply_impl(h, 1, g, f, nrhs, PFMM_PART_ALL, (cudaStream_t)stream);
+}
+
+int pfmm_apply_M(pfmm_handle *h, const double *g, double *f, int32_t nrhs, void *stream)
+{
+    if (!h || !g || !f || nrhs < 1) return fail(PFMM_ERR_INVALID_ARG, "invalid apply_M arguments");
+    launch_apply_M(g, f, h->d_tri_user, h->d_area, nrhs, h->nt, h->nv, h->Et, h->h, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return PFMM_OK;
+}
+
+int pfmm_set_profiling(pfmm_handle *h, int32_t on)
+{
+    if (!h) return fail(PFMM_ERR_INVALID_ARG, "handle is NULL");
+    h->prof = on != 0;
+    return PFMM_OK;
+}
+
+int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies)
+{
+    if (!h || !ms8) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+    prof_collect(h, 0);
+    for (int i = 0; i < 8; ++i) {
+        ms8[i] = h->acc_ms[i];
+        h->acc_ms[i] = 0;
+    }
+    if (n_applies) *n_applies = h->n_prof;
+    h->n_prof = 0;
+    return PFMM_OK;
+}
+
+int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
+{
+    if (!h || !info) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    const Tree &t = h->tree;
+    info->p = t.p;
+    for (int l = 0; l <= t.p && l < 32; ++l) {
+        info->lx[l] = t.lv[l].lx;
+        info->nbox[l] = t.lv[l].nbox;
+        info->pad[l] = t.lv[l].pad;
+    }
+    info->n_m2l_pairs = t.n_m2l_pairs;
+    info->nearfield_bytes = (t.sizeV + t.sizeK) * (int64_t)h->es;
+    info->device_bytes = h->dev_bytes;
+    return PFMM_OK;
+}
+
+void pfmm_destroy(pfmm_handle *h)
+{
+    if (!h) return;
+    delete h;  // cudaFree waits for outstanding work on the buffers
+}
+
+}  // extern "C"

@@ -1,0 +1,591 @@
+// k_apply.cu -- the per-matvec kernels of Alg. 2 (Section 3.4).
+//
+// Layouts (per right-hand side r):
+//   w_int[r][t][i]        input in internal triangle order (triangles grouped by leaf box)
+//   g[r][t][node]         double-layer input in the caller's node order
+//   f_int[r][t][i]        FP64 output in internal order
+//   mu_l[r][k][b][a][i]   moments of level l: interval k, spatial box b, time node a, graded
+//                         multi-index i (all kappa with |kappa| <= q come first)
+//   lam_l                 local contributions, same layout
+// R is the arithmetic type of the FMM passes and of the stored nearfield blocks: double in
+// FP64 mode, float in mixed mode (FP64 output accumulation).
+#include <cstdio>
+
+#include "device_math.cuh"
+#include "kernels.h"
+
+namespace pfmm {
+
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_permute_in(const double *__restrict__ w, T *__restrict__ wi, const int *__restrict__ perm, int nt,
+                             size_t total)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    size_t rt = gid / nt;
+    int i = (int)(gid - rt * nt);
+    wi[gid] = T(w[rt * nt + perm[i]]);
+}
+
+void launch_permute_in(const double *w, void *w_int, bool to_float, int nrhs, const ApplyGeo &g, cudaStream_t st)
+{
+    size_t total = (size_t)nrhs * g.Et * g.nt;
+    unsigned blocks = (unsigned)((total + 255) / 256);
+    if (to_float)
+        k_permute_in<float><<<blocks, 256, 0, st>>>(w, (float *)w_int, g.perm, g.nt, total);
+    else
+        k_permute_in<double><<<blocks, 256, 0, st>>>(w, (double *)w_int, g.perm, g.nt, total);
+}
+
+__global__ void k_permute_out(const double *__restrict__ fi, double *__restrict__ f, const int *__restrict__ perm, int nt,
+                              size_t total)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    size_t rt = gid / nt;
+    int i = (int)(gid - rt * nt);
+    f[rt * nt + perm[i]] = fi[gid];
+}
+
+void launch_permute_out(const double *f_int, double *f, int nrhs, const ApplyGeo &g, cudaStream_t st)
+{
+    size_t total = (size_t)nrhs * g.Et * g.nt;
+    k_permute_out<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(f_int, f, g.perm, g.nt, total);
+}
+
+__global__ void k_cast(const double *__restrict__ x, float *__restrict__ y, size_t n)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < n) y[gid] = (float)x[gid];
+}
+
+void launch_cast_to_float(const double *x, float *y, size_t n, cudaStream_t st)
+{
+    k_cast<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+}
+
+// ------------------------------------------------------------------------------------------
+// Nearfield apply (Alg. 2, last loop; Eq. eval_sl_nf_block) with the block-Toeplitz structure
+// of uniform steps: for target step t = k*ls + s of leaf interval k the temporal nearfield
+// N(I_k) = {I_{k-1}, I_k} contributes the step offsets d = 0 .. ls + s, so
+//   f[t][rows of X] = sum_{d=0}^{ls+s} A_d[X] x[t - d][cols of X].
+// One CTA computes a 64 x 64 tile (64 rows of a panel x 64 steps of one phase s) over all d
+// and all columns, so every output element is written exactly once.
+template <typename S>
+__global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const int *__restrict__ colidx,
+                                                    const int *__restrict__ tiles, const PanelGPU *__restrict__ panels,
+                                                    const S *__restrict__ x, int ncolg, int Et, int ls, int nint,
+                                                    double *__restrict__ f, int nt, int kop)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    constexpr bool kFloat = sizeof(S) == 4;
+    __shared__ S As[BK][BM + 1];
+    __shared__ S Ws[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int rg = tid & 15, cg = tid >> 4;
+    const PanelGPU P = panels[tiles[2 * blockIdx.x]];
+    const int r0 = tiles[2 * blockIdx.x + 1];
+    const int s = blockIdx.y % ls, ib = blockIdx.y / ls;
+    const int rhs = blockIdx.z;
+    const S *xr = x + (size_t)rhs * Et * ncolg;
+    const int *cols = colidx + (kop ? P.colK_at : P.colV_at);
+    const int ncp = kop ? P.colsK_pad : P.colsV_pad;
+    A += kop ? P.offK : P.offV;
+    S acc[4][4];
+    double accd[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            acc[i][j] = S(0);
+            accd[i][j] = 0.0;
+        }
+    const int nd = ls + s + 1;
+    int ktiles = 0;
+    for (int d = 0; d < nd; ++d) {
+        const S *Ad = A + ((size_t)d * P.rows_pad + r0) * ncp;
+        for (int k0 = 0; k0 < ncp; k0 += BK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int e = tid + 256 * q;
+                int i = e >> 4, j = e & 15;
+                As[j][i] = Ad[(size_t)i * ncp + k0 + j];
+                int c = e >> 4;
+                int t = ((ib * BN + c) * ls + s);
+                int col = cols[k0 + j];
+                S v = S(0);
+                if (col >= 0 && ib * BN + c < nint && t - d >= 0) v = xr[(size_t)(t - d) * ncolg + col];
+                Ws[j][c] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < BK; ++j) {
+                S a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = As[j][rg + 16 * q];
+                    b[q] = Ws[j][cg + 16 * q];
+                }
+#pragma unroll
+                for (int qi = 0; qi < 4; ++qi)
+#pragma unroll
+                    for (int qj = 0; qj < 4; ++qj) acc[qi][qj] += a[qi] * b[qj];
+            }
+            __syncthreads();
+            if (kFloat && ++ktiles == 32) {  // FP32 partial sums over 512 columns, then FP64
+                ktiles = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        accd[i][j] += (double)acc[i][j];
+                        acc[i][j] = S(0);
+                    }
+            }
+        }
+    }
+#pragma unroll
+    for (int qj = 0; qj < 4; ++qj) {
+        int iv = ib * BN + cg + 16 * qj;
+        if (iv >= nint) continue;
+        int t = iv * ls + s;
+#pragma unroll
+        for (int qi = 0; qi < 4; ++qi) {
+            int row = r0 + rg + 16 * qi;
+            if (row < P.nrows) f[((size_t)rhs * Et + t) * nt + P.row0 + row] = accd[qi][qj] + (double)acc[qi][qj];
+        }
+    }
+}
+
+void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
+                     const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
+                     cudaStream_t st)
+{
+    int nint = g.Et / g.ls;
+    dim3 grd(ntiles, g.ls * ((nint + 63) / 64), nrhs);
+    if (mixed)
+        k_nf_apply<float><<<grd, 256, 0, st>>>((const float *)A, colidx, tiles, panels, (const float *)x, ncolg, g.Et,
+                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0);
+    else
+        k_nf_apply<double><<<grd, 256, 0, st>>>((const double *)A, colidx, tiles, panels, (const double *)x, ncolg,
+                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0);
+}
+
+// ------------------------------------------------------------------------------------------
+// S2M at the leaves (Eq. s2m): mu[k][X][a][i] = sum_s St[s][a] sum_{x in X} x[k ls + s][x] Sx[x][i]
+// (double layer: sum over the triangle's three nodes with SK).  CTA per (leaf box, interval
+// chunk, rhs).
+template <typename R, bool KOP>
+__global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncolg, const int *__restrict__ tri,
+                                               const R *__restrict__ Stab, const R *__restrict__ St, R *__restrict__ mu,
+                                               const int *__restrict__ leaf_start, int nk, int na, int ls, int Et,
+                                               int nint, int nbox, int IB)
+{
+    extern __shared__ unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    constexpr int XCH = 16;
+    constexpr int PER = KOP ? 3 : 1;
+    const int X = blockIdx.x, k0 = blockIdx.y * IB, rhs = blockIdx.z;
+    const int kend = min(nint, k0 + IB), nts = (kend - k0) * ls, t0 = k0 * ls;
+    const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
+    R *Ws = sm;                        // [nts][XCH*PER]
+    R *Ss = sm + IB * ls * XCH * PER;  // [XCH*PER][nk]
+    const R *xr = xin + (size_t)rhs * Et * ncolg;
+    R acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = R(0);
+    const int nout = nts * nk;
+    for (int xb = x0; xb < x1; xb += XCH) {
+        int nx = min(XCH, x1 - xb);
+        for (int e = threadIdx.x; e < nts * XCH * PER; e += blockDim.x) {
+            int ts = e / (XCH * PER), j = e % (XCH * PER);
+            int xi = j / PER, v = j % PER;
+            R val = R(0);
+            if (xi < nx) {
+                int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
+                val = xr[(size_t)(t0 + ts) * ncolg + col];
+            }
+            Ws[e] = val;
+        }
+        for (int e = threadIdx.x; e < XCH * PER * nk; e += blockDim.x) {
+            int j = e / nk;
+            Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + (e % nk)] : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int o = threadIdx.x + q * blockDim.x;
+            if (o < nout) {
+                int ts = o / nk, i = o % nk;
+                R a = acc[q];
+                for (int j = 0; j < XCH * PER; ++j) a += Ws[ts * XCH * PER + j] * Ss[j * nk + i];
+                acc[q] = a;
+            }
+        }
+        __syncthreads();
+    }
+    R *Ps = sm;  // [nts][nk]
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        int o = threadIdx.x + q * blockDim.x;
+        if (o < nout) Ps[o] = acc[q];
+    }
+    __syncthreads();
+    const int nmo = (kend - k0) * na * nk;
+    for (int o = threadIdx.x; o < nmo; o += blockDim.x) {
+        int kk = o / (na * nk), a = (o / nk) % na, i = o % nk;
+        R v = R(0);
+        for (int s = 0; s < ls; ++s) v += St[s * na + a] * Ps[((kk * ls) + s) * nk + i];
+        mu[((((size_t)rhs * nint + k0 + kk) * nbox + X) * na + a) * nk + i] = v;
+    }
+}
+
+static int s2m_chunk(int ls, int nk, int nint)
+{
+    int IB = 2048 / (ls * nk);
+    if (IB < 1) IB = 1;
+    if (IB > 16) IB = 16;
+    if (IB > nint) IB = nint;
+    return IB;
+}
+
+void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
+                const ApplyGeo &g, cudaStream_t st)
+{
+    int nint = g.Et / g.ls;
+    int IB = s2m_chunk(g.ls, g.nk, nint);
+    int PER = kop ? 3 : 1;
+    size_t es = mixed ? 4 : 8;
+    size_t sm1 = (size_t)IB * g.ls * 16 * PER + (size_t)16 * PER * g.nk, sm2 = (size_t)IB * g.ls * g.nk;
+    size_t smem = (sm1 > sm2 ? sm1 : sm2) * es;
+    dim3 grd(g.nbox_leaf, (nint + IB - 1) / IB, nrhs);
+#define S2M_LAUNCH(R, K)                                                                                          \
+    do {                                                                                                          \
+        cudaFuncSetAttribute(k_s2m<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
+        k_s2m<R, K><<<grd, 256, smem, st>>>((const R *)x, ncolg, g.tri, (const R *)Stab, (const R *)St, (R *)mu_leaf, \
+                                            g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, IB);         \
+    } while (0)
+    if (mixed) {
+        if (kop) S2M_LAUNCH(float, true); else S2M_LAUNCH(float, false);
+    } else {
+        if (kop) S2M_LAUNCH(double, true); else S2M_LAUNCH(double, false);
+    }
+#undef S2M_LAUNCH
+}
+
+// ------------------------------------------------------------------------------------------
+// M2M from level l+1 to level l (Eq. temp_m2m, st_m2m): thread per parent moment.
+template <typename R>
+__global__ void k_m2m(const R *__restrict__ mu_c, R *__restrict__ mu_p, const int *__restrict__ ch_ptr,
+                      const int *__restrict__ ch_idx, const int *__restrict__ oct_c, const R *__restrict__ q1,
+                      const R *__restrict__ qt, const int *__restrict__ kidx, const int *__restrict__ kinv, int st, int na,
+                      int nk, int mx, int nint_p, int nbox_p, int nbox_c, int nrhs)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nrhs * nint_p * nbox_p * na * nk;
+    if (gid >= total) return;
+    int iv = gid % nk;
+    size_t r_ = gid / nk;
+    int ap = r_ % na;
+    r_ /= na;
+    int bp = r_ % nbox_p;
+    r_ /= nbox_p;
+    int kp = r_ % nint_p;
+    int rhs = (int)(r_ / nint_p);
+    const int m1 = mx + 1;
+    int n0 = kidx[3 * iv], n1 = kidx[3 * iv + 1], n2 = kidx[3 * iv + 2];
+    R acc = R(0);
+    for (int e = ch_ptr[bp]; e < ch_ptr[bp + 1]; ++e) {
+        int bc = ch_idx[e], oc = oct_c[bc];
+        const R *qa = q1 + (oc & 1) * m1 * m1, *qb = q1 + ((oc >> 1) & 1) * m1 * m1, *qc = q1 + ((oc >> 2) & 1) * m1 * m1;
+        for (int c = 0; c < 2; ++c) {
+            int kc = 2 * kp + c;
+            const R *mc = mu_c + (((size_t)rhs * 2 * nint_p + kc) * nbox_c + bc) * na * nk;
+            for (int ac = 0; ac < na; ++ac) {
+                R qtv = qt[(c * na + ac) * na + ap];
+                const R *m = mc + ac * nk;
+                if (!st) {
+                    acc += qtv * m[iv];
+                } else {
+                    R s = R(0);
+                    for (int k0 = 0; k0 <= n0; ++k0)
+                        for (int k1 = 0; k1 <= n1; ++k1)
+                            for (int k2 = 0; k2 <= n2; ++k2)
+                                s += qa[k0 * m1 + n0] * qb[k1 * m1 + n1] * qc[k2 * m1 + n2] *
+                                     m[kinv[(k0 * m1 + k1) * m1 + k2]];
+                    acc += qtv * s;
+                }
+            }
+        }
+    }
+    mu_p[gid] = acc;
+}
+
+void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
+{
+    (void)l;
+    (void)mu_stride;
+    size_t total = (size_t)nrhs * par.nint * par.nbox * g.na * g.nk;
+    unsigned blocks = (unsigned)((total + 127) / 128);
+    size_t es = mixed ? 4 : 8;
+    char *base = (char *)mu;
+    if (mixed)
+        k_m2m<float><<<blocks, 128, 0, st>>>((const float *)(base + ch.mom_off * es * nrhs), (float *)(base + par.mom_off * es * nrhs),
+                                             par.ch_ptr, par.ch_idx, ch.octant, (const float *)ch.qx, (const float *)qt,
+                                             g.kidx, g.kinv, ch.st, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox, nrhs);
+    else
+        k_m2m<double><<<blocks, 128, 0, st>>>((const double *)(base + ch.mom_off * es * nrhs),
+                                              (double *)(base + par.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
+                                              ch.octant, (const double *)ch.qx, (const double *)qt, g.kidx, g.kinv,
+                                              ch.st, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox, nrhs);
+}
+
+// ------------------------------------------------------------------------------------------
+// M2L at level l (Eq. m2l with Eq. exp_coeffs_3d): CTA per target (interval k, box bt).
+//   lam[b][nu] = sum_{sources} sum_a pref_ab sum_{|kappa| <= m_x - |nu|}
+//                E1_x[kappa_1][nu_1] E1_y[kappa_2][nu_2] E1_z[kappa_3][nu_3] mu[a][kappa]
+// Temporal sources: I_{k-2} (k even) or I_{k-3}, I_{k-2} (k odd), none for k < 2 (Eq. 03:ILtemp);
+// spatial sources: the interaction area of bt (Eq. 03:Iarea).
+template <typename R>
+__global__ void __launch_bounds__(512) k_m2l(const R *__restrict__ mu, R *__restrict__ lam,
+                                               const int *__restrict__ m2l_ptr, const int *__restrict__ m2l_src,
+                                               const int *__restrict__ m2l_off, const R *__restrict__ E1,
+                                               const R *__restrict__ pref, const int *__restrict__ kidx, int na, int nk,
+                                               int mx, int G, int nint, int nbox)
+{
+    extern __shared__ unsigned char smem_raw[];
+    R *mus = reinterpret_cast<R *>(smem_raw);  // [na][nk]
+    const int m1 = mx + 1, no = 2 * G - 1;
+    R *Es = mus + na * nk;                      // [3][na][na][m1][m1]
+    int *ks = reinterpret_cast<int *>(Es + 3 * na * na * m1 * m1);  // [nk] packed kappa
+    const int k = blockIdx.x / nbox, bt = blockIdx.x % nbox, rhs = blockIdx.z;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) ks[i] = kidx[3 * i] | (kidx[3 * i + 1] << 8) | (kidx[3 * i + 2] << 16);
+    const int nout = na * nk;
+    R acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = R(0);
+    int js[2], nj = 0;
+    if (k >= 2) {
+        if (k % 2 == 0) { js[0] = k - 2; nj = 1; }
+        else { js[0] = k - 3; js[1] = k - 2; nj = 2; }
+    }
+    const size_t lvl_rhs = (size_t)rhs * nint;
+    for (int jj = 0; jj < nj; ++jj) {
+        const int J = js[jj], D = k - J;
+        for (int e = m2l_ptr[bt]; e < m2l_ptr[bt + 1]; ++e) {
+            const int bs = m2l_src[e], off = m2l_off[e];
+            const int o3[3] = {off & 255, (off >> 8) & 255, (off >> 16) & 255};
+            __syncthreads();
+            const R *ms = mu + ((lvl_rhs + J) * nbox + bs) * na * nk;
+            for (int i = threadIdx.x; i < na * nk; i += blockDim.x) mus[i] = ms[i];
+            const int esz = m1 * m1;
+            for (int i = threadIdx.x; i < 3 * na * na * esz; i += blockDim.x) {
+                int c = i / (na * na * esz), r_ = i % (na * na * esz);
+                int ab = r_ / esz, kl = r_ % esz;
+                Es[i] = E1[((size_t)((D - 2) * na * na + ab) * no + o3[c]) * esz + kl];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int o = threadIdx.x + q * blockDim.x;
+                if (o >= nout) break;
+                int b = o / nk, iv = o % nk;
+                int nu = ks[iv];
+                int n0 = nu & 255, n1 = (nu >> 8) & 255, n2 = nu >> 16;
+                int smax = mx - n0 - n1 - n2;
+                int nq = (smax + 1) * (smax + 2) * (smax + 3) / 6;  // |kappa| <= smax: graded prefix
+                R tot = R(0);
+                for (int a = 0; a < na; ++a) {
+                    const R *Ea = Es + (0 * na * na + a * na + b) * esz;
+                    const R *Eb = Es + (1 * na * na + a * na + b) * esz;
+                    const R *Ec = Es + (2 * na * na + a * na + b) * esz;
+                    const R *ma = mus + a * nk;
+                    R s = R(0);
+                    for (int i = 0; i < nq; ++i) {
+                        int kk = ks[i];
+                        s += Ea[(kk & 255) * m1 + n0] * Eb[((kk >> 8) & 255) * m1 + n1] * Ec[(kk >> 16) * m1 + n2] * ma[i];
+                    }
+                    tot += pref[((D - 2) * na + a) * na + b] * s;
+                }
+                acc[q] += tot;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        int o = threadIdx.x + q * blockDim.x;
+        if (o < nout) lam[((lvl_rhs + k) * nbox + bt) * na * nk + o] = acc[q];
+    }
+}
+
+void launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
+                int64_t mu_stride, cudaStream_t st)
+{
+    (void)l;
+    (void)mu_stride;
+    const int m1 = g.mx + 1;
+    size_t es = mixed ? 4 : 8;
+    size_t smem = ((size_t)g.na * g.nk + 3 * (size_t)g.na * g.na * m1 * m1) * es + (size_t)g.nk * 4;
+    dim3 grd(L.nint * L.nbox, 1, nrhs);
+    int nout = g.na * g.nk, thr = 128;
+    while (thr * 8 < nout) thr *= 2;
+    const char *mb = (const char *)mu + L.mom_off * es * nrhs;
+    char *lb = (char *)lam + L.mom_off * es * nrhs;
+    if (mixed) {
+        cudaFuncSetAttribute(k_m2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2l<float><<<grd, thr, smem, st>>>((const float *)mb, (float *)lb, L.m2l_ptr, L.m2l_src, L.m2l_off,
+                                             (const float *)L.E1, (const float *)L.pref, g.kidx, g.na, g.nk, g.mx, L.G,
+                                             L.nint, L.nbox);
+    } else {
+        cudaFuncSetAttribute(k_m2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_m2l<double><<<grd, thr, smem, st>>>((const double *)mb, (double *)lb, L.m2l_ptr, L.m2l_src, L.m2l_off,
+                                              (const double *)L.E1, (const double *)L.pref, g.kidx, g.na, g.nk, g.mx, L.G,
+                                              L.nint, L.nbox);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// L2L from level l-1 to level l (transposes of Eq. temp_m2m, st_m2m): thread per child local.
+template <typename R>
+__global__ void k_l2l(const R *__restrict__ lam_p, R *__restrict__ lam_c, const int *__restrict__ parent,
+                      const int *__restrict__ oct_c, const R *__restrict__ q1, const R *__restrict__ qt,
+                      const int *__restrict__ kidx, const int *__restrict__ kinv, int st, int na, int nk, int mx,
+                      int nint_c, int nbox_c, int nbox_p, int nrhs)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nrhs * nint_c * nbox_c * na * nk;
+    if (gid >= total) return;
+    int ik = gid % nk;
+    size_t r_ = gid / nk;
+    int bcI = r_ % na;
+    r_ /= na;
+    int bc = r_ % nbox_c;
+    r_ /= nbox_c;
+    int kc = r_ % nint_c;
+    int rhs = (int)(r_ / nint_c);
+    const int m1 = mx + 1;
+    int kp = kc >> 1, c = kc & 1, bp = parent[bc], oc = oct_c[bc];
+    const R *qa = q1 + (oc & 1) * m1 * m1, *qb = q1 + ((oc >> 1) & 1) * m1 * m1, *qc = q1 + ((oc >> 2) & 1) * m1 * m1;
+    int k0 = kidx[3 * ik], k1 = kidx[3 * ik + 1], k2 = kidx[3 * ik + 2];
+    const R *lp = lam_p + (((size_t)rhs * (nint_c >> 1) + kp) * nbox_p + bp) * na * nk;
+    R acc = R(0);
+    for (int bpI = 0; bpI < na; ++bpI) {
+        R qtv = qt[(c * na + bcI) * na + bpI];
+        const R *l = lp + bpI * nk;
+        if (!st) {
+            acc += qtv * l[ik];
+        } else {
+            R s = R(0);
+            for (int n0 = k0; n0 <= mx; ++n0)
+                for (int n1 = k1; n0 + n1 <= mx; ++n1)
+                    for (int n2 = k2; n0 + n1 + n2 <= mx; ++n2)
+                        s += qa[k0 * m1 + n0] * qb[k1 * m1 + n1] * qc[k2 * m1 + n2] * l[kinv[(n0 * m1 + n1) * m1 + n2]];
+            acc += qtv * s;
+        }
+    }
+    lam_c[gid] += acc;
+}
+
+void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
+{
+    (void)l;
+    (void)mu_stride;
+    size_t total = (size_t)nrhs * ch.nint * ch.nbox * g.na * g.nk;
+    unsigned blocks = (unsigned)((total + 127) / 128);
+    size_t es = mixed ? 4 : 8;
+    char *base = (char *)lam;
+    if (mixed)
+        k_l2l<float><<<blocks, 128, 0, st>>>((const float *)(base + par.mom_off * es * nrhs), (float *)(base + ch.mom_off * es * nrhs),
+                                             ch.parent, ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx,
+                                             g.kinv, ch.st, g.na, g.nk, g.mx, ch.nint, ch.nbox, par.nbox, nrhs);
+    else
+        k_l2l<double><<<blocks, 128, 0, st>>>((const double *)(base + par.mom_off * es * nrhs),
+                                              (double *)(base + ch.mom_off * es * nrhs), ch.parent, ch.octant,
+                                              (const double *)ch.qx, (const double *)qt, g.kidx, g.kinv, ch.st, g.na,
+                                              g.nk, g.mx, ch.nint, ch.nbox, par.nbox, nrhs);
+}
+
+// ------------------------------------------------------------------------------------------
+// L2T at the leaves (Eq. l2t): f[k ls + s][x] += sum_b St[s][b] sum_nu lam[k][X][b][nu] Sx[x][nu].
+template <typename R>
+__global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R *__restrict__ Sx, const R *__restrict__ St,
+                                               double *__restrict__ f, const int *__restrict__ leaf_start, int nk, int na,
+                                               int ls, int Et, int nint, int nbox, int nt, int IB)
+{
+    extern __shared__ unsigned char smem_raw[];
+    R *Ls = reinterpret_cast<R *>(smem_raw);  // [nts][nk]
+    constexpr int XCH = 32;
+    const int X = blockIdx.x, k0 = blockIdx.y * IB, rhs = blockIdx.z;
+    const int kend = min(nint, k0 + IB), nts = (kend - k0) * ls, t0 = k0 * ls;
+    R *Sxs = Ls + IB * ls * nk;  // [XCH][nk + 1]
+    const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
+    for (int o = threadIdx.x; o < nts * nk; o += blockDim.x) {
+        int ts = o / nk, i = o % nk, kk = ts / ls, s = ts % ls;
+        const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
+        R v = R(0);
+        for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
+        Ls[o] = v;
+    }
+    for (int xb = x0; xb < x1; xb += XCH) {
+        int nx = min(XCH, x1 - xb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < XCH * nk; e += blockDim.x) {
+            int xi = e / nk, i = e % nk;
+            Sxs[xi * (nk + 1) + i] = xi < nx ? Sx[(size_t)(xb + xi) * nk + i] : R(0);
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < nts * XCH; o += blockDim.x) {
+            int ts = o / XCH, xi = o % XCH;
+            if (xi >= nx) continue;
+            const R *lrow = Ls + ts * nk, *srow = Sxs + xi * (nk + 1);
+            R v = R(0);
+            for (int i = 0; i < nk; ++i) v += lrow[i] * srow[i];
+            f[((size_t)rhs * Et + t0 + ts) * nt + xb + xi] += (double)v;
+        }
+    }
+}
+
+void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
+{
+    (void)mu_stride;
+    int nint = g.Et / g.ls;
+    int IB = s2m_chunk(g.ls, g.nk, nint);
+    size_t es = mixed ? 4 : 8;
+    size_t smem = ((size_t)IB * g.ls * g.nk + 32 * (size_t)(g.nk + 1)) * es;
+    dim3 grd(g.nbox_leaf, (nint + IB - 1) / IB, nrhs);
+    if (mixed) {
+        cudaFuncSetAttribute(k_l2t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_l2t<float><<<grd, 256, smem, st>>>((const float *)lam_leaf, (const float *)Sx, (const float *)St, f_int,
+                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, IB);
+    } else {
+        cudaFuncSetAttribute(k_l2t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_l2t<double><<<grd, 256, smem, st>>>((const double *)lam_leaf, (const double *)Sx, (const double *)St, f_int,
+                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, IB);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// f = M_h g: f[t][x] = h |gamma_x| / 3 * sum of g[t] over the vertices of gamma_x (Section 2).
+__global__ void k_apply_M(const double *__restrict__ g, double *__restrict__ f, const int *__restrict__ tri,
+                          const double *__restrict__ area, int nt, int nv, size_t total, double h)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    size_t rt = gid / nt;
+    int x = (int)(gid - rt * nt);
+    const double *gr = g + rt * nv;
+    f[gid] = h * area[x] / 3.0 * (gr[tri[3 * x]] + gr[tri[3 * x + 1]] + gr[tri[3 * x + 2]]);
+}
+
+void launch_apply_M(const double *g_in, double *f, const int *tri_user, const double *area, int nrhs, int nt, int nv,
+                    int Et, double h, cudaStream_t st)
+{
+    size_t total = (size_t)nrhs * Et * nt;
+    k_apply_M<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g_in, f, tri_user, area, nt, nv, total, h);
+}
+
+}  // namespace pfmm

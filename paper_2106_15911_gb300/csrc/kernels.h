@@ -1,0 +1,83 @@
+// kernels.h -- launch interfaces between the host orchestration (capi.cpp) and the CUDA files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pfmm_internal.h"
+
+namespace pfmm {
+
+struct PanelGPU {  // device copy of Panel
+    int index, row0, nrows, rows_pad;
+    int ncolV, colsV_pad, ncolK, colsK_pad;
+    long long offV, offK;
+    int colV_at, colK_at;
+};
+
+struct SetupArgs {
+    const double *verts;   // [nv][3]
+    const int *tri;        // [nt][3] internal order
+    const int *tri_leaf;   // [nt]
+    const int *leaf_grid;  // [nbox_p][3]
+    double corner[3], hx_leaf, hxp_leaf, alpha;
+    int nt, mx, nk;
+    const int *kidx;       // [nk][3] graded multi-indices
+    const double *rule_tab;// collapsed rule s1[nq], s2[nq], w[nq] (exact for degree m_x)
+    int nq_tab;
+    double *Sx, *SK;       // [nt][nk], [nt][3][nk]
+};
+
+struct NfQuadArgs {
+    const double *verts;
+    const int *tri;        // internal order
+    int nv, nd;            // nd = 2 leaf_steps step offsets
+    double h, alpha;
+    const double *rule_reg;// collapsed rule s1, s2, w (n_r^2 points)
+    int nq_reg;
+    const double *gl_sing; // Gauss-Legendre on [0,1]: x[n], w[n]
+    int nq_sing;
+    const int *colV;       // all panels' V columns
+    const int *kmap;       // [npanel][nv]
+};
+
+void launch_space_tables(const SetupArgs &a, cudaStream_t st);
+void launch_e1_table(int na, int mt, int mx, int G, double hx, double hxp, double ht, double alpha, double *E1,
+                     double *pref, cudaStream_t st);
+void launch_nf_regular(const NfQuadArgs &a, const PanelGPU &P, void *AV, void *AK, bool mixed, cudaStream_t st);
+void launch_nf_singular(const NfQuadArgs &a, const int *sing, int nsing, const PanelGPU *panels, void *AV, void *AK,
+                        bool mixed, cudaStream_t st);
+
+// ---- apply ------------------------------------------------------------------------------
+struct ApplyGeo {
+    int nt, nv, Et, ls, nd, na, nk, mx, p;
+    const int *perm;       // [nt] internal -> caller triangle
+    const int *tri;        // [nt][3] internal order
+    const int *leaf_start; // [nbox_p + 1]
+    int nbox_leaf;
+    const int *kidx;       // [nk][3] graded
+    const int *kinv;       // [(m+1)^3] -> graded index
+};
+
+// R: arithmetic/storage type of the FMM passes (double or float)
+void launch_permute_in(const double *w, void *w_int, bool to_float, int nrhs, const ApplyGeo &g, cudaStream_t st);
+void launch_permute_out(const double *f_int, double *f, int nrhs, const ApplyGeo &g, cudaStream_t st);
+void launch_cast_to_float(const double *x, float *y, size_t n, cudaStream_t st);
+void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
+                     const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
+                     cudaStream_t st);
+void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab /*Sx or SK*/, const void *St,
+                void *mu_leaf, int nrhs, const ApplyGeo &g, cudaStream_t st);
+void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
+void launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
+                int64_t mu_stride, cudaStream_t st);
+void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
+void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
+void launch_apply_M(const double *g_in, double *f, const int *tri_user, const double *area, int nrhs, int nt, int nv,
+                    int Et, double h, cudaStream_t st);
+
+}  // namespace pfmm

@@ -1,0 +1,254 @@
+"""Thin Python binding of the C ABI in include/pfmm.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``libpfmm.so`` built in-tree by
+``paper_2106_15911_gb300.build``; there is no CPU fallback: if the library is missing or a
+call fails, an exception is raised.  Device vectors are passed as ``torch.Tensor`` (FP64,
+CUDA, contiguous) or as raw integer device pointers; streams as ``torch.cuda.Stream`` or raw
+``cudaStream_t`` integers (None = torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PFMM_OK = 0
+PFMM_ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "NOT_CONVERGED",
+            -7: "UNSUPPORTED"}
+PFMM_FP64, PFMM_MIXED = 0, 1
+PFMM_NEARFIELD_STORED = 0
+PFMM_PART_NEAR, PFMM_PART_FAR, PFMM_PART_ALL = 1, 2, 3
+
+
+class pfmm_mesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int32), ("n_triangles", ctypes.c_int32),
+                ("vertices", ctypes.POINTER(ctypes.c_double)), ("triangles", ctypes.POINTER(ctypes.c_int32)),
+                ("T", ctypes.c_double), ("n_steps", ctypes.c_int32), ("alpha", ctypes.c_double)]
+
+
+class pfmm_params(ctypes.Structure):
+    _fields_ = [("m_t", ctypes.c_int32), ("m_x", ctypes.c_int32), ("c_st", ctypes.c_double),
+                ("n_tr", ctypes.c_int32), ("eps_tr", ctypes.c_double), ("leaf_steps", ctypes.c_int32),
+                ("leaf_tris", ctypes.c_int32), ("precision", ctypes.c_int32), ("nearfield", ctypes.c_int32),
+                ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32)]
+
+
+class pfmm_info(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("lx", ctypes.c_int32 * 32), ("nbox", ctypes.c_int32 * 32),
+                ("pad", ctypes.c_double * 32), ("n_m2l_pairs", ctypes.c_int32), ("nearfield_bytes", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every entry point declared in include/pfmm.h
+_VP, _I, _DP = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p
+SIGNATURES = {
+    "pfmm_default_params": (ctypes.c_int, [ctypes.POINTER(pfmm_params)]),
+    "pfmm_build_trees": (ctypes.c_int, [ctypes.POINTER(pfmm_mesh), ctypes.POINTER(pfmm_params), _VP,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "pfmm_apply_V": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
+    "pfmm_apply_K": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
+    "pfmm_apply_M": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
+    "pfmm_apply_parts": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, _I, _VP]),
+    "pfmm_set_profiling": (ctypes.c_int, [_VP, _I]),
+    "pfmm_phase_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
+    "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
+    "pfmm_destroy": (None, [_VP]),
+    "pfmm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def _preload_cudart():
+    """Make libcudart resolvable for the dlopen of libpfmm.so (CUDA toolkit or torch's copy)."""
+    for d in ("/usr/local/cuda/lib64", "/usr/local/cuda/targets/sbsa-linux/lib", "/usr/local/cuda/targets/x86_64-linux/lib"):
+        for n in ("libcudart.so.13", "libcudart.so"):
+            p = os.path.join(d, n)
+            if os.path.exists(p):
+                try:
+                    ctypes.CDLL(p, mode=ctypes.RTLD_GLOBAL)
+                    return
+                except OSError:
+                    pass
+
+
+def lib(build_if_missing: bool = True):
+    """Load libpfmm.so (building it first if needed).  Raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+                path = _build.build()
+            _preload_cudart()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class PfmmError(RuntimeError):
+    pass
+
+
+def _check(rc):
+    if rc != PFMM_OK:
+        msg = lib().pfmm_last_error().decode(errors="replace")
+        raise PfmmError(f"pfmm error {rc} ({PFMM_ERR.get(rc, '?')}): {msg}")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+
+    if isinstance(x, torch.Tensor):
+        if not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _stream(s):
+    if isinstance(s, int):
+        return s
+    import torch
+
+    if s is None:
+        s = torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def pfmm_default_params() -> pfmm_params:
+    p = pfmm_params()
+    _check(lib().pfmm_default_params(ctypes.byref(p)))
+    return p
+
+
+def pfmm_build_trees(vertices, triangles, T, n_steps, alpha=1.0, params: pfmm_params | None = None, stream=None):
+    """Build a handle (Alg. 1 tree, lists, tables, stored nearfield).  Returns an opaque handle."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    Tr = np.ascontiguousarray(triangles, dtype=np.int32)
+    m = pfmm_mesh(V.shape[0], Tr.shape[0], V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  Tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(T), int(n_steps), float(alpha))
+    if params is None:
+        params = pfmm_default_params()
+    h = ctypes.c_void_p()
+    _check(lib().pfmm_build_trees(ctypes.byref(m), ctypes.byref(params), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def pfmm_apply_V(h, w, f, nrhs: int, stream=None):
+    _check(lib().pfmm_apply_V(h, _ptr(w), _ptr(f), int(nrhs), _stream(stream)))
+
+
+def pfmm_apply_K(h, g, f, nrhs: int, stream=None):
+    _check(lib().pfmm_apply_K(h, _ptr(g), _ptr(f), int(nrhs), _stream(stream)))
+
+
+def pfmm_apply_M(h, g, f, nrhs: int, stream=None):
+    _check(lib().pfmm_apply_M(h, _ptr(g), _ptr(f), int(nrhs), _stream(stream)))
+
+
+def pfmm_apply_parts(h, op: int, x, f, nrhs: int, parts: int, stream=None):
+    _check(lib().pfmm_apply_parts(h, int(op), _ptr(x), _ptr(f), int(nrhs), int(parts), _stream(stream)))
+
+
+def pfmm_set_profiling(h, on: bool):
+    _check(lib().pfmm_set_profiling(h, 1 if on else 0))
+
+
+PHASES = ("permute_in", "nearfield", "s2m", "m2m", "m2l", "l2l", "l2t", "permute_out")
+
+
+def pfmm_phase_times(h):
+    ms = (ctypes.c_double * 8)()
+    n = ctypes.c_int32()
+    _check(lib().pfmm_phase_times(h, ms, ctypes.byref(n)))
+    return dict(zip(PHASES, list(ms))), n.value
+
+
+def pfmm_get_info(h) -> dict:
+    i = pfmm_info()
+    _check(lib().pfmm_get_info(h, ctypes.byref(i)))
+    n = i.p + 1
+    return dict(p=i.p, lx=list(i.lx[:n]), nbox=list(i.nbox[:n]), pad=list(i.pad[:n]), n_m2l_pairs=i.n_m2l_pairs,
+                nearfield_bytes=i.nearfield_bytes, device_bytes=i.device_bytes)
+
+
+def pfmm_probe_fma_rate(fp64: bool, stream=None) -> float:
+    v = ctypes.c_double()
+    _check(lib().pfmm_probe_fma_rate(1 if fp64 else 0, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def pfmm_destroy(h):
+    if h:
+        lib().pfmm_destroy(h)
+
+
+class Operator:
+    """Convenience owner of a handle: V_h, K_h and M_h applies on torch CUDA tensors."""
+
+    def __init__(self, vertices, triangles, T, n_steps, alpha=1.0, stream=None, **params):
+        p = pfmm_default_params()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        self.nv = int(np.asarray(vertices).shape[0])
+        self.nt = int(np.asarray(triangles).shape[0])
+        self.n_steps = int(n_steps)
+        self.h = pfmm_build_trees(vertices, triangles, T, n_steps, alpha, p, stream)
+
+    def _out(self, x, ncol_in):
+        import torch
+
+        xx = x if x.dim() == 3 else x.unsqueeze(0)
+        if xx.shape[1] != self.n_steps or xx.shape[2] != ncol_in:
+            raise ValueError(f"expected [nrhs, {self.n_steps}, {ncol_in}], got {tuple(x.shape)}")
+        xx = xx.contiguous()
+        return xx, torch.empty((xx.shape[0], self.n_steps, self.nt), dtype=torch.float64, device=xx.device)
+
+    def V(self, w, parts=PFMM_PART_ALL, stream=None):
+        ww, f = self._out(w, self.nt)
+        pfmm_apply_parts(self.h, 0, ww, f, ww.shape[0], parts, stream)
+        return f if w.dim() == 3 else f[0]
+
+    def K(self, g, parts=PFMM_PART_ALL, stream=None):
+        gg, f = self._out(g, self.nv)
+        pfmm_apply_parts(self.h, 1, gg, f, gg.shape[0], parts, stream)
+        return f if g.dim() == 3 else f[0]
+
+    def M(self, g, stream=None):
+        gg, f = self._out(g, self.nv)
+        pfmm_apply_M(self.h, gg, f, gg.shape[0], stream)
+        return f if g.dim() == 3 else f[0]
+
+    def info(self):
+        return pfmm_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            pfmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
