@@ -32,6 +32,11 @@ METRIC = "pFMM matvec space-time DOF/s"
 N_A, ET, M_X, M_T, C_ST = 32, 256, 6, 4, 1.0
 
 
+def _set_size(n_a, et):
+    global N_A, ET
+    N_A, ET = n_a, et
+
+
 def _clock_sampler(stop, out):
     cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
            "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -116,7 +121,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
+    ap.add_argument("--et", type=int, default=ET, help="profiling only: time steps")
     args = ap.parse_args()
+    if (args.n_a, args.et) != (N_A, ET):
+        _set_size(args.n_a, args.et)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

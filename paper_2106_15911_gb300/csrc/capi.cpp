@@ -134,7 +134,13 @@ struct pfmm_handle {
     int ntiles = 0;
     int64_t mom_per_rhs = 0;
 
+    int ne = 0;              // C(m_x+4,4) entries of the separable M2L intermediates per cell
+    int *d_eoff = nullptr;   // [nk] offsets of the budget ranges
+    int64_t m2l_ws_need = 0; // elements of T1 (and of T2) for a whole level, per rhs
+
     int ws_nrhs = 0;
+    size_t ws_m2l = 0;
+    void *d_T1 = nullptr, *d_T2 = nullptr;
     void *d_xint = nullptr, *d_gf = nullptr, *d_mu = nullptr, *d_lam = nullptr;
     double *d_fint = nullptr;
 
@@ -232,6 +238,16 @@ int ensure_workspace(pfmm_handle *H, int nrhs)
     size_t nm = (size_t)nrhs * std::max<int64_t>(H->mom_per_rhs, 1);
     if ((rc = H->alloc((char **)&H->d_mu, nm * H->es, 1))) return rc;
     if ((rc = H->alloc((char **)&H->d_lam, nm * H->es, 1))) return rc;
+    // separable M2L intermediates: a whole level at once when it fits in 2 x 256 MB, else chunks
+    H->release(H->d_T1);
+    H->release(H->d_T2);
+    H->d_T1 = H->d_T2 = nullptr;
+    size_t need = (size_t)nrhs * std::max<int64_t>(H->m2l_ws_need, 1);
+    size_t cap = (size_t)(256u << 20) / H->es;
+    size_t min_chunk = (size_t)nrhs * 2 * H->na * H->na * H->ne * 64;  // at least two pairs of a 4^3 grid
+    H->ws_m2l = std::max(std::min(need, cap), min_chunk);
+    if ((rc = H->alloc((char **)&H->d_T1, H->ws_m2l * H->es, 1))) return rc;
+    if ((rc = H->alloc((char **)&H->d_T2, H->ws_m2l * H->es, 1))) return rc;
     H->ws_nrhs = nrhs;
     return PFMM_OK;
 }
@@ -313,6 +329,12 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
                 kidx.push_back(c);
             }
     H->nk = (int)kidx.size() / 3;
+    std::vector<int> eoff(H->nk);
+    H->ne = 0;
+    for (int t_ = 0; t_ < H->nk; ++t_) {
+        eoff[t_] = H->ne;
+        H->ne += mx - (kidx[3 * t_] + kidx[3 * t_ + 1] + kidx[3 * t_ + 2]) + 1;
+    }
     if (H->ls * H->nk > 2048) return fail(PFMM_ERR_UNSUPPORTED, "leaf_steps * C(m_x+3,3) > 2048");
     if (H->na * H->nk > 4096) return fail(PFMM_ERR_UNSUPPORTED, "(m_t+1) * C(m_x+3,3) > 4096");
 
@@ -334,7 +356,8 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         (rc = upload(H, &H->d_tri_user, tri_user, st)) || (rc = upload(H, &H->d_area, area, st)) ||
         (rc = upload(H, &H->d_perm, t.perm, st)) || (rc = upload(H, &H->d_tri_leaf, t.tri_leaf, st)) ||
         (rc = upload(H, &H->d_leaf_start, t.leaf_start, st)) || (rc = upload(H, &H->d_leaf_grid, t.lv[p].grid, st)) ||
-        (rc = upload(H, &H->d_kidx, kidx, st)) || (rc = upload(H, &H->d_kinv, kinv, st)))
+        (rc = upload(H, &H->d_kidx, kidx, st)) || (rc = upload(H, &H->d_kinv, kinv, st)) ||
+        (rc = upload(H, &H->d_eoff, eoff, st)))
         return rc;
 
     // ---- S2M / L2T tables (Eq. s2m, l2t)
@@ -425,6 +448,27 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             if ((rc = upload_R(H, &D.qx, q1, st))) return rc;
         }
         if (l >= 2) {
+            // separable M2L: dense cell map and the interval pairs of Eq. 03:ILtemp
+            std::vector<int> cellbox((size_t)L.G * L.G * L.G, -1), boxcell(L.nbox), pk, pJ;
+            for (int b = 0; b < L.nbox; ++b) {
+                int c = (L.grid[3 * b] * L.G + L.grid[3 * b + 1]) * L.G + L.grid[3 * b + 2];
+                cellbox[c] = b;
+                boxcell[b] = c;
+            }
+            D.kptr_host.assign(L.nint + 1, 0);
+            for (int k = 0; k < L.nint; ++k) {
+                if (k >= 2) {
+                    if (k % 2 == 0) { pk.push_back(k); pJ.push_back(k - 2); }
+                    else { pk.push_back(k); pJ.push_back(k - 3); pk.push_back(k); pJ.push_back(k - 2); }
+                }
+                D.kptr_host[k + 1] = (int)pk.size();
+            }
+            D.ntr = std::min(L.ntr, L.G - 1);
+            if ((rc = upload(H, &D.cellbox, cellbox, st)) || (rc = upload(H, &D.boxcell, boxcell, st)) ||
+                (rc = upload(H, &D.pk, pk, st)) || (rc = upload(H, &D.pJ, pJ, st)) ||
+                (rc = upload(H, &D.kptr, D.kptr_host, st)))
+                return rc;
+            H->m2l_ws_need = std::max<int64_t>(H->m2l_ws_need, (int64_t)pk.size() * na * na * L.G * L.G * L.G * H->ne);
             size_t ne = 2 * (size_t)na * na * (2 * L.G - 1) * m1 * m1;
             double *E1 = nullptr, *pref = nullptr;
             if ((rc = H->alloc(&E1, ne)) || (rc = H->alloc(&pref, 2 * (size_t)na * na))) return rc;
@@ -541,6 +585,8 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     g.nbox_leaf = t.lv[H->p].nbox;
     g.kidx = H->d_kidx;
     g.kinv = H->d_kinv;
+    g.ne = H->ne;
+    g.eoff = H->d_eoff;
     EvSet *ev = nullptr;
     if (H->prof) {
         if (H->evs.empty()) {
@@ -590,7 +636,9 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
         for (int l = p - 1; l >= 2; --l) launch_m2m(H->mixed, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
     mark(4);
     if (far)
-        for (int l = 2; l <= p; ++l) launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, 0, st);
+        for (int l = 2; l <= p; ++l)
+            if (launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, H->d_T1, H->d_T2, H->ws_m2l, st))
+                return fail(PFMM_ERR_OOM, "M2L workspace too small for one interval");
     mark(5);
     if (far)
         for (int l = 3; l <= p; ++l) launch_l2l(H->mixed, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);

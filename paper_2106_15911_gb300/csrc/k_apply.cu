@@ -9,6 +9,7 @@
 //   lam_l                 local contributions, same layout
 // R is the arithmetic type of the FMM passes and of the stored nearfield blocks: double in
 // FP64 mode, float in mixed mode (FP64 output accumulation).
+#include <algorithm>
 #include <cstdio>
 
 #include "device_math.cuh"
@@ -343,107 +344,189 @@ void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
 }
 
 // ------------------------------------------------------------------------------------------
-// M2L at level l (Eq. m2l with Eq. exp_coeffs_3d): CTA per target (interval k, box bt).
-//   lam[b][nu] = sum_{sources} sum_a pref_ab sum_{|kappa| <= m_x - |nu|}
-//                E1_x[kappa_1][nu_1] E1_y[kappa_2][nu_2] E1_z[kappa_3][nu_3] mu[a][kappa]
-// Temporal sources: I_{k-2} (k even) or I_{k-3}, I_{k-2} (k odd), none for k < 2 (Eq. 03:ILtemp);
-// spatial sources: the interaction area of bt (Eq. 03:Iarea).
+// M2L at level l (Eq. m2l with Eq. exp_coeffs_3d), applied one direction at a time.
+//
+// For a target interval k, a source interval J in I(k) (Eq. 03:ILtemp: I_{k-2} for even k,
+// I_{k-3}, I_{k-2} for odd k) and time nodes (a, b), the coefficients factor as
+// pref_ab * E^x[o_1]_{kap_1 nu_1} E^y[o_2]_{kap_2 nu_2} E^z[o_3]_{kap_3 nu_3}, where o = X - Y is
+// the grid offset of target and source box.  The interaction area (Eq. 03:Iarea) is the cube
+// |o_j| <= n_tr, so the sum over source boxes is a separable convolution over the box grid
+// (empty cells carry zero moments).  The truncation |kappa + nu| <= m_x is kept exactly with
+// a cumulative degree budget B:
+//   T1[nu1,k2,k3][B](X1,Y2,Y3) = sum_{Y1} sum_{k1 <= B - nu1 - k2 - k3} E^x[X1-Y1]_{k1 nu1} mu[k1,k2,k3](Y)
+//   T2[nu1,nu2,k3][B](X1,X2,Y3) = sum_{Y2} sum_{k2 <= B - nu1 - nu2 - k3} E^y[X2-Y2]_{k2 nu2}
+//                                 T1[nu1,k2,k3][B - nu2](X1,Y2,Y3)
+//   lam[b][nu](X) = sum_{J,a} pref_ab sum_{Y3} sum_{k3 <= m - |nu|} E^z[X3-Y3]_{k3 nu3}
+//                   T2[nu1,nu2,k3][m - nu3](X1,X2,Y3)
+// Triples (t0,t1,t2) with t0+t1+t2 <= m use the graded enumeration of the multi-indices;
+// eoff[t] is the offset of the budget range B = |t| .. m of triple t (C(m+4,4) entries).
+struct M2LArgs {
+    int G, ntr, na, nk, mx, ne, nint, nbox;
+    const int *cellbox;                   // [G^3] -> box or -1
+    const int *boxcell;                   // [nbox] -> cell
+    const int *pk, *pJ;                   // problem pairs (target k, source J) of this chunk
+    int npair;
+    const int *kidx, *kinv, *eoff;
+};
+
 template <typename R>
-__global__ void __launch_bounds__(512) k_m2l(const R *__restrict__ mu, R *__restrict__ lam,
-                                               const int *__restrict__ m2l_ptr, const int *__restrict__ m2l_src,
-                                               const int *__restrict__ m2l_off, const R *__restrict__ E1,
-                                               const R *__restrict__ pref, const int *__restrict__ kidx, int na, int nk,
-                                               int mx, int G, int nint, int nbox)
+__global__ void k_m2l_s1(M2LArgs A, const R *__restrict__ mu, const R *__restrict__ E1, R *__restrict__ T1, int nrhs)
 {
-    extern __shared__ unsigned char smem_raw[];
-    R *mus = reinterpret_cast<R *>(smem_raw);  // [na][nk]
-    const int m1 = mx + 1, no = 2 * G - 1;
-    R *Es = mus + na * nk;                      // [3][na][na][m1][m1]
-    int *ks = reinterpret_cast<int *>(Es + 3 * na * na * m1 * m1);  // [nk] packed kappa
-    const int k = blockIdx.x / nbox, bt = blockIdx.x % nbox, rhs = blockIdx.z;
-    for (int i = threadIdx.x; i < nk; i += blockDim.x) ks[i] = kidx[3 * i] | (kidx[3 * i + 1] << 8) | (kidx[3 * i + 2] << 16);
-    const int nout = na * nk;
-    R acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = R(0);
-    int js[2], nj = 0;
-    if (k >= 2) {
-        if (k % 2 == 0) { js[0] = k - 2; nj = 1; }
-        else { js[0] = k - 3; js[1] = k - 2; nj = 2; }
-    }
-    const size_t lvl_rhs = (size_t)rhs * nint;
-    for (int jj = 0; jj < nj; ++jj) {
-        const int J = js[jj], D = k - J;
-        for (int e = m2l_ptr[bt]; e < m2l_ptr[bt + 1]; ++e) {
-            const int bs = m2l_src[e], off = m2l_off[e];
-            const int o3[3] = {off & 255, (off >> 8) & 255, (off >> 16) & 255};
-            __syncthreads();
-            const R *ms = mu + ((lvl_rhs + J) * nbox + bs) * na * nk;
-            for (int i = threadIdx.x; i < na * nk; i += blockDim.x) mus[i] = ms[i];
-            const int esz = m1 * m1;
-            for (int i = threadIdx.x; i < 3 * na * na * esz; i += blockDim.x) {
-                int c = i / (na * na * esz), r_ = i % (na * na * esz);
-                int ab = r_ / esz, kl = r_ % esz;
-                Es[i] = E1[((size_t)((D - 2) * na * na + ab) * no + o3[c]) * esz + kl];
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                int o = threadIdx.x + q * blockDim.x;
-                if (o >= nout) break;
-                int b = o / nk, iv = o % nk;
-                int nu = ks[iv];
-                int n0 = nu & 255, n1 = (nu >> 8) & 255, n2 = nu >> 16;
-                int smax = mx - n0 - n1 - n2;
-                int nq = (smax + 1) * (smax + 2) * (smax + 3) / 6;  // |kappa| <= smax: graded prefix
-                R tot = R(0);
-                for (int a = 0; a < na; ++a) {
-                    const R *Ea = Es + (0 * na * na + a * na + b) * esz;
-                    const R *Eb = Es + (1 * na * na + a * na + b) * esz;
-                    const R *Ec = Es + (2 * na * na + a * na + b) * esz;
-                    const R *ma = mus + a * nk;
-                    R s = R(0);
-                    for (int i = 0; i < nq; ++i) {
-                        int kk = ks[i];
-                        s += Ea[(kk & 255) * m1 + n0] * Eb[((kk >> 8) & 255) * m1 + n1] * Ec[(kk >> 16) * m1 + n2] * ma[i];
-                    }
-                    tot += pref[((D - 2) * na + a) * na + b] * s;
-                }
-                acc[q] += tot;
-            }
+    const int G = A.G, G3 = G * G * G, m1 = A.mx + 1, no = 2 * G - 1, na = A.na;
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nrhs * A.npair * na * na * G3 * A.nk;
+    if (gid >= total) return;
+    int t = gid % A.nk;
+    size_t r_ = gid / A.nk;
+    int cell = r_ % G3;
+    r_ /= G3;
+    int b = r_ % na;
+    r_ /= na;
+    int a = r_ % na;
+    r_ /= na;
+    int pr = r_ % A.npair;
+    int rhs = (int)(r_ / A.npair);
+    const int k = A.pk[pr], J = A.pJ[pr], D = k - J;
+    const int X1 = cell / (G * G), Y2 = (cell / G) % G, Y3 = cell % G;
+    const int nu1 = A.kidx[3 * t], k2 = A.kidx[3 * t + 1], k3 = A.kidx[3 * t + 2];
+    const int s0 = nu1 + k2 + k3;
+    const R *E = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * m1 * m1;
+    const R *mJ = mu + ((size_t)rhs * A.nint + J) * A.nbox * na * A.nk;
+    const int y_lo = max(0, X1 - A.ntr), y_hi = min(G - 1, X1 + A.ntr);
+    R *out = T1 + ((((size_t)rhs * A.npair + pr) * na + a) * na + b) * (size_t)G3 * A.ne + (size_t)cell * A.ne + A.eoff[t];
+    R acc = R(0);
+    for (int B = s0; B <= A.mx; ++B) {
+        const int k1 = B - s0;
+        const int im = A.kinv[(k1 * m1 + k2) * m1 + k3];
+        for (int Y1 = y_lo; Y1 <= y_hi; ++Y1) {
+            int box = A.cellbox[(Y1 * G + Y2) * G + Y3];
+            if (box < 0) continue;
+            acc += E[((X1 - Y1 + G - 1) * m1 + k1) * m1 + nu1] * mJ[((size_t)box * na + a) * A.nk + im];
         }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        int o = threadIdx.x + q * blockDim.x;
-        if (o < nout) lam[((lvl_rhs + k) * nbox + bt) * na * nk + o] = acc[q];
+        out[B - s0] = acc;
     }
 }
 
-void launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
-                int64_t mu_stride, cudaStream_t st)
+template <typename R>
+__global__ void k_m2l_s2(M2LArgs A, const R *__restrict__ E1, const R *__restrict__ T1, R *__restrict__ T2, int nrhs)
+{
+    const int G = A.G, G3 = G * G * G, m1 = A.mx + 1, no = 2 * G - 1, na = A.na;
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nrhs * A.npair * na * na * G3 * A.nk;
+    if (gid >= total) return;
+    int t = gid % A.nk;
+    size_t r_ = gid / A.nk;
+    int cell = r_ % G3;
+    size_t P = r_ / G3;  // ((rhs * npair + pr) * na + a) * na + b
+    int b = P % na, a = (P / na) % na, pr = (P / (na * na)) % A.npair;
+    const int D = A.pk[pr] - A.pJ[pr];
+    const int X1 = cell / (G * G), X2 = (cell / G) % G, Y3 = cell % G;
+    const int nu1 = A.kidx[3 * t], nu2 = A.kidx[3 * t + 1], k3 = A.kidx[3 * t + 2];
+    const int s0 = nu1 + nu2 + k3;
+    const R *E = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * m1 * m1;
+    const R *Tin = T1 + P * (size_t)G3 * A.ne;
+    R *out = T2 + P * (size_t)G3 * A.ne + (size_t)cell * A.ne + A.eoff[t];
+    const int y_lo = max(0, X2 - A.ntr), y_hi = min(G - 1, X2 + A.ntr);
+    for (int Bp = s0; Bp <= A.mx; ++Bp) {
+        R acc = R(0);
+        for (int Y2 = y_lo; Y2 <= y_hi; ++Y2) {
+            const R *Ey = E + (size_t)(X2 - Y2 + G - 1) * m1 * m1;
+            const R *Tc = Tin + (size_t)((X1 * G + Y2) * G + Y3) * A.ne;
+            for (int k2 = 0; k2 <= Bp - s0; ++k2) {
+                int t1 = A.kinv[(nu1 * m1 + k2) * m1 + k3];
+                acc += Ey[k2 * m1 + nu2] * Tc[A.eoff[t1] + (Bp - nu2 - nu1 - k2 - k3)];
+            }
+        }
+        out[Bp - s0] = acc;
+    }
+}
+
+template <typename R>
+__global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restrict__ pref, const R *__restrict__ T2,
+                         R *__restrict__ lam, const int *__restrict__ kptr, int p0, int k_lo, int k_hi, int nrhs)
+{
+    const int G = A.G, G3 = G * G * G, m1 = A.mx + 1, no = 2 * G - 1, na = A.na;
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nk_ = k_hi - k_lo;
+    size_t total = (size_t)nrhs * nk_ * A.nbox * na * A.nk;
+    if (gid >= total) return;
+    int iv = gid % A.nk;
+    size_t r_ = gid / A.nk;
+    int b = r_ % na;
+    r_ /= na;
+    int box = r_ % A.nbox;
+    r_ /= A.nbox;
+    int k = k_lo + (int)(r_ % nk_);
+    int rhs = (int)(r_ / nk_);
+    const int cell = A.boxcell[box];
+    const int X1 = cell / (G * G), X2 = (cell / G) % G, X3 = cell % G;
+    const int nu1 = A.kidx[3 * iv], nu2 = A.kidx[3 * iv + 1], nu3 = A.kidx[3 * iv + 2];
+    const int smax = A.mx - nu1 - nu2 - nu3;
+    const int y_lo = max(0, X3 - A.ntr), y_hi = min(G - 1, X3 + A.ntr);
+    R val = R(0);
+    for (int pr = kptr[k] - p0; pr < kptr[k + 1] - p0; ++pr) {
+        const int D = k - A.pJ[pr];
+        for (int a = 0; a < na; ++a) {
+            const size_t P = (((size_t)rhs * A.npair + pr) * na + a) * na + b;
+            const R *E = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * m1 * m1;
+            const R *Tin = T2 + P * (size_t)G3 * A.ne;
+            R s = R(0);
+            for (int Y3 = y_lo; Y3 <= y_hi; ++Y3) {
+                const R *Ez = E + (size_t)(X3 - Y3 + G - 1) * m1 * m1;
+                const R *Tc = Tin + (size_t)((X1 * G + X2) * G + Y3) * A.ne;
+                for (int k3 = 0; k3 <= smax; ++k3) {
+                    int t2 = A.kinv[(nu1 * m1 + nu2) * m1 + k3];
+                    s += Ez[k3 * m1 + nu3] * Tc[A.eoff[t2] + (A.mx - nu3 - nu1 - nu2 - k3)];
+                }
+            }
+            val += pref[((D - 2) * na + a) * na + b] * s;
+        }
+    }
+    lam[((((size_t)rhs * A.nint + k) * A.nbox + box) * na + b) * A.nk + iv] = val;
+}
+
+// Runs the three passes over chunks of target intervals so that the intermediates fit the
+// workspace (ws_elems elements of R for each of T1 and T2).
+int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
+               void *T1, void *T2, size_t ws_elems, cudaStream_t st)
 {
     (void)l;
-    (void)mu_stride;
-    const int m1 = g.mx + 1;
-    size_t es = mixed ? 4 : 8;
-    size_t smem = ((size_t)g.na * g.nk + 3 * (size_t)g.na * g.na * m1 * m1) * es + (size_t)g.nk * 4;
-    dim3 grd(L.nint * L.nbox, 1, nrhs);
-    int nout = g.na * g.nk, thr = 128;
-    while (thr * 8 < nout) thr *= 2;
+    const size_t es = mixed ? 4 : 8;
+    const int G3 = L.G * L.G * L.G, na = g.na;
+    const size_t per_pair = (size_t)nrhs * na * na * G3 * g.ne;
     const char *mb = (const char *)mu + L.mom_off * es * nrhs;
     char *lb = (char *)lam + L.mom_off * es * nrhs;
-    if (mixed) {
-        cudaFuncSetAttribute(k_m2l<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_m2l<float><<<grd, thr, smem, st>>>((const float *)mb, (float *)lb, L.m2l_ptr, L.m2l_src, L.m2l_off,
-                                             (const float *)L.E1, (const float *)L.pref, g.kidx, g.na, g.nk, g.mx, L.G,
-                                             L.nint, L.nbox);
-    } else {
-        cudaFuncSetAttribute(k_m2l<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_m2l<double><<<grd, thr, smem, st>>>((const double *)mb, (double *)lb, L.m2l_ptr, L.m2l_src, L.m2l_off,
-                                              (const double *)L.E1, (const double *)L.pref, g.kidx, g.na, g.nk, g.mx, L.G,
-                                              L.nint, L.nbox);
+    // intervals 0 and 1 have no interaction list: their locals start at zero
+    for (int r = 0; r < nrhs; ++r)
+        cudaMemsetAsync(lb + es * (size_t)r * L.nint * L.nbox * na * g.nk, 0,
+                        es * (size_t)L.nbox * na * g.nk * std::min(2, L.nint), st);
+    int k = 2;
+    while (k < L.nint) {
+        // largest chunk [k, k1) whose problem pairs fit the workspace
+        int k1 = k, p0 = L.kptr_host[k];
+        while (k1 < L.nint && (size_t)(L.kptr_host[k1 + 1] - p0) * per_pair <= ws_elems) k1++;
+        if (k1 == k) return -1;  // a single interval does not fit: workspace too small
+        int npair = L.kptr_host[k1] - p0;
+        M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk + p0, L.pJ + p0,
+                  npair, g.kidx, g.kinv, g.eoff};
+        size_t n12 = (size_t)nrhs * npair * na * na * G3 * g.nk;
+        unsigned b12 = (unsigned)((n12 + 127) / 128);
+        size_t n3 = (size_t)nrhs * (k1 - k) * L.nbox * na * g.nk;
+        unsigned b3 = (unsigned)((n3 + 127) / 128);
+        if (mixed) {
+            k_m2l_s1<float><<<b12, 128, 0, st>>>(A, (const float *)mb, (const float *)L.E1, (float *)T1, nrhs);
+            k_m2l_s2<float><<<b12, 128, 0, st>>>(A, (const float *)L.E1, (const float *)T1, (float *)T2, nrhs);
+            k_m2l_s3<float><<<b3, 128, 0, st>>>(A, (const float *)L.E1, (const float *)L.pref, (const float *)T2,
+                                                (float *)lb, L.kptr, p0, k, k1, nrhs);
+        } else {
+            k_m2l_s1<double><<<b12, 128, 0, st>>>(A, (const double *)mb, (const double *)L.E1, (double *)T1, nrhs);
+            k_m2l_s2<double><<<b12, 128, 0, st>>>(A, (const double *)L.E1, (const double *)T1, (double *)T2, nrhs);
+            k_m2l_s3<double><<<b3, 128, 0, st>>>(A, (const double *)L.E1, (const double *)L.pref, (const double *)T2,
+                                                 (double *)lb, L.kptr, p0, k, k1, nrhs);
+        }
+        k = k1;
     }
+    return 0;
 }
 
 // ------------------------------------------------------------------------------------------

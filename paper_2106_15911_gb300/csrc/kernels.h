@@ -58,6 +58,8 @@ struct ApplyGeo {
     int nbox_leaf;
     const int *kidx;       // [nk][3] graded
     const int *kinv;       // [(m+1)^3] -> graded index
+    int ne;                // C(m_x+4, 4): budget-indexed entries of the separable M2L intermediates
+    const int *eoff;       // [nk] offset of the budget range of each triple
 };
 
 // R: arithmetic/storage type of the FMM passes (double or float)
@@ -71,8 +73,8 @@ void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab
                 void *mu_leaf, int nrhs, const ApplyGeo &g, cudaStream_t st);
 void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
-void launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
-                int64_t mu_stride, cudaStream_t st);
+int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
+               void *T1, void *T2, size_t ws_elems, cudaStream_t st);
 void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
 void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,

@@ -91,6 +91,12 @@ struct DevLevel {
     void *pref;      // [2][na][na]                (R)
     void *qx;        // [2 bits][m1][m1] q^(x) from this level's boxes into their parents (R)
     int64_t mom_off; // element offset of this level's moments in the moment buffer (per rhs)
+    int ntr;         // interaction-area radius (Eq. 03:Iarea)
+    int *cellbox;    // [G^3] -> box or -1
+    int *boxcell;    // [nbox] -> cell
+    int *pk, *pJ;    // M2L interval pairs (target k, source J in I(k)) for k = 2 .. nint-1
+    int *kptr;       // [nint+1] pairs of target k: [kptr[k], kptr[k+1])
+    std::vector<int> kptr_host;
 };
 
 }  // namespace pfmm
