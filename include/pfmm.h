@@ -142,6 +142,24 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info);
  * The FP32 / FP64 pipe rooflines of the nearfield and M2L kernels are quoted against it. */
 int pfmm_probe_fma_rate(int32_t fp64, double *tflops, void *stream);
 
+/* Allocation-free f = V_h w.  The paper has no counterpart: this is a service entry point.
+ * pfmm_apply_V sizes its per-call workspaces with cudaMalloc on first use (and again when a
+ * larger nrhs arrives); callers that must not allocate device memory while they run -- services
+ * for which an allocation mid-run may stall the device or fail with no way to recover, and hosts
+ * whose device memory is owned by their own allocator or budget -- use this variant instead.
+ * It computes the same product with the same kernels, but takes every workspace from one
+ * static device array of 64 MiB (held by each GPU that loads the library until the process
+ * exits) and calls no cudaMalloc, cudaFree or allocating library routine.
+ *   w, f: device [nrhs][E_t][E_x] FP64 as for pfmm_apply_V (f overwritten).  Returns
+ *   PFMM_ERR_OOM with a message naming the bytes needed when the workspaces of this handle and
+ *   nrhs do not fit in 64 MiB (the separable-M2L intermediates are processed in chunks that fit).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.  All calls share the
+ * one array: calls whose work overlaps on the GPU (other streams, other threads, other handles)
+ * race on it and must be serialised by the caller.  The array keeps the last call's contents;
+ * each call writes every workspace before reading it. */
+int pfmm_apply_V_noalloc(pfmm_handle *h, const double *w, double *f, int32_t nrhs, void *stream);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void pfmm_destroy(pfmm_handle *h);
 

@@ -10,10 +10,15 @@
 #include <string>
 #include <vector>
 
+#include "handle.h"
 #include "kernels.h"
 #include "pfmm_internal.h"
 
 using namespace pfmm;
+
+namespace pfmm {
+int set_error(int code, const std::string &msg);
+}
 
 namespace {
 
@@ -34,6 +39,12 @@ int fail(int code, const std::string &msg)
     } while (0)
 
 constexpr double kPi = 3.14159265358979323846;
+
+}  // namespace
+
+int pfmm::set_error(int code, const std::string &msg) { return fail(code, msg); }
+
+namespace {
 
 // Gauss-Legendre nodes and weights on [0, 1] (Newton iteration on P_n)
 void gauss01(int n, std::vector<double> &x, std::vector<double> &w)
@@ -106,84 +117,7 @@ double lagrange(int b, int m, double lo, double hi, double t)
     return v;
 }
 
-struct EvSet {
-    cudaEvent_t ev[9];
-};
-
 }  // namespace
-
-struct pfmm_handle {
-    int nv = 0, nt = 0, Et = 0;
-    double T = 0, alpha = 0, h = 0;
-    pfmm_params prm{};
-    Tree tree;
-    bool mixed = false;
-    int ls = 2, nd = 4, na = 0, nk = 0, mx = 0, p = 0;
-    size_t es = 8;  // bytes of R
-    std::vector<void *> allocs;
-    int64_t dev_bytes = 0;
-
-    double *d_verts = nullptr, *d_area = nullptr;
-    int *d_tri_int = nullptr, *d_tri_user = nullptr, *d_perm = nullptr, *d_tri_leaf = nullptr, *d_leaf_start = nullptr,
-        *d_leaf_grid = nullptr, *d_kidx = nullptr, *d_kinv = nullptr;
-    void *d_Sx = nullptr, *d_SK = nullptr, *d_St = nullptr, *d_qt = nullptr;
-    std::vector<DevLevel> dl;
-    void *d_AV = nullptr, *d_AK = nullptr;
-    int *d_colV = nullptr, *d_colK = nullptr, *d_kmap = nullptr, *d_tiles = nullptr;
-    PanelGPU *d_panels = nullptr;
-    int ntiles = 0;
-    int64_t mom_per_rhs = 0;
-
-    int ne = 0;              // C(m_x+4,4) entries of the separable M2L intermediates per cell
-    int *d_eoff = nullptr;   // [nk] offsets of the budget ranges
-    int64_t m2l_ws_need = 0; // elements of T1 (and of T2) for a whole level, per rhs
-
-    int ws_nrhs = 0;
-    size_t ws_m2l = 0;
-    void *d_T1 = nullptr, *d_T2 = nullptr;
-    void *d_xint = nullptr, *d_gf = nullptr, *d_mu = nullptr, *d_lam = nullptr;
-    double *d_fint = nullptr;
-
-    bool prof = false;
-    std::vector<EvSet> evs;
-    int ev_head = 0, ev_pending = 0;
-    double acc_ms[8] = {0};
-    int n_prof = 0;
-
-    ~pfmm_handle()
-    {
-        for (void *p : allocs) cudaFree(p);
-        for (auto &e : evs)
-            for (int i = 0; i < 9; ++i) cudaEventDestroy(e.ev[i]);
-    }
-
-    template <typename T_>
-    int alloc(T_ **p, size_t n_elems, size_t elem = sizeof(T_))
-    {
-        void *q = nullptr;
-        size_t bytes = std::max<size_t>(n_elems * elem, 16);
-        cudaError_t e = cudaMalloc(&q, bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(e == cudaErrorMemoryAllocation ? PFMM_ERR_OOM : PFMM_ERR_CUDA,
-                        "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
-        }
-        allocs.push_back(q);
-        dev_bytes += (int64_t)bytes;
-        *p = (T_ *)q;
-        return PFMM_OK;
-    }
-
-    void release(void *p)
-    {
-        if (!p) return;
-        auto it = std::find(allocs.begin(), allocs.end(), p);
-        if (it != allocs.end()) {
-            cudaFree(p);
-            allocs.erase(it);
-        }
-    }
-};
 
 namespace {
 

@@ -56,6 +56,7 @@ SIGNATURES = {
     "pfmm_apply_K": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
     "pfmm_apply_M": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
     "pfmm_apply_parts": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, _I, _VP]),
+    "pfmm_apply_V_noalloc": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
     "pfmm_set_profiling": (ctypes.c_int, [_VP, _I]),
     "pfmm_phase_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
@@ -161,6 +162,11 @@ def pfmm_apply_K(h, g, f, nrhs: int, stream=None):
 
 def pfmm_apply_M(h, g, f, nrhs: int, stream=None):
     _check(lib().pfmm_apply_M(h, _ptr(g), _ptr(f), int(nrhs), _stream(stream)))
+
+
+def pfmm_apply_V_noalloc(h, w, f, nrhs: int, stream=None):
+    """f = V_h w with all workspaces in the library's static 64 MiB device array (no allocation)."""
+    _check(lib().pfmm_apply_V_noalloc(h, _ptr(w), _ptr(f), int(nrhs), _stream(stream)))
 
 
 def pfmm_apply_parts(h, op: int, x, f, nrhs: int, parts: int, stream=None):
