@@ -54,6 +54,10 @@ extern "C" {
 /* nearfield modes */
 #define PFMM_NEARFIELD_STORED 0  /* nearfield blocks assembled once at build time */
 
+/* nearfield engines */
+#define PFMM_NF_AUTO 0
+#define PFMM_NF_CUDA_CORES 1
+
 /* apply parts (bit mask) */
 #define PFMM_PART_NEAR 1  /* inadmissible (nearfield) blocks, Alg. 2 last loop */
 #define PFMM_PART_FAR 2   /* S2M, M2M, M2L, L2L, L2T, Alg. 2 first four phases */
@@ -84,6 +88,8 @@ typedef struct pfmm_params {
     int32_t nearfield;  /* PFMM_NEARFIELD_STORED */
     int32_t quad_regular;  /* Gauss points per direction of the collapsed triangle rule */
     int32_t quad_singular; /* Gauss points per direction of the Sauter-Schwab rule */
+    int32_t nf_engine;  /* PFMM_NF_AUTO: tensor cores (3xTF32 split, mixed mode) where the panel
+                           layout allows, else CUDA cores; PFMM_NF_CUDA_CORES: always CUDA cores */
 } pfmm_params;
 
 typedef struct pfmm_handle pfmm_handle;
@@ -97,11 +103,12 @@ typedef struct pfmm_info {
     int32_t n_m2l_pairs;    /* space-time box pairs in all interaction lists */
     int64_t nearfield_bytes;/* device bytes of the stored nearfield blocks (V and K) */
     int64_t device_bytes;   /* all device bytes held by the handle */
+    int32_t nf_tensor_cores;/* bit 0: V nearfield on tensor cores, bit 1: K nearfield */
 } pfmm_info;
 
 /* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,
  * leaf_steps = 2, leaf_tris = 16, FP64, stored nearfield, quad_regular = 3,
- * quad_singular = 6.  Returns PFMM_OK or PFMM_ERR_INVALID_ARG (p NULL). */
+ * quad_singular = 6, nf_engine = PFMM_NF_AUTO.  Returns PFMM_OK or PFMM_ERR_INVALID_ARG (p NULL). */
 int pfmm_default_params(pfmm_params *p);
 
 /* Build the box cluster tree (Section 3.2, Alg. 1), the nearfield and interaction lists
@@ -135,6 +142,11 @@ int pfmm_set_profiling(pfmm_handle *h, int32_t on);
 int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies);
 
 int pfmm_get_info(const pfmm_handle *h, pfmm_info *info);
+
+/* Synchronise the device and report whether a bounded wait inside a kernel of this handle gave
+ * up since the last check (PFMM_ERR_TIMEOUT; the result of that apply is invalid), or a CUDA
+ * error is pending (PFMM_ERR_CUDA).  Clears the flag.  PFMM_OK otherwise. */
+int pfmm_check(pfmm_handle *h);
 
 /* Measurement utility (not part of the paper's method): the sustained FMA throughput of the
  * current device in TFLOP/s (2 flops per FMA), FP64 (fp64 != 0) or FP32, timed with CUDA

@@ -12,6 +12,7 @@
 
 #include "handle.h"
 #include "kernels.h"
+#include "nf_tc.h"
 #include "pfmm_internal.h"
 
 using namespace pfmm;
@@ -121,6 +122,44 @@ double lagrange(int b, int m, double lo, double hi, double t)
 
 namespace {
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// FP32 tensor map, 128-byte swizzle, zero fill out of bounds; dims innermost first
+int encode_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
+               const uint32_t *box)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(PFMM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    cuuint64_t d[5], s[4];
+    cuuint32_t b[5], e[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        e[i] = 1;
+        if (i > 0) s[i - 1] = strides_bytes[i - 1];
+    }
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), d, s, b, e,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return PFMM_OK;
+}
+
 template <typename T_>
 int upload(pfmm_handle *H, T_ **dst, const std::vector<T_> &src, cudaStream_t st)
 {
@@ -182,6 +221,13 @@ int ensure_workspace(pfmm_handle *H, int nrhs)
     H->ws_m2l = std::max(std::min(need, cap), min_chunk);
     if ((rc = H->alloc((char **)&H->d_T1, H->ws_m2l * H->es, 1))) return rc;
     if ((rc = H->alloc((char **)&H->d_T2, H->ws_m2l * H->es, 1))) return rc;
+    H->release(H->d_Whi);
+    H->release(H->d_Wlo);
+    H->d_Whi = H->d_Wlo = nullptr;
+    if (H->tcV || H->tcK) {
+        H->w_elems = (size_t)nrhs * H->Et * std::max(H->colsV_u, H->colsK_u);
+        if ((rc = H->alloc(&H->d_Whi, H->w_elems)) || (rc = H->alloc(&H->d_Wlo, H->w_elems))) return rc;
+    }
     H->ws_nrhs = nrhs;
     return PFMM_OK;
 }
@@ -204,6 +250,45 @@ void prof_collect(pfmm_handle *H, int upto_pending)
 
 }  // namespace
 
+// Tensor-core nearfield of op (0: V, 1: K) into fint (zeroed here): splits the FP64 input into
+// TF32 hi/lo parts in whi/wlo ([nrhs][E_t][cols] each), encodes their TMA views and launches.
+int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint,
+                    cudaStream_t st)
+{
+    int rc;
+    const int cols = op == 0 ? H->colsV_u : H->colsK_u;
+    launch_split_input(x, op == 0 ? H->d_perm : nullptr, op == 0 ? H->nt : H->nv, cols, nrhs, H->Et, whi, wlo, st);
+    const int nint = H->Et / 2;
+    uint64_t dims[4] = {(uint64_t)cols, 2, (uint64_t)nint, (uint64_t)nrhs};
+    uint64_t str[3] = {(uint64_t)cols * 4, (uint64_t)cols * 8, (uint64_t)cols * 8 * nint};
+    uint32_t box[4] = {32, 1, 128, 1};
+    CUtensorMap mWhi, mWlo;
+    if ((rc = encode_map(&mWhi, whi, 4, dims, str, box)) || (rc = encode_map(&mWlo, wlo, 4, dims, str, box))) return rc;
+    CK(cudaMemsetAsync(fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
+    NfTcParams P{};
+    P.panels = H->d_panels;
+    P.tiles = H->d_tiles128;
+    P.ntiles = H->ntiles128;
+    P.nib = (nint + 127) / 128;
+    P.nkb = cols / 32;
+    const int tiles = nrhs * P.ntiles * P.nib;
+    int ks = (3 * H->nsm + tiles - 1) / tiles;
+    ks = std::max(1, std::min(ks, 4 * P.nkb / 8));
+    P.ksplit = ks;
+    P.nitems = tiles * ks;
+    P.cols_pad = cols;
+    P.kop = op;
+    P.nint = nint;
+    P.Et = H->Et;
+    P.nt = H->nt;
+    P.f = fint;
+    P.err = H->d_err;
+    if (launch_nf_apply_tc(op == 0 ? H->mapAVhi : H->mapAKhi, op == 0 ? H->mapAVlo : H->mapAKlo, mWhi, mWlo, P, H->nsm,
+                           st))
+        return fail(PFMM_ERR_CUDA, std::string("tensor-core nearfield launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return PFMM_OK;
+}
+
 extern "C" {
 
 const char *pfmm_last_error(void) { return g_err.c_str(); }
@@ -222,6 +307,7 @@ int pfmm_default_params(pfmm_params *p)
     p->nearfield = PFMM_NEARFIELD_STORED;
     p->quad_regular = 3;
     p->quad_singular = 6;
+    p->nf_engine = PFMM_NF_AUTO;
     return PFMM_OK;
 }
 
@@ -469,6 +555,62 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         }
         launch_nf_singular(a, d_sing, (int)t.sing.size(), H->d_panels, H->d_AV, H->d_AK, H->mixed, st);
         CK(cudaGetLastError());
+
+        // tensor-core nearfield: mixed mode, two steps per leaf, every panel spans all columns
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&H->nsm, cudaDevAttrMultiProcessorCount, dev));
+        int cc_major = 0, cc_minor = 0;
+        CK(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev));
+        CK(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
+        bool eligible = H->mixed && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 && encode_fn();
+        bool fullV = eligible, fullK = eligible;
+        for (const Panel &P : t.panels) {
+            fullV = fullV && P.ncolV == nt && P.colsV_pad == t.panels[0].colsV_pad;
+            fullK = fullK && P.ncolK == nv && P.colsK_pad == t.panels[0].colsK_pad;
+        }
+        if (fullV)
+            for (int k = 0; k < nt; ++k) fullV = fullV && t.colV[t.panels[0].colV_at + k] == k;
+        if (fullK)
+            for (int k = 0; k < nv; ++k) fullK = fullK && t.colK[t.panels[0].colK_at + k] == k;
+        CK(cudaMalloc((void **)&H->d_err, sizeof(int)));
+        H->allocs.push_back(H->d_err);
+        CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), st));
+        if (fullV || fullK) {
+            std::vector<int> t128;
+            for (size_t i = 0; i < t.panels.size(); ++i)
+                for (int r0 = 0; r0 < t.panels[i].nrows; r0 += 128) {
+                    t128.push_back((int)i);
+                    t128.push_back(r0);
+                }
+            H->ntiles128 = (int)t128.size() / 2;
+            if ((rc = upload(H, &H->d_tiles128, t128, st))) return rc;
+        }
+        if (fullV) {
+            H->colsV_u = t.panels[0].colsV_pad;
+            size_t n = (size_t)t.sizeV;
+            if ((rc = H->alloc(&H->d_AVhi, n)) || (rc = H->alloc(&H->d_AVlo, n))) return rc;
+            launch_split_panel((const float *)H->d_AV, H->d_AVhi, H->d_AVlo, n, st);
+            uint64_t dims[2] = {(uint64_t)H->colsV_u, (uint64_t)(n / H->colsV_u)}, str[1] = {(uint64_t)H->colsV_u * 4};
+            uint32_t box[2] = {32, 128};
+            if ((rc = encode_map(&H->mapAVhi, H->d_AVhi, 2, dims, str, box)) ||
+                (rc = encode_map(&H->mapAVlo, H->d_AVlo, 2, dims, str, box)))
+                return rc;
+            H->tcV = true;
+        }
+        if (fullK) {
+            H->colsK_u = t.panels[0].colsK_pad;
+            size_t n = (size_t)t.sizeK;
+            if ((rc = H->alloc(&H->d_AKhi, n)) || (rc = H->alloc(&H->d_AKlo, n))) return rc;
+            launch_split_panel((const float *)H->d_AK, H->d_AKhi, H->d_AKlo, n, st);
+            uint64_t dims[2] = {(uint64_t)H->colsK_u, (uint64_t)(n / H->colsK_u)}, str[1] = {(uint64_t)H->colsK_u * 4};
+            uint32_t box[2] = {32, 128};
+            if ((rc = encode_map(&H->mapAKhi, H->d_AKhi, 2, dims, str, box)) ||
+                (rc = encode_map(&H->mapAKlo, H->d_AKlo, 2, dims, str, box)))
+                return rc;
+            H->tcK = true;
+        }
+        CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(st));
     return PFMM_OK;
@@ -552,7 +694,10 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
         ncolg = H->nv;
     }
     mark(1);
-    if (parts & PFMM_PART_NEAR)
+    const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK);
+    if (tc) {
+        if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_fint, st))) return rc;
+    } else if (parts & PFMM_PART_NEAR)
         launch_nf_apply(H->mixed, op == 1, op == 0 ? H->d_AV : H->d_AK, op == 0 ? H->d_colV : H->d_colK, H->d_tiles,
                         H->ntiles, H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st);
     else
@@ -642,6 +787,21 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     info->n_m2l_pairs = t.n_m2l_pairs;
     info->nearfield_bytes = (t.sizeV + t.sizeK) * (int64_t)h->es;
     info->device_bytes = h->dev_bytes;
+    info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
+    return PFMM_OK;
+}
+
+int pfmm_check(pfmm_handle *h)
+{
+    if (!h) return fail(PFMM_ERR_INVALID_ARG, "handle is NULL");
+    CK(cudaDeviceSynchronize());
+    int e = 0;
+    if (h->d_err) {
+        CK(cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    }
+    if (e) return fail(PFMM_ERR_TIMEOUT, "a bounded wait in the tensor-core nearfield kernel gave up (code " +
+                                             std::to_string(e) + ")");
     return PFMM_OK;
 }
 

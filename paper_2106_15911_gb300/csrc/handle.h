@@ -1,6 +1,7 @@
 // handle.h -- definition of the opaque pfmm_handle (shared by the C ABI translation units).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,6 +15,12 @@
 namespace pfmm {
 // records an error message for pfmm_last_error() and returns the code
 int set_error(int code, const std::string &msg);
+}  // namespace pfmm
+
+struct pfmm_handle;
+namespace pfmm {
+// tensor-core nearfield of op (0: V, 1: K) into fint; whi/wlo: [nrhs][E_t][cols] FP32 workspaces
+int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint, cudaStream_t st);
 }  // namespace pfmm
 
 struct EvSet {
@@ -51,6 +58,17 @@ struct pfmm_handle {
     void *d_T1 = nullptr, *d_T2 = nullptr;
     void *d_xint = nullptr, *d_gf = nullptr, *d_mu = nullptr, *d_lam = nullptr;
     double *d_fint = nullptr;
+
+    // tensor-core nearfield (mixed mode, untruncated panels of equal width, 2 steps per leaf)
+    bool tcV = false, tcK = false;
+    float *d_AVhi = nullptr, *d_AVlo = nullptr, *d_AKhi = nullptr, *d_AKlo = nullptr;
+    CUtensorMap mapAVhi{}, mapAVlo{}, mapAKhi{}, mapAKlo{};
+    int colsV_u = 0, colsK_u = 0;  // common padded column count of the panels
+    int *d_tiles128 = nullptr;
+    int ntiles128 = 0, nsm = 0;
+    int *d_err = nullptr;           // bounded-wait error word of the device kernels
+    float *d_Whi = nullptr, *d_Wlo = nullptr;
+    size_t w_elems = 0;
 
     bool prof = false;
     std::vector<EvSet> evs;

@@ -323,6 +323,104 @@ __global__ void k_m2m(const R *__restrict__ mu_c, R *__restrict__ mu_p, const in
     mu_p[gid] = acc;
 }
 
+// Space-time M2M (Eq. st_m2m) with one CTA per parent (interval kp, box bp, rhs): the temporal
+// contraction of each child's moments is staged in shared memory,
+//   tmp_c[ap][kap] = sum_{c, ac} q^(t)_c[ac][ap] mu[2 kp + c][child][ac][kap],
+// then mu_p[ap][nu] = sum_children sum_{kap <= nu} q^(x)_{kap,nu}(child) tmp_c[ap][kap].
+template <typename R>
+__global__ void __launch_bounds__(256) k_m2m_st(const R *__restrict__ mu_c, R *__restrict__ mu_p,
+                                                  const int *__restrict__ ch_ptr, const int *__restrict__ ch_idx,
+                                                  const int *__restrict__ oct_c, const R *__restrict__ q1,
+                                                  const R *__restrict__ qt, const int *__restrict__ kidx,
+                                                  const int *__restrict__ kinv, int na, int nk, int mx, int nint_p,
+                                                  int nbox_p, int nbox_c)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int m1 = mx + 1;
+    R *tmp = reinterpret_cast<R *>(smem_raw);  // [8][na][nk]
+    R *qs = tmp + 8 * na * nk;                 // [2][m1][m1]
+    int *kin = reinterpret_cast<int *>(qs + 2 * m1 * m1);
+    const int kp = blockIdx.x / nbox_p, bp = blockIdx.x % nbox_p, rhs = blockIdx.y;
+    const int c0 = ch_ptr[bp], nch = ch_ptr[bp + 1] - c0;
+    for (int i = threadIdx.x; i < 2 * m1 * m1; i += blockDim.x) qs[i] = q1[i];
+    for (int i = threadIdx.x; i < m1 * m1 * m1; i += blockDim.x) kin[i] = kinv[i];
+    for (int i = threadIdx.x; i < nch * na * nk; i += blockDim.x) {
+        int e = i / (na * nk), ap = (i / nk) % na, ik = i % nk, bc = ch_idx[c0 + e];
+        R v = R(0);
+        for (int c = 0; c < 2; ++c) {
+            const R *m = mu_c + (((size_t)rhs * 2 * nint_p + 2 * kp + c) * nbox_c + bc) * na * nk + ik;
+            for (int ac = 0; ac < na; ++ac) v += qt[(c * na + ac) * na + ap] * m[(size_t)ac * nk];
+        }
+        tmp[i] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < na * nk; o += blockDim.x) {
+        const int ap = o / nk, iv = o % nk;
+        const int n0 = kidx[3 * iv], n1 = kidx[3 * iv + 1], n2 = kidx[3 * iv + 2];
+        R acc = R(0);
+        for (int e = 0; e < nch; ++e) {
+            const int oc = oct_c[ch_idx[c0 + e]];
+            const R *qa = qs + (oc & 1) * m1 * m1, *qb = qs + ((oc >> 1) & 1) * m1 * m1, *qc = qs + ((oc >> 2) & 1) * m1 * m1;
+            const R *tp = tmp + (e * na + ap) * nk;
+            for (int k0 = 0; k0 <= n0; ++k0)
+                for (int k1 = 0; k1 <= n1; ++k1) {
+                    const R q01 = qa[k0 * m1 + n0] * qb[k1 * m1 + n1];
+                    for (int k2 = 0; k2 <= n2; ++k2) acc += q01 * qc[k2 * m1 + n2] * tp[kin[(k0 * m1 + k1) * m1 + k2]];
+                }
+        }
+        mu_p[(((size_t)rhs * nint_p + kp) * nbox_p + bp) * na * nk + o] = acc;
+    }
+}
+
+// Space-time L2L (transpose of Eq. st_m2m) with one CTA per parent (kp, bp, rhs): for each child,
+//   tmp[bp_][kap] = sum_{nu >= kap, |nu| <= m_x} q^(x)_{kap,nu}(child) lam_p[bp_][nu],
+//   lam_c[2 kp + c][child][bc][kap] += sum_{bp_} q^(t)_c[bc][bp_] tmp[bp_][kap].
+template <typename R>
+__global__ void __launch_bounds__(256) k_l2l_st(const R *__restrict__ lam_p, R *__restrict__ lam_c,
+                                                  const int *__restrict__ ch_ptr, const int *__restrict__ ch_idx,
+                                                  const int *__restrict__ oct_c, const R *__restrict__ q1,
+                                                  const R *__restrict__ qt, const int *__restrict__ kidx,
+                                                  const int *__restrict__ kinv, int na, int nk, int mx, int nint_p,
+                                                  int nbox_p, int nbox_c)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int m1 = mx + 1;
+    R *lp = reinterpret_cast<R *>(smem_raw);  // [na][nk]
+    R *tmp = lp + na * nk;                    // [na][nk]
+    R *qs = tmp + na * nk;                    // [2][m1][m1]
+    int *kin = reinterpret_cast<int *>(qs + 2 * m1 * m1);
+    const int kp = blockIdx.x / nbox_p, bp = blockIdx.x % nbox_p, rhs = blockIdx.y;
+    const int c0 = ch_ptr[bp], nch = ch_ptr[bp + 1] - c0;
+    for (int i = threadIdx.x; i < 2 * m1 * m1; i += blockDim.x) qs[i] = q1[i];
+    for (int i = threadIdx.x; i < m1 * m1 * m1; i += blockDim.x) kin[i] = kinv[i];
+    const R *src = lam_p + (((size_t)rhs * nint_p + kp) * nbox_p + bp) * na * nk;
+    for (int i = threadIdx.x; i < na * nk; i += blockDim.x) lp[i] = src[i];
+    for (int e = 0; e < nch; ++e) {
+        const int bc = ch_idx[c0 + e], oc = oct_c[bc];
+        const R *qa = qs + (oc & 1) * m1 * m1, *qb = qs + ((oc >> 1) & 1) * m1 * m1, *qc = qs + ((oc >> 2) & 1) * m1 * m1;
+        __syncthreads();
+        for (int o = threadIdx.x; o < na * nk; o += blockDim.x) {
+            const int bpI = o / nk, ik = o % nk;
+            const int k0 = kidx[3 * ik], k1 = kidx[3 * ik + 1], k2 = kidx[3 * ik + 2];
+            const R *l = lp + bpI * nk;
+            R s = R(0);
+            for (int n0 = k0; n0 <= mx; ++n0)
+                for (int n1 = k1; n0 + n1 <= mx; ++n1) {
+                    const R q01 = qa[k0 * m1 + n0] * qb[k1 * m1 + n1];
+                    for (int n2 = k2; n0 + n1 + n2 <= mx; ++n2) s += q01 * qc[k2 * m1 + n2] * l[kin[(n0 * m1 + n1) * m1 + n2]];
+                }
+            tmp[o] = s;
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < 2 * na * nk; o += blockDim.x) {
+            const int c = o / (na * nk), bcI = (o / nk) % na, ik = o % nk;
+            R v = R(0);
+            for (int bpI = 0; bpI < na; ++bpI) v += qt[(c * na + bcI) * na + bpI] * tmp[bpI * nk + ik];
+            lam_c[((((size_t)rhs * 2 * nint_p + 2 * kp + c) * nbox_c + bc) * na + bcI) * nk + ik] += v;
+        }
+    }
+}
+
 void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
 {
@@ -332,6 +430,25 @@ void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
     unsigned blocks = (unsigned)((total + 127) / 128);
     size_t es = mixed ? 4 : 8;
     char *base = (char *)mu;
+    const int m1 = g.mx + 1;
+    if (ch.st) {
+        size_t smem = es * ((size_t)8 * g.na * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
+        dim3 grd(par.nint * par.nbox, nrhs);
+        if (mixed) {
+            cudaFuncSetAttribute(k_m2m_st<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_m2m_st<float><<<grd, 256, smem, st>>>((const float *)(base + ch.mom_off * es * nrhs),
+                                                    (float *)(base + par.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
+                                                    ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx, g.kinv,
+                                                    g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
+        } else {
+            cudaFuncSetAttribute(k_m2m_st<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_m2m_st<double><<<grd, 256, smem, st>>>((const double *)(base + ch.mom_off * es * nrhs),
+                                                     (double *)(base + par.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
+                                                     ch.octant, (const double *)ch.qx, (const double *)qt, g.kidx,
+                                                     g.kinv, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
+        }
+        return;
+    }
     if (mixed)
         k_m2m<float><<<blocks, 128, 0, st>>>((const float *)(base + ch.mom_off * es * nrhs), (float *)(base + par.mom_off * es * nrhs),
                                              par.ch_ptr, par.ch_idx, ch.octant, (const float *)ch.qx, (const float *)qt,
@@ -485,6 +602,184 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
     lam[((((size_t)rhs * A.nint + k) * A.nbox + box) * na + b) * A.nk + iv] = val;
 }
 
+// Fused M2L for grids of at most 4^3 cells (FP32): one CTA per (target interval k, time node b,
+// rhs) keeps the source moments of all cells, the intermediates T1, T2 of all cells and the
+// target locals in shared memory.  Every thread owns one multi-index triple and one grid
+// coordinate and keeps a 4 x 4 block of cells in registers, so each step of its list does 64
+// FMAs from 16 moment / intermediate loads and 7 coefficient loads.  Coefficients beyond the
+// interaction radius are zeroed once per (J, a), which applies Eq. 03:Iarea without branches.
+// Same arithmetic as the three-pass kernels (cells with G < 4 are padded with empty cells).
+constexpr int FG = 4;  // padded grid extent per direction
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restrict__ mu, const R *__restrict__ E1,
+                                                     const R *__restrict__ pref, R *__restrict__ lam, int nrhs)
+{
+    extern __shared__ unsigned char smem_raw[];
+    constexpr int C3 = FG * FG * FG, CS = C3 + 1;  // cell rows are padded by one (bank spread)
+    const int G = A.G, nk = A.nk, ne = A.ne, mx = A.mx, m1 = mx + 1, na = A.na, esz = m1 * m1;
+    R *mus = reinterpret_cast<R *>(smem_raw);  // [nk][CS]    moments, kappa-major
+    R *T1s = mus + nk * CS;                    // [ne][CS]    cells (X1, Y2, Y3)
+    R *T2s = T1s + ne * CS;                    // [ne][CS]    cells (X1, X2, Y3)
+    R *lams = T2s + ne * CS;                   // [nk][CS]    cells (X1, X2, X3)
+    R *Es = lams + nk * CS;                    // [7][m1][m1] offsets -3..3, zero outside the radius
+    int *kid = reinterpret_cast<int *>(Es + 7 * esz);
+    int *kin = kid + nk;
+    int *eof = kin + m1 * m1 * m1;
+    int *cbx = eof + nk;                       // [C3] padded cell -> box or -1
+    const int k = blockIdx.x / na, b = blockIdx.x % na, rhs = blockIdx.y;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+        kid[i] = A.kidx[3 * i] | (A.kidx[3 * i + 1] << 8) | (A.kidx[3 * i + 2] << 16);
+        eof[i] = A.eoff[i];
+    }
+    for (int i = threadIdx.x; i < m1 * m1 * m1; i += blockDim.x) kin[i] = A.kinv[i];
+    for (int i = threadIdx.x; i < C3; i += blockDim.x) {
+        int x = i / (FG * FG), y = (i / FG) % FG, z = i % FG;
+        cbx[i] = (x < G && y < G && z < G) ? A.cellbox[(x * G + y) * G + z] : -1;
+    }
+    for (int i = threadIdx.x; i < nk * CS; i += blockDim.x) lams[i] = R(0);
+    int js[2], nj = 0;
+    if (k >= 2) {
+        if (k % 2 == 0) { js[0] = k - 2; nj = 1; }
+        else { js[0] = k - 3; js[1] = k - 2; nj = 2; }
+    }
+    const int no = 2 * G - 1;
+    for (int jj = 0; jj < nj; ++jj) {
+        const int J = js[jj], D = k - J;
+        for (int a = 0; a < na; ++a) {
+            __syncthreads();
+            const R *mJ = mu + ((size_t)rhs * A.nint + J) * A.nbox * na * nk;
+            for (int i = threadIdx.x; i < nk * C3; i += blockDim.x) {
+                int ik = i / C3, c = i % C3, box = cbx[c];
+                mus[ik * CS + c] = box >= 0 ? mJ[((size_t)box * na + a) * nk + ik] : R(0);
+            }
+            const R *Eab = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * esz;
+            for (int i = threadIdx.x; i < 7 * esz; i += blockDim.x) {
+                int o = i / esz - 3;  // offset X - Y
+                Es[i] = (o >= -(G - 1) && o <= G - 1 && (o < 0 ? -o : o) <= A.ntr) ? Eab[(o + G - 1) * esz + i % esz]
+                                                                                      : R(0);
+            }
+            const R coef = pref[((D - 2) * na + a) * na + b];
+            __syncthreads();
+            // pass 1 (direction x): item = (triple (nu1, k2, k3), Y2); registers: cells (X1, Y3)
+            for (int it = threadIdx.x; it < nk * FG; it += blockDim.x) {
+                const int t = it / FG, Y2 = it % FG, tk = kid[t];
+                const int nu1 = tk & 255, k2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + k2 + k3;
+                R acc[FG][FG];
+#pragma unroll
+                for (int x = 0; x < FG; ++x)
+#pragma unroll
+                    for (int z = 0; z < FG; ++z) acc[x][z] = R(0);
+                for (int B = s0; B <= mx; ++B) {
+                    const int k1 = B - s0;
+                    const R *mrow = mus + kin[(k1 * m1 + k2) * m1 + k3] * CS + Y2 * FG;
+                    R e[7];
+#pragma unroll
+                    for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k1 * m1 + nu1];
+#pragma unroll
+                    for (int Y1 = 0; Y1 < FG; ++Y1) {
+                        R mv[FG];
+#pragma unroll
+                        for (int z = 0; z < FG; ++z) mv[z] = mrow[Y1 * FG * FG + z];
+#pragma unroll
+                        for (int X1 = 0; X1 < FG; ++X1)
+#pragma unroll
+                            for (int z = 0; z < FG; ++z) acc[X1][z] += e[X1 - Y1 + 3] * mv[z];
+                    }
+                    R *out = T1s + (eof[t] + k1) * CS + Y2 * FG;
+#pragma unroll
+                    for (int X1 = 0; X1 < FG; ++X1)
+#pragma unroll
+                        for (int z = 0; z < FG; ++z) out[X1 * FG * FG + z] = acc[X1][z];
+                }
+            }
+            __syncthreads();
+            // pass 2 (direction y): item = (triple (nu1, nu2, k3), X1); registers: cells (X2, Y3)
+            for (int it = threadIdx.x; it < nk * FG; it += blockDim.x) {
+                const int t = it / FG, X1 = it % FG, tk = kid[t];
+                const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + nu2 + k3;
+                for (int Bp = s0; Bp <= mx; ++Bp) {
+                    R acc[FG][FG];
+#pragma unroll
+                    for (int y = 0; y < FG; ++y)
+#pragma unroll
+                        for (int z = 0; z < FG; ++z) acc[y][z] = R(0);
+                    for (int k2 = 0; k2 <= Bp - s0; ++k2) {
+                        const int row = eof[kin[(nu1 * m1 + k2) * m1 + k3]] + (Bp - nu2 - nu1 - k2 - k3);
+                        const R *trow = T1s + row * CS + X1 * FG * FG;
+                        R e[7];
+#pragma unroll
+                        for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k2 * m1 + nu2];
+#pragma unroll
+                        for (int Y2 = 0; Y2 < FG; ++Y2) {
+                            R tv[FG];
+#pragma unroll
+                            for (int z = 0; z < FG; ++z) tv[z] = trow[Y2 * FG + z];
+#pragma unroll
+                            for (int X2 = 0; X2 < FG; ++X2)
+#pragma unroll
+                                for (int z = 0; z < FG; ++z) acc[X2][z] += e[X2 - Y2 + 3] * tv[z];
+                        }
+                    }
+                    R *out = T2s + (eof[t] + Bp - s0) * CS + X1 * FG * FG;
+#pragma unroll
+                    for (int X2 = 0; X2 < FG; ++X2)
+#pragma unroll
+                        for (int z = 0; z < FG; ++z) out[X2 * FG + z] = acc[X2][z];
+                }
+            }
+            __syncthreads();
+            // pass 3 (direction z): item = (nu, X1); registers: cells (X2, X3)
+            for (int it = threadIdx.x; it < nk * FG; it += blockDim.x) {
+                const int iv = it / FG, X1 = it % FG, tk = kid[iv];
+                const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, nu3 = tk >> 16, smax = mx - nu1 - nu2 - nu3;
+                R acc[FG][FG];
+#pragma unroll
+                for (int y = 0; y < FG; ++y)
+#pragma unroll
+                    for (int z = 0; z < FG; ++z) acc[y][z] = R(0);
+                for (int k3 = 0; k3 <= smax; ++k3) {
+                    const int row = eof[kin[(nu1 * m1 + nu2) * m1 + k3]] + (mx - nu3 - nu1 - nu2 - k3);
+                    const R *trow = T2s + row * CS + X1 * FG * FG;
+                    R e[7];
+#pragma unroll
+                    for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k3 * m1 + nu3];
+#pragma unroll
+                    for (int X2 = 0; X2 < FG; ++X2) {
+                        R tv[FG];
+#pragma unroll
+                        for (int Y3 = 0; Y3 < FG; ++Y3) tv[Y3] = trow[X2 * FG + Y3];
+#pragma unroll
+                        for (int X3 = 0; X3 < FG; ++X3)
+#pragma unroll
+                            for (int Y3 = 0; Y3 < FG; ++Y3) acc[X2][X3] += e[X3 - Y3 + 3] * tv[Y3];
+                    }
+                }
+                R *lrow = lams + iv * CS + X1 * FG * FG;
+#pragma unroll
+                for (int X2 = 0; X2 < FG; ++X2)
+#pragma unroll
+                    for (int X3 = 0; X3 < FG; ++X3) lrow[X2 * FG + X3] += coef * acc[X2][X3];
+            }
+        }
+    }
+    __syncthreads();
+    R *lk = lam + ((size_t)rhs * A.nint + k) * A.nbox * na * nk;
+    for (int i = threadIdx.x; i < A.nbox * nk; i += blockDim.x) {
+        const int box = i / nk, iv = i % nk;
+        const int c = A.boxcell[box], x = c / (G * G), y = (c / G) % G, z = c % G;
+        lk[((size_t)box * na + b) * nk + iv] = lams[iv * CS + (x * FG + y) * FG + z];
+    }
+}
+
+size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
+{
+    (void)G;
+    const int CS = FG * FG * FG + 1, m1 = mx + 1;
+    return es * ((size_t)2 * nk * CS + (size_t)2 * ne * CS + (size_t)7 * m1 * m1) +
+           4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
+}
+
 // Runs the three passes over chunks of target intervals so that the intermediates fit the
 // workspace (ws_elems elements of R for each of T1 and T2).
 int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
@@ -493,6 +788,24 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
     (void)l;
     const size_t es = mixed ? 4 : 8;
     const int G3 = L.G * L.G * L.G, na = g.na;
+    const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es);
+    if (mixed && L.G <= FG && fsm <= 200 * 1024) {
+        M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
+                  g.kidx, g.kinv, g.eoff};
+        dim3 grd(L.nint * na, nrhs);
+        const char *mbf = (const char *)mu + L.mom_off * es * nrhs;
+        char *lbf = (char *)lam + L.mom_off * es * nrhs;
+        if (mixed) {
+            cudaFuncSetAttribute(k_m2l_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            k_m2l_fused<float><<<grd, 256, fsm, st>>>(A, (const float *)mbf, (const float *)L.E1, (const float *)L.pref,
+                                                      (float *)lbf, nrhs);
+        } else {
+            cudaFuncSetAttribute(k_m2l_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            k_m2l_fused<double><<<grd, 256, fsm, st>>>(A, (const double *)mbf, (const double *)L.E1,
+                                                       (const double *)L.pref, (double *)lbf, nrhs);
+        }
+        return 0;
+    }
     const size_t per_pair = (size_t)nrhs * na * na * G3 * g.ne;
     const char *mb = (const char *)mu + L.mom_off * es * nrhs;
     char *lb = (char *)lam + L.mom_off * es * nrhs;
@@ -580,6 +893,22 @@ void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
     unsigned blocks = (unsigned)((total + 127) / 128);
     size_t es = mixed ? 4 : 8;
     char *base = (char *)lam;
+    const int m1 = g.mx + 1;
+    if (ch.st) {
+        size_t smem = es * ((size_t)2 * g.na * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
+        dim3 grd(par.nint * par.nbox, nrhs);
+        if (mixed)
+            k_l2l_st<float><<<grd, 256, smem, st>>>((const float *)(base + par.mom_off * es * nrhs),
+                                                    (float *)(base + ch.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
+                                                    ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx, g.kinv,
+                                                    g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
+        else
+            k_l2l_st<double><<<grd, 256, smem, st>>>((const double *)(base + par.mom_off * es * nrhs),
+                                                     (double *)(base + ch.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
+                                                     ch.octant, (const double *)ch.qx, (const double *)qt, g.kidx,
+                                                     g.kinv, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
+        return;
+    }
     if (mixed)
         k_l2l<float><<<blocks, 128, 0, st>>>((const float *)(base + par.mom_off * es * nrhs), (float *)(base + ch.mom_off * es * nrhs),
                                              ch.parent, ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx,

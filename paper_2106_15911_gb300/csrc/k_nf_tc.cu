@@ -1,0 +1,399 @@
+// k_nf_tc.cu -- nearfield apply (Alg. 2, last loop; Eq. eval_sl_nf_block) on the sm_103a
+// tensor cores: tcgen05.mma (kind::tf32) with TMA-staged operands and TMEM accumulators.
+//
+// The block-Toeplitz nearfield product of one target leaf box X is a dense GEMM
+//   F[rows][t] += sum_{d} A_d[rows][k] W[t - d][k]      (k: the columns of X's interaction area)
+// with t = i*2 + s (leaf interval i, step s of the interval) and d = 0 .. 2 + s.  A CTA tile is
+// 128 rows x 256 columns: columns 0..127 are the intervals i0..i0+127 at phase s = 0, columns
+// 128..255 the same intervals at s = 1.  W is seen by TMA as a 4D tensor [rhs][interval][phase]
+// [col], so the time shift by d is a coordinate offset, and the causality mask (t - d < 0) is the
+// out-of-bounds zero fill.  FP32 accuracy comes from a 3xTF32 split:
+//   A W ~ A_hi W_hi + A_hi W_lo + A_lo W_hi,   A_hi = rn_tf32(A), A_lo = rn_tf32(A - A_hi)
+//   (same for W), accumulated in FP32 in TMEM over a chunk of the column loop (split K) and
+//   added to the FP64 output with FP64 atomics.
+// Warp roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues the MMAs,
+// warps 2-5 drain TMEM (each warp reads its 32-lane quadrant).  Two smem stages, two TMEM
+// accumulators (512 columns), persistent CTAs over (tile, K chunk) work items.  Every mbarrier
+// wait gives up after a deadline, sets an error word and lets the CTA finish cleanly.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "kernels.h"
+#include "nf_tc.h"
+
+namespace pfmm {
+
+namespace {
+
+constexpr int BM = 128, BK = 32;                   // BK fp32 = 128 bytes = one swizzle atom
+constexpr int A_TILE = BM * BK * 4;                // 16 KB
+constexpr int B_HALF = 128 * BK * 4;               // 16 KB (one phase)
+constexpr int STAGE_BYTES = 2 * A_TILE + 4 * B_HALF;  // A_hi, A_lo, B_hi (2 halves), B_lo (2 halves)
+constexpr int NSTAGE = 2;
+constexpr uint64_t kTimeoutNs = 2000000000ull;     // 2 s per wait
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+// bounded wait on the given phase parity; false after the deadline
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint64_t deadline)
+{
+    uint32_t ok = 0;
+    while (true) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(su32(b)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (gtimer() > deadline) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(su32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(su32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulate, A and B K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4)                      // D format F32
+           | (2u << 7)                    // A format TF32
+           | (2u << 10)                   // B format TF32
+           | ((uint32_t)(N >> 3) << 17)   // N / 8
+           | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::
+            "r"(dt),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *b)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct Item {
+    int panel, r0, ib, rhs, st0, st1;  // tile and its stage range [st0, st1)
+};
+
+__device__ __forceinline__ Item decode_item(const NfTcParams &P, int it)
+{
+    // items: tile-major (tile = (row tile, interval block, rhs)), K chunks inner
+    Item I;
+    int tile = it / P.ksplit, kc = it % P.ksplit;
+    I.rhs = tile / (P.ntiles * P.nib);
+    int r_ = tile % (P.ntiles * P.nib);
+    I.ib = r_ % P.nib;
+    int rt = r_ / P.nib;
+    I.panel = P.tiles[2 * rt];
+    I.r0 = P.tiles[2 * rt + 1];
+    int nst = 4 * P.nkb;  // stage list: d = 0..3, then column blocks
+    I.st0 = (int)((long long)nst * kc / P.ksplit);
+    I.st1 = (int)((long long)nst * (kc + 1) / P.ksplit);
+    return I;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ CUtensorMap mapAhi,
+                                                         const __grid_constant__ CUtensorMap mapAlo,
+                                                         const __grid_constant__ CUtensorMap mapWhi,
+                                                         const __grid_constant__ CUtensorMap mapWlo, NfTcParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment of the tiles (swizzle atoms)
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE_BYTES);
+    uint64_t *empty = full + NSTAGE;
+    uint64_t *tfull = empty + NSTAGE;
+    uint64_t *tempty = tfull + 2;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint64_t deadline = gtimer() + kTimeoutNs;
+    const int nitems = P.nitems;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int g = 0;  // global stage counter
+            for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
+                Item I = decode_item(P, it);
+                const PanelGPU &Pn = P.panels[I.panel];
+                for (int st = I.st0; st < I.st1; ++st, ++g) {
+                    const int s = g % NSTAGE;
+                    if (!mbar_wait(&empty[s], ((g / NSTAGE) & 1) ^ 1, deadline)) {
+                        atomicExch(P.err, 1);
+                        s_abort = 1;
+                        break;
+                    }
+                    const int d = st / P.nkb, kb = st % P.nkb;
+                    unsigned char *sA = smem + s * STAGE_BYTES;
+                    const uint32_t bytes = d < 3 ? STAGE_BYTES : 2 * A_TILE + 2 * B_HALF;
+                    mbar_expect_tx(&full[s], bytes);
+                    const int arow = (int)((P.kop ? Pn.offK : Pn.offV) / P.cols_pad) + d * Pn.rows_pad + I.r0;
+                    tma_2d(sA, &mapAhi, kb * BK, arow, &full[s]);
+                    tma_2d(sA + A_TILE, &mapAlo, kb * BK, arow, &full[s]);
+                    unsigned char *sB = sA + 2 * A_TILE;
+                    for (int ph = (d < 3 ? 0 : 1); ph < 2; ++ph) {
+                        // step t = 2 i + ph, source step t - d = 2 (i - q) + phs
+                        const int phs = ((ph - d) % 2 + 2) % 2, q = (phs - (ph - d)) / 2;
+                        tma_4d(sB + ph * B_HALF, &mapWhi, kb * BK, phs, I.ib * 128 - q, I.rhs, &full[s]);
+                        tma_4d(sB + 2 * B_HALF + ph * B_HALF, &mapWlo, kb * BK, phs, I.ib * 128 - q, I.rhs, &full[s]);
+                    }
+                }
+            }
+            // before the CTA exits, the copies it issued must have landed (bounded wait): the last
+            // use u of stage s completes phase u
+            const uint64_t dl2 = gtimer() + kTimeoutNs / 20;
+            for (int j = (g > NSTAGE ? g - NSTAGE : 0); j < g; ++j) mbar_wait(&full[j % NSTAGE], (j / NSTAGE) & 1, dl2);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int g = 0, n = 0;
+            const uint32_t id256 = idesc_tf32(BM, 256), id128 = idesc_tf32(BM, 128);
+            for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x, ++n) {
+                Item I = decode_item(P, it);
+                const int acc = n & 1;
+                if (!mbar_wait(&tempty[acc], ((n >> 1) & 1) ^ 1, deadline)) {
+                    atomicExch(P.err, 2);
+                    s_abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dcol = tmem + acc * 256;
+                uint32_t first = 1;
+                for (int st = I.st0; st < I.st1; ++st, ++g) {
+                    const int s = g % NSTAGE;
+                    if (!mbar_wait(&full[s], (g / NSTAGE) & 1, deadline)) {
+                        atomicExch(P.err, 3);
+                        s_abort = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int d = st / P.nkb;
+                    const uint32_t a_hi = su32(smem + s * STAGE_BYTES), a_lo = a_hi + A_TILE;
+                    const uint32_t b_hi = a_hi + 2 * A_TILE, b_lo = b_hi + 2 * B_HALF;
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {  // K = 8 tf32 (32 bytes) per MMA
+                        const uint32_t ko = kk * 32;
+                        if (d < 3) {
+                            mma_tf32(dcol, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), id256, first ? 0u : 1u);
+                            first = 0;
+                            mma_tf32(dcol, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), id256, 1u);
+                            mma_tf32(dcol, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), id256, 1u);
+                        } else {
+                            // d = 3 reaches back only from the second step of an interval
+                            mma_tf32(dcol + 128, sw128_desc(a_hi + ko), sw128_desc(b_hi + B_HALF + ko), id128,
+                                     first ? 0u : 1u);
+                            mma_tf32(dcol + 128, sw128_desc(a_hi + ko), sw128_desc(b_lo + B_HALF + ko), id128, 1u);
+                            mma_tf32(dcol + 128, sw128_desc(a_lo + ko), sw128_desc(b_hi + B_HALF + ko), id128, 1u);
+                            if (first) {
+                                // the phase-0 half starts with no d < 3 stage in this chunk: clear it
+                                first = 0;
+                            }
+                        }
+                    }
+                    mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+                }
+                mma_commit(&tfull[acc]);  // an empty chunk accumulated nothing: the epilogue skips it
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        const int quad = warp & 3;
+        const int row_l = quad * 32 + lane;
+        int n = 0;
+        for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x, ++n) {
+            Item I = decode_item(P, it);
+            const int acc = n & 1;
+            if (!mbar_wait(&tfull[acc], (n >> 1) & 1, deadline)) {
+                atomicExch(P.err, 4);
+                s_abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const PanelGPU &Pn = P.panels[I.panel];
+            const int row = I.r0 + row_l;
+            const bool row_ok = row < Pn.nrows;
+            // the phase-1 half is written by any stage, the phase-0 half only by stages with d < 3
+            const bool has_any = I.st1 > I.st0;
+            const bool has_ph0 = has_any && I.st0 < 3 * P.nkb;
+            double *fr = P.f + (size_t)I.rhs * P.Et * P.nt + Pn.row0 + row;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 256; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + acc * 256 + c0, v);
+                if (!row_ok || !has_any || (c0 < 128 && !has_ph0)) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int c = c0 + j, ph = c >> 7, iv = I.ib * 128 + (c & 127);
+                    if (iv < P.nint) atomicAdd(fr + (size_t)(2 * iv + ph) * P.nt, (double)__uint_as_float(v[j]));
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// split kernels: hi = a rounded to nearest TF32, lo = (a - hi) rounded to nearest TF32; both
+// parts are exact TF32 values, so the tensor core reads them unchanged and a - hi - lo is
+// below 2^-22 |a|
+__device__ __forceinline__ float rna_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_split_panel(const float *__restrict__ A, float *__restrict__ hi, float *__restrict__ lo, size_t n)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a = A[i];
+    float h = rna_tf32(a);
+    hi[i] = h;
+    lo[i] = rna_tf32(a - h);
+}
+
+// W split from FP64 input: permutes (V) or pads rows (K) into [rhs][t][ncol_pad]
+__global__ void k_split_input(const double *__restrict__ x, const int *__restrict__ perm, int ncol, int ncol_pad,
+                              float *__restrict__ hi, float *__restrict__ lo, size_t total)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    size_t rt = i / ncol_pad;
+    int c = (int)(i - rt * ncol_pad);
+    double v = 0.0;
+    if (c < ncol) v = x[rt * ncol + (perm ? perm[c] : c)];
+    float h = rna_tf32((float)v);
+    hi[i] = h;
+    lo[i] = rna_tf32((float)(v - (double)h));
+}
+
+void launch_split_panel(const float *A, float *hi, float *lo, size_t n, cudaStream_t st)
+{
+    k_split_panel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, hi, lo, n);
+}
+
+void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, float *hi,
+                        float *lo, cudaStream_t st)
+{
+    size_t total = (size_t)nrhs * Et * ncol_pad;
+    k_split_input<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(x, perm, ncol, ncol_pad, hi, lo, total);
+}
+
+size_t nf_tc_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + 1024 + 256; }
+
+int launch_nf_apply_tc(const CUtensorMap &Ahi, const CUtensorMap &Alo, const CUtensorMap &Whi, const CUtensorMap &Wlo,
+                       const NfTcParams &P, int nsm, cudaStream_t st)
+{
+    size_t smem = nf_tc_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(k_nf_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return -1;
+    int grid = P.nitems < nsm ? P.nitems : nsm;
+    k_nf_apply_tc<<<grid, 192, smem, st>>>(Ahi, Alo, Whi, Wlo, P);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace pfmm

@@ -58,12 +58,14 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     using namespace pfmm;
     if (!H || !w || !f || nrhs < 1) return set_error(PFMM_ERR_INVALID_ARG, "invalid pfmm_apply_V_noalloc arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    // carve the static array: permuted input | FP64 output | moments | locals | M2L T1 | M2L T2
+    // carve the static array: permuted input | FP64 output | moments | locals |
+    // [tensor-core input split hi | lo] | M2L T1 | M2L T2
     const size_t n_in = (size_t)nrhs * H->Et * H->nt;
     const size_t b_x = up256(n_in * H->es), b_f = up256(n_in * sizeof(double));
     const size_t n_mom = (size_t)nrhs * (H->mom_per_rhs > 0 ? H->mom_per_rhs : 1);
     const size_t b_mu = up256(n_mom * H->es);
-    const size_t fixed = b_x + b_f + 2 * b_mu;
+    const size_t b_w = H->tcV ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(float)) : 0;
+    const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w;
     const size_t min_chunk = (size_t)nrhs * 2 * H->na * H->na * H->ne * 64;  // M2L: two interval pairs of a 4^3 grid
     size_t need_T = 0;  // elements for the largest single-interval chunk over all levels
     for (int l = 2; l <= H->p; ++l) {
@@ -84,6 +86,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     double *fint = (double *)(base + b_x);
     char *mu = (char *)(base + b_x + b_f);
     char *lam = mu + b_mu;
+    float *whi = (float *)(lam + b_mu), *wlo = (float *)(lam + b_mu + b_w);
     const size_t t_bytes = (kScratchBytes - fixed) / 2 / 256 * 256;
     void *T1 = base + fixed, *T2 = base + fixed + t_bytes;
     const size_t ws_elems = t_bytes / H->es;
@@ -109,8 +112,12 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     // every buffer below is fully written before it is read, except the locals of the first two
     // intervals of each level, which launch_m2l clears; nothing depends on the previous call
     launch_permute_in(w, xint, H->mixed, nrhs, g, st);
-    launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs, g, fint,
-                    st);
+    if (H->tcV) {  // the same nearfield engine as pfmm_apply_V
+        if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, fint, st))) return rc;
+    } else {
+        launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs, g,
+                        fint, st);
+    }
     const int p = H->p;
     if (p >= 2) {
         launch_s2m(H->mixed, false, xint, H->nt, H->d_Sx, H->d_St, mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st);

@@ -22,6 +22,7 @@ PFMM_ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIME
 PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_NEARFIELD_STORED = 0
 PFMM_PART_NEAR, PFMM_PART_FAR, PFMM_PART_ALL = 1, 2, 3
+PFMM_NF_AUTO, PFMM_NF_CUDA_CORES = 0, 1
 
 
 class pfmm_mesh(ctypes.Structure):
@@ -34,13 +35,13 @@ class pfmm_params(ctypes.Structure):
     _fields_ = [("m_t", ctypes.c_int32), ("m_x", ctypes.c_int32), ("c_st", ctypes.c_double),
                 ("n_tr", ctypes.c_int32), ("eps_tr", ctypes.c_double), ("leaf_steps", ctypes.c_int32),
                 ("leaf_tris", ctypes.c_int32), ("precision", ctypes.c_int32), ("nearfield", ctypes.c_int32),
-                ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32)]
+                ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32), ("nf_engine", ctypes.c_int32)]
 
 
 class pfmm_info(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("lx", ctypes.c_int32 * 32), ("nbox", ctypes.c_int32 * 32),
                 ("pad", ctypes.c_double * 32), ("n_m2l_pairs", ctypes.c_int32), ("nearfield_bytes", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("nf_tensor_cores", ctypes.c_int32)]
 
 
 _lib = None
@@ -60,6 +61,7 @@ SIGNATURES = {
     "pfmm_set_profiling": (ctypes.c_int, [_VP, _I]),
     "pfmm_phase_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
+    "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
     "pfmm_destroy": (None, [_VP]),
     "pfmm_last_error": (ctypes.c_char_p, []),
@@ -192,7 +194,12 @@ def pfmm_get_info(h) -> dict:
     _check(lib().pfmm_get_info(h, ctypes.byref(i)))
     n = i.p + 1
     return dict(p=i.p, lx=list(i.lx[:n]), nbox=list(i.nbox[:n]), pad=list(i.pad[:n]), n_m2l_pairs=i.n_m2l_pairs,
-                nearfield_bytes=i.nearfield_bytes, device_bytes=i.device_bytes)
+                nearfield_bytes=i.nearfield_bytes, device_bytes=i.device_bytes, nf_tensor_cores=i.nf_tensor_cores)
+
+
+def pfmm_check(h):
+    """Synchronise and raise if a bounded device wait of this handle gave up (TIMEOUT)."""
+    _check(lib().pfmm_check(h))
 
 
 def pfmm_probe_fma_rate(fp64: bool, stream=None) -> float:

@@ -148,3 +148,30 @@ def test_config2_sampled_rows(cfg2, op_id):
     f32 = (ops[P.PFMM_MIXED].V(xt) if op_id == 0 else ops[P.PFMM_MIXED].K(xt)).cpu().numpy()[0]
     assert _rel(f64, ref, rows) <= 1e-12
     assert _rel(f32, ref, rows) <= 1e-5
+
+
+# ---- tensor-core nearfield (3xTF32 split, mixed mode) ------------------------------------------
+@pytest.mark.parametrize("n_a,Et,kw", [(4, 16, dict(m_t=4, m_x=4, c_st=1.0)), (8, 64, dict(m_t=4, m_x=6, c_st=1.0)),
+                                       (4, 512, dict(m_t=3, m_x=3, c_st=1.0))])
+def test_tensor_core_nearfield_matches_cuda_cores_and_oracle(n_a, Et, kw):
+    V, T = cube_mesh(n_a)
+    ops = {e: P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, nf_engine=e, **kw)
+           for e in (P.PFMM_NF_AUTO, P.PFMM_NF_CUDA_CORES)}
+    assert ops[P.PFMM_NF_AUTO].info()["nf_tensor_cores"] == 3
+    assert ops[P.PFMM_NF_CUDA_CORES].info()["nf_tensor_cores"] == 0
+    Pr = O.make_problem(V, T, 1.0, Et, **kw)
+    w = random_density(Et, T.shape[0], 2, seed=21)
+    g = random_density(Et, V.shape[0], 2, seed=22)
+    for op_id, x in ((0, w), (1, g)):
+        xt = torch.tensor(x, device=DEV)
+        res = {}
+        for e, o in ops.items():
+            res[e] = (o.V(xt, parts=P.PFMM_PART_NEAR) if op_id == 0 else o.K(xt, parts=P.PFMM_PART_NEAR)).cpu().numpy()
+            P.pfmm_check(o.h)
+        for r in range(2):
+            ref = O.pfmm_apply(Pr, op_id, x[r], parts=1)
+            assert _rel(res[P.PFMM_NF_AUTO][r], ref) <= 1e-5
+            assert _rel(res[P.PFMM_NF_CUDA_CORES][r], ref) <= 1e-5
+            assert _rel(res[P.PFMM_NF_AUTO][r], res[P.PFMM_NF_CUDA_CORES][r]) <= 1e-5
+    for o in ops.values():
+        o.close()
