@@ -89,6 +89,37 @@ def _oracle_sample(n_targets=16, nthreads=0):
                        f"M2L/L2L/L2T on their box chains, their nearfield rows); {dt:.1f} s"), dt
 
 
+def _solve_comparison(dev):
+    """Wall time to 1e-8 relative residual (Eq. 02:linear:system, direct formulation) on the
+    3072-triangle x 128-step cube: plain FP64 FGMRES(50) vs GMRES-IR (FP32 mixed inner FGMRES,
+    FP64 residuals).  Datum: 8 heat sources in the shell 1.2 <= |y - c| <= 2, t0 in [-0.5, -0.05]."""
+    import torch
+
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_mesh, heat_source_datum, shell_sources
+
+    V, T = cube_mesh(16)
+    Et = 128
+    kw = dict(m_t=4, m_x=6, c_st=1.0)
+    g = torch.tensor(heat_source_datum(V, 1.0, Et, shell_sources(8))[None], device=dev)
+    x = torch.empty((1, Et, T.shape[0]), dtype=torch.float64, device=dev)
+    op64 = P.Operator(V, T, 1.0, Et, **kw)
+    opm = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, **kw)
+    P.pfmm_solve(op64.h, P.PFMM_DIRECT, g, x, 1)  # warm-up (workspaces, clocks)
+    plain = P.pfmm_solve(op64.h, P.PFMM_DIRECT, g, x, 1)
+    x64 = x.clone()
+    o = P.pfmm_default_solve_opts()
+    o.refine = op64.h
+    P.pfmm_solve(opm.h, P.PFMM_DIRECT, g, x, 1, o)
+    ir = P.pfmm_solve(opm.h, P.PFMM_DIRECT, g, x, 1, o)
+    diff = float((x - x64).abs().max() / x64.abs().max())
+    op64.close()
+    opm.close()
+    return {"workload": f"cube 16x16 faces ({T.shape[0]} tri) x {Et} steps, direct formulation, tol 1e-8",
+            "fp64_fgmres": plain, "mixed_gmres_ir": ir, "speedup": plain["seconds"] / ir["seconds"],
+            "solution_rel_diff": diff}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -121,6 +152,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
     ap.add_argument("--et", type=int, default=ET, help="profiling only: time steps")
     args = ap.parse_args()
@@ -248,6 +280,10 @@ def main():
                      "fp64_fma_tflops": P.pfmm_probe_fma_rate(True, stream)}
         op64.close()
 
+    solve = None
+    if rank == 0 and not args.no_solve:
+        solve = _solve_comparison(dev)
+
     launches = 3 * info["p"]  # permute in/out, nearfield, S2M, L2T, (p-2) M2M, (p-1) M2L, (p-2) L2L
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -265,7 +301,8 @@ def main():
                                  f"{info['nearfield_bytes'] / 1e9:.2f} GB > L2",
                            "parallelism": f"replicas x{world}", "build_s": t_build},
                 "phases_ms": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches * args.steps, "clocks": _clocks_summary(samples), "fp64": fp64_line}
+                "gpu_launches": launches * args.steps, "clocks": _clocks_summary(samples), "fp64": fp64_line,
+                "solve": solve}
         print(json.dumps(line), flush=True)
     op.close()
     if world > 1:

@@ -172,6 +172,40 @@ int pfmm_probe_fma_rate(int32_t fp64, double *tflops, void *stream);
  * each call writes every workspace before reading it. */
 int pfmm_apply_V_noalloc(pfmm_handle *h, const double *w, double *f, int32_t nrhs, void *stream);
 
+/* ---- solver ------------------------------------------------------------------------------ */
+#define PFMM_DIRECT 0    /* V_h w = (1/2 M_h + K_h) g  (Section 2, Eq. 02:linear:system) */
+#define PFMM_INDIRECT 1  /* V_h w = M_h g              (single-layer ansatz) */
+
+typedef struct pfmm_solve_opts {
+    double tol;           /* stop when ||b - V_h x||_2 <= tol ||b||_2 (default 1e-8) */
+    int32_t restart;      /* FGMRES restart length m (default 50, at most 500) */
+    int32_t max_it;       /* cap on inner iterations (V_h applies of the inner handle), default 1000 */
+    pfmm_handle *refine;  /* optional FP64 handle of the same problem: GMRES-IR (default NULL) */
+    double inner_tol;     /* GMRES-IR: relative tolerance of each inner solve (default 1e-4) */
+    int32_t max_outer;    /* GMRES-IR: cap on refinement steps (default 20) */
+} pfmm_solve_opts;
+
+typedef struct pfmm_solve_info {
+    int32_t iterations;   /* inner FGMRES iterations over all right-hand sides */
+    int32_t outer;        /* refinement steps (GMRES-IR) */
+    double rel_res;       /* largest final ||b - V_h x|| / ||b|| (FP64 operator when refining) */
+    double seconds;       /* wall time of the call */
+} pfmm_solve_info;
+
+int pfmm_default_solve_opts(pfmm_solve_opts *opts);
+
+/* Solve V_h x = b for every right-hand side, b = (1/2 M_h + K_h) g (PFMM_DIRECT) or M_h g
+ * (PFMM_INDIRECT), with restarted right-preconditioned flexible GMRES (x0 = 0, Arnoldi by
+ * classical Gram-Schmidt applied twice), all Krylov vectors FP64 on the device.  With
+ * opts->refine (an FP64 handle of the same mesh and steps) the residual is formed in FP64 with
+ * it and inner FGMRES solves run with h (typically PFMM_MIXED): iterative refinement.
+ *   g: device [nrhs][E_t][N_v] (p0 in time, p1 in space, already projected), x: device
+ *   [nrhs][E_t][E_x] (overwritten).  Synchronises `stream`; allocates its Krylov workspace
+ *   ((2 restart + 4) E_t E_x doubles).  Returns PFMM_ERR_NOT_CONVERGED when a cap is reached
+ *   (x holds the last iterate and info is filled), PFMM_ERR_NONFINITE for NaN / Inf in g. */
+int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, double *x, int32_t nrhs,
+               const pfmm_solve_opts *opts, pfmm_solve_info *info, void *stream);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void pfmm_destroy(pfmm_handle *h);
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -272,7 +273,10 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *wh
     P.nib = (nint + 127) / 128;
     P.nkb = cols / 32;
     const int tiles = nrhs * P.ntiles * P.nib;
-    int ks = (3 * H->nsm + tiles - 1) / tiles;
+    // split K into chunks of at most 32 stages (1024 columns): shorter FP32 accumulation in TMEM
+    // and at least three work items per SM; the FP64 atomics of the partials are cheap
+    int ks = std::max((3 * H->nsm + tiles - 1) / tiles, (4 * P.nkb + 31) / 32);
+    if (const char *env = std::getenv("PFMM_TC_KSPLIT")) ks = std::atoi(env);  // tuning override
     ks = std::max(1, std::min(ks, 4 * P.nkb / 8));
     P.ksplit = ks;
     P.nitems = tiles * ks;

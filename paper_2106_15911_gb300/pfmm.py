@@ -44,6 +44,18 @@ class pfmm_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("nf_tensor_cores", ctypes.c_int32)]
 
 
+class pfmm_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_it", ctypes.c_int32),
+                ("refine", ctypes.c_void_p), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+
+
+class pfmm_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+PFMM_DIRECT, PFMM_INDIRECT = 0, 1
+
 _lib = None
 _lock = threading.Lock()
 
@@ -63,6 +75,9 @@ SIGNATURES = {
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
     "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
+    "pfmm_default_solve_opts": (ctypes.c_int, [ctypes.POINTER(pfmm_solve_opts)]),
+    "pfmm_solve": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, ctypes.POINTER(pfmm_solve_opts),
+                                  ctypes.POINTER(pfmm_solve_info), _VP]),
     "pfmm_destroy": (None, [_VP]),
     "pfmm_last_error": (ctypes.c_char_p, []),
 }
@@ -206,6 +221,26 @@ def pfmm_probe_fma_rate(fp64: bool, stream=None) -> float:
     v = ctypes.c_double()
     _check(lib().pfmm_probe_fma_rate(1 if fp64 else 0, ctypes.byref(v), _stream(stream)))
     return v.value
+
+
+def pfmm_default_solve_opts() -> pfmm_solve_opts:
+    o = pfmm_solve_opts()
+    _check(lib().pfmm_default_solve_opts(ctypes.byref(o)))
+    return o
+
+
+def pfmm_solve(h, formulation: int, g, x, nrhs: int, opts: pfmm_solve_opts | None = None, stream=None,
+               allow_not_converged: bool = False) -> dict:
+    """Solve V_h x = b (b from g by the chosen formulation); returns the solve info as a dict."""
+    info = pfmm_solve_info()
+    if opts is None:
+        opts = pfmm_default_solve_opts()
+    rc = lib().pfmm_solve(h, int(formulation), _ptr(g), _ptr(x), int(nrhs), ctypes.byref(opts), ctypes.byref(info),
+                          _stream(stream))
+    if not (rc == -6 and allow_not_converged):
+        _check(rc)
+    return dict(iterations=info.iterations, outer=info.outer, rel_res=info.rel_res, seconds=info.seconds,
+                converged=rc == PFMM_OK)
 
 
 def pfmm_destroy(h):
