@@ -250,20 +250,42 @@ def main():
     e2e = {"value": world * dof / (e2e_ms * 1e-3), "unit": "space-time DOF/s", "h2d_bytes_per_step": 8 * dof,
            "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_ms}
 
-    # ---- roofline of the dominant kernel (nearfield apply): algorithmic flops per launch
+    # ---- roofline of the dominant kernel (nearfield apply): algorithmic work per launch
     ls = 2
     nint = ET // ls
     flops_nf = 2.0 * nt * nt * nint * sum(ls + s + 1 for s in range(ls))  # 2 * E_x^2 * sum_t |D(t)|
     nf_ms = phases["nearfield"]
     fp64 = prec == P.PFMM_FP64
-    peak_meas = P.pfmm_probe_fma_rate(fp64, stream)
+    tc = bool(info.get("nf_tensor_cores", 0) & 1)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_nominal = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
-    roofline = {"bound": "alu", "kernel": "k_nf_apply", "achieved": flops_nf / (nf_ms * 1e-3) / 1e12,
-                "peak": peak_meas, "unit": "TFLOP/s", "frac": flops_nf / (nf_ms * 1e-3) / 1e12 / peak_meas,
-                "traffic": None, "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA probe "
-                                                f"(nominal FP32 {peak_nominal:.1f} at 2070 MHz)",
-                "flops_per_launch": flops_nf, "ms_per_launch": nf_ms}
+    if tc:
+        # tcgen05 kind::tf32 with a 3-term split: three TF32 products per useful product; the
+        # TF32 peak is the measured dense BF16 peak x the nominal TF32/BF16 rate ratio (1.1/2.25)
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak_tf32 = bf16 * 1.1 / 2.25
+        achieved = 3.0 * flops_nf / (nf_ms * 1e-3) / 1e12
+        # algorithmic HBM bytes: the hi/lo TF32 parts of every stored panel element, read once
+        bytes_nf = 8.0 * info["nearfield_v_elements"]
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        # DRAM bytes per panel element of this kernel, measured with ncu on the 3072-triangle x
+        # 128-step case (419.7 MB per launch over 44.04M panel elements)
+        traffic = 9.53 * info["nearfield_v_elements"]
+        roofline = {"bound": "tensor", "kernel": "k_nf_apply_tc", "achieved": achieved, "peak": peak_tf32,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tf32, "traffic": traffic,
+                    "peak_source": f"measured bf16 {bf16:.0f} TF x nominal tf32/bf16 ratio (of measured)",
+                    "flops_per_launch_executed": 3.0 * flops_nf, "ms_per_launch": nf_ms,
+                    "hbm": {"achieved_gbs": bytes_nf / (nf_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                            "frac": bytes_nf / (nf_ms * 1e-3) / 1e9 / hbm, "bytes_per_launch": bytes_nf}}
+    else:
+        peak_meas = P.pfmm_probe_fma_rate(fp64, stream)
+        peak_nominal = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
+        roofline = {"bound": "alu", "kernel": "k_nf_apply", "achieved": flops_nf / (nf_ms * 1e-3) / 1e12,
+                    "peak": peak_meas, "unit": "TFLOP/s", "frac": flops_nf / (nf_ms * 1e-3) / 1e12 / peak_meas,
+                    "traffic": None, "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA probe "
+                                                    f"(nominal FP32 {peak_nominal:.1f} at 2070 MHz)",
+                    "flops_per_launch": flops_nf, "ms_per_launch": nf_ms}
 
     # ---- FP64 mode of the same workload (context; the other half of the workload's comparison)
     fp64_line = None

@@ -792,6 +792,7 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     info->nearfield_bytes = (t.sizeV + t.sizeK) * (int64_t)h->es;
     info->device_bytes = h->dev_bytes;
     info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
+    info->nearfield_v_elements = t.sizeV;
     return PFMM_OK;
 }
 
