@@ -611,18 +611,19 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
 // Same arithmetic as the three-pass kernels (cells with G < 4 are padded with empty cells).
 constexpr int FG = 4;  // padded grid extent per direction
 
+constexpr int kM2LThreads = 384;
+
 template <typename R>
-__global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restrict__ mu, const R *__restrict__ E1,
-                                                     const R *__restrict__ pref, R *__restrict__ lam, int nrhs)
+__global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
+                                                                const R *__restrict__ E1, const R *__restrict__ pref,
+                                                                R *__restrict__ lam, int nrhs)
 {
     extern __shared__ unsigned char smem_raw[];
     constexpr int C3 = FG * FG * FG, CS = C3 + 1;  // cell rows are padded by one (bank spread)
     const int G = A.G, nk = A.nk, ne = A.ne, mx = A.mx, m1 = mx + 1, na = A.na, esz = m1 * m1;
-    R *mus = reinterpret_cast<R *>(smem_raw);  // [nk][CS]    moments, kappa-major
-    R *T1s = mus + nk * CS;                    // [ne][CS]    cells (X1, Y2, Y3)
-    R *T2s = T1s + ne * CS;                    // [ne][CS]    cells (X1, X2, Y3)
-    R *lams = T2s + ne * CS;                   // [nk][CS]    cells (X1, X2, X3)
-    R *Es = lams + nk * CS;                    // [7][m1][m1] offsets -3..3, zero outside the radius
+    R *T1s = reinterpret_cast<R *>(smem_raw);  // [ne][CS]  cells (X1, Y2, Y3)
+    R *U = T1s + ne * CS;                      // [ne][CS]  moments [nk][CS] in pass 1, then T2 (X1, X2, Y3)
+    R *Es = U + ne * CS;                       // [7][m1][m1] offsets -3..3, zero outside the radius
     int *kid = reinterpret_cast<int *>(Es + 7 * esz);
     int *kin = kid + nk;
     int *eof = kin + m1 * m1 * m1;
@@ -637,13 +638,20 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
         int x = i / (FG * FG), y = (i / FG) % FG, z = i % FG;
         cbx[i] = (x < G && y < G && z < G) ? A.cellbox[(x * G + y) * G + z] : -1;
     }
-    for (int i = threadIdx.x; i < nk * CS; i += blockDim.x) lams[i] = R(0);
+    // target locals of this thread's pass-3 items (nu, X1), cells (X1, X2, X3), kept in registers
+    R lamr[2][FG][FG];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int y = 0; y < FG; ++y)
+#pragma unroll
+            for (int z = 0; z < FG; ++z) lamr[q][y][z] = R(0);
     int js[2], nj = 0;
     if (k >= 2) {
         if (k % 2 == 0) { js[0] = k - 2; nj = 1; }
         else { js[0] = k - 3; js[1] = k - 2; nj = 2; }
     }
-    const int no = 2 * G - 1;
+    const int no = 2 * G - 1, nitems = nk * FG;
     for (int jj = 0; jj < nj; ++jj) {
         const int J = js[jj], D = k - J;
         for (int a = 0; a < na; ++a) {
@@ -651,7 +659,7 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
             const R *mJ = mu + ((size_t)rhs * A.nint + J) * A.nbox * na * nk;
             for (int i = threadIdx.x; i < nk * C3; i += blockDim.x) {
                 int ik = i / C3, c = i % C3, box = cbx[c];
-                mus[ik * CS + c] = box >= 0 ? mJ[((size_t)box * na + a) * nk + ik] : R(0);
+                U[ik * CS + c] = box >= 0 ? mJ[((size_t)box * na + a) * nk + ik] : R(0);
             }
             const R *Eab = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * esz;
             for (int i = threadIdx.x; i < 7 * esz; i += blockDim.x) {
@@ -662,7 +670,7 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
             const R coef = pref[((D - 2) * na + a) * na + b];
             __syncthreads();
             // pass 1 (direction x): item = (triple (nu1, k2, k3), Y2); registers: cells (X1, Y3)
-            for (int it = threadIdx.x; it < nk * FG; it += blockDim.x) {
+            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
                 const int t = it / FG, Y2 = it % FG, tk = kid[t];
                 const int nu1 = tk & 255, k2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + k2 + k3;
                 R acc[FG][FG];
@@ -672,7 +680,7 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
                     for (int z = 0; z < FG; ++z) acc[x][z] = R(0);
                 for (int B = s0; B <= mx; ++B) {
                     const int k1 = B - s0;
-                    const R *mrow = mus + kin[(k1 * m1 + k2) * m1 + k3] * CS + Y2 * FG;
+                    const R *mrow = U + kin[(k1 * m1 + k2) * m1 + k3] * CS + Y2 * FG;
                     R e[7];
 #pragma unroll
                     for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k1 * m1 + nu1];
@@ -694,8 +702,8 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
                 }
             }
             __syncthreads();
-            // pass 2 (direction y): item = (triple (nu1, nu2, k3), X1); registers: cells (X2, Y3)
-            for (int it = threadIdx.x; it < nk * FG; it += blockDim.x) {
+            // pass 2 (direction y): item = (triple (nu1, nu2, k3), X1); registers: cells (X2, Y3); T2 -> U
+            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
                 const int t = it / FG, X1 = it % FG, tk = kid[t];
                 const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + nu2 + k3;
                 for (int Bp = s0; Bp <= mx; ++Bp) {
@@ -721,7 +729,7 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
                                 for (int z = 0; z < FG; ++z) acc[X2][z] += e[X2 - Y2 + 3] * tv[z];
                         }
                     }
-                    R *out = T2s + (eof[t] + Bp - s0) * CS + X1 * FG * FG;
+                    R *out = U + (eof[t] + Bp - s0) * CS + X1 * FG * FG;
 #pragma unroll
                     for (int X2 = 0; X2 < FG; ++X2)
 #pragma unroll
@@ -729,8 +737,11 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
                 }
             }
             __syncthreads();
-            // pass 3 (direction z): item = (nu, X1); registers: cells (X2, X3)
-            for (int it = threadIdx.x; it < nk * FG; it += blockDim.x) {
+            // pass 3 (direction z): item = (nu, X1), fixed per thread; registers: cells (X2, X3)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int it = threadIdx.x + q * blockDim.x;
+                if (it >= nitems) break;
                 const int iv = it / FG, X1 = it % FG, tk = kid[iv];
                 const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, nu3 = tk >> 16, smax = mx - nu1 - nu2 - nu3;
                 R acc[FG][FG];
@@ -740,7 +751,7 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
                     for (int z = 0; z < FG; ++z) acc[y][z] = R(0);
                 for (int k3 = 0; k3 <= smax; ++k3) {
                     const int row = eof[kin[(nu1 * m1 + nu2) * m1 + k3]] + (mx - nu3 - nu1 - nu2 - k3);
-                    const R *trow = T2s + row * CS + X1 * FG * FG;
+                    const R *trow = U + row * CS + X1 * FG * FG;
                     R e[7];
 #pragma unroll
                     for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k3 * m1 + nu3];
@@ -755,20 +766,29 @@ __global__ void __launch_bounds__(256) k_m2l_fused(M2LArgs A, const R *__restric
                             for (int Y3 = 0; Y3 < FG; ++Y3) acc[X2][X3] += e[X3 - Y3 + 3] * tv[Y3];
                     }
                 }
-                R *lrow = lams + iv * CS + X1 * FG * FG;
 #pragma unroll
                 for (int X2 = 0; X2 < FG; ++X2)
 #pragma unroll
-                    for (int X3 = 0; X3 < FG; ++X3) lrow[X2 * FG + X3] += coef * acc[X2][X3];
+                    for (int X3 = 0; X3 < FG; ++X3) lamr[q][X2][X3] += coef * acc[X2][X3];
             }
         }
     }
-    __syncthreads();
+    // write the locals of the non-empty target boxes (intervals 0 and 1 get zeros)
     R *lk = lam + ((size_t)rhs * A.nint + k) * A.nbox * na * nk;
-    for (int i = threadIdx.x; i < A.nbox * nk; i += blockDim.x) {
-        const int box = i / nk, iv = i % nk;
-        const int c = A.boxcell[box], x = c / (G * G), y = (c / G) % G, z = c % G;
-        lk[((size_t)box * na + b) * nk + iv] = lams[iv * CS + (x * FG + y) * FG + z];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int it = threadIdx.x + q * blockDim.x;
+        if (it >= nitems) break;
+        const int iv = it / FG, X1 = it % FG;
+        if (X1 >= G) continue;
+#pragma unroll
+        for (int X2 = 0; X2 < FG; ++X2)
+#pragma unroll
+            for (int X3 = 0; X3 < FG; ++X3) {
+                if (X2 >= G || X3 >= G) continue;
+                const int box = A.cellbox[(X1 * G + X2) * G + X3];
+                if (box >= 0) lk[((size_t)box * na + b) * nk + iv] = lamr[q][X2][X3];
+            }
     }
 }
 
@@ -776,7 +796,7 @@ size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
 {
     (void)G;
     const int CS = FG * FG * FG + 1, m1 = mx + 1;
-    return es * ((size_t)2 * nk * CS + (size_t)2 * ne * CS + (size_t)7 * m1 * m1) +
+    return es * ((size_t)2 * std::max(ne, nk) * CS + (size_t)7 * m1 * m1) +
            4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
 }
 
@@ -789,7 +809,7 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
     const size_t es = mixed ? 4 : 8;
     const int G3 = L.G * L.G * L.G, na = g.na;
     const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es);
-    if (mixed && L.G <= FG && fsm <= 200 * 1024) {
+    if (mixed && L.G <= FG && fsm <= 200 * 1024 && g.nk * FG <= 2 * kM2LThreads) {
         M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
                   g.kidx, g.kinv, g.eoff};
         dim3 grd(L.nint * na, nrhs);
@@ -797,11 +817,11 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
         char *lbf = (char *)lam + L.mom_off * es * nrhs;
         if (mixed) {
             cudaFuncSetAttribute(k_m2l_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            k_m2l_fused<float><<<grd, 256, fsm, st>>>(A, (const float *)mbf, (const float *)L.E1, (const float *)L.pref,
+            k_m2l_fused<float><<<grd, kM2LThreads, fsm, st>>>(A, (const float *)mbf, (const float *)L.E1, (const float *)L.pref,
                                                       (float *)lbf, nrhs);
         } else {
             cudaFuncSetAttribute(k_m2l_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            k_m2l_fused<double><<<grd, 256, fsm, st>>>(A, (const double *)mbf, (const double *)L.E1,
+            k_m2l_fused<double><<<grd, kM2LThreads, fsm, st>>>(A, (const double *)mbf, (const double *)L.E1,
                                                        (const double *)L.pref, (double *)lbf, nrhs);
         }
         return 0;
