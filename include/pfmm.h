@@ -207,6 +207,33 @@ int pfmm_default_solve_opts(pfmm_solve_opts *opts);
 int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, double *x, int32_t nrhs,
                const pfmm_solve_opts *opts, pfmm_solve_info *info, void *stream);
 
+/* ---- batches of independent problems ------------------------------------------------------ */
+typedef struct pfmm_batch pfmm_batch;
+
+/* Choose the spatial degree m_x in [m_lo, m_hi] for a problem a priori: the smallest degree
+ * whose first dropped Chebyshev coefficient of the Gaussian factor (Eq. exp_coeffs_1d, at the
+ * smallest d_ab over the M2L levels of the problem's tree) is below tol times the leading one.
+ * *out = *base with m_x replaced.  Host only. */
+int pfmm_autotune_params(const pfmm_mesh *mesh, const pfmm_params *base, double tol, int32_t m_lo, int32_t m_hi,
+                         pfmm_params *out);
+
+/* Build n independent problems (one handle each, own tree, tables and nearfield).  With
+ * tune_engines != 0 the tensor-core and CUDA-core nearfield applies of every problem that can
+ * use tensor cores are timed and the faster engine is kept.  Synchronises `stream`. */
+int pfmm_build_trees_batched(int32_t n, const pfmm_mesh *meshes, const pfmm_params *params, int32_t tune_engines,
+                             void *stream, pfmm_batch **out);
+
+/* f[i] = V_h(i) w[i] for all problems i of the batch (device pointers, layouts as for
+ * pfmm_apply_V, nrhs[i] right-hand sides each).  The first call (and any call with different
+ * pointers or counts) sizes the workspaces and captures the whole batch into one CUDA graph, one
+ * branch per problem on a pool of up to 16 streams; later calls replay it on `stream`. */
+int pfmm_apply_V_batched(pfmm_batch *b, const double *const *w, double *const *f, const int32_t *nrhs,
+                         void *stream);
+
+int pfmm_batch_handle(pfmm_batch *b, int32_t i, pfmm_handle **h);  /* the i-th problem's handle */
+int32_t pfmm_batch_size(const pfmm_batch *b);
+void pfmm_batch_destroy(pfmm_batch *b);
+
 /* Release the handle and its device memory (NULL is ignored). */
 void pfmm_destroy(pfmm_handle *h);
 

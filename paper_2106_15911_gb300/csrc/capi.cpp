@@ -251,6 +251,8 @@ void prof_collect(pfmm_handle *H, int upto_pending)
 
 }  // namespace
 
+int pfmm::ensure_ws(pfmm_handle *H, int nrhs) { return ensure_workspace(H, nrhs); }
+
 // Tensor-core nearfield of op (0: V, 1: K) into fint (zeroed here): splits the FP64 input into
 // TF32 hi/lo parts in whi/wlo ([nrhs][E_t][cols] each), encodes their TMA views and launches.
 int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint,
@@ -698,7 +700,7 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
         ncolg = H->nv;
     }
     mark(1);
-    const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK);
+    const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK) && !H->nf_cuda_cores;
     if (tc) {
         if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_fint, st))) return rc;
     } else if (parts & PFMM_PART_NEAR)

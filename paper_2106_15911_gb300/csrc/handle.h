@@ -21,6 +21,8 @@ struct pfmm_handle;
 namespace pfmm {
 // tensor-core nearfield of op (0: V, 1: K) into fint; whi/wlo: [nrhs][E_t][cols] FP32 workspaces
 int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint, cudaStream_t st);
+// size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
+int ensure_ws(pfmm_handle *H, int nrhs);
 }  // namespace pfmm
 
 struct EvSet {
@@ -61,6 +63,7 @@ struct pfmm_handle {
 
     // tensor-core nearfield (mixed mode, untruncated panels of equal width, 2 steps per leaf)
     bool tcV = false, tcK = false;
+    bool nf_cuda_cores = false;     // engine override chosen by the batch autotuner
     float *d_AVhi = nullptr, *d_AVlo = nullptr, *d_AKhi = nullptr, *d_AKlo = nullptr;
     CUtensorMap mapAVhi{}, mapAVlo{}, mapAKhi{}, mapAKlo{};
     int colsV_u = 0, colsK_u = 0;  // common padded column count of the panels

@@ -64,7 +64,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     const size_t b_x = up256(n_in * H->es), b_f = up256(n_in * sizeof(double));
     const size_t n_mom = (size_t)nrhs * (H->mom_per_rhs > 0 ? H->mom_per_rhs : 1);
     const size_t b_mu = up256(n_mom * H->es);
-    const size_t b_w = H->tcV ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(float)) : 0;
+    const size_t b_w = (H->tcV && !H->nf_cuda_cores) ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(float)) : 0;
     const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w;
     const size_t min_chunk = (size_t)nrhs * 2 * H->na * H->na * H->ne * 64;  // M2L: two interval pairs of a 4^3 grid
     size_t need_T = 0;  // elements for the largest single-interval chunk over all levels
@@ -112,7 +112,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     // every buffer below is fully written before it is read, except the locals of the first two
     // intervals of each level, which launch_m2l clears; nothing depends on the previous call
     launch_permute_in(w, xint, H->mixed, nrhs, g, st);
-    if (H->tcV) {  // the same nearfield engine as pfmm_apply_V
+    if (H->tcV && !H->nf_cuda_cores) {  // the same nearfield engine as pfmm_apply_V
         if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, fint, st))) return rc;
     } else {
         launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs, g,

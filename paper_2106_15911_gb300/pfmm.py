@@ -79,6 +79,15 @@ SIGNATURES = {
     "pfmm_default_solve_opts": (ctypes.c_int, [ctypes.POINTER(pfmm_solve_opts)]),
     "pfmm_solve": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, ctypes.POINTER(pfmm_solve_opts),
                                   ctypes.POINTER(pfmm_solve_info), _VP]),
+    "pfmm_autotune_params": (ctypes.c_int, [ctypes.POINTER(pfmm_mesh), ctypes.POINTER(pfmm_params), ctypes.c_double,
+                                            _I, _I, ctypes.POINTER(pfmm_params)]),
+    "pfmm_build_trees_batched": (ctypes.c_int, [_I, ctypes.POINTER(pfmm_mesh), ctypes.POINTER(pfmm_params), _I, _VP,
+                                                ctypes.POINTER(ctypes.c_void_p)]),
+    "pfmm_apply_V_batched": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                            ctypes.POINTER(ctypes.c_int32), _VP]),
+    "pfmm_batch_handle": (ctypes.c_int, [_VP, _I, ctypes.POINTER(ctypes.c_void_p)]),
+    "pfmm_batch_size": (ctypes.c_int32, [_VP]),
+    "pfmm_batch_destroy": (None, [_VP]),
     "pfmm_destroy": (None, [_VP]),
     "pfmm_last_error": (ctypes.c_char_p, []),
 }
@@ -243,6 +252,67 @@ def pfmm_solve(h, formulation: int, g, x, nrhs: int, opts: pfmm_solve_opts | Non
         _check(rc)
     return dict(iterations=info.iterations, outer=info.outer, rel_res=info.rel_res, seconds=info.seconds,
                 converged=rc == PFMM_OK)
+
+
+def _mesh_struct(vertices, triangles, T, n_steps, alpha):
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    Tr = np.ascontiguousarray(triangles, dtype=np.int32)
+    m = pfmm_mesh(V.shape[0], Tr.shape[0], V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  Tr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), float(T), int(n_steps), float(alpha))
+    m._keep = (V, Tr)
+    return m
+
+
+def pfmm_autotune_params(vertices, triangles, T, n_steps, alpha=1.0, base: pfmm_params | None = None, tol=1e-6,
+                         m_lo=4, m_hi=8) -> pfmm_params:
+    m = _mesh_struct(vertices, triangles, T, n_steps, alpha)
+    out = pfmm_params()
+    _check(lib().pfmm_autotune_params(ctypes.byref(m), ctypes.byref(base or pfmm_default_params()), float(tol),
+                                      int(m_lo), int(m_hi), ctypes.byref(out)))
+    return out
+
+
+class Batch:
+    """A batch of independent problems applied through one captured CUDA graph."""
+
+    def __init__(self, problems, tune_engines=False, stream=None):
+        """problems: list of (vertices, triangles, T, n_steps, alpha, pfmm_params)."""
+        n = len(problems)
+        meshes = (pfmm_mesh * n)()
+        params = (pfmm_params * n)()
+        self._keep = []
+        for i, (V, Tr, T, Et, alpha, prm) in enumerate(problems):
+            m = _mesh_struct(V, Tr, T, Et, alpha)
+            self._keep.append(m._keep)
+            meshes[i] = m
+            params[i] = prm
+        self.b = ctypes.c_void_p()
+        _check(lib().pfmm_build_trees_batched(n, meshes, params, 1 if tune_engines else 0, _stream(stream),
+                                              ctypes.byref(self.b)))
+        self.n = n
+
+    def handle(self, i):
+        h = ctypes.c_void_p()
+        _check(lib().pfmm_batch_handle(self.b, int(i), ctypes.byref(h)))
+        return h
+
+    def apply_V(self, ws, fs, stream=None):
+        n = self.n
+        wp = (ctypes.c_void_p * n)(*[_ptr(w) for w in ws])
+        fp = (ctypes.c_void_p * n)(*[_ptr(f) for f in fs])
+        nr = (ctypes.c_int32 * n)(*[int(w.shape[0]) for w in ws])
+        _check(lib().pfmm_apply_V_batched(self.b, wp, fp, nr, _stream(stream)))
+
+    def close(self):
+        if self.b:
+            lib().pfmm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pfmm_destroy(h):
