@@ -120,6 +120,59 @@ def _solve_comparison(dev):
             "solution_rel_diff": diff}
 
 
+def _batch_comparison(dev, n_problems, seed=3):
+    """Ragged batch of independent problems (cube and cube-sphere surfaces alternating, triangle
+    counts drawn from {768, 1536, 3072, 6144, 12288}, 32..256 steps, 1..8 right-hand sides,
+    degrees chosen by the autotuner for 1e-5, mixed precision): one replay of the captured CUDA
+    graph vs the same applies issued one after the other on one stream."""
+    import numpy as np
+    import torch
+
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_mesh, cube_sphere_mesh, random_density
+
+    rng = np.random.default_rng(seed)
+    probs, dofs = [], 0
+    for i in range(n_problems):
+        n_a, split = [(8, "diag"), (8, "cross"), (16, "diag"), (16, "cross"), (32, "diag")][int(rng.integers(0, 5))]
+        V, T = (cube_mesh if i % 2 == 0 else cube_sphere_mesh)(n_a, split)
+        Et = int(rng.choice([32, 64, 128, 256]))
+        nr = int(rng.integers(1, 9))
+        prm = P.pfmm_default_params()
+        prm.precision = P.PFMM_MIXED
+        prm = P.pfmm_autotune_params(V, T, 1.0, Et, base=prm, tol=1e-5, m_lo=4, m_hi=8)
+        probs.append((V, T, 1.0, Et, 1.0, prm, nr))
+        dofs += T.shape[0] * Et * nr
+    tb = time.perf_counter()
+    B = P.Batch([p[:6] for p in probs], tune_engines=True)
+    t_build = time.perf_counter() - tb
+    ws = [torch.tensor(random_density(p[3], p[1].shape[0], p[6], seed=100 + i), device=dev) for i, p in enumerate(probs)]
+    fs = [torch.empty_like(w) for w in ws]
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        B.apply_V(ws, fs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        B.apply_V(ws, fs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / 5
+    hs = [B.handle(i) for i in range(len(probs))]
+    e0.record(stream)
+    for _ in range(5):
+        for h, w, f in zip(hs, ws, fs):
+            P.pfmm_apply_V(h, w, f, w.shape[0], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 5
+    B.close()
+    return {"workload": f"{n_problems} problems, 768..12288 triangles, 32..256 steps, 1..8 rhs, mixed, autotuned m_x",
+            "space_time_dofs": dofs, "graph_ms": t_graph, "sequential_ms": t_seq,
+            "dofs_per_s": dofs / (t_graph * 1e-3), "build_s": t_build, "m_x": [int(p[5].m_x) for p in probs]}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -153,6 +206,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
+    ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
     ap.add_argument("--et", type=int, default=ET, help="profiling only: time steps")
     args = ap.parse_args()
@@ -305,6 +359,9 @@ def main():
     solve = None
     if rank == 0 and not args.no_solve:
         solve = _solve_comparison(dev)
+    batch = None
+    if rank == 0 and args.batch > 0:
+        batch = _batch_comparison(dev, args.batch)
 
     launches = 3 * info["p"]  # permute in/out, nearfield, S2M, L2T, (p-2) M2M, (p-1) M2L, (p-2) L2L
     cpu = None
@@ -324,7 +381,7 @@ def main():
                            "parallelism": f"replicas x{world}", "build_s": t_build},
                 "phases_ms": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": _clocks_summary(samples), "fp64": fp64_line,
-                "solve": solve}
+                "solve": solve, "batch": batch}
         print(json.dumps(line), flush=True)
     op.close()
     if world > 1:
