@@ -177,6 +177,8 @@ int pfmm_apply_V_noalloc(pfmm_handle *h, const double *w, double *f, int32_t nrh
 #define PFMM_DIRECT 0    /* V_h w = (1/2 M_h + K_h) g  (Section 2, Eq. 02:linear:system) */
 #define PFMM_INDIRECT 1  /* V_h w = M_h g              (single-layer ansatz) */
 
+typedef struct pfmm_mpnn pfmm_mpnn;  /* learned preconditioner (see the end of this header) */
+
 typedef struct pfmm_solve_opts {
     double tol;           /* stop when ||b - V_h x||_2 <= tol ||b||_2 (default 1e-8) */
     int32_t restart;      /* FGMRES restart length m (default 50, at most 500) */
@@ -184,6 +186,11 @@ typedef struct pfmm_solve_opts {
     pfmm_handle *refine;  /* optional FP64 handle of the same problem: GMRES-IR (default NULL) */
     double inner_tol;     /* GMRES-IR: relative tolerance of each inner solve (default 1e-4) */
     int32_t max_outer;    /* GMRES-IR: cap on refinement steps (default 20) */
+    pfmm_mpnn *precond;   /* optional learned right preconditioner z = P(v); NULL: identity */
+    double *rec_r;        /* optional device [rec_cap][E_t][E_x]: recorded residuals r_k = b - V x_k */
+    double *rec_e;        /* optional (nullable) device [rec_cap][E_t][E_x]: errors e_k = x - x_k */
+    int32_t rec_cap;      /* number of (r, e) slots (0: no recording; needs refine == NULL) */
+    int32_t rec_every;    /* record at every rec_every-th Arnoldi step of each cycle (default 5) */
 } pfmm_solve_opts;
 
 typedef struct pfmm_solve_info {
@@ -191,6 +198,9 @@ typedef struct pfmm_solve_info {
     int32_t outer;        /* refinement steps (GMRES-IR) */
     double rel_res;       /* largest final ||b - V_h x|| / ||b|| (FP64 operator when refining) */
     double seconds;       /* wall time of the call */
+    int32_t recorded;     /* (r, e) pairs written to rec_r / rec_e */
+    int32_t precond_off;  /* cycles after which the preconditioner was dropped (non-finite output
+                           * or a cycle that cut the residual by less than 10 %) */
 } pfmm_solve_info;
 
 int pfmm_default_solve_opts(pfmm_solve_opts *opts);
@@ -200,6 +210,13 @@ int pfmm_default_solve_opts(pfmm_solve_opts *opts);
  * classical Gram-Schmidt applied twice), all Krylov vectors FP64 on the device.  With
  * opts->refine (an FP64 handle of the same mesh and steps) the residual is formed in FP64 with
  * it and inner FGMRES solves run with h (typically PFMM_MIXED): iterative refinement.
+ * With opts->precond the Krylov directions are z_j = P(v_j) (flexible GMRES, so P may be
+ * nonlinear); the residuals are still those of the exact operator, and P is dropped for the rest
+ * of the solve when it yields a non-finite vector or a cycle that cuts the residual by < 10 %.
+ * Recording (rec_cap > 0, plain FGMRES only): at Arnoldi steps j = 0, rec_every, 2 rec_every ...
+ * of every cycle, while the residual is above 100 tol ||b||, the iterate x_j and its residual
+ * r_j = b - V_h x_j (from the Arnoldi relation) are kept; after convergence rec_e holds x - x_j:
+ * the (residual, error) pairs a preconditioner is trained on.
  *   g: device [nrhs][E_t][N_v] (p0 in time, p1 in space, already projected), x: device
  *   [nrhs][E_t][E_x] (overwritten).  Synchronises `stream`; allocates its Krylov workspace
  *   ((2 restart + 4) E_t E_x doubles).  Returns PFMM_ERR_NOT_CONVERGED when a cap is reached
@@ -233,6 +250,56 @@ int pfmm_apply_V_batched(pfmm_batch *b, const double *const *w, double *const *f
 int pfmm_batch_handle(pfmm_batch *b, int32_t i, pfmm_handle **h);  /* the i-th problem's handle */
 int32_t pfmm_batch_size(const pfmm_batch *b);
 void pfmm_batch_destroy(pfmm_batch *b);
+
+/* ---- learned preconditioner ---------------------------------------------------------------
+ * The paper has no counterpart (it solves with unpreconditioned GMRES).  A message-passing
+ * network over the triangle edge adjacency acts on each time slice v_t ([E_x] values) of a vector:
+ *   x_i = (v_i / s_t, |gamma_i| / mean area, outward unit normal n_i, (t + 1/2) / E_t),
+ *   s_t = RMS(v_t) + 1e-30,  h^0 = SiLU(W_0^T x + b_0),
+ *   h^{l+1} = h^l + SiLU(W_s^T h^l + W_n^T mean_{j ~ i} h^l_j + b^l)  (l < layers),
+ *   z_i = c s_t (w_o . h^L_i + b_o),  j ~ i: triangles sharing an edge with i.
+ * Weights are used in BF16 (FP32 master copies for Adam), arithmetic is FP32.  Parameters
+ * (FP32, this order, matrices input-major M[k][o]): W_0 [6][W], b_0 [W], per layer
+ * {W_s [W][W], W_n [W][W], b [W]}, w_o [W], b_o.  Training data are residual slices r_b recorded
+ * by pfmm_solve (with their errors e_b, V_h e = r).  Two losses over a batch of S slices:
+ *   same-step form (a pFMM handle h of the mesh given): the correction wanted for r_b is
+ *     c_b = A_0^{-1} r_b, A_0 the same-step (time-block-diagonal) nearfield block of V_h, measured
+ *     in the residual norm:  (1/S) sum_b ||A_0 z(r_b) - r_b||^2 / (||r_b||^2 + 1e-30);
+ *     the gradient uses A_0 for A_0^T (symmetric up to the singular quadrature error);
+ *   error form (h NULL):  (1/S) sum_b ||z(r_b) - e_b||^2 / (||e_b||^2 + 1e-30). */
+
+/* Network for a mesh (host arrays copied; E_t = mesh->n_steps).  width: 16, 32 or 64; layers
+ * 0..16; weights drawn from `seed`.  The output scale c is unset (0) until set or estimated by
+ * the first pfmm_mpnn_train call. */
+int pfmm_mpnn_create(const pfmm_mesh *mesh, int32_t width, int32_t layers, uint64_t seed, pfmm_mpnn **out);
+int64_t pfmm_mpnn_num_params(const pfmm_mpnn *net);
+/* FP32 master parameters to / from host memory (n = pfmm_mpnn_num_params); set resets Adam. */
+int pfmm_mpnn_get_params(const pfmm_mpnn *net, float *host, int64_t n);
+int pfmm_mpnn_set_params(pfmm_mpnn *net, const float *host, int64_t n);
+int pfmm_mpnn_set_output_scale(pfmm_mpnn *net, float c);
+int pfmm_mpnn_get_output_scale(const pfmm_mpnn *net, float *c);
+/* z = P(v) for nvec vectors, v and z device [nvec][E_t][E_x] FP64 (z overwritten). */
+int pfmm_mpnn_apply(pfmm_mpnn *net, const double *v, double *z, int32_t nvec, void *stream);
+/* Loss and gradient w.r.t. the parameters for the slices slices[0..n) (host array of indices
+ * s into the device arrays R, E of [*][E_t][E_x] FP64: slice s holds elements s E_x .. s E_x +
+ * E_x - 1 and has step s mod E_t; the caller guarantees s < the arrays' slice count).  h: a
+ * handle of the same mesh and E_t for the same-step form, NULL for the error form (then E is
+ * required; otherwise it may be NULL).  loss / grad (host, nullable) receive the values; no
+ * parameter update.  Synchronises `stream`. */
+int pfmm_mpnn_loss_grad(pfmm_mpnn *net, pfmm_handle *h, const double *R, const double *E, const int32_t *slices,
+                        int32_t nslices, float *loss, float *grad, void *stream);
+/* `steps` Adam steps on batches of batch_slices slices drawn uniformly (generator seeded by
+ * `seed`) from the nvec recorded vectors R (and E), device [nvec][E_t][E_x] FP64, with the loss
+ * form chosen by h as for pfmm_mpnn_loss_grad; step size lr, cosine-decayed to lr / 10.  An unset
+ * output scale is first estimated from one batch.  loss_history (host, nullable) receives each
+ * step's loss.  Synchronises `stream`. */
+int pfmm_mpnn_train(pfmm_mpnn *net, pfmm_handle *h, const double *R, const double *E, int64_t nvec, int32_t steps,
+                    int32_t batch_slices, float lr, uint64_t seed, float *loss_history, void *stream);
+/* Reads and clears the network's error word: PFMM_ERR_TIMEOUT when a bounded wait of its
+ * tensor-core kernels gave up since the last check (pfmm_mpnn_apply is asynchronous; training
+ * and pfmm_solve check on return).  Synchronises the device. */
+int pfmm_mpnn_check(pfmm_mpnn *net);
+void pfmm_mpnn_destroy(pfmm_mpnn *net);
 
 /* Release the handle and its device memory (NULL is ignored). */
 void pfmm_destroy(pfmm_handle *h);

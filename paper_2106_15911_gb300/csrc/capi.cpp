@@ -295,6 +295,26 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *wh
     return PFMM_OK;
 }
 
+// f_b = A_0 x_b for ns independent slices b (user triangle order, [ns][E_x] FP64): the stored
+// nearfield block of offset d = 0 (same time step, neighbouring leaf boxes), applied with each
+// slice taken as its own step.  xint: ns E_x elements of the arithmetic type, fint: ns E_x doubles.
+int pfmm::apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, void *xint, double *fint, cudaStream_t st)
+{
+    ApplyGeo g{};
+    g.nt = H->nt;
+    g.nv = H->nv;
+    g.Et = ns;
+    g.ls = 1;
+    g.perm = H->d_perm;
+    launch_permute_in(x, xint, H->mixed, 1, g, st);
+    launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, 1, g, fint, st,
+                    1);
+    launch_permute_out(fint, f, 1, g, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, std::string("same-step apply: ") + cudaGetErrorString(e));
+    return PFMM_OK;
+}
+
 extern "C" {
 
 const char *pfmm_last_error(void) { return g_err.c_str(); }

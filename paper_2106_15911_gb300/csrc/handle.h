@@ -23,6 +23,11 @@ namespace pfmm {
 int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint, cudaStream_t st);
 // size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
 int ensure_ws(pfmm_handle *H, int nrhs);
+// f_b = A_0 x_b (same-step nearfield block) for ns slices [ns][E_x] in user order; xint holds
+// ns E_x elements of the arithmetic type, fint ns E_x doubles
+int apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, void *xint, double *fint, cudaStream_t st);
+// triangles and time steps a learned preconditioner was built for
+void mpnn_dims(const pfmm_mpnn *net, int *nt, int *Et);
 }  // namespace pfmm
 
 struct EvSet {

@@ -77,7 +77,7 @@ template <typename S>
 __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const int *__restrict__ colidx,
                                                     const int *__restrict__ tiles, const PanelGPU *__restrict__ panels,
                                                     const S *__restrict__ x, int ncolg, int Et, int ls, int nint,
-                                                    double *__restrict__ f, int nt, int kop)
+                                                    double *__restrict__ f, int nt, int kop, int ndmax)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
     constexpr bool kFloat = sizeof(S) == 4;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
             acc[i][j] = S(0);
             accd[i][j] = 0.0;
         }
-    const int nd = ls + s + 1;
+    const int nd = min(ls + s + 1, ndmax);
     int ktiles = 0;
     for (int d = 0; d < nd; ++d) {
         const S *Ad = A + ((size_t)d * P.rows_pad + r0) * ncp;
@@ -161,16 +161,16 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
 
 void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
                      const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
-                     cudaStream_t st)
+                     cudaStream_t st, int ndmax)
 {
     int nint = g.Et / g.ls;
     dim3 grd(ntiles, g.ls * ((nint + 63) / 64), nrhs);
     if (mixed)
         k_nf_apply<float><<<grd, 256, 0, st>>>((const float *)A, colidx, tiles, panels, (const float *)x, ncolg, g.Et,
-                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0);
+                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax);
     else
         k_nf_apply<double><<<grd, 256, 0, st>>>((const double *)A, colidx, tiles, panels, (const double *)x, ncolg,
-                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0);
+                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax);
 }
 
 // ------------------------------------------------------------------------------------------

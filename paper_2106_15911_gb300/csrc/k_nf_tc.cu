@@ -23,10 +23,13 @@
 
 #include "kernels.h"
 #include "nf_tc.h"
+#include "tc_ptx.cuh"
 
 namespace pfmm {
 
 namespace {
+
+using namespace tc;
 
 constexpr int BM = 128, BK = 32;                   // BK fp32 = 128 bytes = one swizzle atom
 constexpr int A_TILE = BM * BK * 4;                // 16 KB
@@ -34,45 +37,6 @@ constexpr int B_HALF = 128 * BK * 4;               // 16 KB (one phase)
 constexpr int STAGE_BYTES = 2 * A_TILE + 4 * B_HALF;  // A_hi, A_lo, B_hi (2 halves), B_lo (2 halves)
 constexpr int NSTAGE = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // 2 s per wait
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-
-// bounded wait on the given phase parity; false after the deadline
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint64_t deadline)
-{
-    uint32_t ok = 0;
-    while (true) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(su32(b)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (gtimer() > deadline) return false;
-    }
-}
 
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
 {
@@ -92,18 +56,6 @@ __device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int x,
         : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
-    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
-    d |= (uint64_t)1 << 46;                    // descriptor version
-    d |= (uint64_t)2 << 61;                    // SWIZZLE_128B
-    return d;
-}
-
 // instruction descriptor: kind::tf32, FP32 accumulate, A and B K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 {
@@ -121,25 +73,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, ui
             "r"(dt),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *b)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 struct Item {

@@ -4,8 +4,14 @@
 //
 //   b = (1/2 M_h + K_h) g   (direct formulation, Section 2)   or   b = M_h g   (indirect)
 //   FGMRES(m): right-preconditioned, Arnoldi with classical Gram-Schmidt applied twice,
-//              Givens rotations on the host, x0 = 0 (Saad 1993).  The preconditioner slot is the
-//              identity.
+//              Givens rotations on the host, x0 = 0 (Saad 1993).  The preconditioner is the
+//              identity or a learned network z = P(v) (mpnn.cu); P is dropped for the rest of
+//              the solve when it yields a non-finite direction or a cycle that cuts the residual
+//              by less than 10 %, so plain FGMRES is the fallback.
+//   Recording: at every rec_every-th Arnoldi step j of a cycle, x_j = x + Z_j y_j and
+//              r_j = V_{j+1} (beta e_1 - Hbar_j y_j) (the Arnoldi relation, no extra matvec) are
+//              stored; once the right-hand side is solved the stored iterates become errors
+//              x - x_j.
 //   GMRES-IR:  when opts->refine is an FP64 handle of the same problem, the outer loop computes
 //              r = b - V_h x with it in FP64 and the inner FGMRES runs with the (mixed-precision)
 //              handle h to opts->inner_tol, then x += d (Carson & Higham 2017, 2018).
@@ -108,7 +114,8 @@ __global__ void k_finite(const double *__restrict__ x, size_t n, int *__restrict
 unsigned nblk(size_t n) { return (unsigned)((n + 255) / 256); }
 
 struct Ws {
-    double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *d = nullptr, *part = nullptr, *hv = nullptr;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *d = nullptr, *part = nullptr, *hv = nullptr,
+           *cy = nullptr;
     int *bad = nullptr;
     std::vector<void *> mem;
     ~Ws()
@@ -134,16 +141,36 @@ int dots(Ws &W, const double *V, size_t ldv, int nvec, const double *w, size_t n
     return PFMM_OK;
 }
 
+struct Rec {
+    double *R = nullptr, *E = nullptr;
+    int cap = 0, every = 5, count = 0;
+    double floor_abs = 0.0;  // record only while the residual norm is above this
+};
+
+struct Prec {
+    pfmm_mpnn *net = nullptr;
+    bool on = false;
+    int dropped = 0;
+};
+
 // one right-hand side: FGMRES(m) on op(h) for V x = b, x updated in place (x0 as given).
 // Returns PFMM_OK when ||b - V x|| <= tol_abs, PFMM_ERR_NOT_CONVERGED when max_it was reached.
-int fgmres(pfmm_handle *h, const double *b, double *x, double tol_abs, int restart, int max_it, int *iters, Ws &W,
-           size_t n, cudaStream_t st, double *res_out)
+int fgmres(pfmm_handle *h, Prec &P, Rec *rec, const double *b, double *x, double tol_abs, int restart, int max_it,
+           int *iters, Ws &W, size_t n, cudaStream_t st, double *res_out)
 {
     const size_t ld = n;
-    std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), gv(restart + 1), hh(restart + 2),
-        y(restart);
+    std::vector<double> H((size_t)(restart + 1) * restart), Hraw((size_t)(restart + 1) * restart), cs(restart),
+        sn(restart), gv(restart + 1), hh(restart + 2), y(restart), c(restart + 1);
     int total = 0;
-    double beta = 0.0;
+    double beta = 0.0, beta_prev = HUGE_VAL;
+    // y = R_j^{-1} g_j from the rotated Hessenberg rows 0 .. j-1
+    auto solve_r = [&](int j) {
+        for (int i = j - 1; i >= 0; --i) {
+            double s = gv[i];
+            for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * restart + k] * y[k];
+            y[i] = s / H[(size_t)i * restart + i];
+        }
+    };
     while (true) {
         // r = b - V x
         int rc = pfmm_apply_V(h, x, W.w, 1, st);
@@ -154,53 +181,89 @@ int fgmres(pfmm_handle *h, const double *b, double *x, double tol_abs, int resta
         beta = std::sqrt(d2);
         *res_out = beta;
         if (!(beta > tol_abs) || total >= max_it) break;
+        if (P.on && beta > 0.9 * beta_prev) {  // the last preconditioned cycle stagnated
+            P.on = false;
+            ++P.dropped;
+        }
+        beta_prev = beta;
         k_scale_to<<<nblk(n), 256, 0, st>>>(1.0 / beta, W.w, W.V, n);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
         int j = 0;
-        for (; j < restart && total < max_it; ++j, ++total) {
-            // z_j = P(v_j): identity preconditioner; w = V_h z_j
-            SCK(cudaMemcpyAsync(W.Z + (size_t)j * ld, W.V + (size_t)j * ld, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            if ((rc = pfmm_apply_V(h, W.Z + (size_t)j * ld, W.w, 1, st))) return rc;
+        while (j < restart && total < max_it) {
+            if (rec && rec->count < rec->cap && j % rec->every == 0 && std::fabs(gv[j]) > rec->floor_abs) {
+                // x_j and r_j of the current cycle into the next slot
+                double *Rs = rec->R + (size_t)rec->count * n, *Es = rec->E ? rec->E + (size_t)rec->count * n : nullptr;
+                if (Es) SCK(cudaMemcpyAsync(Es, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                if (j == 0) {
+                    k_scale_to<<<nblk(n), 256, 0, st>>>(beta, W.V, Rs, n);
+                } else {
+                    solve_r(j);
+                    for (int i = 0; i <= j; ++i) {
+                        double s = i == 0 ? beta : 0.0;
+                        for (int k = 0; k < j; ++k) s -= Hraw[(size_t)i * restart + k] * y[k];
+                        c[i] = s;
+                    }
+                    SCK(cudaMemcpyAsync(W.cy, c.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+                    SCK(cudaMemcpyAsync(W.cy + restart + 1, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
+                    SCK(cudaMemsetAsync(Rs, 0, n * sizeof(double), st));
+                    k_add_combo<<<nblk(n), 256, 0, st>>>(W.V, ld, j + 1, W.cy, Rs, n);
+                    if (Es) k_add_combo<<<nblk(n), 256, 0, st>>>(W.Z, ld, j, W.cy + restart + 1, Es, n);
+                    SCK(cudaStreamSynchronize(st));  // c and y are reused by the next record
+                }
+                ++rec->count;
+            }
+            // z_j = P(v_j); w = V_h z_j
+            double *zj = W.Z + (size_t)j * ld;
+            if (P.on) {
+                if ((rc = pfmm_mpnn_apply(P.net, W.V + (size_t)j * ld, zj, 1, st))) return rc;
+            } else {
+                SCK(cudaMemcpyAsync(zj, W.V + (size_t)j * ld, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            }
+            if ((rc = pfmm_apply_V(h, zj, W.w, 1, st))) return rc;
             // classical Gram-Schmidt, twice
             for (int i = 0; i <= j; ++i) H[(size_t)i * restart + j] = 0.0;
-            for (int pass = 0; pass < 2; ++pass) {
+            bool finite = true;
+            for (int pass = 0; pass < 2 && finite; ++pass) {
                 if ((rc = dots(W, W.V, ld, j + 1, W.w, n, hh.data(), st))) return rc;
+                for (int i = 0; i <= j; ++i) finite = finite && std::isfinite(hh[i]);
+                if (!finite) break;
                 SCK(cudaMemcpyAsync(W.hv, hh.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
                 k_sub_combo<<<nblk(n), 256, 0, st>>>(W.V, ld, j + 1, W.hv, W.w, n);
                 for (int i = 0; i <= j; ++i) H[(size_t)i * restart + j] += hh[i];
             }
-            double nw2;
-            if ((rc = dots(W, W.w, ld, 1, W.w, n, &nw2, st))) return rc;
+            double nw2 = 0.0;
+            if (finite && (rc = dots(W, W.w, ld, 1, W.w, n, &nw2, st))) return rc;
+            if (!finite || !std::isfinite(nw2)) {
+                if (!P.on) return set_error(PFMM_ERR_NONFINITE, "non-finite Krylov vector (operator output)");
+                P.on = false;  // the network gave a non-finite direction: redo this step without it
+                ++P.dropped;
+                continue;
+            }
             const double hn = std::sqrt(nw2);
             H[(size_t)(j + 1) * restart + j] = hn;
+            for (int i = 0; i <= j + 1; ++i) Hraw[(size_t)i * restart + j] = H[(size_t)i * restart + j];
             if (hn > 0.0) k_scale_to<<<nblk(n), 256, 0, st>>>(1.0 / hn, W.w, W.V + (size_t)(j + 1) * ld, n);
             // Givens rotations
             for (int i = 0; i < j; ++i) {
-                double a = H[(size_t)i * restart + j], c = H[(size_t)(i + 1) * restart + j];
-                H[(size_t)i * restart + j] = cs[i] * a + sn[i] * c;
-                H[(size_t)(i + 1) * restart + j] = -sn[i] * a + cs[i] * c;
+                double a = H[(size_t)i * restart + j], cc = H[(size_t)(i + 1) * restart + j];
+                H[(size_t)i * restart + j] = cs[i] * a + sn[i] * cc;
+                H[(size_t)(i + 1) * restart + j] = -sn[i] * a + cs[i] * cc;
             }
-            double a = H[(size_t)j * restart + j], c = H[(size_t)(j + 1) * restart + j];
-            double den = std::hypot(a, c);
+            double a = H[(size_t)j * restart + j], cc = H[(size_t)(j + 1) * restart + j];
+            double den = std::hypot(a, cc);
             cs[j] = den > 0 ? a / den : 1.0;
-            sn[j] = den > 0 ? c / den : 0.0;
+            sn[j] = den > 0 ? cc / den : 0.0;
             H[(size_t)j * restart + j] = den;
             H[(size_t)(j + 1) * restart + j] = 0.0;
             gv[j + 1] = -sn[j] * gv[j];
             gv[j] = cs[j] * gv[j];
-            if (std::fabs(gv[j + 1]) <= tol_abs || hn == 0.0) {
-                ++j;
-                ++total;
-                break;
-            }
+            ++j;
+            ++total;
+            if (std::fabs(gv[j]) <= tol_abs || hn == 0.0) break;
         }
         // y = R^{-1} g, x += Z y
-        for (int i = j - 1; i >= 0; --i) {
-            double s = gv[i];
-            for (int k = i + 1; k < j; ++k) s -= H[(size_t)i * restart + k] * y[k];
-            y[i] = s / H[(size_t)i * restart + i];
-        }
+        solve_r(j);
         SCK(cudaMemcpyAsync(W.hv, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
         k_add_combo<<<nblk(n), 256, 0, st>>>(W.Z, ld, j, W.hv, x, n);
         SCK(cudaGetLastError());
@@ -224,14 +287,31 @@ extern "C" int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, 
     pfmm_handle *h64 = o.refine;
     if (h64 && (h64->nt != h->nt || h64->Et != h->Et || h64->nv != h->nv))
         return set_error(PFMM_ERR_INVALID_ARG, "refinement handle describes a different problem");
+    if (o.rec_cap < 0 || (o.rec_cap > 0 && (!o.rec_r || h64 || o.rec_every < 1)))
+        return set_error(PFMM_ERR_INVALID_ARG, "recording needs rec_r, rec_every >= 1 and no refine handle");
+    if (o.precond) {
+        int pnt = 0, pEt = 0;
+        pfmm::mpnn_dims(o.precond, &pnt, &pEt);
+        if (pnt != h->nt || pEt != h->Et) return set_error(PFMM_ERR_INVALID_ARG, "the preconditioner is for another mesh");
+    }
     cudaStream_t st = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     const size_t n = (size_t)h->Et * h->nt, ng = (size_t)h->Et * h->nv;
+    Prec P;
+    P.net = o.precond;
+    P.on = o.precond != nullptr;
+    Rec rec;
+    rec.R = o.rec_r;
+    rec.E = o.rec_e;
+    rec.cap = o.rec_cap;
+    rec.every = o.rec_every;
+    Rec *recp = o.rec_cap > 0 ? &rec : nullptr;
     Ws W;
     int rc;
     if ((rc = W.get(&W.V, (size_t)(o.restart + 1) * n)) || (rc = W.get(&W.Z, (size_t)o.restart * n)) ||
         (rc = W.get(&W.w, n)) || (rc = W.get(&W.r, n)) || (rc = W.get(&W.d, n)) ||
-        (rc = W.get(&W.part, (size_t)kDotBlocks * (o.restart + 2))) || (rc = W.get(&W.hv, (size_t)o.restart + 2)))
+        (rc = W.get(&W.part, (size_t)kDotBlocks * (o.restart + 2))) || (rc = W.get(&W.hv, (size_t)o.restart + 2)) ||
+        (rc = W.get(&W.cy, 2 * (size_t)o.restart + 2)))
         return rc;
     SCK(cudaMalloc((void **)&W.bad, sizeof(int)));
     W.mem.push_back(W.bad);
@@ -263,14 +343,22 @@ extern "C" int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, 
         double res = bn;
         if (bn == 0.0) continue;
         if (!h64) {
-            int s = fgmres(h, b, xr, o.tol * bn, o.restart, o.max_it, &iters, W, n, st, &res);
+            const int first = rec.count;
+            rec.floor_abs = 100.0 * o.tol * bn;
+            int s = fgmres(h, P, recp, b, xr, o.tol * bn, o.restart, o.max_it, &iters, W, n, st, &res);
             if (s == PFMM_ERR_NOT_CONVERGED) status = s;
             else if (s) return s;
+            for (int k = first; rec.E && k < rec.count; ++k)  // stored iterates -> errors x - x_k
+                k_axpby<<<nblk(n), 256, 0, st>>>(1.0, xr, -1.0, rec.E + (size_t)k * n, n);
         } else {
             // GMRES-IR: FP64 residual with h64, inner solve with h
             for (int it = 0;; ++it) {
-                if ((rc = pfmm_apply_V(h64, xr, W.r, 1, st))) return rc;
-                k_axpby<<<nblk(n), 256, 0, st>>>(1.0, b, -1.0, W.r, n);
+                if (it == 0) {  // x = 0: the residual is b itself
+                    SCK(cudaMemcpyAsync(W.r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                } else {
+                    if ((rc = pfmm_apply_V(h64, xr, W.r, 1, st))) return rc;
+                    k_axpby<<<nblk(n), 256, 0, st>>>(1.0, b, -1.0, W.r, n);
+                }
                 double rn2;
                 if ((rc = dots(W, W.r, n, 1, W.r, n, &rn2, st))) return rc;
                 res = std::sqrt(rn2);
@@ -282,7 +370,8 @@ extern "C" int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, 
                 ++outer;
                 SCK(cudaMemsetAsync(W.d, 0, n * sizeof(double), st));
                 double ires = res;
-                int s = fgmres(h, W.r, W.d, o.inner_tol * res, o.restart, o.max_it - iters, &iters, W, n, st, &ires);
+                int s = fgmres(h, P, nullptr, W.r, W.d, o.inner_tol * res, o.restart, o.max_it - iters, &iters, W, n,
+                               st, &ires);
                 if (s && s != PFMM_ERR_NOT_CONVERGED) return s;
                 k_axpby<<<nblk(n), 256, 0, st>>>(1.0, W.d, 1.0, xr, n);
             }
@@ -290,11 +379,14 @@ extern "C" int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, 
         worst = std::max(worst, res / bn);
     }
     SCK(cudaStreamSynchronize(st));
+    if (o.precond && (rc = pfmm_mpnn_check(o.precond))) return rc;
     if (info) {
         info->iterations = iters;
         info->outer = outer;
         info->rel_res = worst;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->recorded = rec.count;
+        info->precond_off = P.dropped;
     }
     if (status) set_error(status, "the solver reached max_it / max_outer before the tolerance");
     return status;
@@ -309,5 +401,10 @@ extern "C" int pfmm_default_solve_opts(pfmm_solve_opts *o)
     o->refine = nullptr;
     o->inner_tol = 1e-4;
     o->max_outer = 20;
+    o->precond = nullptr;
+    o->rec_r = nullptr;
+    o->rec_e = nullptr;
+    o->rec_cap = 0;
+    o->rec_every = 5;
     return PFMM_OK;
 }

@@ -47,12 +47,14 @@ class pfmm_info(ctypes.Structure):
 
 class pfmm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_it", ctypes.c_int32),
-                ("refine", ctypes.c_void_p), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+                ("refine", ctypes.c_void_p), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
+                ("precond", ctypes.c_void_p), ("rec_r", ctypes.c_void_p), ("rec_e", ctypes.c_void_p),
+                ("rec_cap", ctypes.c_int32), ("rec_every", ctypes.c_int32)]
 
 
 class pfmm_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("rel_res", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("recorded", ctypes.c_int32), ("precond_off", ctypes.c_int32)]
 
 
 PFMM_DIRECT, PFMM_INDIRECT = 0, 1
@@ -88,6 +90,20 @@ SIGNATURES = {
     "pfmm_batch_handle": (ctypes.c_int, [_VP, _I, ctypes.POINTER(ctypes.c_void_p)]),
     "pfmm_batch_size": (ctypes.c_int32, [_VP]),
     "pfmm_batch_destroy": (None, [_VP]),
+    "pfmm_mpnn_create": (ctypes.c_int, [ctypes.POINTER(pfmm_mesh), _I, _I, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "pfmm_mpnn_num_params": (ctypes.c_int64, [_VP]),
+    "pfmm_mpnn_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "pfmm_mpnn_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int64]),
+    "pfmm_mpnn_set_output_scale": (ctypes.c_int, [_VP, ctypes.c_float]),
+    "pfmm_mpnn_get_output_scale": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pfmm_mpnn_apply": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
+    "pfmm_mpnn_loss_grad": (ctypes.c_int, [_VP, _VP, _DP, _DP, ctypes.POINTER(ctypes.c_int32), _I,
+                                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _VP]),
+    "pfmm_mpnn_train": (ctypes.c_int, [_VP, _VP, _DP, _DP, ctypes.c_int64, _I, _I, ctypes.c_float, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_float), _VP]),
+    "pfmm_mpnn_check": (ctypes.c_int, [_VP]),
+    "pfmm_mpnn_destroy": (None, [_VP]),
     "pfmm_destroy": (None, [_VP]),
     "pfmm_last_error": (ctypes.c_char_p, []),
 }
@@ -251,7 +267,7 @@ def pfmm_solve(h, formulation: int, g, x, nrhs: int, opts: pfmm_solve_opts | Non
     if not (rc == -6 and allow_not_converged):
         _check(rc)
     return dict(iterations=info.iterations, outer=info.outer, rel_res=info.rel_res, seconds=info.seconds,
-                converged=rc == PFMM_OK)
+                converged=rc == PFMM_OK, recorded=info.recorded, precond_off=info.precond_off)
 
 
 def _mesh_struct(vertices, triangles, T, n_steps, alpha):
@@ -366,6 +382,75 @@ class Operator:
         if self.h:
             pfmm_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mpnn:
+    """Learned right preconditioner of pfmm_solve (message passing over the triangle adjacency)."""
+
+    def __init__(self, vertices, triangles, T, n_steps, alpha=1.0, width=64, layers=4, seed=0):
+        m = _mesh_struct(vertices, triangles, T, n_steps, alpha)
+        out = ctypes.c_void_p()
+        _check(lib().pfmm_mpnn_create(ctypes.byref(m), int(width), int(layers), int(seed), ctypes.byref(out)))
+        self.ptr = out.value
+        self.nt = int(np.asarray(triangles).shape[0])
+        self.n_steps = int(n_steps)
+
+    def num_params(self) -> int:
+        return int(lib().pfmm_mpnn_num_params(self.ptr))
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().pfmm_mpnn_get_params(self.ptr, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+        return p
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().pfmm_mpnn_set_params(self.ptr, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+
+    @property
+    def output_scale(self) -> float:
+        c = ctypes.c_float()
+        _check(lib().pfmm_mpnn_get_output_scale(self.ptr, ctypes.byref(c)))
+        return c.value
+
+    @output_scale.setter
+    def output_scale(self, c: float) -> None:
+        _check(lib().pfmm_mpnn_set_output_scale(self.ptr, float(c)))
+
+    def apply(self, v, z, stream=None) -> None:
+        _check(lib().pfmm_mpnn_apply(self.ptr, _ptr(v), _ptr(z), int(v.shape[0]), _stream(stream)))
+
+    def loss_grad(self, R, E, slices, handle=None, stream=None):
+        """Loss and gradient; same-step form with a pFMM handle, error form (needs E) without."""
+        sl = np.ascontiguousarray(slices, dtype=np.int32)
+        loss = ctypes.c_float()
+        g = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().pfmm_mpnn_loss_grad(self.ptr, handle, _ptr(R), _ptr(E),
+                                         sl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), sl.size,
+                                         ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         _stream(stream)))
+        return loss.value, g
+
+    def train(self, R, E, nvec, steps, batch_slices=32, lr=1e-3, seed=0, handle=None, stream=None) -> np.ndarray:
+        hist = np.zeros(max(int(steps), 1), dtype=np.float32)
+        _check(lib().pfmm_mpnn_train(self.ptr, handle, _ptr(R), _ptr(E), int(nvec), int(steps), int(batch_slices),
+                                     float(lr), int(seed), hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                     _stream(stream)))
+        return hist[:steps]
+
+    def check(self) -> None:
+        _check(lib().pfmm_mpnn_check(self.ptr))
+
+    def close(self):
+        if self.ptr:
+            lib().pfmm_mpnn_destroy(self.ptr)
+            self.ptr = None
 
     def __del__(self):
         try:
