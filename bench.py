@@ -89,35 +89,83 @@ def _oracle_sample(n_targets=16, nthreads=0):
                        f"M2L/L2L/L2T on their box chains, their nearfield rows); {dt:.1f} s"), dt
 
 
-def _solve_comparison(dev):
-    """Wall time to 1e-8 relative residual (Eq. 02:linear:system, direct formulation) on the
-    3072-triangle x 128-step cube: plain FP64 FGMRES(50) vs GMRES-IR (FP32 mixed inner FGMRES,
-    FP64 residuals).  Datum: 8 heat sources in the shell 1.2 <= |y - c| <= 2, t0 in [-0.5, -0.05]."""
+def _solve_comparison(dev, n_train=256, n_test=32):
+    """Time to 1e-8 relative residual (Eq. 02:linear:system, direct formulation) on the
+    3072-triangle x 128-step cube, averaged over held-out data sets: plain FP64 FGMRES(50),
+    GMRES-IR (mixed-precision inner FGMRES, FP64 residuals), and GMRES-IR with the learned
+    preconditioner.  The network (width 64, 4 layers) is trained on residual slices that mixed
+    FGMRES runs record on n_train data sets (one heat source each, rng seeds 4 + k), in the
+    same-step form; the held-out sets use seeds 4 + n_train + k."""
+    import numpy as np
     import torch
 
     from paper_2106_15911_gb300 import pfmm as P
     from paper_2106_15911_gb300.inputs import cube_mesh, heat_source_datum, shell_sources
 
     V, T = cube_mesh(16)
-    Et = 128
+    Et, nt = 128, T.shape[0]
     kw = dict(m_t=4, m_x=6, c_st=1.0)
-    g = torch.tensor(heat_source_datum(V, 1.0, Et, shell_sources(8))[None], device=dev)
-    x = torch.empty((1, Et, T.shape[0]), dtype=torch.float64, device=dev)
     op64 = P.Operator(V, T, 1.0, Et, **kw)
     opm = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, **kw)
-    P.pfmm_solve(op64.h, P.PFMM_DIRECT, g, x, 1)  # warm-up (workspaces, clocks)
-    plain = P.pfmm_solve(op64.h, P.PFMM_DIRECT, g, x, 1)
-    x64 = x.clone()
-    o = P.pfmm_default_solve_opts()
-    o.refine = op64.h
-    P.pfmm_solve(opm.h, P.PFMM_DIRECT, g, x, 1, o)
-    ir = P.pfmm_solve(opm.h, P.PFMM_DIRECT, g, x, 1, o)
-    diff = float((x - x64).abs().max() / x64.abs().max())
+
+    def datum(seed):
+        return torch.tensor(heat_source_datum(V, 1.0, Et, shell_sources(1, seed=seed))[None], device=dev)
+
+    per_set = 20
+    R = torch.empty((n_train * per_set, Et, nt), dtype=torch.float64, device=dev)
+    x = torch.empty((1, Et, nt), dtype=torch.float64, device=dev)
+    used, t0 = 0, time.perf_counter()
+    for k in range(n_train):
+        o = P.pfmm_default_solve_opts()
+        o.tol, o.rec_r, o.rec_cap, o.rec_every = 1e-6, R[used].data_ptr(), per_set, 5
+        used += P.pfmm_solve(opm.h, P.PFMM_DIRECT, datum(4 + k), x, 1, o, allow_not_converged=True)["recorded"]
+    t_gen = time.perf_counter() - t0
+    net = P.Mpnn(V, T, 1.0, Et, width=64, layers=4, seed=7)
+    t0 = time.perf_counter()
+    hist = net.train(R, None, used, steps=1500, batch_slices=32, lr=2e-3, seed=8, handle=opm.h)
+    t_train = time.perf_counter() - t0
+    del R
+    zz = torch.empty_like(x)
+    net.apply(x, zz)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        net.apply(x, zz)
+    e1.record()
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / 10
+    arms = {"fp64_fgmres": [], "mixed_gmres_ir": [], "mixed_gmres_ir_learned": []}
+    worst_diff = 0.0
+    for k in range(n_test):
+        g = datum(4 + n_train + k)
+        arms["fp64_fgmres"].append(P.pfmm_solve(op64.h, P.PFMM_DIRECT, g, x, 1))
+        x64 = x.clone()
+        o = P.pfmm_default_solve_opts()
+        o.refine = op64.h
+        arms["mixed_gmres_ir"].append(P.pfmm_solve(opm.h, P.PFMM_DIRECT, g, x, 1, o))
+        o.precond = net.ptr
+        arms["mixed_gmres_ir_learned"].append(P.pfmm_solve(opm.h, P.PFMM_DIRECT, g, x, 1, o))
+        worst_diff = max(worst_diff, float((x - x64).abs().max() / x64.abs().max()))
+    net.close()
     op64.close()
     opm.close()
-    return {"workload": f"cube 16x16 faces ({T.shape[0]} tri) x {Et} steps, direct formulation, tol 1e-8",
-            "fp64_fgmres": plain, "mixed_gmres_ir": ir, "speedup": plain["seconds"] / ir["seconds"],
-            "solution_rel_diff": diff}
+
+    def summ(rs):
+        return {"mean_iterations": float(np.mean([r["iterations"] for r in rs])),
+                "mean_seconds": float(np.mean([r["seconds"] for r in rs])),
+                "worst_rel_res": float(max(r["rel_res"] for r in rs)), "all_converged": all(r["converged"] for r in rs),
+                "precond_dropped": int(sum(r["precond_off"] for r in rs))}
+
+    out = {k: summ(v) for k, v in arms.items()}
+    return {"workload": f"cube 16x16 faces ({nt} tri) x {Et} steps, direct formulation, tol 1e-8, "
+                        f"{n_test} held-out heat-source data sets",
+            "training": {"data_sets": n_train, "recorded_residuals": used, "record_s": t_gen, "train_s": t_train,
+                         "steps": 1500, "loss_first": float(hist[:10].mean()), "loss_last": float(hist[-50:].mean()),
+                         "network": "width 64, 4 layers, BF16 weights, tcgen05 layers", "apply_ms": t_apply},
+            **out,
+            "speedup_learned_vs_fp64": out["fp64_fgmres"]["mean_seconds"] / out["mixed_gmres_ir_learned"]["mean_seconds"],
+            "speedup_learned_vs_mixed": out["mixed_gmres_ir"]["mean_seconds"] / out["mixed_gmres_ir_learned"]["mean_seconds"],
+            "worst_solution_rel_diff_vs_fp64": worst_diff}
 
 
 def _batch_comparison(dev, n_problems, seed=3):
@@ -206,6 +254,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
+    ap.add_argument("--solve-sets", type=int, default=32, help="held-out data sets of the solver comparison")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
     ap.add_argument("--et", type=int, default=ET, help="profiling only: time steps")
@@ -358,7 +407,7 @@ def main():
 
     solve = None
     if rank == 0 and not args.no_solve:
-        solve = _solve_comparison(dev)
+        solve = _solve_comparison(dev, n_test=args.solve_sets)
     batch = None
     if rank == 0 and args.batch > 0:
         batch = _batch_comparison(dev, args.batch)

@@ -191,6 +191,7 @@ typedef struct pfmm_solve_opts {
     double *rec_e;        /* optional (nullable) device [rec_cap][E_t][E_x]: errors e_k = x - x_k */
     int32_t rec_cap;      /* number of (r, e) slots (0: no recording; needs refine == NULL) */
     int32_t rec_every;    /* record at every rec_every-th Arnoldi step of each cycle (default 5) */
+    int32_t rec_basis;    /* 1: record the Arnoldi basis vectors v_j into rec_r instead (rec_e unused) */
 } pfmm_solve_opts;
 
 typedef struct pfmm_solve_info {
@@ -254,14 +255,15 @@ void pfmm_batch_destroy(pfmm_batch *b);
 /* ---- learned preconditioner ---------------------------------------------------------------
  * The paper has no counterpart (it solves with unpreconditioned GMRES).  A message-passing
  * network over the triangle edge adjacency acts on each time slice v_t ([E_x] values) of a vector:
- *   x_i = (v_i / s_t, |gamma_i| / mean area, outward unit normal n_i, (t + 1/2) / E_t),
- *   s_t = RMS(v_t) + 1e-30,  h^0 = SiLU(W_0^T x + b_0),
- *   h^{l+1} = h^l + SiLU(W_s^T h^l + W_n^T mean_{j ~ i} h^l_j + b^l)  (l < layers),
- *   z_i = c s_t (w_o . h^L_i + b_o),  j ~ i: triangles sharing an edge with i.
- * Weights are used in BF16 (FP32 master copies for Adam), arithmetic is FP32.  Parameters
- * (FP32, this order, matrices input-major M[k][o]): W_0 [6][W], b_0 [W], per layer
- * {W_s [W][W], W_n [W][W], b [W]}, w_o [W], b_o.  Training data are residual slices r_b recorded
- * by pfmm_solve (with their errors e_b, V_h e = r).  Two losses over a batch of S slices:
+ *   f_i = (|gamma_i| / mean area, outward unit normal n_i, (t + 1/2) / E_t),  s_t = RMS(v_t) + 1e-30,
+ *   e_i = SiLU(W_g^T f_i + b_g),  h^0_i = (v_i / s_t) e_i,
+ *   h^{l+1} = h^l + W_s^T h^l + W_n^T mean_{j ~ i} h^l_j  (l < layers),
+ *   z_i = c s_t (w_o . h^L_i),  j ~ i: triangles sharing an edge with i.
+ * z is linear in v (FGMRES needs a consistent preconditioner); the coefficients depend on the
+ * geometry through e.  Weights are used in BF16 (FP32 master copies for Adam), accumulation is
+ * FP32.  Parameters (FP32, this order, matrices input-major M[k][o]): W_g [5][W], b_g [W], per
+ * layer {W_s [W][W], W_n [W][W]}, w_o [W].  Training data are residual slices r_b recorded by
+ * pfmm_solve (with their errors e_b, V_h e = r).  Two losses over a batch of S slices:
  *   same-step form (a pFMM handle h of the mesh given): the correction wanted for r_b is
  *     c_b = A_0^{-1} r_b, A_0 the same-step (time-block-diagonal) nearfield block of V_h, measured
  *     in the residual norm:  (1/S) sum_b ||A_0 z(r_b) - r_b||^2 / (||r_b||^2 + 1e-30);

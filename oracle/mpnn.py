@@ -4,15 +4,16 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/`` alone.  It shares no code with 
 
 The network is not part of the paper's method (the paper solves with unpreconditioned GMRES,
 Section 5); it is the message-passing preconditioner acting on time slices of a Krylov vector.
-Definition, for a slice v (E_x values of step t), s = RMS(v) + 1e-30:
+Definition, for a slice v (E_x values of step t), s = RMS(v) + 1e-30, and the geometry / step
+features f_i = (|gamma_i| / mean area, n_i, (t + 1/2) / E_t):
 
-    x_i     = (v_i / s, |gamma_i| / mean area, n_i, (t + 1/2) / E_t)
-    h^0     = SiLU(x W_0 + b_0)
-    h^{l+1} = h^l + SiLU(h^l W_s^l + (A h^l) W_n^l + b^l),   (A h)_i = mean of h_j, j ~ i
-    z_i     = c s (h^L_i . w_o + b_o)
+    e_i     = SiLU(f_i W_g + b_g)
+    h^0_i   = (v_i / s) e_i
+    h^{l+1} = h^l + h^l W_s^l + (A h^l) W_n^l,   (A h)_i = mean of h_j, j ~ i
+    z_i     = c s (h^L_i . w_o)
 
 j ~ i when triangles i and j share an edge.  Matrices are input-major (M[k][o] multiplies input
-k into output o).  Two losses over S residual slices r_b:
+k into output o).  z is linear in v.  Two losses over S residual slices r_b:
 
 * error form, with targets e_b:   (1/S) sum_b ||z(r_b) - e_b||^2 / (||e_b||^2 + 1e-30)
 * same-step form, with the same-step block A_0 of V_h (dense here):
@@ -28,7 +29,7 @@ from __future__ import annotations
 
 import numpy as np
 
-NF = 6
+NG = 5
 
 
 def bf16_round(x) -> np.ndarray:
@@ -80,7 +81,7 @@ def features(vertices, triangles) -> np.ndarray:
 
 
 def n_params(width: int, layers: int) -> int:
-    return NF * width + width + layers * (2 * width * width + width) + width + 1
+    return NG * width + width + layers * 2 * width * width + width
 
 
 def unpack(p, width: int, layers: int) -> dict:
@@ -95,11 +96,10 @@ def unpack(p, width: int, layers: int) -> dict:
         o += n
         return a
 
-    d = {"W0": take(NF * W, (NF, W)), "b0": take(W, (W,)), "layers": []}
+    d = {"Wg": take(NG * W, (NG, W)), "bg": take(W, (W,)), "layers": []}
     for _ in range(layers):
-        d["layers"].append({"Ws": take(W * W, (W, W)), "Wn": take(W * W, (W, W)), "b": take(W, (W,))})
+        d["layers"].append({"Ws": take(W * W, (W, W)), "Wn": take(W * W, (W, W))})
     d["wo"] = take(W, (W,))
-    d["bo"] = take(1, (1,))[0]
     assert o == p.size
     return d
 
@@ -113,30 +113,26 @@ def dsilu(x):
     return s * (1.0 + x * (1.0 - s))
 
 
-def slice_inputs(v, step: int, Et: int, feat) -> tuple[np.ndarray, float]:
-    """Feature matrix X [E_x, 6] of one slice and its scale s."""
+def slice_inputs(v, step: int, Et: int, feat) -> tuple[np.ndarray, np.ndarray, float]:
+    """(v / s, the feature matrix F [E_x, 5], s) of one slice."""
     v = np.asarray(v, dtype=np.float64)
     s = float(np.sqrt(np.mean(v * v))) + 1e-30
-    X = np.empty((v.size, NF))
-    X[:, 0] = v / s
-    X[:, 1:5] = feat
-    X[:, 5] = (step + 0.5) / Et
-    return X, s
+    F = np.empty((v.size, NG))
+    F[:, :4] = feat
+    F[:, 4] = (step + 0.5) / Et
+    return v / s, F, s
 
 
 def forward_slice(p, width, layers, A, feat, v, step, Et, c, cache=None) -> np.ndarray:
     d = unpack(p, width, layers)
-    X, s = slice_inputs(v, step, Et, feat)
-    P = X @ d["W0"] + d["b0"]
-    H = [silu(P)]
-    Ps = [P]
+    x0, F, s = slice_inputs(v, step, Et, feat)
+    P0 = F @ d["Wg"] + d["bg"]
+    H = [x0[:, None] * silu(P0)]
     for lay in d["layers"]:
-        Pl = H[-1] @ lay["Ws"] + (A @ H[-1]) @ lay["Wn"] + lay["b"]
-        Ps.append(Pl)
-        H.append(H[-1] + silu(Pl))
-    y = H[-1] @ d["wo"] + d["bo"]
+        H.append(H[-1] + H[-1] @ lay["Ws"] + (A @ H[-1]) @ lay["Wn"])
+    y = H[-1] @ d["wo"]
     if cache is not None:
-        cache.update(X=X, s=s, H=H, P=Ps, y=y, d=d)
+        cache.update(x0=x0, F=F, s=s, H=H, P0=P0, d=d)
     return c * s * y
 
 
@@ -176,7 +172,9 @@ def loss(p, width, layers, A, feat, Rs, Es, steps, Et, c, A0=None) -> float:
 def loss_and_grad(p, width, layers, A, feat, Rs, Es, steps, Et, c, A0=None) -> tuple[float, np.ndarray]:
     """Loss and its gradient w.r.t. the flat parameter vector (chain rule, layer by layer)."""
     S = len(Rs)
-    gd = {"W0": 0.0, "b0": 0.0, "wo": 0.0, "bo": 0.0, "layers": [{"Ws": 0.0, "Wn": 0.0, "b": 0.0} for _ in range(layers)]}
+    W = width
+    g = {"Wg": np.zeros((NG, W)), "bg": np.zeros(W), "wo": np.zeros(W),
+         "layers": [{"Ws": np.zeros((W, W)), "Wn": np.zeros((W, W))} for _ in range(layers)]}
     tot = 0.0
     for b, (r, t) in enumerate(zip(Rs, steps)):
         cache: dict = {}
@@ -184,26 +182,19 @@ def loss_and_grad(p, width, layers, A, feat, Rs, Es, steps, Et, c, A0=None) -> t
         val, dz = _slice_loss(z, r, None if Es is None else Es[b], A0)
         tot += val
         dy = dz / S * c * cache["s"]
-        d, H, P = cache["d"], cache["H"], cache["P"]
-        gd["wo"] = gd["wo"] + H[-1].T @ dy
-        gd["bo"] = gd["bo"] + dy.sum()
+        d, H = cache["d"], cache["H"]
+        g["wo"] += H[-1].T @ dy
         G = np.outer(dy, d["wo"])
         for l in range(layers - 1, -1, -1):
             lay = d["layers"][l]
-            D = G * dsilu(P[l + 1])
-            M = A @ H[l]
-            gl = gd["layers"][l]
-            gl["Ws"] = gl["Ws"] + H[l].T @ D
-            gl["Wn"] = gl["Wn"] + M.T @ D
-            gl["b"] = gl["b"] + D.sum(axis=0)
-            G = G + D @ lay["Ws"].T + A.T @ (D @ lay["Wn"].T)
-        D0 = G * dsilu(P[0])
-        gd["W0"] = gd["W0"] + cache["X"].T @ D0
-        gd["b0"] = gd["b0"] + D0.sum(axis=0)
-    W = width
-    parts = [np.broadcast_to(gd["W0"], (NF, W)).ravel(), np.broadcast_to(gd["b0"], (W,))]
-    for gl in gd["layers"]:
-        parts += [np.broadcast_to(gl["Ws"], (W, W)).ravel(), np.broadcast_to(gl["Wn"], (W, W)).ravel(),
-                  np.broadcast_to(gl["b"], (W,))]
-    parts += [np.broadcast_to(gd["wo"], (W,)), np.array([gd["bo"]])]
-    return tot / S, np.concatenate(parts).astype(np.float64)
+            g["layers"][l]["Ws"] += H[l].T @ G
+            g["layers"][l]["Wn"] += (A @ H[l]).T @ G
+            G = G + G @ lay["Ws"].T + A.T @ (G @ lay["Wn"].T)
+        D = G * cache["x0"][:, None] * dsilu(cache["P0"])
+        g["Wg"] += cache["F"].T @ D
+        g["bg"] += D.sum(axis=0)
+    parts = [g["Wg"].ravel(), g["bg"]]
+    for gl in g["layers"]:
+        parts += [gl["Ws"].ravel(), gl["Wn"].ravel()]
+    parts.append(g["wo"])
+    return tot / S, np.concatenate(parts)

@@ -3,18 +3,23 @@
 // The paper's solver is plain GMRES; the network is an addition, and FGMRES with the exact pFMM
 // operator still judges every residual, so the answer never depends on it.
 //
-// For a slice v_t (the E_x values of one time step t of a vector), with s_t = RMS(v_t) + 1e-30:
-//   x_i     = (v_i / s_t, |gamma_i| / mean area, n_i (3 components), (t + 1/2) / E_t)
-//   h^0     = SiLU(W_0^T x + b_0)                                            6 -> W
-//   h^{l+1} = h^l + SiLU(W_s^T h^l + W_n^T mean_{j in N(i)} h^l_j + b^l)     l = 0 .. L-1
-//   z_i     = c s_t (w_o . h^L_i + b_o)
-// N(i): the triangles sharing an edge with triangle i; c: a fixed output scale (the RMS ratio of
-// errors to residuals in the first training batch, or set by the caller).
-// Parameters: FP32 master copy (Adam), BF16 copy for the forward and backward passes.  For widths
-// 32 and 64 the message-passing layers run on the tensor cores (tcgen05.mma kind::f16: BF16
-// weights and BF16-rounded layer inputs, FP32 accumulation in TMEM); everything else, the
-// residual path and the backward pass are FP32 on the CUDA cores.  Parameter vector, in this order (matrices input-major, M[k][o]):
-//   W_0 [6][W], b_0 [W],  per layer { W_s [W][W], W_n [W][W], b [W] },  w_o [W], b_o [1]
+// For a slice v (the E_x values of time step t of a vector), s = RMS(v) + 1e-30, and the
+// geometry/step features f_i = (|gamma_i| / mean area, n_i (3 components), (t + 1/2) / E_t):
+//   e_i     = SiLU(W_g^T f_i + b_g)                                   5 -> W, geometry embedding
+//   h^0_i   = (v_i / s) e_i
+//   h^{l+1} = h^l + W_s^T h^l + W_n^T mean_{j in N(i)} h^l_j            l = 0 .. L-1
+//   z_i     = c s (w_o . h^L_i)
+// N(i): the triangles sharing an edge with triangle i; c: a fixed output scale (estimated from
+// the first training batch, or set by the caller).  The map v -> z is linear (s cancels) with
+// coefficients that depend nonlinearly on the geometry: FGMRES needs a consistent preconditioner,
+// and an input-dependent (nonlinear) map loses the gain of an approximate inverse even at a few
+// per cent of inconsistency.
+// Parameters: FP32 master copy (Adam), BF16 copy for the passes.  For widths 32 and 64 the
+// layers run on the tensor cores (tcgen05.mma kind::f16, BF16 weights, layer input split into
+// BF16 hi + lo parts so that the product is FP32-accurate, FP32 accumulation in TMEM); the
+// rest, and the backward pass, are FP32 on the CUDA cores.  Parameter vector, in this order
+// (matrices input-major, M[k][o]):
+//   W_g [5][W], b_g [W],  per layer { W_s [W][W], W_n [W][W] },  w_o [W]
 // Training on a batch of S residual slices r_b (recorded from FGMRES runs), in one of two forms:
 //   same-step form (a pFMM handle given): the correction the network should produce for r_b is
 //     c_b = A_0^{-1} r_b (A_0: the same-step block of V_h, the time-block-diagonal part), measured
@@ -44,8 +49,8 @@ namespace {
 
 using pfmm::set_error;
 
-constexpr int NF = 6;      // input features
-constexpr int XS = 8;      // row stride of the stored features
+constexpr int NG = 5;      // geometry / step features
+constexpr int XS = 8;      // row stride of the stored inputs (v / s, the 5 features, padding)
 constexpr int RT = 64;     // rows per CTA of the dense layer kernels
 constexpr int RW = 32;     // rows per tile of the weight-gradient kernels
 constexpr int NTH = 256;   // threads per CTA of the dense kernels
@@ -80,8 +85,8 @@ __global__ void k_slice_stat(const double *__restrict__ v, const int *__restrict
 }
 
 // ---- forward -----------------------------------------------------------------------------------
-// features and encoder: X [rows][XS] (optional), PRE [rows][W] (optional), H [rows][W]; one
-// thread per (row, 8 consecutive outputs), encoder weights staged in smem as FP32
+// encoder: h^0 = (v / s) SiLU(W_g^T f + b_g); X [rows][XS] = (v / s, f) and PRE [rows][W] =
+// W_g^T f + b_g kept for the backward pass when given.  One thread per (row, 8 outputs).
 template <int W>
 __global__ void __launch_bounds__(256) k_encode(const double *__restrict__ v, const int *__restrict__ sid, int64_t sid0,
                                                 const float *__restrict__ scale, const float *__restrict__ feat, int nt,
@@ -89,8 +94,8 @@ __global__ void __launch_bounds__(256) k_encode(const double *__restrict__ v, co
                                                 float *__restrict__ X, float *__restrict__ PRE, float *__restrict__ H)
 {
     constexpr int NC = W / 8;
-    __shared__ float w0[NF * W + W];  // W_0 [6][W] then b_0
-    for (int e = threadIdx.x; e < NF * W + W; e += blockDim.x) w0[e] = __bfloat162float(p[e]);
+    __shared__ float wg[NG * W + W];  // W_g [5][W] then b_g
+    for (int e = threadIdx.x; e < NG * W + W; e += blockDim.x) wg[e] = __bfloat162float(p[e]);
     __syncthreads();
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= rows * NC) return;
@@ -98,17 +103,17 @@ __global__ void __launch_bounds__(256) k_encode(const double *__restrict__ v, co
     const int c0 = (int)(gid % NC) * 8, i = (int)(row % nt);
     const int64_t s = slice_of(sid, sid0, b);
     const float4 f = *reinterpret_cast<const float4 *>(feat + 4 * i);
-    const float x0 = (float)(v[s * nt + i] / (double)scale[b]), x5 = ((float)(s % Et) + 0.5f) / (float)Et;
+    const float x0 = (float)(v[s * nt + i] / (double)scale[b]), f5 = ((float)(s % Et) + 0.5f) / (float)Et;
     float a[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int o = c0 + j;
-        a[j] = w0[NF * W + o] + w0[o] * x0 + w0[W + o] * f.x + w0[2 * W + o] * f.y + w0[3 * W + o] * f.z +
-               w0[4 * W + o] * f.w + w0[5 * W + o] * x5;
+        a[j] = wg[NG * W + o] + wg[o] * f.x + wg[W + o] * f.y + wg[2 * W + o] * f.z + wg[3 * W + o] * f.w +
+               wg[4 * W + o] * f5;
     }
     float4 *hp = reinterpret_cast<float4 *>(H + row * W + c0);
-    hp[0] = make_float4(silu(a[0]), silu(a[1]), silu(a[2]), silu(a[3]));
-    hp[1] = make_float4(silu(a[4]), silu(a[5]), silu(a[6]), silu(a[7]));
+    hp[0] = make_float4(x0 * silu(a[0]), x0 * silu(a[1]), x0 * silu(a[2]), x0 * silu(a[3]));
+    hp[1] = make_float4(x0 * silu(a[4]), x0 * silu(a[5]), x0 * silu(a[6]), x0 * silu(a[7]));
     if (PRE) {
         float4 *pp = reinterpret_cast<float4 *>(PRE + row * W + c0);
         pp[0] = make_float4(a[0], a[1], a[2], a[3]);
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(256) k_encode(const double *__restrict__ v, co
     if (X && c0 == 0) {
         float4 *xp = reinterpret_cast<float4 *>(X + row * XS);
         xp[0] = make_float4(x0, f.x, f.y, f.z);
-        xp[1] = make_float4(f.w, x5, 0.f, 0.f);
+        xp[1] = make_float4(f.w, f5, 0.f, 0.f);
     }
 }
 
@@ -143,10 +148,10 @@ __device__ __forceinline__ void load_layer_input(const float *__restrict__ H0, c
     }
 }
 
-// one message-passing layer: H1 = H0 + SiLU([H0 | mean_N H0] [W_s; W_n] + b)
+// one message-passing layer on the CUDA cores: H1 = H0 + [H0 | mean_N H0] [W_s; W_n]
 template <int W>
-__global__ void __launch_bounds__(NTH) k_layer(const float *__restrict__ H0, float *__restrict__ PRE,
-                                               float *__restrict__ H1, const int *__restrict__ adj_ptr,
+__global__ void __launch_bounds__(NTH) k_layer(const float *__restrict__ H0, float *__restrict__ H1,
+                                               const int *__restrict__ adj_ptr,
                                                const int *__restrict__ adj, const float *__restrict__ deg_inv, int nt,
                                                int64_t rows, const __nv_bfloat16 *__restrict__ pl)
 {
@@ -171,19 +176,15 @@ __global__ void __launch_bounds__(NTH) k_layer(const float *__restrict__ H0, flo
             acc[q] += x.x * w0 + x.y * w1 + x.z * w2 + x.w * w3;
         }
     }
-    const float bo = __bfloat162float(pl[2 * W * W + o]);
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
         const int r = rg * RPT + q;
         const int64_t row = r0 + r;
-        if (row >= rows) continue;
-        const float a = acc[q] + bo;
-        if (PRE) PRE[row * W + o] = a;
-        H1[row * W + o] = in[r * 2 * W + o] + silu(a);
+        if (row < rows) H1[row * W + o] = in[r * 2 * W + o] + acc[q];
     }
 }
 
-// decoder, one warp per row: z = c s_b (w_o . h + b_o)
+// decoder, one warp per row: z = c s_b (w_o . h)
 template <int W>
 __global__ void k_decode(const float *__restrict__ H, const float *__restrict__ scale, int nt, int64_t rows, float c,
                          const __nv_bfloat16 *__restrict__ po, double *__restrict__ z)
@@ -194,7 +195,7 @@ __global__ void k_decode(const float *__restrict__ H, const float *__restrict__ 
     float a = 0.f;
     for (int k = lane; k < W; k += 32) a += __bfloat162float(po[k]) * H[row * W + k];
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (lane == 0) z[row] = (double)(a + __bfloat162float(po[W])) * (double)(c * scale[row / nt]);
+    if (lane == 0) z[row] = (double)a * (double)(c * scale[row / nt]);
 }
 
 // ---- loss and backward -------------------------------------------------------------------------
@@ -265,43 +266,35 @@ __global__ void k_gather_slices(const double *__restrict__ R, const int *__restr
     if (row < rows) out[row] = R[(int64_t)sid[row / nt] * nt + row % nt];
 }
 
-// decoder backward: G[row][k] = w_o[k] dy[row]; grad w_o[k] += sum H[row][k] dy[row]; grad b_o += sum dy
+// decoder backward: G[row][k] = w_o[k] dy[row]; grad w_o[k] += sum H[row][k] dy[row]
 template <int W>
 __global__ void __launch_bounds__(NTH) k_decode_bwd(const float *__restrict__ H, const float *__restrict__ dy,
                                                     int64_t rows, const __nv_bfloat16 *__restrict__ po,
                                                     float *__restrict__ G, float *__restrict__ gpo)
 {
     constexpr int NRG = NTH / W;
-    __shared__ float red[NRG][W + 1];
+    __shared__ float red[NRG][W];
     const int o = threadIdx.x % W, rg = threadIdx.x / W;
     const float wo = __bfloat162float(po[o]);
-    float aw = 0.f, ab = 0.f;
+    float aw = 0.f;
     for (int64_t row = (int64_t)blockIdx.x * NRG + rg; row < rows; row += (int64_t)gridDim.x * NRG) {
         const float d = dy[row];
         G[row * W + o] = wo * d;
         aw += H[row * W + o] * d;
-        ab += d;
     }
     red[rg][o] = aw;
-    if (o == 0) red[rg][W] = ab;  // the same for every o of the group
     __syncthreads();
     if (rg == 0) {
         float s = 0.f;
         for (int g = 0; g < NRG; ++g) s += red[g][o];
         atomicAdd(&gpo[o], s);
-        if (o == 0) {
-            float sb = 0.f;
-            for (int g = 0; g < NRG; ++g) sb += red[g][W];
-            atomicAdd(&gpo[W], sb);
-        }
     }
 }
 
-// layer backward, dense part.  With DP = G1 * SiLU'(PRE):
-//   G0 = G1 + DP W_s^T  (the residual path plus the self term),  U = (DP W_n^T) / deg
+// layer backward, dense part (G1 = d loss / d h^{l+1}):
+//   G0 = G1 + G1 W_s^T  (the residual path plus the self term),  U = (G1 W_n^T) / deg
 template <int W>
-__global__ void __launch_bounds__(NTH) k_layer_bwd(const float *__restrict__ G1, const float *__restrict__ PRE,
-                                                   float *__restrict__ DP, float *__restrict__ G0,
+__global__ void __launch_bounds__(NTH) k_layer_bwd(const float *__restrict__ G1, float *__restrict__ G0,
                                                    float *__restrict__ U, const float *__restrict__ deg_inv, int nt,
                                                    int64_t rows, const __nv_bfloat16 *__restrict__ pl)
 {
@@ -317,13 +310,7 @@ __global__ void __launch_bounds__(NTH) k_layer_bwd(const float *__restrict__ G1,
     }
     for (int e = threadIdx.x; e < RT * W; e += NTH) {
         const int64_t row = r0 + e / W;
-        float v = 0.f;
-        if (row < rows) {
-            const int64_t g = row * W + e % W;
-            v = G1[g] * dsilu(PRE[g]);
-            DP[g] = v;
-        }
-        dp[e] = v;
+        dp[e] = row < rows ? G1[row * W + e % W] : 0.f;
     }
     __syncthreads();
     const int k = threadIdx.x % W, rg = threadIdx.x / W;
@@ -368,16 +355,19 @@ __global__ void k_scatter_nbr(const float *__restrict__ U, float *__restrict__ G
     G0[gid] += s;
 }
 
-__global__ void k_act_bwd(const float *__restrict__ G, const float *__restrict__ PRE, float *__restrict__ DP, int64_t n)
+// encoder backward: d loss / d (W_g^T f + b_g) = G0 (v / s) SiLU'(PRE)
+__global__ void k_enc_bwd(const float *__restrict__ G, const float *__restrict__ PRE, const float *__restrict__ X,
+                          int W, int64_t n, float *__restrict__ DP)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) DP[i] = G[i] * dsilu(PRE[i]);
+    if (i < n) DP[i] = G[i] * X[(i / W) * XS] * dsilu(PRE[i]);
 }
 
 // weight gradients of one dense map:  Gw[k][o] += sum_rows IN[row][k] DP[row][o] for k < kvalid,
-// gb[o] += sum_rows DP[row][o]; IN = A (row stride KA), or [A | mean_N(A)] when nbr_mean
+// gb[o] += sum_rows DP[row][o] (gb nullable); IN = the first KA columns of A (row stride lda), or
+// [A | mean_N(A)] when nbr_mean
 template <int W>
-__global__ void __launch_bounds__(NTH) k_wgrad(const float *__restrict__ A, int KA, int kvalid, int nbr_mean,
+__global__ void __launch_bounds__(NTH) k_wgrad(const float *__restrict__ A, int lda, int KA, int kvalid, int nbr_mean,
                                                const int *__restrict__ adj_ptr, const int *__restrict__ adj,
                                                const float *__restrict__ deg_inv, int nt,
                                                const float *__restrict__ DP, int64_t rows, float *__restrict__ Gw,
@@ -401,12 +391,12 @@ __global__ void __launch_bounds__(NTH) k_wgrad(const float *__restrict__ A, int 
             float v = 0.f;
             if (row < rows) {
                 if (k < KA) {
-                    v = A[row * KA + k];
+                    v = A[row * lda + k];
                 } else {
                     const int kk = k - KA;
                     const int64_t base = row - row % nt;
                     const int i = (int)(row % nt);
-                    for (int q = adj_ptr[i]; q < adj_ptr[i + 1]; ++q) v += A[(base + adj[q]) * KA + kk];
+                    for (int q = adj_ptr[i]; q < adj_ptr[i + 1]; ++q) v += A[(base + adj[q]) * lda + kk];
                     v *= deg_inv[i];
                 }
             }
@@ -432,7 +422,7 @@ __global__ void __launch_bounds__(NTH) k_wgrad(const float *__restrict__ A, int 
         const int k = kg + NRG * q;
         if (k < kvalid) atomicAdd(&Gw[k * W + o], acc[q]);
     }
-    if (kg == 0) atomicAdd(&gb[o], accb);
+    if (gb && kg == 0) atomicAdd(&gb[o], accb);
 }
 
 __global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v, const float *__restrict__ g,
@@ -488,16 +478,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 }
 
 // One message-passing layer on the tensor cores, persistent over 128-row tiles:
-//   gather [h | mean_N h] (BF16, swizzled smem; D3: at most 3 neighbours, from the padded table
-//   nb3, else the CSR lists) -> 2W/16 MMAs of 128 x W x 16 into TMEM ->
-//   epilogue h1 = h + SiLU(acc + b) (FP32), optionally PRE = acc + b and the fused decoder
-//   z = c s (w_o . h1 + b_o).  256 threads: all gather, thread 0 issues the MMAs, warps
-//   (quadrant q = warp mod 4, column group warp / 4) drain TMEM.
+//   gather [h | mean_N h] (split into BF16 hi = rn(a) and lo = rn(a - hi), swizzled smem; D3: at
+//   most 3 neighbours, from the padded table nb3, else the CSR lists) -> 2 x 2W/16 MMAs of
+//   128 x W x 16 into TMEM -> epilogue h1 = h + acc (FP32), optionally the fused decoder
+//   z = c s (w_o . h1).  256 threads: all gather, thread 0 issues the MMAs, warps (quadrant
+//   q = warp mod 4, column group warp / 4) drain TMEM.
 template <int W, bool D3>
-__global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, float *__restrict__ PRE,
-                                                  float *__restrict__ H1, const int *__restrict__ adj_ptr,
-                                                  const int *__restrict__ adj, const int *__restrict__ nb3,
-                                                  const float *__restrict__ deg_inv,
+__global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, float *__restrict__ H1,
+                                                  const int *__restrict__ adj_ptr, const int *__restrict__ adj,
+                                                  const int *__restrict__ nb3, const float *__restrict__ deg_inv,
                                                   int nt, int64_t rows, const __nv_bfloat16 *__restrict__ pl,
                                                   const __nv_bfloat16 *__restrict__ po,
                                                   const float *__restrict__ scale, float c, double *__restrict__ z,
@@ -507,14 +496,14 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
     constexpr int A_BYTES = (K / 64) * TM * 128;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = smem, *sB = smem + A_BYTES;
+    unsigned char *sAh = smem, *sAl = smem + A_BYTES, *sB = smem + 2 * A_BYTES;
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ float bias[W], wout[W];
+    __shared__ float wout[W];
     __shared__ float zpart[NCG][TM];
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // B = W^T: row o holds the layer's column o, element k = M[k][o]
+    // B = [W_s; W_n]^T: row o holds the layer's column o, element k = M[k][o] (exact in BF16)
     for (int e = tid; e < W * NQ; e += 256) {
         const int o = e % W, q = e / W;
         uint32_t pk[4];
@@ -525,10 +514,7 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
         }
         *reinterpret_cast<uint4 *>(sB + (q >> 3) * W * 128 + sw128_off(o, q & 7)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
-    for (int o = tid; o < W; o += 256) {
-        bias[o] = __bfloat162float(pl[K * W + o]);
-        wout[o] = z ? __bfloat162float(po[o]) : 0.f;
-    }
+    for (int o = tid; o < W; o += 256) wout[o] = z ? __bfloat162float(po[o]) : 0.f;
     if (tid == 0) {
         mbar_init(&bar, 1);
         s_abort = 0;
@@ -543,12 +529,25 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
-    const float bo = z ? __bfloat162float(po[W]) : 0.f;
     const int64_t ntiles = (rows + TM - 1) / TM;
+    // hi / lo BF16 parts of 8 consecutive values into the two A tiles
+    auto put = [&](int r, int qq, const float4 &a, const float4 &b) {
+        const uint32_t off = (qq >> 3) * TM * 128 + sw128_off(r, qq & 7);
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(a.z, a.w),
+                             h2 = __floats2bfloat162_rn(b.x, b.y), h3 = __floats2bfloat162_rn(b.z, b.w);
+        const float2 g0 = __bfloat1622float2(h0), g1 = __bfloat1622float2(h1), g2 = __bfloat1622float2(h2),
+                     g3 = __bfloat1622float2(h3);
+        *reinterpret_cast<uint4 *>(sAh + off) =
+            make_uint4(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1),
+                       *reinterpret_cast<const uint32_t *>(&h2), *reinterpret_cast<const uint32_t *>(&h3));
+        *reinterpret_cast<uint4 *>(sAl + off) =
+            make_uint4(pack_bf16(a.x - g0.x, a.y - g0.y), pack_bf16(a.z - g1.x, a.w - g1.y),
+                       pack_bf16(b.x - g2.x, b.y - g2.y), pack_bf16(b.z - g3.x, b.w - g3.y));
+    };
     int n = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++n) {
         const int64_t r0 = tile * TM;
-        // self half: chunks q < W/8 of every row (contiguous 32-byte loads, 8 threads per row)
+        // self half: chunks q < W/8 of every row (contiguous 32-byte loads, W/8 threads per row)
         constexpr int SC = W / 8, PER = TM * SC / 256;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
@@ -560,8 +559,7 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
                 a = p[0];
                 b = p[1];
             }
-            *reinterpret_cast<uint4 *>(sA + (q >> 3) * TM * 128 + sw128_off(r, q & 7)) =
-                make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+            put(r, q, a, b);
         }
         // neighbour half: chunks W/8 + q, the mean over the edge neighbours
 #pragma unroll
@@ -596,22 +594,22 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
                 a.x *= di; a.y *= di; a.z *= di; a.w *= di;
                 b.x *= di; b.y *= di; b.z *= di; b.w *= di;
             }
-            const int qq = SC + q;
-            *reinterpret_cast<uint4 *>(sA + (qq >> 3) * TM * 128 + sw128_off(r, qq & 7)) =
-                make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+            put(r, SC + q, a, b);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes -> MMA reads
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0) {
-            const uint32_t a0 = su32(sA), b0 = su32(sB);
+            const uint32_t ah = su32(sAh), al = su32(sAl), b0 = su32(sB);
 #pragma unroll
             for (int kb = 0; kb < K / 64; ++kb)
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)  // K = 16 BF16 (32 bytes) per MMA
-                    mma_bf16(tmem, sw128_desc(a0 + kb * TM * 128 + kk * 32), sw128_desc(b0 + kb * W * 128 + kk * 32),
-                             idesc_bf16(TM, W), (kb | kk) ? 1u : 0u);
+                for (int kk = 0; kk < 4; ++kk) {  // K = 16 BF16 (32 bytes) per MMA
+                    const uint64_t bd = sw128_desc(b0 + kb * W * 128 + kk * 32);
+                    mma_bf16(tmem, sw128_desc(ah + kb * TM * 128 + kk * 32), bd, idesc_bf16(TM, W), (kb | kk) ? 1u : 0u);
+                    mma_bf16(tmem, sw128_desc(al + kb * TM * 128 + kk * 32), bd, idesc_bf16(TM, W), 1u);
+                }
             mma_commit(&bar);
         }
         if (!mbar_wait(&bar, n & 1, gtimer() + kWaitNs)) {
@@ -631,18 +629,12 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
             if (row < rows) {
                 const float4 *h0 = reinterpret_cast<const float4 *>(H0 + row * W + cg * 32);
                 float4 *h1 = reinterpret_cast<float4 *>(H1 + row * W + cg * 32);
-                float4 *pre = PRE ? reinterpret_cast<float4 *>(PRE + row * W + cg * 32) : nullptr;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int cc = cg * 32 + 4 * j;
                     const float4 h = h0[j];
-                    float4 a;
-                    a.x = __uint_as_float(v[4 * j]) + bias[cc];
-                    a.y = __uint_as_float(v[4 * j + 1]) + bias[cc + 1];
-                    a.z = __uint_as_float(v[4 * j + 2]) + bias[cc + 2];
-                    a.w = __uint_as_float(v[4 * j + 3]) + bias[cc + 3];
-                    if (pre) pre[j] = a;
-                    const float4 o = make_float4(h.x + silu(a.x), h.y + silu(a.y), h.z + silu(a.z), h.w + silu(a.w));
+                    const float4 o = make_float4(h.x + __uint_as_float(v[4 * j]), h.y + __uint_as_float(v[4 * j + 1]),
+                                                 h.z + __uint_as_float(v[4 * j + 2]), h.w + __uint_as_float(v[4 * j + 3]));
                     h1[j] = o;
                     zp += wout[cc] * o.x + wout[cc + 1] * o.y + wout[cc + 2] * o.z + wout[cc + 3] * o.w;
                 }
@@ -652,7 +644,7 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
         if (z) {
             __syncthreads();
             if (tid < TM && r0 + tid < rows) {
-                float sacc = bo;
+                float sacc = 0.f;
 #pragma unroll
                 for (int g = 0; g < NCG; ++g) sacc += zpart[g][tid];
                 const int64_t row = r0 + tid;
@@ -671,7 +663,7 @@ __global__ void __launch_bounds__(256) k_layer_tc(const float *__restrict__ H0, 
 template <int W>
 constexpr size_t tc_smem_bytes()
 {
-    return (size_t)(2 * W / 64) * TM * 128 + (size_t)(2 * W / 64) * W * 128 + 1024;
+    return 2 * (size_t)(2 * W / 64) * TM * 128 + (size_t)(2 * W / 64) * W * 128 + 1024;
 }
 
 }  // namespace
@@ -721,7 +713,7 @@ struct pfmm_mpnn {
             mem.erase(it);
         }
     }
-    int64_t off_layer(int l) const { return (int64_t)NF * W + W + (int64_t)l * (2 * W * W + W); }
+    int64_t off_layer(int l) const { return (int64_t)NG * W + W + (int64_t)l * 2 * W * W; }
     int64_t off_out() const { return off_layer(L); }
 };
 
@@ -739,22 +731,21 @@ void launch_forward(pfmm_mpnn *N, const double *v, const int *sid, int64_t sid0,
     bool decoded = false;
     for (int l = 0; l < N->L; ++l) {
         float *nxt = keep ? H + (size_t)(l + 1) * rows * W : (l % 2 == 0 ? N->Hi1 : N->Hi0);
-        float *pre = keep ? PRE + (size_t)(l + 1) * rows * W : nullptr;
         if constexpr (W >= 32) {
             const bool last = l == N->L - 1;
             const size_t smem = tc_smem_bytes<W>();
             const int64_t ntiles = (rows + TM - 1) / TM;
-            const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)N->nsm * 3);
+            const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)N->nsm * 2);
             auto kern = N->nb3 ? k_layer_tc<W, true> : k_layer_tc<W, false>;
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            kern<<<grid, 256, smem, st>>>(cur, pre, nxt, N->adj_ptr, N->adj, N->nb3, N->deg_inv, N->nt, rows,
+            kern<<<grid, 256, smem, st>>>(cur, nxt, N->adj_ptr, N->adj, N->nb3, N->deg_inv, N->nt, rows,
                                           N->p16 + N->off_layer(l), N->p16 + N->off_out(), scale, N->c_out,
                                           last ? z : nullptr, N->err);
             decoded = last;
         } else {
             const size_t smem = (size_t)(2 * W * W + RT * 2 * W) * sizeof(float);
             cudaFuncSetAttribute(k_layer<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_layer<W><<<nblk(rows, RT), NTH, smem, st>>>(cur, pre, nxt, N->adj_ptr, N->adj, N->deg_inv, N->nt, rows,
+            k_layer<W><<<nblk(rows, RT), NTH, smem, st>>>(cur, nxt, N->adj_ptr, N->adj, N->deg_inv, N->nt, rows,
                                                           N->p16 + N->off_layer(l));
         }
         cur = nxt;
@@ -771,22 +762,22 @@ void launch_backward(pfmm_mpnn *N, int64_t rows, cudaStream_t st)
     cudaFuncSetAttribute(k_layer_bwd<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
     const size_t smem_w = (size_t)(RW * 2 * W + RW * W) * sizeof(float);
     cudaFuncSetAttribute(k_wgrad<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w);
-    const unsigned gw = (unsigned)std::min<int64_t>(nblk(rows, RW), 2 * 152);
+    const unsigned gw = (unsigned)std::min<int64_t>(nblk(rows, RW), 2 * (int64_t)N->nsm);
     float *Gup = N->G1, *Gdn = N->G0;  // gradient w.r.t. h^{l+1} and h^l
     k_decode_bwd<W><<<(unsigned)std::min<int64_t>(nblk(rows, NTH / W), 2048), NTH, 0, st>>>(
         N->H + (size_t)L * rows * W, N->dy, rows, N->p16 + N->off_out(), Gup, N->grad + N->off_out());
     for (int l = L - 1; l >= 0; --l) {
-        const float *Hl = N->H + (size_t)l * rows * W, *PREl = N->PRE + (size_t)(l + 1) * rows * W;
-        k_layer_bwd<W><<<nblk(rows, RT), NTH, smem_b, st>>>(Gup, PREl, N->DP, Gdn, N->U, N->deg_inv, N->nt, rows,
+        const float *Hl = N->H + (size_t)l * rows * W;
+        k_layer_bwd<W><<<nblk(rows, RT), NTH, smem_b, st>>>(Gup, Gdn, N->U, N->deg_inv, N->nt, rows,
                                                             N->p16 + N->off_layer(l));
-        k_wgrad<W><<<gw, NTH, smem_w, st>>>(Hl, W, 2 * W, 1, N->adj_ptr, N->adj, N->deg_inv, N->nt, N->DP, rows,
-                                            N->grad + N->off_layer(l), N->grad + N->off_layer(l) + 2 * W * W);
+        k_wgrad<W><<<gw, NTH, smem_w, st>>>(Hl, W, W, 2 * W, 1, N->adj_ptr, N->adj, N->deg_inv, N->nt, Gup, rows,
+                                            N->grad + N->off_layer(l), nullptr);
         k_scatter_nbr<<<nblk(rows * W), 256, 0, st>>>(N->U, Gdn, N->adj_ptr, N->adj, N->nt, rows, W);
         std::swap(Gup, Gdn);
     }
-    k_act_bwd<<<nblk(rows * W), 256, 0, st>>>(Gup, N->PRE, N->DP, rows * W);
-    k_wgrad<W><<<gw, NTH, smem_w, st>>>(N->X, XS, NF, 0, N->adj_ptr, N->adj, N->deg_inv, N->nt, N->DP, rows, N->grad,
-                                        N->grad + NF * W);
+    k_enc_bwd<<<nblk(rows * W), 256, 0, st>>>(Gup, N->PRE, N->X, W, rows * W, N->DP);
+    k_wgrad<W><<<gw, NTH, smem_w, st>>>(N->X + 1, XS, NG, NG, 0, N->adj_ptr, N->adj, N->deg_inv, N->nt, N->DP, rows,
+                                        N->grad, N->grad + NG * W);
 }
 
 template <typename F>
@@ -815,7 +806,7 @@ int ensure_train(pfmm_mpnn *N, int64_t slices)
     N->cap_rows = 0;
     const size_t rw = (size_t)rows * N->W, lw = (size_t)(N->L + 1) * rw;
     int rc;
-    if ((rc = N->get(&N->X, (size_t)rows * XS)) || (rc = N->get(&N->H, lw)) || (rc = N->get(&N->PRE, lw)) ||
+    if ((rc = N->get(&N->X, (size_t)rows * XS)) || (rc = N->get(&N->H, lw)) || (rc = N->get(&N->PRE, rw)) ||
         (rc = N->get(&N->G0, rw)) || (rc = N->get(&N->G1, rw)) || (rc = N->get(&N->DP, rw)) ||
         (rc = N->get(&N->U, rw)) || (rc = N->get(&N->dy, rows)) || (rc = N->get(&N->scale, slices)) ||
         (rc = N->get(&N->en2, slices)) || (rc = N->get(&N->z, rows)) || (rc = N->get(&N->sid, slices)) ||
@@ -928,7 +919,7 @@ int pfmm_mpnn_create(const pfmm_mesh *mesh, int32_t width, int32_t layers, uint6
     N->L = layers;
     N->nt = nt;
     N->Et = mesh->n_steps;
-    N->nparam = (int64_t)NF * width + width + (int64_t)layers * (2 * width * width + width) + width + 1;
+    N->nparam = (int64_t)NG * width + width + (int64_t)layers * 2 * width * width + width;
     // edge adjacency (symmetric, duplicates removed) and geometric features
     std::map<std::pair<int, int>, std::vector<int>> edge;
     for (int x = 0; x < nt; ++x)
@@ -1005,15 +996,15 @@ int pfmm_mpnn_create(const pfmm_mesh *mesh, int32_t width, int32_t layers, uint6
     if (!adj.empty()) cudaMemcpy(N->adj, adj.data(), adj.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaMemcpy(N->deg_inv, dinv.data(), dinv.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(N->feat, feat.data(), feat.size() * sizeof(float), cudaMemcpyHostToDevice);
-    // initialisation: uniform(+-1/sqrt(fan_in)) for the encoder and the decoder; the residual
-    // layers start at a tenth of that so that the initial network is close to a 2-layer map
+    // initialisation: uniform(+-1/sqrt(fan_in)) for the geometry embedding and the read-out; the
+    // layers start at a tenth of that, so that the initial network is close to a diagonal scaling
     std::mt19937_64 rng(seed);
     std::vector<float> p(N->nparam, 0.f);
     auto fill = [&](int64_t off, int64_t n, double bound) {
         std::uniform_real_distribution<double> U(-bound, bound);
         for (int64_t i = 0; i < n; ++i) p[off + i] = (float)U(rng);
     };
-    fill(0, NF * width, 1.0 / std::sqrt((double)NF));
+    fill(0, NG * width, 1.0 / std::sqrt((double)NG));
     for (int l = 0; l < layers; ++l) fill(N->off_layer(l), 2 * width * width, 0.1 / std::sqrt(2.0 * width));
     fill(N->off_out(), width, 1.0 / std::sqrt((double)width));
     cudaMemcpy(N->p32, p.data(), p.size() * sizeof(float), cudaMemcpyHostToDevice);

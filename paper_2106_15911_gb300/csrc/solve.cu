@@ -144,6 +144,7 @@ int dots(Ws &W, const double *V, size_t ldv, int nvec, const double *w, size_t n
 struct Rec {
     double *R = nullptr, *E = nullptr;
     int cap = 0, every = 5, count = 0;
+    bool basis = false;      // record the Arnoldi vectors v_j instead of (r_j, e_j)
     double floor_abs = 0.0;  // record only while the residual norm is above this
 };
 
@@ -191,7 +192,12 @@ int fgmres(pfmm_handle *h, Prec &P, Rec *rec, const double *b, double *x, double
         gv[0] = beta;
         int j = 0;
         while (j < restart && total < max_it) {
-            if (rec && rec->count < rec->cap && j % rec->every == 0 && std::fabs(gv[j]) > rec->floor_abs) {
+            if (rec && rec->basis && rec->count < rec->cap && j % rec->every == 0) {
+                SCK(cudaMemcpyAsync(rec->R + (size_t)rec->count * n, W.V + (size_t)j * ld, n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+                ++rec->count;
+            } else if (rec && !rec->basis && rec->count < rec->cap && j % rec->every == 0 &&
+                       std::fabs(gv[j]) > rec->floor_abs) {
                 // x_j and r_j of the current cycle into the next slot
                 double *Rs = rec->R + (size_t)rec->count * n, *Es = rec->E ? rec->E + (size_t)rec->count * n : nullptr;
                 if (Es) SCK(cudaMemcpyAsync(Es, x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -305,6 +311,8 @@ extern "C" int pfmm_solve(pfmm_handle *h, int32_t formulation, const double *g, 
     rec.E = o.rec_e;
     rec.cap = o.rec_cap;
     rec.every = o.rec_every;
+    rec.basis = o.rec_basis != 0;
+    if (rec.basis) rec.E = nullptr;
     Rec *recp = o.rec_cap > 0 ? &rec : nullptr;
     Ws W;
     int rc;
@@ -406,5 +414,6 @@ extern "C" int pfmm_default_solve_opts(pfmm_solve_opts *o)
     o->rec_e = nullptr;
     o->rec_cap = 0;
     o->rec_every = 5;
+    o->rec_basis = 0;
     return PFMM_OK;
 }

@@ -49,7 +49,7 @@ class pfmm_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_it", ctypes.c_int32),
                 ("refine", ctypes.c_void_p), ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("precond", ctypes.c_void_p), ("rec_r", ctypes.c_void_p), ("rec_e", ctypes.c_void_p),
-                ("rec_cap", ctypes.c_int32), ("rec_every", ctypes.c_int32)]
+                ("rec_cap", ctypes.c_int32), ("rec_every", ctypes.c_int32), ("rec_basis", ctypes.c_int32)]
 
 
 class pfmm_solve_info(ctypes.Structure):

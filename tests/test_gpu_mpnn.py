@@ -35,16 +35,16 @@ def test_forward_matches_oracle(width, layers, n_a):
     net.check()
     want = O.forward(O.bf16_round(p), width, layers, V, T, Et, c, v)
     got = z.cpu().numpy()
-    # widths 32 and 64 run the layers on the tensor cores with BF16-rounded layer inputs (relative
-    # rounding 2^-9 per layer); width 16 (and 0 layers) is FP32 throughout
-    tol = 1e-2 if width >= 32 and layers > 0 else 1e-4
+    # widths 32 and 64 run the layers on the tensor cores with the layer input split into BF16
+    # hi + lo parts (about 16 significant bits); width 16 is FP32 on the CUDA cores
+    tol = 1e-4
     for r in range(nvec):
         for t in range(Et):
             assert _rel(got[r, t], want[r, t]) <= tol, (r, t)
     net.close()
 
 
-@pytest.mark.parametrize("width,tol", [(64, 2e-2), (16, 1e-3)])
+@pytest.mark.parametrize("width,tol", [(64, 1e-3), (16, 1e-3)])
 def test_gradient_matches_oracle(width, tol):
     V, T = cube_mesh(2, "cross")
     Et, layers, c = 4, 4, 0.7
@@ -61,8 +61,6 @@ def test_gradient_matches_oracle(width, tol):
     Rs = [R.reshape(-1, len(T))[s] for s in slices]
     Es = [E.reshape(-1, len(T))[s] for s in slices]
     want_l, want_g = O.loss_and_grad(O.bf16_round(p), width, layers, A, feat, Rs, Es, [s % Et for s in slices], Et, c)
-    # width 64: BF16-rounded layer inputs in the tensor-core forward pass (the backward pass is
-    # FP32); width 16: FP32 throughout
     assert loss == pytest.approx(want_l, rel=tol / 2)
     assert np.max(np.abs(g - want_g)) <= tol * np.max(np.abs(want_g))
     net.close()
@@ -93,10 +91,10 @@ def test_same_step_gradient_matches_oracle():
     Rs = [R.reshape(-1, len(T))[s] for s in slices]
     want_l, want_g = O.loss_and_grad(O.bf16_round(p), width, layers, A, O.features(V, T), Rs, None,
                                      [s % Et for s in slices], Et, c, A0)
-    assert loss == pytest.approx(want_l, rel=1e-2)
+    assert loss == pytest.approx(want_l, rel=1e-4)
     # the device gradient applies A_0 for A_0^T: equal up to the singular rules' asymmetry
     assert np.max(np.abs(A0 - A0.T)) <= 1e-4 * np.max(np.abs(A0))
-    assert np.max(np.abs(g - want_g)) <= 2e-2 * np.max(np.abs(want_g))
+    assert np.max(np.abs(g - want_g)) <= 2e-3 * np.max(np.abs(want_g))
     net.close()
     op.close()
 
@@ -140,8 +138,8 @@ def test_recorded_pairs_are_residual_error_pairs(recorded):
 @pytest.mark.parametrize("same_step", [False, True])
 def test_training_lowers_the_loss_and_preconditions(recorded, same_step):
     V, T, Et, op, R, E, used, sols = recorded
-    net = P.Mpnn(V, T, 1.0, Et, width=32, layers=4, seed=3)
-    hist = net.train(R, E, used, steps=300, batch_slices=16, lr=2e-3, seed=4, handle=op.h if same_step else None)
+    net = P.Mpnn(V, T, 1.0, Et, width=64, layers=4, seed=3)
+    hist = net.train(R, E, used, steps=600, batch_slices=32, lr=3e-3, seed=4, handle=op.h if same_step else None)
     assert np.all(np.isfinite(hist))
     assert hist[-30:].mean() < 0.7 * hist[:10].mean()
     assert net.output_scale > 0
@@ -156,9 +154,9 @@ def test_training_lowers_the_loss_and_preconditions(recorded, same_step):
     assert float(torch.linalg.norm(b - op.V(x))) <= 1.01e-8 * float(torch.linalg.norm(b))
     plain = P.pfmm_solve(op.h, P.PFMM_DIRECT, g, torch.empty_like(x), 1)
     if same_step:
-        # trained towards the same-step inverse A_0^{-1}, the network is a block-Jacobi-like
-        # preconditioner: fewer FGMRES iterations than without it (exact block Jacobi halves
-        # them on this mesh)
+        # trained towards the same-step inverse A_0^{-1}, the (linear) network is a block-Jacobi-
+        # like preconditioner: fewer FGMRES iterations than without it (exact block Jacobi halves
+        # them on this mesh, a first-degree polynomial in the mean adjacency removes 28 %)
         assert info["iterations"] < 0.85 * plain["iterations"], (info["iterations"], plain["iterations"])
     net.close()
 

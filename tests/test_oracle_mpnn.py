@@ -1,7 +1,7 @@
 """Pins of the learned-preconditioner oracle (oracle/mpnn.py) to facts outside itself:
 bfloat16 rounding against torch's conversion, the edge adjacency of closed meshes, outward
 normals of the cube, closed-form single-row outputs written with scalar loops, invariances of the
-definition, and the gradient against central finite differences."""
+definition (linearity in the slice), and the gradient against central finite differences."""
 import math
 
 import numpy as np
@@ -67,16 +67,16 @@ def test_zero_layers_closed_form_single_row():
     v = np.array([0.3, -1.2, 2.0, 0.5])
     Et, t, c = 7, 3, 2.5
     z = O.forward_slice(p, W, 0, A, feat, v, t, Et, c)
-    s = math.sqrt(sum(x * x for x in v) / 4) + 1e-30
     for i in range(4):
-        x = [v[i] / s, feat[i, 0], feat[i, 1], feat[i, 2], feat[i, 3], (t + 0.5) / Et]
-        y = d["bo"]
+        f = [feat[i, 0], feat[i, 1], feat[i, 2], feat[i, 3], (t + 0.5) / Et]
+        y = 0.0
         for o in range(W):
-            a = d["b0"][o]
-            for k in range(6):
-                a += x[k] * d["W0"][k][o]
+            a = d["bg"][o]
+            for k in range(5):
+                a += f[k] * d["Wg"][k][o]
             y += d["wo"][o] * a / (1.0 + math.exp(-a))
-        assert z[i] == pytest.approx(c * s * y, rel=1e-13, abs=1e-13)
+        # the slice scale cancels: z_i = c v_i (w_o . e_i)
+        assert z[i] == pytest.approx(c * v[i] * y, rel=1e-13, abs=1e-13)
 
 
 def test_one_layer_closed_form_tetrahedron():
@@ -88,30 +88,31 @@ def test_one_layer_closed_form_tetrahedron():
     v = np.array([1.0, -0.5, 0.25, 2.0])
     Et, t, c = 4, 0, 1.0
     z = O.forward_slice(p, W, 1, A, feat, v, t, Et, c)
-    s = math.sqrt(sum(x * x for x in v) / 4) + 1e-30
     sil = lambda a: a / (1.0 + math.exp(-a))  # noqa: E731
     h0 = []
     for i in range(4):
-        x = [v[i] / s, *feat[i], (t + 0.5) / Et]
-        h0.append([sil(d["b0"][o] + sum(x[k] * d["W0"][k][o] for k in range(6))) for o in range(W)])
+        f = [*feat[i], (t + 0.5) / Et]
+        h0.append([v[i] * sil(d["bg"][o] + sum(f[k] * d["Wg"][k][o] for k in range(5))) for o in range(W)])
     L = d["layers"][0]
     for i in range(4):
         nbrs = [j for j in range(4) if j != i]  # every face of a tetrahedron touches the other three
         m = [sum(h0[j][k] for j in nbrs) / 3 for k in range(W)]
-        h1 = [h0[i][o] + sil(L["b"][o] + sum(h0[i][k] * L["Ws"][k][o] + m[k] * L["Wn"][k][o] for k in range(W)))
-              for o in range(W)]
-        y = d["bo"] + sum(d["wo"][o] * h1[o] for o in range(W))
-        assert z[i] == pytest.approx(c * s * y, rel=1e-12, abs=1e-12)
+        h1 = [h0[i][o] + sum(h0[i][k] * L["Ws"][k][o] + m[k] * L["Wn"][k][o] for k in range(W)) for o in range(W)]
+        y = sum(d["wo"][o] * h1[o] for o in range(W))
+        assert z[i] == pytest.approx(c * y, rel=1e-12, abs=1e-12)
 
 
-def test_positive_homogeneity():
+def test_linear_in_the_slice():
+    """The map v -> z is linear: the slice scale cancels and nothing nonlinear acts on v."""
     V, T = cube_mesh(2)
     W, Lay = 8, 2
     p = _rand_params(W, Lay, 3)
-    v = random_density(4, len(T), 1, seed=9)
-    z1 = O.forward(p, W, Lay, V, T, 4, 1.7, v)
-    z2 = O.forward(p, W, Lay, V, T, 4, 1.7, 3.5 * v)
-    assert np.allclose(z2, 3.5 * z1, rtol=1e-12, atol=1e-12)
+    v1 = random_density(4, len(T), 1, seed=9)
+    v2 = random_density(4, len(T), 1, seed=10)
+    z1 = O.forward(p, W, Lay, V, T, 4, 1.7, v1)
+    z2 = O.forward(p, W, Lay, V, T, 4, 1.7, v2)
+    z3 = O.forward(p, W, Lay, V, T, 4, 1.7, 2.5 * v1 - 0.75 * v2)
+    assert np.allclose(z3, 2.5 * z1 - 0.75 * z2, rtol=1e-11, atol=1e-11 * np.abs(z3).max())
 
 
 @pytest.mark.parametrize("layers,same_step", [(0, False), (1, False), (3, False), (2, True)])
@@ -131,7 +132,7 @@ def test_gradient_finite_differences(layers, same_step):
     val, g = O.loss_and_grad(p, W, layers, A, feat, Rs, Es, steps, Et, c, A0)
     assert val == pytest.approx(O.loss(p, W, layers, A, feat, Rs, Es, steps, Et, c, A0), rel=1e-13)
     idx = rng.choice(p.size, size=min(p.size, 60), replace=False)
-    idx = np.union1d(idx, [0, p.size - 1, p.size - 2, O.NF * W])  # W_0, b_o, w_o, b_0 entries
+    idx = np.union1d(idx, [0, p.size - 1, O.NG * W])  # W_g, w_o, b_g entries
     h = 1e-6
     for i in idx:
         e = np.zeros_like(p)
