@@ -122,7 +122,7 @@ def _solve_comparison(dev, n_train=256, n_test=32):
     t_gen = time.perf_counter() - t0
     net = P.Mpnn(V, T, 1.0, Et, width=64, layers=4, seed=7)
     t0 = time.perf_counter()
-    hist = net.train(R, None, used, steps=1500, batch_slices=32, lr=2e-3, seed=8, handle=opm.h)
+    hist = net.train(R, None, used, steps=1500, batch_slices=32, lr=3e-3, seed=8, handle=opm.h)
     t_train = time.perf_counter() - t0
     del R
     zz = torch.empty_like(x)
@@ -168,11 +168,12 @@ def _solve_comparison(dev, n_train=256, n_test=32):
             "worst_solution_rel_diff_vs_fp64": worst_diff}
 
 
-def _batch_comparison(dev, n_problems, seed=3):
+def _batch_comparison(dev, n_problems, seed=3, tol=3e-3):
     """Ragged batch of independent problems (cube and cube-sphere surfaces alternating, triangle
     counts drawn from {768, 1536, 3072, 6144, 12288}, 32..256 steps, 1..8 right-hand sides,
-    degrees chosen by the autotuner for 1e-5, mixed precision): one replay of the captured CUDA
-    graph vs the same applies issued one after the other on one stream."""
+    mixed precision, degree m_x in [4, 8] chosen by the autotuner for a farfield truncation
+    estimate of `tol`, nearfield engine chosen by timing): replays of the captured CUDA graph
+    with 16, 4 and 1 streams vs the same applies issued one after the other on one stream."""
     import numpy as np
     import torch
 
@@ -188,7 +189,7 @@ def _batch_comparison(dev, n_problems, seed=3):
         nr = int(rng.integers(1, 9))
         prm = P.pfmm_default_params()
         prm.precision = P.PFMM_MIXED
-        prm = P.pfmm_autotune_params(V, T, 1.0, Et, base=prm, tol=1e-5, m_lo=4, m_hi=8)
+        prm = P.pfmm_autotune_params(V, T, 1.0, Et, base=prm, tol=tol, m_lo=4, m_hi=8)
         probs.append((V, T, 1.0, Et, 1.0, prm, nr))
         dofs += T.shape[0] * Et * nr
     tb = time.perf_counter()
@@ -197,28 +198,38 @@ def _batch_comparison(dev, n_problems, seed=3):
     ws = [torch.tensor(random_density(p[3], p[1].shape[0], p[6], seed=100 + i), device=dev) for i, p in enumerate(probs)]
     fs = [torch.empty_like(w) for w in ws]
     stream = torch.cuda.current_stream()
-    for _ in range(3):
-        B.apply_V(ws, fs)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(5):
-        B.apply_V(ws, fs)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_graph = e0.elapsed_time(e1) / 5
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    graph_ms = {}
+    for ns in (16, 4, 1):
+        B.set_streams(ns)
+        graph_ms[ns] = timed(lambda: B.apply_V(ws, fs))
     hs = [B.handle(i) for i in range(len(probs))]
-    e0.record(stream)
-    for _ in range(5):
+
+    def seq():
         for h, w, f in zip(hs, ws, fs):
             P.pfmm_apply_V(h, w, f, w.shape[0], stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_seq = e0.elapsed_time(e1) / 5
+
+    t_seq = timed(seq)
     B.close()
-    return {"workload": f"{n_problems} problems, 768..12288 triangles, 32..256 steps, 1..8 rhs, mixed, autotuned m_x",
-            "space_time_dofs": dofs, "graph_ms": t_graph, "sequential_ms": t_seq,
-            "dofs_per_s": dofs / (t_graph * 1e-3), "build_s": t_build, "m_x": [int(p[5].m_x) for p in probs]}
+    best = min(graph_ms.values())
+    mx = [int(p[5].m_x) for p in probs]
+    return {"workload": f"{n_problems} problems, 768..12288 triangles, 32..256 steps, 1..8 rhs, mixed, "
+                        f"autotuned m_x (truncation estimate {tol:g})",
+            "space_time_dofs": dofs, "graph_ms_by_streams": graph_ms, "sequential_ms": t_seq,
+            "dofs_per_s": dofs / (best * 1e-3), "build_s": t_build,
+            "m_x_histogram": {str(m): mx.count(m) for m in sorted(set(mx))}}
 
 
 def reference_arm(args, rank, world):

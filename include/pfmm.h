@@ -52,7 +52,10 @@ extern "C" {
                          passes; FP64 singular quadrature, FP64 output accumulation */
 
 /* nearfield modes */
-#define PFMM_NEARFIELD_STORED 0  /* nearfield blocks assembled once at build time */
+#define PFMM_NEARFIELD_STORED 0    /* nearfield blocks assembled once at build time */
+#define PFMM_NEARFIELD_ONTHEFLY 1  /* blocks recomputed tile by tile inside every apply (only the
+                                      Sauter-Schwab values of touching pairs are stored); for
+                                      meshes whose blocks do not fit the memory budget */
 
 /* nearfield engines */
 #define PFMM_NF_AUTO 0
@@ -85,7 +88,7 @@ typedef struct pfmm_params {
     int32_t leaf_steps; /* time steps per temporal leaf (E_t / leaf_steps a power of two) */
     int32_t leaf_tris;  /* no spatial refinement once no box holds more triangles */
     int32_t precision;  /* PFMM_FP64 or PFMM_MIXED */
-    int32_t nearfield;  /* PFMM_NEARFIELD_STORED */
+    int32_t nearfield;  /* PFMM_NEARFIELD_STORED (default) or PFMM_NEARFIELD_ONTHEFLY */
     int32_t quad_regular;  /* Gauss points per direction of the collapsed triangle rule */
     int32_t quad_singular; /* Gauss points per direction of the Sauter-Schwab rule */
     int32_t nf_engine;  /* PFMM_NF_AUTO: tensor cores (3xTF32 split, mixed mode) where the panel
@@ -250,6 +253,9 @@ int pfmm_apply_V_batched(pfmm_batch *b, const double *const *w, double *const *f
 
 int pfmm_batch_handle(pfmm_batch *b, int32_t i, pfmm_handle **h);  /* the i-th problem's handle */
 int32_t pfmm_batch_size(const pfmm_batch *b);
+/* Branches of the captured graph run on a pool of nstreams streams (default min(n, 16)); the
+ * next pfmm_apply_V_batched captures again. */
+int pfmm_batch_set_streams(pfmm_batch *b, int32_t nstreams);
 void pfmm_batch_destroy(pfmm_batch *b);
 
 /* ---- learned preconditioner ---------------------------------------------------------------

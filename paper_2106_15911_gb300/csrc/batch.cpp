@@ -221,6 +221,22 @@ int pfmm_apply_V_batched(pfmm_batch *b, const double *const *w, double *const *f
 
 int32_t pfmm_batch_size(const pfmm_batch *b) { return b ? (int32_t)b->h.size() : 0; }
 
+int pfmm_batch_set_streams(pfmm_batch *b, int32_t nstreams)
+{
+    if (!b || nstreams < 1 || nstreams > 64) return set_error(PFMM_ERR_INVALID_ARG, "stream count must be 1..64");
+    for (auto s : b->pool) cudaStreamDestroy(s);
+    b->pool.assign(std::min<int>(nstreams, (int)b->h.size()), nullptr);
+    for (auto &s : b->pool)
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+            return set_error(PFMM_ERR_CUDA, "stream creation failed");
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->last_w.clear();  // the next apply captures again
+    return PFMM_OK;
+}
+
 void pfmm_batch_destroy(pfmm_batch *b) { delete b; }
 
 }  // extern "C"

@@ -295,6 +295,32 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *wh
     return PFMM_OK;
 }
 
+int pfmm::run_nf_otf(pfmm_handle *H, int op, const void *xin, int ncolg, int Et, int ls, int nrhs, int ndmax,
+                     double *fint, cudaStream_t st)
+{
+    OtfArgs a{};
+    a.q = H->quad;
+    a.panels = H->d_panels;
+    a.tiles = H->d_tiles;
+    a.ntiles = H->ntiles;
+    a.tile_sing = H->d_tile_sing;
+    a.sing = H->d_sing;
+    a.singV = H->d_singV;
+    a.singK = H->d_singK;
+    a.x = xin;
+    a.ncolg = ncolg;
+    a.Et = Et;
+    a.ls = ls;
+    a.nrhs = nrhs;
+    a.ndmax = ndmax;
+    a.f = fint;
+    a.nt = H->nt;
+    launch_nf_otf(H->mixed, op == 1, a, H->nsm, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, std::string("on-the-fly nearfield: ") + cudaGetErrorString(e));
+    return PFMM_OK;
+}
+
 // f_b = A_0 x_b for ns independent slices b (user triangle order, [ns][E_x] FP64): the stored
 // nearfield block of offset d = 0 (same time step, neighbouring leaf boxes), applied with each
 // slice taken as its own step.  xint: ns E_x elements of the arithmetic type, fint: ns E_x doubles.
@@ -307,8 +333,14 @@ int pfmm::apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, vo
     g.ls = 1;
     g.perm = H->d_perm;
     launch_permute_in(x, xint, H->mixed, 1, g, st);
-    launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, 1, g, fint, st,
-                    1);
+    if (H->otf) {
+        cudaMemsetAsync(fint, 0, sizeof(double) * ns * (size_t)H->nt, st);
+        int rc = pfmm::run_nf_otf(H, 0, xint, H->nt, ns, 1, 1, 1, fint, st);
+        if (rc) return rc;
+    } else {
+        launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, 1, g, fint,
+                        st, 1);
+    }
     launch_permute_out(fint, f, 1, g, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, std::string("same-step apply: ") + cudaGetErrorString(e));
@@ -348,8 +380,10 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
     H->prm = *prm;
     if (prm->precision != PFMM_FP64 && prm->precision != PFMM_MIXED)
         return fail(PFMM_ERR_INVALID_ARG, "precision must be PFMM_FP64 or PFMM_MIXED");
-    if (prm->nearfield != PFMM_NEARFIELD_STORED)
-        return fail(PFMM_ERR_UNSUPPORTED, "only the stored nearfield mode is implemented");
+    if (prm->nearfield != PFMM_NEARFIELD_STORED && prm->nearfield != PFMM_NEARFIELD_ONTHEFLY)
+        return fail(PFMM_ERR_INVALID_ARG, "unknown nearfield mode");
+    if (prm->nearfield == PFMM_NEARFIELD_ONTHEFLY && 2 * prm->leaf_steps > 8)
+        return fail(PFMM_ERR_UNSUPPORTED, "the on-the-fly nearfield supports leaf_steps <= 4");
     H->mixed = prm->precision == PFMM_MIXED;
     H->es = H->mixed ? 4 : 8;
     std::string err;
@@ -547,15 +581,40 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             o[6] = s.colK[0]; o[7] = s.colK[1]; o[8] = s.colK[2];
         }
         int *d_sing = nullptr;
+        H->otf = prm->nearfield == PFMM_NEARFIELD_ONTHEFLY;
         if ((rc = upload(H, &H->d_panels, pg, st)) || (rc = upload(H, &H->d_tiles, tiles, st)) ||
-            (rc = upload(H, &H->d_colV, t.colV, st)) || (rc = upload(H, &H->d_colK, t.colK, st)) ||
-            (rc = upload(H, &H->d_kmap, t.kmap, st)) || (rc = upload(H, &d_sing, sing, st)))
+            (rc = upload(H, &H->d_colV, t.colV, st)) || (rc = upload(H, &d_sing, sing, st)))
             return rc;
-        if ((rc = H->alloc((char **)&H->d_AV, (size_t)t.sizeV * H->es, 1)) ||
-            (rc = H->alloc((char **)&H->d_AK, (size_t)t.sizeK * H->es, 1)))
-            return rc;
-        CK(cudaMemsetAsync(H->d_AV, 0, (size_t)t.sizeV * H->es, st));
-        CK(cudaMemsetAsync(H->d_AK, 0, (size_t)t.sizeK * H->es, st));
+        if (!H->otf) {
+            if ((rc = upload(H, &H->d_colK, t.colK, st)) || (rc = upload(H, &H->d_kmap, t.kmap, st))) return rc;
+            if ((rc = H->alloc((char **)&H->d_AV, (size_t)t.sizeV * H->es, 1)) ||
+                (rc = H->alloc((char **)&H->d_AK, (size_t)t.sizeK * H->es, 1)))
+                return rc;
+            CK(cudaMemsetAsync(H->d_AV, 0, (size_t)t.sizeV * H->es, st));
+            CK(cudaMemsetAsync(H->d_AK, 0, (size_t)t.sizeK * H->es, st));
+        } else {
+            // singular pairs grouped by 64-row tile (the list is ordered by panel, then row)
+            std::vector<int> tile_base(t.panels.size() + 1, 0), tsing(H->ntiles + 1, 0);
+            for (size_t i = 0; i < t.panels.size(); ++i)
+                tile_base[i + 1] = tile_base[i] + (t.panels[i].nrows + kRowTile - 1) / kRowTile;
+            for (size_t i = 0; i < t.sing.size(); ++i) {
+                const SingularPair &sp = t.sing[i];
+                const int tile = tile_base[sp.panel] + sp.row / kRowTile;
+                if (i > 0) {
+                    const SingularPair &q = t.sing[i - 1];
+                    if (tile < tile_base[q.panel] + q.row / kRowTile)
+                        return fail(PFMM_ERR_UNSUPPORTED, "singular pairs are not ordered by tile");
+                }
+                tsing[tile + 1]++;
+            }
+            for (int i = 0; i < H->ntiles; ++i) tsing[i + 1] += tsing[i];
+            if ((rc = upload(H, &H->d_tile_sing, tsing, st)) ||
+                (rc = H->alloc(&H->d_singV, 2 * std::max<size_t>(t.sing.size(), 1))) ||
+                (rc = H->alloc(&H->d_singK, 6 * std::max<size_t>(t.sing.size(), 1))))
+                return rc;
+            H->d_sing = d_sing;
+            H->otf_bytes = (int64_t)t.sing.size() * (12 * 4 + 8 * 8) + (int64_t)(H->ntiles + 1) * 4;
+        }
         std::vector<double> rreg = collapsed_rule(prm->quad_regular), gx, gw;
         gauss01(prm->quad_singular, gx, gw);
         std::vector<double> gls(gx);
@@ -575,11 +634,17 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         a.nq_sing = prm->quad_singular;
         a.colV = H->d_colV;
         a.kmap = H->d_kmap;
-        for (size_t i = 0; i < t.panels.size(); ++i) {
-            launch_nf_regular(a, pg[i], H->d_AV, H->d_AK, H->mixed, st);
-            CK(cudaGetLastError());
+        if (H->otf) {
+            H->quad = a;
+            launch_nf_singular(a, d_sing, (int)t.sing.size(), H->d_panels, nullptr, nullptr, H->mixed, st, H->d_singV,
+                               H->d_singK);
+        } else {
+            for (size_t i = 0; i < t.panels.size(); ++i) {
+                launch_nf_regular(a, pg[i], H->d_AV, H->d_AK, H->mixed, st);
+                CK(cudaGetLastError());
+            }
+            launch_nf_singular(a, d_sing, (int)t.sing.size(), H->d_panels, H->d_AV, H->d_AK, H->mixed, st);
         }
-        launch_nf_singular(a, d_sing, (int)t.sing.size(), H->d_panels, H->d_AV, H->d_AK, H->mixed, st);
         CK(cudaGetLastError());
 
         // tensor-core nearfield: mixed mode, two steps per leaf, every panel spans all columns
@@ -589,7 +654,8 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         int cc_major = 0, cc_minor = 0;
         CK(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev));
         CK(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
-        bool eligible = H->mixed && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 && encode_fn();
+        bool eligible = !H->otf && H->mixed && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 &&
+                        encode_fn();
         bool fullV = eligible, fullK = eligible;
         for (const Panel &P : t.panels) {
             fullV = fullV && P.ncolV == nt && P.colsV_pad == t.panels[0].colsV_pad;
@@ -723,6 +789,9 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK) && !H->nf_cuda_cores;
     if (tc) {
         if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_fint, st))) return rc;
+    } else if ((parts & PFMM_PART_NEAR) && H->otf) {
+        CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
+        if ((rc = pfmm::run_nf_otf(H, op, xin, ncolg, H->Et, H->ls, nrhs, 1 << 30, H->d_fint, st))) return rc;
     } else if (parts & PFMM_PART_NEAR)
         launch_nf_apply(H->mixed, op == 1, op == 0 ? H->d_AV : H->d_AK, op == 0 ? H->d_colV : H->d_colK, H->d_tiles,
                         H->ntiles, H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st);
@@ -811,7 +880,7 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
         info->pad[l] = t.lv[l].pad;
     }
     info->n_m2l_pairs = t.n_m2l_pairs;
-    info->nearfield_bytes = (t.sizeV + t.sizeK) * (int64_t)h->es;
+    info->nearfield_bytes = h->otf ? h->otf_bytes : (t.sizeV + t.sizeK) * (int64_t)h->es;
     info->device_bytes = h->dev_bytes;
     info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
     info->nearfield_v_elements = t.sizeV;

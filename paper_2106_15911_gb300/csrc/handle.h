@@ -23,6 +23,9 @@ namespace pfmm {
 int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint, cudaStream_t st);
 // size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
 int ensure_ws(pfmm_handle *H, int nrhs);
+// the on-the-fly nearfield of op into fint (+=): arguments of launch_nf_otf for this handle
+int run_nf_otf(pfmm_handle *H, int op, const void *xin, int ncolg, int Et, int ls, int nrhs, int ndmax, double *fint,
+               cudaStream_t st);
 // f_b = A_0 x_b (same-step nearfield block) for ns slices [ns][E_x] in user order; xint holds
 // ns E_x elements of the arithmetic type, fint ns E_x doubles
 int apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, void *xint, double *fint, cudaStream_t st);
@@ -55,6 +58,12 @@ struct pfmm_handle {
     pfmm::PanelGPU *d_panels = nullptr;
     int ntiles = 0;
     int64_t mom_per_rhs = 0;
+    // on-the-fly nearfield: no stored blocks, the compact singular values and the quadrature setup
+    bool otf = false;
+    pfmm::NfQuadArgs quad{};
+    int *d_sing = nullptr, *d_tile_sing = nullptr;
+    double *d_singV = nullptr, *d_singK = nullptr;
+    int64_t otf_bytes = 0;
 
     int ne = 0;              // C(m_x+4,4) entries of the separable M2L intermediates per cell
     int *d_eoff = nullptr;   // [nk] offsets of the budget ranges

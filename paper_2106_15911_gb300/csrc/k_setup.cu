@@ -15,6 +15,7 @@
 
 #include "device_math.cuh"
 #include "kernels.h"
+#include "nf_geom.cuh"
 
 namespace pfmm {
 
@@ -126,43 +127,6 @@ void launch_e1_table(int na, int mt, int mx, int G, double hx, double hxp, doubl
 
 // ------------------------------------------------------------------------------------------
 // Regular nearfield quadrature.  Thread per (row, column) of one panel.
-__device__ __forceinline__ void load_tri(const double *verts, const int *tri, int x, double P[3][3])
-{
-    for (int v = 0; v < 3; ++v)
-        for (int c = 0; c < 3; ++c) P[v][c] = verts[3 * tri[3 * x + v] + c];
-}
-
-__device__ __forceinline__ double tri_jac(const double P[3][3], double n[3])
-{
-    double e1[3], e2[3];
-    for (int c = 0; c < 3; ++c) { e1[c] = P[1][c] - P[0][c]; e2[c] = P[2][c] - P[1][c]; }
-    double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    double J = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-    n[0] = cr[0] / J; n[1] = cr[1] / J; n[2] = cr[2] / J;
-    return J;
-}
-
-__device__ __forceinline__ double tri_normal_orig(const double P[3][3], double n[3])
-{
-    // outward normal from the stored vertex order: (P1 - P0) x (P2 - P0)
-    double a[3], b[3];
-    for (int c = 0; c < 3; ++c) { a[c] = P[1][c] - P[0][c]; b[c] = P[2][c] - P[0][c]; }
-    n[0] = a[1] * b[2] - a[2] * b[1];
-    n[1] = a[2] * b[0] - a[0] * b[2];
-    n[2] = a[0] * b[1] - a[1] * b[0];
-    double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    n[0] /= l; n[1] /= l; n[2] /= l;
-    return l;
-}
-
-__device__ __forceinline__ int shared_count(const int *tri, int x, int y)
-{
-    int s = 0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) s += tri[3 * x + i] == tri[3 * y + j];
-    return s;
-}
-
 template <typename R, typename S, bool KOP>
 __global__ void __launch_bounds__(256) k_nf_regular(NfQuadArgs a, int panel_rows0, int nrows, int rows_pad,
                                                       int cols_pad, const int *__restrict__ cols, S *__restrict__ A,
@@ -174,48 +138,11 @@ __global__ void __launch_bounds__(256) k_nf_regular(NfQuadArgs a, int panel_rows
     int y = cols[col];
     if (y < 0) return;
     int x = panel_rows0 + row;
-    double PX[3][3], PY[3][3], nx[3], ny[3];
-    load_tri(a.verts, a.tri, x, PX);
-    load_tri(a.verts, a.tri, y, PY);
-    double Jx = tri_jac(PX, nx), Jy = tri_jac(PY, ny);
-    tri_normal_orig(PY, ny);
-    const int nd = a.nd;
-    int d0 = shared_count(a.tri, x, y) > 0 ? 2 : 0;  // d = 0, 1 of touching pairs: singular rule
-    const int nq = a.nq_reg;
     R acc[3 * 8];
 #pragma unroll
     for (int i = 0; i < 3 * 8; ++i) acc[i] = R(0);
-    const R h = R(a.h), alpha = R(a.alpha);
-    for (int i = 0; i < nq; ++i) {
-        double s1 = a.rule_reg[i], s2 = a.rule_reg[nq + i], wi = a.rule_reg[2 * nq + i];
-        double xp[3];
-        for (int c = 0; c < 3; ++c) xp[c] = PX[0][c] + s1 * (PX[1][c] - PX[0][c]) + s2 * (PX[2][c] - PX[1][c]);
-        for (int j = 0; j < nq; ++j) {
-            double t1 = a.rule_reg[j], t2 = a.rule_reg[nq + j], wj = a.rule_reg[2 * nq + j];
-            double yp[3], dx[3];
-            for (int c = 0; c < 3; ++c) {
-                yp[c] = PY[0][c] + t1 * (PY[1][c] - PY[0][c]) + t2 * (PY[2][c] - PY[1][c]);
-                dx[c] = xp[c] - yp[c];
-            }
-            double r = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
-            R wt = R(wi * wj * Jx * Jy);
-            R vals[8];
-            if (!KOP) {
-                time_V_all<R>(R(r), h, alpha, nd, vals);
-                for (int d = d0; d < nd; ++d) acc[d] += wt * vals[d];
-            } else {
-                time_K_all<R>(R(r), h, alpha, nd, vals);
-                R dn = R(dx[0] * ny[0] + dx[1] * ny[1] + dx[2] * ny[2]);
-                R by[3] = {R(1.0 - t1), R(t1 - t2), R(t2)};
-                for (int d = d0; d < nd; ++d) {
-                    R v = wt * dn * vals[d];
-                    acc[3 * d + 0] += v * by[0];
-                    acc[3 * d + 1] += v * by[1];
-                    acc[3 * d + 2] += v * by[2];
-                }
-            }
-        }
-    }
+    const int d0 = nf_regular_pair<R, KOP>(a, x, y, acc);
+    const int nd = a.nd;
     if (!KOP) {
         for (int d = d0; d < nd; ++d) A[((size_t)d * rows_pad + row) * cols_pad + col] = S(acc[d]);
     } else {
@@ -247,10 +174,13 @@ void launch_nf_regular(const NfQuadArgs &a, const PanelGPU &P, void *AV, void *A
 
 // ------------------------------------------------------------------------------------------
 // Sauter-Schwab quadrature of touching pairs at d = 0, 1: one warp per pair, FP64.
+// Output: into the stored panels (AV, AK), or, when cV is given (on-the-fly nearfield), compactly
+// per pair: cV[pair][d], cK[pair][d][v] (v: the source triangle's vertices in mesh order).
 template <typename S>
 __global__ void __launch_bounds__(128) k_nf_singular(NfQuadArgs a, const int *__restrict__ sing /*[n][12]*/, int nsing,
                                                        const PanelGPU *__restrict__ panels, S *__restrict__ AV,
-                                                       S *__restrict__ AK)
+                                                       S *__restrict__ AK, double *__restrict__ cV,
+                                                       double *__restrict__ cK)
 {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nsing) return;
@@ -340,7 +270,12 @@ __global__ void __launch_bounds__(128) k_nf_singular(NfQuadArgs a, const int *__
             for (int v = 0; v < 3; ++v) accK[d][v] += __shfl_xor_sync(0xffffffffu, accK[d][v], off);
         }
     }
-    if (lane == 0) {
+    if (lane == 0 && cV) {
+        for (int d = 0; d < 2; ++d) {
+            cV[2 * (size_t)warp + d] = d < a.nd ? accV[d] : 0.0;
+            for (int v = 0; v < 3; ++v) cK[6 * (size_t)warp + 3 * d + v] = d < a.nd ? accK[d][v] : 0.0;
+        }
+    } else if (lane == 0) {
         const PanelGPU &P = panels[panel];
         for (int d = 0; d < 2 && d < a.nd; ++d) {
             AV[P.offV + ((size_t)d * P.rows_pad + row) * P.colsV_pad + colV] = S(accV[d]);
@@ -351,14 +286,14 @@ __global__ void __launch_bounds__(128) k_nf_singular(NfQuadArgs a, const int *__
 }
 
 void launch_nf_singular(const NfQuadArgs &a, const int *sing, int nsing, const PanelGPU *panels, void *AV, void *AK,
-                        bool mixed, cudaStream_t st)
+                        bool mixed, cudaStream_t st, double *cV, double *cK)
 {
     if (nsing == 0) return;
     int blocks = (nsing * 32 + 127) / 128;
     if (mixed)
-        k_nf_singular<float><<<blocks, 128, 0, st>>>(a, sing, nsing, panels, (float *)AV, (float *)AK);
+        k_nf_singular<float><<<blocks, 128, 0, st>>>(a, sing, nsing, panels, (float *)AV, (float *)AK, cV, cK);
     else
-        k_nf_singular<double><<<blocks, 128, 0, st>>>(a, sing, nsing, panels, (double *)AV, (double *)AK);
+        k_nf_singular<double><<<blocks, 128, 0, st>>>(a, sing, nsing, panels, (double *)AV, (double *)AK, cV, cK);
 }
 
 }  // namespace pfmm

@@ -47,7 +47,25 @@ void launch_e1_table(int na, int mt, int mx, int G, double hx, double hxp, doubl
                      double *pref, cudaStream_t st);
 void launch_nf_regular(const NfQuadArgs &a, const PanelGPU &P, void *AV, void *AK, bool mixed, cudaStream_t st);
 void launch_nf_singular(const NfQuadArgs &a, const int *sing, int nsing, const PanelGPU *panels, void *AV, void *AK,
-                        bool mixed, cudaStream_t st);
+                        bool mixed, cudaStream_t st, double *cV = nullptr, double *cK = nullptr);
+
+// on-the-fly nearfield (quadrature fused into the apply, no stored panels)
+struct OtfArgs {
+    NfQuadArgs q;              // geometry, time step, regular rule
+    const PanelGPU *panels;
+    const int *tiles;          // [ntiles][2] (panel, first row) of 64-row tiles
+    int ntiles;
+    const int *tile_sing;      // [ntiles + 1] ranges of the singular list per tile
+    const int *sing;           // [n][12] singular pairs (x, y, panel, row, colV, code, ...)
+    const double *singV;       // [n][2] Sauter-Schwab values, d = 0, 1
+    const double *singK;       // [n][2][3]
+    const void *x;             // V: permuted input [rhs][Et][nt]; K: nodal input [rhs][Et][nv] (arithmetic type)
+    int ncolg, Et, ls, nrhs, ndmax;
+    double *f;                 // [rhs][Et][nt] internal rows, accumulated (+=)
+    int nt;
+};
+// f += nearfield(x) with the panels recomputed tile by tile; kop: double layer (node columns)
+void launch_nf_otf(bool mixed, bool kop, const OtfArgs &a, int nsm, cudaStream_t st);
 
 // ---- apply ------------------------------------------------------------------------------
 struct ApplyGeo {

@@ -114,6 +114,9 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     launch_permute_in(w, xint, H->mixed, nrhs, g, st);
     if (H->tcV && !H->nf_cuda_cores) {  // the same nearfield engine as pfmm_apply_V
         if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, fint, st))) return rc;
+    } else if (H->otf) {
+        cudaMemsetAsync(fint, 0, n_in * sizeof(double), st);
+        if ((rc = run_nf_otf(H, 0, xint, H->nt, H->Et, H->ls, nrhs, 1 << 30, fint, st))) return rc;
     } else {
         launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs, g,
                         fint, st);

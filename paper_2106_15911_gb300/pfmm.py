@@ -20,7 +20,7 @@ PFMM_OK = 0
 PFMM_ERR = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "NOT_CONVERGED",
             -7: "UNSUPPORTED"}
 PFMM_FP64, PFMM_MIXED = 0, 1
-PFMM_NEARFIELD_STORED = 0
+PFMM_NEARFIELD_STORED, PFMM_NEARFIELD_ONTHEFLY = 0, 1
 PFMM_PART_NEAR, PFMM_PART_FAR, PFMM_PART_ALL = 1, 2, 3
 PFMM_NF_AUTO, PFMM_NF_CUDA_CORES = 0, 1
 
@@ -89,6 +89,7 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_int32), _VP]),
     "pfmm_batch_handle": (ctypes.c_int, [_VP, _I, ctypes.POINTER(ctypes.c_void_p)]),
     "pfmm_batch_size": (ctypes.c_int32, [_VP]),
+    "pfmm_batch_set_streams": (ctypes.c_int, [_VP, _I]),
     "pfmm_batch_destroy": (None, [_VP]),
     "pfmm_mpnn_create": (ctypes.c_int, [ctypes.POINTER(pfmm_mesh), _I, _I, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_void_p)]),
@@ -311,6 +312,9 @@ class Batch:
         h = ctypes.c_void_p()
         _check(lib().pfmm_batch_handle(self.b, int(i), ctypes.byref(h)))
         return h
+
+    def set_streams(self, n: int) -> None:
+        _check(lib().pfmm_batch_set_streams(self.b, int(n)))
 
     def apply_V(self, ws, fs, stream=None):
         n = self.n
