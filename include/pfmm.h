@@ -108,6 +108,8 @@ typedef struct pfmm_info {
     int64_t device_bytes;   /* all device bytes held by the handle */
     int32_t nf_tensor_cores;/* bit 0: V nearfield on tensor cores, bit 1: K nearfield */
     int64_t nearfield_v_elements; /* stored V nearfield entries (all panels, all step offsets) */
+    int32_t nf_dense_columns;     /* 1: the panels share one column space (all triangles / nodes,
+                                     zero where the source is not near), 0: compact per panel */
 } pfmm_info;
 
 /* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,

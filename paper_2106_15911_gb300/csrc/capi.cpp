@@ -338,8 +338,8 @@ int pfmm::apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, vo
         int rc = pfmm::run_nf_otf(H, 0, xint, H->nt, ns, 1, 1, 1, fint, st);
         if (rc) return rc;
     } else {
-        launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, 1, g, fint,
-                        st, 1);
+        launch_nf_apply(H->mixed, false, H->nf_blocks(0), H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, 1, g,
+                        fint, st, 1, H->nf_blocks_lo(0));
     }
     launch_permute_out(fint, f, 1, g, st);
     cudaError_t e = cudaGetLastError();
@@ -661,10 +661,11 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             fullV = fullV && P.ncolV == nt && P.colsV_pad == t.panels[0].colsV_pad;
             fullK = fullK && P.ncolK == nv && P.colsK_pad == t.panels[0].colsK_pad;
         }
-        if (fullV)
-            for (int k = 0; k < nt; ++k) fullV = fullV && t.colV[t.panels[0].colV_at + k] == k;
-        if (fullK)
-            for (int k = 0; k < nv; ++k) fullK = fullK && t.colK[t.panels[0].colK_at + k] == k;
+        // every panel's column k is triangle (node) k or a hole: one column space for all panels
+        for (const Panel &P : t.panels) {
+            for (int k = 0; fullV && k < nt; ++k) fullV = t.colV[P.colV_at + k] == k || t.colV[P.colV_at + k] == -1;
+            for (int k = 0; fullK && k < nv; ++k) fullK = t.colK[P.colK_at + k] == k;
+        }
         CK(cudaMalloc((void **)&H->d_err, sizeof(int)));
         H->allocs.push_back(H->d_err);
         CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), st));
@@ -683,6 +684,9 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             size_t n = (size_t)t.sizeV;
             if ((rc = H->alloc(&H->d_AVhi, n)) || (rc = H->alloc(&H->d_AVlo, n))) return rc;
             launch_split_panel((const float *)H->d_AV, H->d_AVhi, H->d_AVlo, n, st);
+            CK(cudaStreamSynchronize(st));
+            H->release(H->d_AV);  // hi + lo represent it; the CUDA-core path reads their sum
+            H->d_AV = nullptr;
             uint64_t dims[2] = {(uint64_t)H->colsV_u, (uint64_t)(n / H->colsV_u)}, str[1] = {(uint64_t)H->colsV_u * 4};
             uint32_t box[2] = {32, 128};
             if ((rc = encode_map(&H->mapAVhi, H->d_AVhi, 2, dims, str, box)) ||
@@ -695,6 +699,9 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             size_t n = (size_t)t.sizeK;
             if ((rc = H->alloc(&H->d_AKhi, n)) || (rc = H->alloc(&H->d_AKlo, n))) return rc;
             launch_split_panel((const float *)H->d_AK, H->d_AKhi, H->d_AKlo, n, st);
+            CK(cudaStreamSynchronize(st));
+            H->release(H->d_AK);
+            H->d_AK = nullptr;
             uint64_t dims[2] = {(uint64_t)H->colsK_u, (uint64_t)(n / H->colsK_u)}, str[1] = {(uint64_t)H->colsK_u * 4};
             uint32_t box[2] = {32, 128};
             if ((rc = encode_map(&H->mapAKhi, H->d_AKhi, 2, dims, str, box)) ||
@@ -793,8 +800,8 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
         CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
         if ((rc = pfmm::run_nf_otf(H, op, xin, ncolg, H->Et, H->ls, nrhs, 1 << 30, H->d_fint, st))) return rc;
     } else if (parts & PFMM_PART_NEAR)
-        launch_nf_apply(H->mixed, op == 1, op == 0 ? H->d_AV : H->d_AK, op == 0 ? H->d_colV : H->d_colK, H->d_tiles,
-                        H->ntiles, H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st);
+        launch_nf_apply(H->mixed, op == 1, H->nf_blocks(op), op == 0 ? H->d_colV : H->d_colK, H->d_tiles, H->ntiles,
+                        H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st, 1 << 30, H->nf_blocks_lo(op));
     else
         CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
     mark(2);
@@ -880,10 +887,13 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
         info->pad[l] = t.lv[l].pad;
     }
     info->n_m2l_pairs = t.n_m2l_pairs;
-    info->nearfield_bytes = h->otf ? h->otf_bytes : (t.sizeV + t.sizeK) * (int64_t)h->es;
+    // stored blocks: the arithmetic-type panels, or their two FP32 parts once split for tcgen05
+    info->nearfield_bytes = h->otf ? h->otf_bytes
+                                   : t.sizeV * (h->tcV ? 8 : (int64_t)h->es) + t.sizeK * (h->tcK ? 8 : (int64_t)h->es);
     info->device_bytes = h->dev_bytes;
     info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
     info->nearfield_v_elements = t.sizeV;
+    info->nf_dense_columns = t.dense_cols ? 1 : 0;
     return PFMM_OK;
 }
 

@@ -93,6 +93,19 @@ struct pfmm_handle {
     double acc_ms[8] = {0};
     int n_prof = 0;
 
+    // stored nearfield blocks of op for the CUDA-core engine: the FP32/FP64 panels, or, once
+    // the tensor-core split exists, its hi part (and nf_blocks_lo the lo part, added on load)
+    const void *nf_blocks(int op) const
+    {
+        const void *a = op == 0 ? d_AV : d_AK;
+        return a ? a : (op == 0 ? (const void *)d_AVhi : (const void *)d_AKhi);
+    }
+    const float *nf_blocks_lo(int op) const
+    {
+        if (op == 0) return d_AV ? nullptr : d_AVlo;
+        return d_AK ? nullptr : d_AKlo;
+    }
+
     ~pfmm_handle()
     {
         for (void *p : allocs) cudaFree(p);

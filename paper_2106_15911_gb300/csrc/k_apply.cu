@@ -77,7 +77,8 @@ template <typename S>
 __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const int *__restrict__ colidx,
                                                     const int *__restrict__ tiles, const PanelGPU *__restrict__ panels,
                                                     const S *__restrict__ x, int ncolg, int Et, int ls, int nint,
-                                                    double *__restrict__ f, int nt, int kop, int ndmax)
+                                                    double *__restrict__ f, int nt, int kop, int ndmax,
+                                                    const S *__restrict__ Alo)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
     constexpr bool kFloat = sizeof(S) == 4;
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
     const int *cols = colidx + (kop ? P.colK_at : P.colV_at);
     const int ncp = kop ? P.colsK_pad : P.colsV_pad;
     A += kop ? P.offK : P.offV;
+    if (Alo) Alo += kop ? P.offK : P.offV;
     S acc[4][4];
     double accd[4][4];
 #pragma unroll
@@ -106,12 +108,13 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
     int ktiles = 0;
     for (int d = 0; d < nd; ++d) {
         const S *Ad = A + ((size_t)d * P.rows_pad + r0) * ncp;
+        const S *Adl = Alo ? Alo + ((size_t)d * P.rows_pad + r0) * ncp : nullptr;
         for (int k0 = 0; k0 < ncp; k0 += BK) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 int e = tid + 256 * q;
                 int i = e >> 4, j = e & 15;
-                As[j][i] = Ad[(size_t)i * ncp + k0 + j];
+                As[j][i] = Adl ? Ad[(size_t)i * ncp + k0 + j] + Adl[(size_t)i * ncp + k0 + j] : Ad[(size_t)i * ncp + k0 + j];
                 int c = e >> 4;
                 int t = ((ib * BN + c) * ls + s);
                 int col = cols[k0 + j];
@@ -161,16 +164,16 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
 
 void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
                      const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
-                     cudaStream_t st, int ndmax)
+                     cudaStream_t st, int ndmax, const float *A_lo)
 {
     int nint = g.Et / g.ls;
     dim3 grd(ntiles, g.ls * ((nint + 63) / 64), nrhs);
     if (mixed)
         k_nf_apply<float><<<grd, 256, 0, st>>>((const float *)A, colidx, tiles, panels, (const float *)x, ncolg, g.Et,
-                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax);
+                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax, A_lo);
     else
         k_nf_apply<double><<<grd, 256, 0, st>>>((const double *)A, colidx, tiles, panels, (const double *)x, ncolg,
-                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax);
+                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax, nullptr);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -118,8 +118,8 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
         cudaMemsetAsync(fint, 0, n_in * sizeof(double), st);
         if ((rc = run_nf_otf(H, 0, xint, H->nt, H->Et, H->ls, nrhs, 1 << 30, fint, st))) return rc;
     } else {
-        launch_nf_apply(H->mixed, false, H->d_AV, H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs, g,
-                        fint, st);
+        launch_nf_apply(H->mixed, false, H->nf_blocks(0), H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs,
+                        g, fint, st, 1 << 30, H->nf_blocks_lo(0));
     }
     const int p = H->p;
     if (p >= 2) {

@@ -71,6 +71,7 @@ struct Tree {
     std::vector<int> colK;        // concatenated K column lists (nodes, -1 pad)
     std::vector<int> kmap;        // [npanel][N_v] node -> K column of the panel or -1
     std::vector<SingularPair> sing;
+    bool dense_cols = false;      // panels index all triangles / nodes (holes: -1 in colV)
     int64_t sizeV = 0, sizeK = 0; // panel elements per operator (all d)
     int n_m2l_pairs = 0;
 };

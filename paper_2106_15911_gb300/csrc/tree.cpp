@@ -257,13 +257,45 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
     const int ND = 2 * prm.leaf_steps;  // step offsets inside the temporal nearfield
     int64_t offV = 0, offK = 0;
     std::vector<std::vector<int>> srcboxes(npan);
+    int64_t covered = 0;
+    for (int X = 0; X < npan; ++X) {
+        for (int Y = 0; Y < npan; ++Y)
+            if (gdist(&Lp.grid[3 * X], &Lp.grid[3 * Y]) <= t.ntr_near) {
+                srcboxes[X].push_back(Y);
+                covered += t.leaf_start[Y + 1] - t.leaf_start[Y];
+            }
+    }
+    // Dense-column layout when the interaction areas cover most of the mesh: every panel
+    // indexes all triangles (column = internal index, -1 where the source is not near) and all
+    // nodes, so the panels share one column space (tensor-core engine) at a small cost in zeros.
+    t.dense_cols = covered >= (int64_t)(0.75 * (double)npan * (double)nt);
     for (int X = 0; X < npan; ++X) {
         Panel &P = t.panels[X];
         P.row0 = t.leaf_start[X];
         P.nrows = t.leaf_start[X + 1] - t.leaf_start[X];
         P.rows_pad = (P.nrows + kRowTile - 1) / kRowTile * kRowTile;
-        for (int Y = 0; Y < npan; ++Y)
-            if (gdist(&Lp.grid[3 * X], &Lp.grid[3 * Y]) <= t.ntr_near) srcboxes[X].push_back(Y);
+        if (t.dense_cols) {
+            std::vector<char> near(npan, 0);
+            for (int Y : srcboxes[X]) near[Y] = 1;
+            P.colV_at = (int)t.colV.size();
+            for (int i = 0; i < nt; ++i) t.colV.push_back(near[t.tri_leaf[i]] ? i : -1);
+            P.ncolV = nt;
+            P.colsV_pad = (nt + kColTile - 1) / kColTile * kColTile;
+            while ((int)t.colV.size() < P.colV_at + P.colsV_pad) t.colV.push_back(-1);
+            P.colK_at = (int)t.colK.size();
+            for (int nd = 0; nd < nv; ++nd) {
+                t.kmap[(size_t)X * nv + nd] = nd;
+                t.colK.push_back(nd);
+            }
+            P.ncolK = nv;
+            P.colsK_pad = (nv + kColTile - 1) / kColTile * kColTile;
+            while ((int)t.colK.size() < P.colK_at + P.colsK_pad) t.colK.push_back(-1);
+            P.offV = offV;
+            P.offK = offK;
+            offV += (int64_t)ND * P.rows_pad * P.colsV_pad;
+            offK += (int64_t)ND * P.rows_pad * P.colsK_pad;
+            continue;
+        }
         P.colV_at = (int)t.colV.size();
         std::set<int> nodes;
         for (int Y : srcboxes[X])
@@ -336,9 +368,13 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
             s.panel = X;
             s.row = x - P.row0;
             int colv = -1, acc = 0;
-            for (int Yb : srcboxes[X]) {
-                if (Yb == Y) { colv = acc + (y - t.leaf_start[Y]); break; }
-                acc += t.leaf_start[Yb + 1] - t.leaf_start[Yb];
+            if (t.dense_cols) {
+                colv = y;
+            } else {
+                for (int Yb : srcboxes[X]) {
+                    if (Yb == Y) { colv = acc + (y - t.leaf_start[Y]); break; }
+                    acc += t.leaf_start[Yb + 1] - t.leaf_start[Yb];
+                }
             }
             s.colV = colv;
             for (int v = 0; v < 3; ++v) s.colK[v] = t.kmap[(size_t)X * nv + ty[v]];

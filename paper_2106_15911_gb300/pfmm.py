@@ -42,7 +42,7 @@ class pfmm_info(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("lx", ctypes.c_int32 * 32), ("nbox", ctypes.c_int32 * 32),
                 ("pad", ctypes.c_double * 32), ("n_m2l_pairs", ctypes.c_int32), ("nearfield_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("nf_tensor_cores", ctypes.c_int32),
-                ("nearfield_v_elements", ctypes.c_int64)]
+                ("nearfield_v_elements", ctypes.c_int64), ("nf_dense_columns", ctypes.c_int32)]
 
 
 class pfmm_solve_opts(ctypes.Structure):
@@ -237,7 +237,7 @@ def pfmm_get_info(h) -> dict:
     n = i.p + 1
     return dict(p=i.p, lx=list(i.lx[:n]), nbox=list(i.nbox[:n]), pad=list(i.pad[:n]), n_m2l_pairs=i.n_m2l_pairs,
                 nearfield_bytes=i.nearfield_bytes, device_bytes=i.device_bytes, nf_tensor_cores=i.nf_tensor_cores,
-                nearfield_v_elements=i.nearfield_v_elements)
+                nearfield_v_elements=i.nearfield_v_elements, nf_dense_columns=i.nf_dense_columns)
 
 
 def pfmm_check(h):

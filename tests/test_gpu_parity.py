@@ -175,3 +175,33 @@ def test_tensor_core_nearfield_matches_cuda_cores_and_oracle(n_a, Et, kw):
             assert _rel(res[P.PFMM_NF_AUTO][r], res[P.PFMM_NF_CUDA_CORES][r]) <= 1e-5
     for o in ops.values():
         o.close()
+
+
+def test_dense_column_layout_with_holes():
+    """Interaction areas that cover most but not all of the mesh (8^3-like leaf grid, n_tr = 6):
+    the panels share one column space with zero (hole) columns for sources outside the area.
+    FP64 against the oracle on sampled rows; mixed precision on the tensor cores against the
+    CUDA-core engine on the same blocks."""
+    V, T = cube_sphere_mesh(16)  # 3072 triangles
+    Et = 64
+    kw = dict(m_t=4, m_x=5, c_st=0.1, n_tr=6)
+    op = P.Operator(V, T, 1.0, Et, **kw)
+    info = op.info()
+    assert info["nf_dense_columns"] == 1 and info["p"] == 5
+    Pr = O.make_problem(V, T, 1.0, Et, **kw)
+    w = random_density(Et, len(T), 1, seed=41)
+    g = random_density(Et, len(V), 1, seed=42)
+    rows = sample_triangles(len(T), 5, seed=43)
+    fV = op.V(torch.tensor(w, device=DEV))[0].cpu().numpy()
+    fK = op.K(torch.tensor(g, device=DEV))[0].cpu().numpy()
+    assert _rel(fV, O.pfmm_apply(Pr, 0, w[0], targets=rows), rows) <= 1e-12
+    assert _rel(fK, O.pfmm_apply(Pr, 1, g[0], targets=rows), rows) <= 1e-12
+    op.close()
+    opt = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, **kw)
+    opc = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, nf_engine=P.PFMM_NF_CUDA_CORES, **kw)
+    assert opt.info()["nf_tensor_cores"] == 3 and opc.info()["nf_tensor_cores"] == 0
+    wt, gt = torch.tensor(w, device=DEV), torch.tensor(g, device=DEV)
+    assert _rel(opt.V(wt).cpu().numpy(), opc.V(wt).cpu().numpy()) <= 1e-5
+    assert _rel(opt.K(gt).cpu().numpy(), opc.K(gt).cpu().numpy()) <= 1e-5
+    opt.close()
+    opc.close()
