@@ -232,6 +232,24 @@ def _batch_comparison(dev, n_problems, seed=3, tol=3e-3):
             "m_x_histogram": {str(m): mx.count(m) for m in sorted(set(mx))}}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest per-rank value (the slowest replica's time) on every rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_throughput(units_per_rank: float, ms_step: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas: all ranks' units over the slowest
+    rank's time (weak scaling, no data-path collective)."""
+    return world * units_per_rank / (ms_step * 1e-3)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
@@ -336,12 +354,8 @@ def main():
     ms, phases = run_device_timed(args.steps, args.warmup, op, prof=True)
     stop.set()
     th.join(timeout=5)
-    ms_step = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * dof / (ms_step * 1e-3)
+    ms_step = max_over_ranks(statistics.mean(ms), world, dev)
+    value = replicas_throughput(dof, ms_step, world)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     wh = torch.tensor(random_density(ET, nt, 1, seed=99 + rank)).pin_memory()
@@ -360,8 +374,8 @@ def main():
         fh.copy_(fd, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    e2e = {"value": world * dof / (e2e_ms * 1e-3), "unit": "space-time DOF/s", "h2d_bytes_per_step": 8 * dof,
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    e2e = {"value": replicas_throughput(dof, e2e_ms, world), "unit": "space-time DOF/s", "h2d_bytes_per_step": 8 * dof,
            "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_ms}
 
     # ---- roofline of the dominant kernel (nearfield apply): algorithmic work per launch
