@@ -232,6 +232,85 @@ def _batch_comparison(dev, n_problems, seed=3, tol=3e-3):
             "m_x_histogram": {str(m): mx.count(m) for m in sorted(set(mx))}}
 
 
+def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
+    """Large combined run: cube-sphere 49152 triangles x 1024 steps (50.3M space-time DOF),
+    m_x 6, m_t 4, mixed precision with the stored (dense-column, tensor-core) nearfield, learned
+    preconditioner retrained at this size on residuals recorded by mixed FGMRES(30) runs, then
+    n_rhs heat-source data sets solved with FGMRES(30) + the network (and one without it) to
+    `tol` in the mixed operator; device memory is sampled after every stage (cap 180 GB)."""
+    import torch
+
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_sphere_mesh, heat_source_datum, shell_sources
+
+    V, T = cube_sphere_mesh(64)
+    Et, nt = 1024, T.shape[0]
+    free0, total = torch.cuda.mem_get_info()
+    peak = [0.0]
+
+    def track():
+        peak[0] = max(peak[0], (free0 - torch.cuda.mem_get_info()[0]) / 1e9)
+
+    t0 = time.perf_counter()
+    opm = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_MIXED)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = opm.info()
+    track()
+    w = torch.randn((n_rhs, Et, nt), dtype=torch.float64, device=dev)
+    f = torch.empty_like(w)
+    P.pfmm_apply_V(opm.h, w, f, n_rhs, None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    P.pfmm_apply_V(opm.h, w, f, n_rhs, None)
+    e1.record()
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1)
+    track()
+    del w, f
+
+    def datum(seed):
+        return torch.tensor(heat_source_datum(V, 1.0, Et, shell_sources(1, seed=seed))[None], device=dev)
+
+    per = 8
+    R = torch.empty((n_record * per, Et, nt), dtype=torch.float64, device=dev)
+    x = torch.empty((1, Et, nt), dtype=torch.float64, device=dev)
+    used, t0 = 0, time.perf_counter()
+    for k in range(n_record):
+        o = P.pfmm_default_solve_opts()
+        o.tol, o.restart, o.rec_r, o.rec_cap, o.rec_every = tol, 30, R[used].data_ptr(), per, 4
+        used += P.pfmm_solve(opm.h, P.PFMM_DIRECT, datum(4 + k), x, 1, o, allow_not_converged=True)["recorded"]
+        track()
+    rec_s = time.perf_counter() - t0
+    net = P.Mpnn(V, T, 1.0, Et, width=64, layers=4, seed=7)
+    t0 = time.perf_counter()
+    hist = net.train(R, None, used, steps=1000, batch_slices=16, lr=3e-3, seed=8, handle=opm.h)
+    train_s = time.perf_counter() - t0
+    track()
+    del R
+    torch.cuda.empty_cache()
+    solves = []
+    for k in range(n_rhs):
+        o = P.pfmm_default_solve_opts()
+        o.tol, o.restart, o.precond = tol, 30, net.ptr
+        solves.append(P.pfmm_solve(opm.h, P.PFMM_DIRECT, datum(5000 + k), x, 1, o, allow_not_converged=True))
+        track()
+    o = P.pfmm_default_solve_opts()
+    o.tol, o.restart = tol, 30
+    plain = P.pfmm_solve(opm.h, P.PFMM_DIRECT, datum(5000), x, 1, o, allow_not_converged=True)
+    track()
+    net.close()
+    opm.close()
+    return {"workload": f"cube-sphere {nt} tri x {Et} steps ({nt * Et} DOF), m_x 6, m_t 4, mixed, stored nearfield",
+            "build_s": build_s, "nearfield_GB": info["nearfield_bytes"] / 1e9, "nf_tensor_cores": info["nf_tensor_cores"],
+            "matvec_ms_nrhs": {str(n_rhs): mv_ms}, "matvec_dofs_per_s": n_rhs * nt * Et / (mv_ms * 1e-3),
+            "record": {"data_sets": n_record, "residuals": used, "seconds": rec_s},
+            "train": {"steps": 1000, "seconds": train_s, "loss_first": float(hist[:10].mean()),
+                      "loss_last": float(hist[-50:].mean())},
+            "solve_tol": tol, "learned": solves, "plain_first_rhs": plain,
+            "peak_device_GB": peak[0], "device_total_GB": total / 1e9, "cap_GB": 180}
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest per-rank value (the slowest replica's time) on every rank."""
     if world <= 1:
@@ -284,6 +363,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
     ap.add_argument("--solve-sets", type=int, default=32, help="held-out data sets of the solver comparison")
+    ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
     ap.add_argument("--et", type=int, default=ET, help="profiling only: time steps")
@@ -305,6 +385,10 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.config5:
+        if rank == 0:
+            print(json.dumps({"config5": _config5(dev)}), flush=True)
+        return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
