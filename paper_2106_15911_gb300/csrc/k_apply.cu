@@ -340,15 +340,18 @@ __global__ void __launch_bounds__(256) k_m2m_st(const R *__restrict__ mu_c, R *_
 {
     extern __shared__ unsigned char smem_raw[];
     const int m1 = mx + 1;
-    R *tmp = reinterpret_cast<R *>(smem_raw);  // [8][na][nk]
-    R *qs = tmp + 8 * na * nk;                 // [2][m1][m1]
+    R *tmp = reinterpret_cast<R *>(smem_raw);  // [8][nk]: children's contracted moments for node ap
+    R *part = tmp + 8 * nk;                    // [8][nk]: partial sums over children, per thread group
+    R *qs = part + 8 * nk;                     // [2][m1][m1]
     int *kin = reinterpret_cast<int *>(qs + 2 * m1 * m1);
-    const int kp = blockIdx.x / nbox_p, bp = blockIdx.x % nbox_p, rhs = blockIdx.y;
+    // one CTA per (kp, bp, ap): the outputs of one parent time node
+    const int ap = blockIdx.x % na, pb = blockIdx.x / na;
+    const int kp = pb / nbox_p, bp = pb % nbox_p, rhs = blockIdx.y;
     const int c0 = ch_ptr[bp], nch = ch_ptr[bp + 1] - c0;
     for (int i = threadIdx.x; i < 2 * m1 * m1; i += blockDim.x) qs[i] = q1[i];
     for (int i = threadIdx.x; i < m1 * m1 * m1; i += blockDim.x) kin[i] = kinv[i];
-    for (int i = threadIdx.x; i < nch * na * nk; i += blockDim.x) {
-        int e = i / (na * nk), ap = (i / nk) % na, ik = i % nk, bc = ch_idx[c0 + e];
+    for (int i = threadIdx.x; i < nch * nk; i += blockDim.x) {
+        int e = i / nk, ik = i % nk, bc = ch_idx[c0 + e];
         R v = R(0);
         for (int c = 0; c < 2; ++c) {
             const R *m = mu_c + (((size_t)rhs * 2 * nint_p + 2 * kp + c) * nbox_c + bc) * na * nk + ik;
@@ -357,25 +360,35 @@ __global__ void __launch_bounds__(256) k_m2m_st(const R *__restrict__ mu_c, R *_
         tmp[i] = v;
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < na * nk; o += blockDim.x) {
-        const int ap = o / nk, iv = o % nk;
+    // output iv: `per` threads take every per-th child; their partial sums are added in a fixed
+    // order afterwards (deterministic)
+    const int per = max(1, min((int)blockDim.x / nk, 8));
+    for (int o = threadIdx.x; o < nk * per; o += blockDim.x) {
+        const int iv = o % nk, g = o / nk;
         const int n0 = kidx[3 * iv], n1 = kidx[3 * iv + 1], n2 = kidx[3 * iv + 2];
         R acc = R(0);
-        for (int e = 0; e < nch; ++e) {
+        for (int e = g; e < nch; e += per) {
             const int oc = oct_c[ch_idx[c0 + e]];
             const R *qa = qs + (oc & 1) * m1 * m1, *qb = qs + ((oc >> 1) & 1) * m1 * m1, *qc = qs + ((oc >> 2) & 1) * m1 * m1;
-            const R *tp = tmp + (e * na + ap) * nk;
+            const R *tp = tmp + e * nk;
             for (int k0 = 0; k0 <= n0; ++k0)
                 for (int k1 = 0; k1 <= n1; ++k1) {
                     const R q01 = qa[k0 * m1 + n0] * qb[k1 * m1 + n1];
                     for (int k2 = 0; k2 <= n2; ++k2) acc += q01 * qc[k2 * m1 + n2] * tp[kin[(k0 * m1 + k1) * m1 + k2]];
                 }
         }
-        mu_p[(((size_t)rhs * nint_p + kp) * nbox_p + bp) * na * nk + o] = acc;
+        part[g * nk + iv] = acc;
+    }
+    __syncthreads();
+    R *out = mu_p + (((size_t)rhs * nint_p + kp) * nbox_p + bp) * na * nk + (size_t)ap * nk;
+    for (int iv = threadIdx.x; iv < nk; iv += blockDim.x) {
+        R sum = R(0);
+        for (int g = 0; g < per; ++g) sum += part[g * nk + iv];
+        out[iv] = sum;
     }
 }
 
-// Space-time L2L (transpose of Eq. st_m2m) with one CTA per parent (kp, bp, rhs): for each child,
+// Space-time L2L (transpose of Eq. st_m2m) with one CTA per (parent (kp, bp), child box, rhs):
 //   tmp[bp_][kap] = sum_{nu >= kap, |nu| <= m_x} q^(x)_{kap,nu}(child) lam_p[bp_][nu],
 //   lam_c[2 kp + c][child][bc][kap] += sum_{bp_} q^(t)_c[bc][bp_] tmp[bp_][kap].
 template <typename R>
@@ -392,13 +405,15 @@ __global__ void __launch_bounds__(256) k_l2l_st(const R *__restrict__ lam_p, R *
     R *tmp = lp + na * nk;                    // [na][nk]
     R *qs = tmp + na * nk;                    // [2][m1][m1]
     int *kin = reinterpret_cast<int *>(qs + 2 * m1 * m1);
-    const int kp = blockIdx.x / nbox_p, bp = blockIdx.x % nbox_p, rhs = blockIdx.y;
+    const int e = blockIdx.x % 8, pb = blockIdx.x / 8;
+    const int kp = pb / nbox_p, bp = pb % nbox_p, rhs = blockIdx.y;
     const int c0 = ch_ptr[bp], nch = ch_ptr[bp + 1] - c0;
+    if (e >= nch) return;  // the parent has fewer children
     for (int i = threadIdx.x; i < 2 * m1 * m1; i += blockDim.x) qs[i] = q1[i];
     for (int i = threadIdx.x; i < m1 * m1 * m1; i += blockDim.x) kin[i] = kinv[i];
     const R *src = lam_p + (((size_t)rhs * nint_p + kp) * nbox_p + bp) * na * nk;
     for (int i = threadIdx.x; i < na * nk; i += blockDim.x) lp[i] = src[i];
-    for (int e = 0; e < nch; ++e) {
+    {
         const int bc = ch_idx[c0 + e], oc = oct_c[bc];
         const R *qa = qs + (oc & 1) * m1 * m1, *qb = qs + ((oc >> 1) & 1) * m1 * m1, *qc = qs + ((oc >> 2) & 1) * m1 * m1;
         __syncthreads();
@@ -435,8 +450,8 @@ void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
     char *base = (char *)mu;
     const int m1 = g.mx + 1;
     if (ch.st) {
-        size_t smem = es * ((size_t)8 * g.na * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
-        dim3 grd(par.nint * par.nbox, nrhs);
+        size_t smem = es * ((size_t)16 * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
+        dim3 grd(par.nint * par.nbox * g.na, nrhs);
         if (mixed) {
             cudaFuncSetAttribute(k_m2m_st<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_m2m_st<float><<<grd, 256, smem, st>>>((const float *)(base + ch.mom_off * es * nrhs),
@@ -612,14 +627,19 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
 // FMAs from 16 moment / intermediate loads and 7 coefficient loads.  Coefficients beyond the
 // interaction radius are zeroed once per (J, a), which applies Eq. 03:Iarea without branches.
 // Same arithmetic as the three-pass kernels (cells with G < 4 are padded with empty cells).
+// Split mode (levels with too few intervals to fill the GPU): one CTA per (k, b, source term)
+// with source term = (J, a) of the interaction list; each term's locals go to its own slice of a
+// workspace and k_m2l_sum_terms adds the slices in a fixed order (deterministic).
 constexpr int FG = 4;  // padded grid extent per direction
 
 constexpr int kM2LThreads = 384;
+constexpr int kM2LSms = 152;  // CTA-count threshold of the split mode (two CTAs per SM on GB300)
 
 template <typename R>
 __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
                                                                 const R *__restrict__ E1, const R *__restrict__ pref,
-                                                                R *__restrict__ lam, int nrhs)
+                                                                R *__restrict__ lam, int nrhs, int split,
+                                                                R *__restrict__ part)
 {
     extern __shared__ unsigned char smem_raw[];
     constexpr int C3 = FG * FG * FG, CS = C3 + 1;  // cell rows are padded by one (bank spread)
@@ -631,7 +651,9 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
     int *kin = kid + nk;
     int *eof = kin + m1 * m1 * m1;
     int *cbx = eof + nk;                       // [C3] padded cell -> box or -1
-    const int k = blockIdx.x / na, b = blockIdx.x % na, rhs = blockIdx.y;
+    const int nterm = split ? 2 * na : 1;  // source terms per CTA group: (J index, a)
+    const int kb = blockIdx.x / nterm, term = blockIdx.x % nterm;
+    const int k = kb / na, b = kb % na, rhs = blockIdx.y;
     for (int i = threadIdx.x; i < nk; i += blockDim.x) {
         kid[i] = A.kidx[3 * i] | (A.kidx[3 * i + 1] << 8) | (A.kidx[3 * i + 2] << 16);
         eof[i] = A.eoff[i];
@@ -655,9 +677,12 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
         else { js[0] = k - 3; js[1] = k - 2; nj = 2; }
     }
     const int no = 2 * G - 1, nitems = nk * FG;
-    for (int jj = 0; jj < nj; ++jj) {
+    const int j_lo = split ? term / na : 0, j_hi = split ? j_lo + 1 : nj;
+    const int a_lo = split ? term % na : 0, a_hi = split ? a_lo + 1 : na;
+    if (split && j_lo >= nj) return;  // this (k) has fewer source intervals
+    for (int jj = j_lo; jj < j_hi; ++jj) {
         const int J = js[jj], D = k - J;
-        for (int a = 0; a < na; ++a) {
+        for (int a = a_lo; a < a_hi; ++a) {
             __syncthreads();
             const R *mJ = mu + ((size_t)rhs * A.nint + J) * A.nbox * na * nk;
             for (int i = threadIdx.x; i < nk * C3; i += blockDim.x) {
@@ -776,8 +801,10 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
             }
         }
     }
-    // write the locals of the non-empty target boxes (intervals 0 and 1 get zeros)
-    R *lk = lam + ((size_t)rhs * A.nint + k) * A.nbox * na * nk;
+    // write the locals of the non-empty target boxes (intervals 0 and 1 get zeros); split mode:
+    // this term's slice of the workspace
+    R *lk = (split ? part + (size_t)term * nrhs * A.nint * A.nbox * na * nk : lam) +
+            ((size_t)rhs * A.nint + k) * A.nbox * na * nk;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int it = threadIdx.x + q * blockDim.x;
@@ -793,6 +820,16 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
                 if (box >= 0) lk[((size_t)box * na + b) * nk + iv] = lamr[q][X2][X3];
             }
     }
+}
+
+template <typename R>
+__global__ void k_m2l_sum_terms(const R *__restrict__ part, int nterm, size_t n, R *__restrict__ lam)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    R s = R(0);
+    for (int t = 0; t < nterm; ++t) s += part[(size_t)t * n + i];
+    lam[i] = s;
 }
 
 size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
@@ -815,17 +852,25 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
     if (mixed && L.G <= FG && fsm <= 200 * 1024 && g.nk * FG <= 2 * kM2LThreads) {
         M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
                   g.kidx, g.kinv, g.eoff};
-        dim3 grd(L.nint * na, nrhs);
+        // too few (interval, node) CTAs for two per SM: one CTA per source term as well, when the
+        // terms' partial locals fit the workspace
+        const size_t nlev = (size_t)nrhs * L.nint * L.nbox * na * g.nk;
+        const int nterm = 2 * na;
+        const int split = ((int64_t)L.nint * na * nrhs < 2 * kM2LSms && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
+        dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
         const char *mbf = (const char *)mu + L.mom_off * es * nrhs;
         char *lbf = (char *)lam + L.mom_off * es * nrhs;
+        if (split) cudaMemsetAsync(T1, 0, es * nterm * nlev, st);  // terms a CTA does not cover stay zero
         if (mixed) {
             cudaFuncSetAttribute(k_m2l_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
             k_m2l_fused<float><<<grd, kM2LThreads, fsm, st>>>(A, (const float *)mbf, (const float *)L.E1, (const float *)L.pref,
-                                                      (float *)lbf, nrhs);
+                                                      (float *)lbf, nrhs, split, (float *)T1);
+            if (split) k_m2l_sum_terms<float><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const float *)T1, nterm, nlev, (float *)lbf);
         } else {
             cudaFuncSetAttribute(k_m2l_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
             k_m2l_fused<double><<<grd, kM2LThreads, fsm, st>>>(A, (const double *)mbf, (const double *)L.E1,
-                                                       (const double *)L.pref, (double *)lbf, nrhs);
+                                                       (const double *)L.pref, (double *)lbf, nrhs, split, (double *)T1);
+            if (split) k_m2l_sum_terms<double><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const double *)T1, nterm, nlev, (double *)lbf);
         }
         return 0;
     }
@@ -919,7 +964,7 @@ void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
     const int m1 = g.mx + 1;
     if (ch.st) {
         size_t smem = es * ((size_t)2 * g.na * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
-        dim3 grd(par.nint * par.nbox, nrhs);
+        dim3 grd(par.nint * par.nbox * 8, nrhs);  // one CTA per (parent, child slot); empty slots exit
         if (mixed)
             k_l2l_st<float><<<grd, 256, smem, st>>>((const float *)(base + par.mom_off * es * nrhs),
                                                     (float *)(base + ch.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
