@@ -126,14 +126,22 @@ def _solve_comparison(dev, n_train=256, n_test=32):
     t_train = time.perf_counter() - t0
     del R
     zz = torch.empty_like(x)
-    net.apply(x, zz)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(10):
+
+    def t_net():
         net.apply(x, zz)
-    e1.record()
-    torch.cuda.synchronize()
-    t_apply = e0.elapsed_time(e1) / 10
+        e0.record()
+        for _ in range(10):
+            net.apply(x, zz)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 10
+
+    t_apply = t_net()  # the network's layer kernels
+    t0 = time.perf_counter()
+    net.compile()  # its per-step sparse operators, used by the solves below
+    t_compile = time.perf_counter() - t0
+    t_apply_c = t_net()
     arms = {"fp64_fgmres": [], "mixed_gmres_ir": [], "mixed_gmres_ir_learned": []}
     worst_diff = 0.0
     for k in range(n_test):
@@ -161,7 +169,8 @@ def _solve_comparison(dev, n_train=256, n_test=32):
                         f"{n_test} held-out heat-source data sets",
             "training": {"data_sets": n_train, "recorded_residuals": used, "record_s": t_gen, "train_s": t_train,
                          "steps": 1500, "loss_first": float(hist[:10].mean()), "loss_last": float(hist[-50:].mean()),
-                         "network": "width 64, 4 layers, BF16 weights, tcgen05 layers", "apply_ms": t_apply},
+                         "network": "width 64, 4 layers, BF16 weights, tcgen05 layers", "apply_ms": t_apply,
+                         "compile_s": t_compile, "compiled_apply_ms": t_apply_c},
             **out,
             "speedup_learned_vs_fp64": out["fp64_fgmres"]["mean_seconds"] / out["mixed_gmres_ir_learned"]["mean_seconds"],
             "speedup_learned_vs_mixed": out["mixed_gmres_ir"]["mean_seconds"] / out["mixed_gmres_ir_learned"]["mean_seconds"],
@@ -289,6 +298,11 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
     track()
     del R
     torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    net.compile()
+    compile_s = time.perf_counter() - t0
+    track()
+    torch.cuda.empty_cache()
     solves = []
     for k in range(n_rhs):
         o = P.pfmm_default_solve_opts()
@@ -306,7 +320,7 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
             "matvec_ms_nrhs": {str(n_rhs): mv_ms}, "matvec_dofs_per_s": n_rhs * nt * Et / (mv_ms * 1e-3),
             "record": {"data_sets": n_record, "residuals": used, "seconds": rec_s},
             "train": {"steps": 1000, "seconds": train_s, "loss_first": float(hist[:10].mean()),
-                      "loss_last": float(hist[-50:].mean())},
+                      "loss_last": float(hist[-50:].mean()), "compile_s": compile_s},
             "solve_tol": tol, "learned": solves, "plain_first_rhs": plain,
             "peak_device_GB": peak[0], "device_total_GB": total / 1e9, "cap_GB": 180}
 

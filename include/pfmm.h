@@ -305,6 +305,15 @@ int pfmm_mpnn_loss_grad(pfmm_mpnn *net, pfmm_handle *h, const double *R, const d
  * step's loss.  Synchronises `stream`. */
 int pfmm_mpnn_train(pfmm_mpnn *net, pfmm_handle *h, const double *R, const double *E, int64_t nvec, int32_t steps,
                     int32_t batch_slices, float lr, uint64_t seed, float *loss_history, void *stream);
+/* Compiled form: the network is linear in each slice and each layer reaches one more edge
+ * neighbour, so for every step t it equals a sparse operator P_t whose row i lives on the ball
+ * of `layers` edges around triangle i.  This assembles P_t (FP32) by probing: the triangles are
+ * coloured so that any two within 2 layers edges differ, the network is applied (with its own
+ * kernels) to one 0/1 probe per colour, and each result fills the ball entries of that colour.
+ * Afterwards pfmm_mpnn_apply computes z = P_t v (FP64 sums); any parameter change (set_params,
+ * training, set_output_scale) drops the compiled form.  Needs E_t * E_x * max ball size floats.
+ * Synchronises `stream`. */
+int pfmm_mpnn_compile(pfmm_mpnn *net, void *stream);
 /* Reads and clears the network's error word: PFMM_ERR_TIMEOUT when a bounded wait of its
  * tensor-core kernels gave up since the last check (pfmm_mpnn_apply is asynchronous; training
  * and pfmm_solve check on return).  Synchronises the device. */

@@ -447,6 +447,48 @@ __global__ void k_to_bf16(const float *__restrict__ p, __nv_bfloat16 *__restrict
 
 unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// ---- compiled form ------------------------------------------------------------------------------
+// probe of colour q on every slice: u[t][j] = 1 where colour(j) = q
+__global__ void k_probe(const int *__restrict__ colour, int q, int nt, int64_t n, double *__restrict__ u)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] = colour[i % nt] == q ? 1.0 : 0.0;
+}
+
+// P_t[i][k] = z_q[t][i] for the ball member k of row i that has colour q (at most one)
+__global__ void k_extract(const double *__restrict__ zq, const int *__restrict__ supc, int q, int nt, int kmax,
+                          int64_t n, float *__restrict__ Pc)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t t = r / nt;
+    const int i = (int)(r % nt);
+    for (int k = 0; k < kmax; ++k)
+        if (supc[(size_t)k * nt + i] == q) {
+            Pc[((size_t)t * kmax + k) * nt + i] = (float)zq[r];
+            break;
+        }
+}
+
+// z[b][i] = sum_k P_t[i][k] v[b][ball_k(i)], t = b mod E_t (one thread per row, FP64 sum)
+__global__ void k_spmv_compiled(const double *__restrict__ v, double *__restrict__ z, const float *__restrict__ Pc,
+                                const int *__restrict__ sup, int nt, int Et, int kmax, int64_t rows)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int64_t b = r / nt;
+    const int i = (int)(r % nt), t = (int)(b % Et);
+    const double *vb = v + b * nt;
+    const float *P = Pc + (size_t)t * kmax * nt + i;
+    double acc = 0.0;
+    for (int k = 0; k < kmax; ++k) {
+        const int j = sup[(size_t)k * nt + i];
+        if (j < 0) break;
+        acc += (double)P[(size_t)k * nt] * vb[j];
+    }
+    z[r] = acc;
+}
+
 // ---- tensor-core layer -------------------------------------------------------------------------
 using namespace pfmm::tc;
 constexpr int TM = 128;                              // rows per tensor-core tile (MMA M)
@@ -687,6 +729,14 @@ struct pfmm_mpnn {
           *dy = nullptr, *scale = nullptr, *en2 = nullptr;
     double *z = nullptr, *u = nullptr, *du = nullptr, *ssx = nullptr, *ssf = nullptr;
     int *sid = nullptr;
+    // host copy of the edge adjacency (CSR), for the compiled form
+    std::vector<int> hptr, hadj;
+    // compiled form: z_t = P_t v with P_t[i][k] on the radius-L ball of triangle i
+    bool compiled = false;
+    int kmax = 0, ncolor = 0;
+    int *sup = nullptr;   // [kmax][nt] ball members (-1 after the last)
+    int *supc = nullptr;  // [kmax][nt] their colours
+    float *Pc = nullptr;  // [Et][kmax][nt]
     std::vector<void *> mem;
     ~pfmm_mpnn()
     {
@@ -980,6 +1030,8 @@ int pfmm_mpnn_create(const pfmm_mesh *mesh, int32_t width, int32_t layers, uint6
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&N->nsm, cudaDevAttrMultiProcessorCount, dev);
     }
+    N->hptr = ptr;
+    N->hadj = adj;
     size_t maxdeg = 0;
     for (int x = 0; x < nt; ++x) maxdeg = std::max(maxdeg, nb[x].size());
     if (maxdeg <= 3) {
@@ -1034,6 +1086,7 @@ int pfmm_mpnn_set_params(pfmm_mpnn *net, const float *host, int64_t n)
     if (!net || !host || n != net->nparam) return set_error(PFMM_ERR_INVALID_ARG, "parameter count mismatch");
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(host[i])) return set_error(PFMM_ERR_NONFINITE, "parameters hold NaN or Inf");
+    net->compiled = false;
     cudaMemcpy(net->p32, host, n * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemset(net->m1, 0, n * sizeof(float));
     cudaMemset(net->m2, 0, n * sizeof(float));
@@ -1047,6 +1100,7 @@ int pfmm_mpnn_set_output_scale(pfmm_mpnn *net, float c)
 {
     if (!net || !(c > 0) || !std::isfinite(c)) return set_error(PFMM_ERR_INVALID_ARG, "output scale must be > 0");
     net->c_out = c;
+    net->compiled = false;
     return PFMM_OK;
 }
 
@@ -1063,6 +1117,11 @@ int pfmm_mpnn_apply(pfmm_mpnn *net, const double *v, double *z, int32_t nvec, vo
     if (!(net->c_out > 0)) return set_error(PFMM_ERR_INVALID_ARG, "the network has no output scale (train it or set one)");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t total = (int64_t)nvec * net->Et, per = std::max<int64_t>(kChunkRows / net->nt, 1);
+    if (net->compiled) {
+        const int64_t rows = total * net->nt;
+        k_spmv_compiled<<<nblk(rows), 256, 0, st>>>(v, z, net->Pc, net->sup, net->nt, net->Et, net->kmax, rows);
+        return cuda_status("compiled network apply");
+    }
     for (int64_t s0 = 0; s0 < total; s0 += per) {
         const int64_t ns = std::min(per, total - s0);
         dispatch_w(net->W, [&](auto w) {
@@ -1099,6 +1158,7 @@ int pfmm_mpnn_train(pfmm_mpnn *net, pfmm_handle *h, const double *R, const doubl
     if (nvec < 1 || steps < 0 || batch_slices < 1 || !(lr > 0))
         return set_error(PFMM_ERR_INVALID_ARG, "invalid training arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    net->compiled = false;
     const int64_t total = nvec * net->Et;
     const int ns = (int)std::min<int64_t>(batch_slices, total);
     std::mt19937_64 rng(seed);
@@ -1131,6 +1191,92 @@ int pfmm_mpnn_train(pfmm_mpnn *net, pfmm_handle *h, const double *R, const doubl
     if (loss_history && steps > 0) cudaMemcpy(loss_history, hist, steps * sizeof(float), cudaMemcpyDeviceToHost);
     net->drop(hist);
     if ((rc = cuda_status("training"))) return rc;
+    return pfmm_mpnn_check(net);
+}
+
+int pfmm_mpnn_compile(pfmm_mpnn *net, void *stream)
+{
+    if (!net) return set_error(PFMM_ERR_INVALID_ARG, "net is NULL");
+    if (!(net->c_out > 0)) return set_error(PFMM_ERR_INVALID_ARG, "the network has no output scale");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nt = net->nt, Et = net->Et, L = net->L;
+    // radius-L balls (breadth first over the edge adjacency), then a greedy colouring in which
+    // triangles closer than 2L + 1 edges get different colours: two members of one ball never
+    // share a colour, so one probe per colour recovers every coefficient
+    auto bfs = [&](int src, int depth, std::vector<int> &out, std::vector<int> &mark, int stamp) {
+        out.clear();
+        out.push_back(src);
+        mark[src] = stamp;
+        size_t lo = 0;
+        for (int d = 0; d < depth; ++d) {
+            const size_t hi = out.size();
+            for (size_t a = lo; a < hi; ++a)
+                for (int q = net->hptr[out[a]]; q < net->hptr[out[a] + 1]; ++q) {
+                    const int j = net->hadj[q];
+                    if (mark[j] != stamp) {
+                        mark[j] = stamp;
+                        out.push_back(j);
+                    }
+                }
+            lo = hi;
+        }
+    };
+    std::vector<int> mark(nt, -1), ball, colour(nt, -1);
+    std::vector<std::vector<int>> balls(nt);
+    int kmax = 0, stamp = 0;
+    for (int i = 0; i < nt; ++i) {
+        bfs(i, L, ball, mark, stamp++);
+        balls[i] = ball;
+        kmax = std::max(kmax, (int)ball.size());
+    }
+    int ncolour = 0;
+    std::vector<int> used;
+    for (int j = 0; j < nt; ++j) {
+        bfs(j, 2 * L, ball, mark, stamp++);
+        used.assign(ncolour + 1, 0);
+        for (int x : ball)
+            if (colour[x] >= 0) used[colour[x]] = 1;
+        int c = 0;
+        while (c < ncolour && used[c]) ++c;
+        colour[j] = c;
+        ncolour = std::max(ncolour, c + 1);
+    }
+    std::vector<int> sup((size_t)kmax * nt, -1), supc((size_t)kmax * nt, -1);
+    for (int i = 0; i < nt; ++i)
+        for (size_t k = 0; k < balls[i].size(); ++k) {
+            sup[k * nt + i] = balls[i][k];
+            supc[k * nt + i] = colour[balls[i][k]];
+        }
+    for (void *p : {(void *)net->sup, (void *)net->supc, (void *)net->Pc}) net->drop(p);
+    net->sup = net->supc = nullptr;
+    net->Pc = nullptr;
+    int *dcol = nullptr;
+    double *u = nullptr, *zq = nullptr;
+    const int64_t n = (int64_t)Et * nt;
+    int rc;
+    if ((rc = net->get(&net->sup, sup.size())) || (rc = net->get(&net->supc, supc.size())) ||
+        (rc = net->get(&net->Pc, (size_t)Et * kmax * nt)) || (rc = net->get(&dcol, nt)) || (rc = net->get(&u, n)) ||
+        (rc = net->get(&zq, n)))
+        return rc;
+    cudaMemcpy(net->sup, sup.data(), sup.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(net->supc, supc.data(), supc.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(dcol, colour.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemsetAsync(net->Pc, 0, (size_t)Et * kmax * nt * sizeof(float), st);
+    net->compiled = false;
+    for (int q = 0; q < ncolour && !rc; ++q) {
+        k_probe<<<nblk(n), 256, 0, st>>>(dcol, q, nt, n, u);
+        if ((rc = pfmm_mpnn_apply(net, u, zq, 1, stream))) break;
+        k_extract<<<nblk(n), 256, 0, st>>>(zq, net->supc, q, nt, kmax, n, net->Pc);
+    }
+    if (!rc) rc = cuda_status("network compile");
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = cuda_status("network compile");
+    net->drop(dcol);
+    net->drop(u);
+    net->drop(zq);
+    if (rc) return rc;
+    net->kmax = kmax;
+    net->ncolor = ncolour;
+    net->compiled = true;
     return pfmm_mpnn_check(net);
 }
 

@@ -104,6 +104,7 @@ SIGNATURES = {
     "pfmm_mpnn_train": (ctypes.c_int, [_VP, _VP, _DP, _DP, ctypes.c_int64, _I, _I, ctypes.c_float, ctypes.c_uint64,
                                        ctypes.POINTER(ctypes.c_float), _VP]),
     "pfmm_mpnn_check": (ctypes.c_int, [_VP]),
+    "pfmm_mpnn_compile": (ctypes.c_int, [_VP, _VP]),
     "pfmm_mpnn_destroy": (None, [_VP]),
     "pfmm_destroy": (None, [_VP]),
     "pfmm_last_error": (ctypes.c_char_p, []),
@@ -450,6 +451,10 @@ class Mpnn:
 
     def check(self) -> None:
         _check(lib().pfmm_mpnn_check(self.ptr))
+
+    def compile(self, stream=None) -> None:
+        """Assemble the per-step sparse operators the (linear) network equals; apply uses them."""
+        _check(lib().pfmm_mpnn_compile(self.ptr, _stream(stream)))
 
     def close(self):
         if self.ptr:

@@ -191,3 +191,34 @@ def test_invalid_preconditioner_arguments(recorded):
         P.Mpnn(V, T, 1.0, Et, width=48, layers=1)
     other.close()
     net.close()
+
+
+@pytest.mark.parametrize("width,layers", [(64, 4), (16, 2), (32, 0)])
+def test_compiled_form_equals_the_network(width, layers):
+    """The assembled per-step sparse operators reproduce the network (and the oracle)."""
+    V, T = cube_mesh(3, "cross")  # 216 triangles
+    Et, nvec, c = 6, 2, 0.9
+    net = P.Mpnn(V, T, 1.0, Et, width=width, layers=layers, seed=8)
+    p = (np.random.default_rng(51).standard_normal(net.num_params()) * 0.3).astype(np.float32)
+    net.set_params(p)
+    net.output_scale = c
+    v = torch.tensor(random_density(Et, len(T), nvec, seed=52), device=DEV)
+    z_net = torch.empty_like(v)
+    net.apply(v, z_net)
+    net.compile()
+    z_c = torch.empty_like(v)
+    net.apply(v, z_c)
+    torch.cuda.synchronize()
+    a, b = z_c.cpu().numpy(), z_net.cpu().numpy()
+    # two FP32 evaluations of one linear map (the assembled coefficients are FP32 roundings)
+    assert _rel(a, b) <= 5e-5
+    want = O.forward(O.bf16_round(p), width, layers, V, T, Et, c, v.cpu().numpy())
+    assert _rel(a, want) <= 1e-4
+    # a parameter change drops the compiled form: apply follows the new weights again
+    net.set_params(2.0 * p)
+    net.output_scale = c
+    z2 = torch.empty_like(v)
+    net.apply(v, z2)
+    want2 = O.forward(O.bf16_round(2.0 * p), width, layers, V, T, Et, c, v.cpu().numpy())
+    assert _rel(z2.cpu().numpy(), want2) <= 1e-4
+    net.close()
