@@ -325,6 +325,43 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
             "peak_device_GB": peak[0], "device_total_GB": total / 1e9, "cap_GB": 180}
 
 
+def _profile_case(dev, case):
+    """Small cases for ncu captures of kernels the matvec does not launch: the learned
+    preconditioner's layers (`mpnn`), its compiled form (`mpnn_compiled`), the on-the-fly
+    nearfield (`otf`).  3072-triangle cube; 128 steps (network) or 32 steps (on-the-fly)."""
+    import numpy as np
+    import torch
+
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_mesh
+
+    V, T = cube_mesh(16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if case in ("mpnn", "mpnn_compiled"):
+        Et = 128
+        net = P.Mpnn(V, T, 1.0, Et, width=64, layers=4, seed=1)
+        net.set_params((np.random.default_rng(0).standard_normal(net.num_params()) * 0.1).astype(np.float32))
+        net.output_scale = 1.0
+        if case == "mpnn_compiled":
+            net.compile()
+        v = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
+        z = torch.empty_like(v)
+        run = lambda: net.apply(v, z)  # noqa: E731
+    else:
+        Et = 32
+        op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_MIXED,
+                        nearfield=P.PFMM_NEARFIELD_ONTHEFLY)
+        w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
+        run = lambda: op.V(w, parts=P.PFMM_PART_NEAR)  # noqa: E731
+    run()
+    e0.record()
+    for _ in range(2):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    return {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest per-rank value (the slowest replica's time) on every rank."""
     if world <= 1:
@@ -378,6 +415,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
     ap.add_argument("--solve-sets", type=int, default=32, help="held-out data sets of the solver comparison")
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
+    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf"], default=None,
+                    help="profiling only: run one small case of a kernel outside the matvec and exit")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
     ap.add_argument("--et", type=int, default=ET, help="profiling only: time steps")
@@ -402,6 +441,10 @@ def main():
     if args.config5:
         if rank == 0:
             print(json.dumps({"config5": _config5(dev)}), flush=True)
+        return 0
+    if args.profile_case:
+        if rank == 0:
+            print(json.dumps(_profile_case(dev, args.profile_case)), flush=True)
         return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)

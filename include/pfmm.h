@@ -310,7 +310,8 @@ int pfmm_mpnn_train(pfmm_mpnn *net, pfmm_handle *h, const double *R, const doubl
  * of `layers` edges around triangle i.  This assembles P_t (FP32) by probing: the triangles are
  * coloured so that any two within 2 layers edges differ, the network is applied (with its own
  * kernels) to one 0/1 probe per colour, and each result fills the ball entries of that colour.
- * Afterwards pfmm_mpnn_apply computes z = P_t v (FP64 sums); any parameter change (set_params,
+ * Afterwards pfmm_mpnn_apply computes z = P_t v (FP32 input copy and sums, FP64 output); any
+ * parameter change (set_params,
  * training, set_output_scale) drops the compiled form.  Needs E_t * E_x * max ball size floats.
  * Synchronises `stream`. */
 int pfmm_mpnn_compile(pfmm_mpnn *net, void *stream);

@@ -470,23 +470,29 @@ __global__ void k_extract(const double *__restrict__ zq, const int *__restrict__
         }
 }
 
-// z[b][i] = sum_k P_t[i][k] v[b][ball_k(i)], t = b mod E_t (one thread per row, FP64 sum)
-__global__ void k_spmv_compiled(const double *__restrict__ v, double *__restrict__ z, const float *__restrict__ Pc,
+__global__ void k_to_f32(const double *__restrict__ v, float *__restrict__ vf, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) vf[i] = (float)v[i];
+}
+
+// z[b][i] = sum_k P_t[i][k] v[b][ball_k(i)], t = b mod E_t: one thread per row, the input
+// converted to FP32 once (vf), FP32 sums over the ball, FP64 output
+__global__ void k_spmv_compiled(const float *__restrict__ vf, double *__restrict__ z, const float *__restrict__ Pc,
                                 const int *__restrict__ sup, int nt, int Et, int kmax, int64_t rows)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     const int64_t b = r / nt;
     const int i = (int)(r % nt), t = (int)(b % Et);
-    const double *vb = v + b * nt;
+    const float *vb = vf + b * nt;
     const float *P = Pc + (size_t)t * kmax * nt + i;
-    double acc = 0.0;
-    for (int k = 0; k < kmax; ++k) {
-        const int j = sup[(size_t)k * nt + i];
-        if (j < 0) break;
-        acc += (double)P[(size_t)k * nt] * vb[j];
-    }
-    z[r] = acc;
+    // padding entries (index -1) have zero coefficients: read vb[0] for them, no branch, so the
+    // index and gather loads of several k are in flight together
+    float acc = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < kmax; ++k) acc += P[(size_t)k * nt] * vb[max(sup[(size_t)k * nt + i], 0)];
+    z[r] = (double)acc;
 }
 
 // ---- tensor-core layer -------------------------------------------------------------------------
@@ -737,6 +743,8 @@ struct pfmm_mpnn {
     int *sup = nullptr;   // [kmax][nt] ball members (-1 after the last)
     int *supc = nullptr;  // [kmax][nt] their colours
     float *Pc = nullptr;  // [Et][kmax][nt]
+    float *vf = nullptr;  // FP32 copy of the input of a compiled apply
+    int64_t vf_cap = 0;
     std::vector<void *> mem;
     ~pfmm_mpnn()
     {
@@ -1119,7 +1127,16 @@ int pfmm_mpnn_apply(pfmm_mpnn *net, const double *v, double *z, int32_t nvec, vo
     const int64_t total = (int64_t)nvec * net->Et, per = std::max<int64_t>(kChunkRows / net->nt, 1);
     if (net->compiled) {
         const int64_t rows = total * net->nt;
-        k_spmv_compiled<<<nblk(rows), 256, 0, st>>>(v, z, net->Pc, net->sup, net->nt, net->Et, net->kmax, rows);
+        if (rows > net->vf_cap) {
+            net->drop(net->vf);
+            net->vf = nullptr;
+            net->vf_cap = 0;
+            int rc = net->get(&net->vf, rows);
+            if (rc) return rc;
+            net->vf_cap = rows;
+        }
+        k_to_f32<<<nblk(rows), 256, 0, st>>>(v, net->vf, rows);
+        k_spmv_compiled<<<nblk(rows), 256, 0, st>>>(net->vf, z, net->Pc, net->sup, net->nt, net->Et, net->kmax, rows);
         return cuda_status("compiled network apply");
     }
     for (int64_t s0 = 0; s0 < total; s0 += per) {
