@@ -685,8 +685,8 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
         for (int a = a_lo; a < a_hi; ++a) {
             __syncthreads();
             const R *mJ = mu + ((size_t)rhs * A.nint + J) * A.nbox * na * nk;
-            for (int i = threadIdx.x; i < nk * C3; i += blockDim.x) {
-                int ik = i / C3, c = i % C3, box = cbx[c];
+            for (int i = threadIdx.x; i < nk * C3; i += blockDim.x) {  // consecutive threads: consecutive kappa
+                int c = i / nk, ik = i % nk, box = cbx[c];
                 U[ik * CS + c] = box >= 0 ? mJ[((size_t)box * na + a) * nk + ik] : R(0);
             }
             const R *Eab = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * esz;
@@ -697,71 +697,57 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
             }
             const R coef = pref[((D - 2) * na + a) * na + b];
             __syncthreads();
-            // pass 1 (direction x): item = (triple (nu1, k2, k3), Y2); registers: cells (X1, Y3)
-            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-                const int t = it / FG, Y2 = it % FG, tk = kid[t];
+            // pass 1 (direction x): unit = (triple (nu1, k2, k3), Y2, Y3); registers: cells X1.  The
+            // budget loop over B is a prefix sum (T1 holds the cumulative budget), so a unit is a
+            // sequential chain of 1 .. m_x + 1 steps; units are spread over all threads
+            for (int u = threadIdx.x; u < nitems * FG; u += blockDim.x) {
+                const int z = u % FG, Y2 = (u / FG) % FG, t = u / (FG * FG), tk = kid[t];
                 const int nu1 = tk & 255, k2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + k2 + k3;
-                R acc[FG][FG];
+                R acc[FG];
 #pragma unroll
-                for (int x = 0; x < FG; ++x)
-#pragma unroll
-                    for (int z = 0; z < FG; ++z) acc[x][z] = R(0);
+                for (int x = 0; x < FG; ++x) acc[x] = R(0);
                 for (int B = s0; B <= mx; ++B) {
                     const int k1 = B - s0;
-                    const R *mrow = U + kin[(k1 * m1 + k2) * m1 + k3] * CS + Y2 * FG;
+                    const R *mrow = U + kin[(k1 * m1 + k2) * m1 + k3] * CS + Y2 * FG + z;
                     R e[7];
 #pragma unroll
                     for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k1 * m1 + nu1];
 #pragma unroll
                     for (int Y1 = 0; Y1 < FG; ++Y1) {
-                        R mv[FG];
+                        const R mv = mrow[Y1 * FG * FG];
 #pragma unroll
-                        for (int z = 0; z < FG; ++z) mv[z] = mrow[Y1 * FG * FG + z];
-#pragma unroll
-                        for (int X1 = 0; X1 < FG; ++X1)
-#pragma unroll
-                            for (int z = 0; z < FG; ++z) acc[X1][z] += e[X1 - Y1 + 3] * mv[z];
+                        for (int X1 = 0; X1 < FG; ++X1) acc[X1] += e[X1 - Y1 + 3] * mv;
                     }
-                    R *out = T1s + (eof[t] + k1) * CS + Y2 * FG;
+                    R *out = T1s + (eof[t] + k1) * CS + Y2 * FG + z;
 #pragma unroll
-                    for (int X1 = 0; X1 < FG; ++X1)
-#pragma unroll
-                        for (int z = 0; z < FG; ++z) out[X1 * FG * FG + z] = acc[X1][z];
+                    for (int X1 = 0; X1 < FG; ++X1) out[X1 * FG * FG] = acc[X1];
                 }
             }
             __syncthreads();
-            // pass 2 (direction y): item = (triple (nu1, nu2, k3), X1); registers: cells (X2, Y3); T2 -> U
-            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
-                const int t = it / FG, X1 = it % FG, tk = kid[t];
+            // pass 2 (direction y): unit = (triple (nu1, nu2, k3), X1, Y3); registers: cells X2; T2 -> U
+            for (int u = threadIdx.x; u < nitems * FG; u += blockDim.x) {
+                const int z = u % FG, X1 = (u / FG) % FG, t = u / (FG * FG), tk = kid[t];
                 const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + nu2 + k3;
                 for (int Bp = s0; Bp <= mx; ++Bp) {
-                    R acc[FG][FG];
+                    R acc[FG];
 #pragma unroll
-                    for (int y = 0; y < FG; ++y)
-#pragma unroll
-                        for (int z = 0; z < FG; ++z) acc[y][z] = R(0);
+                    for (int y = 0; y < FG; ++y) acc[y] = R(0);
                     for (int k2 = 0; k2 <= Bp - s0; ++k2) {
                         const int row = eof[kin[(nu1 * m1 + k2) * m1 + k3]] + (Bp - nu2 - nu1 - k2 - k3);
-                        const R *trow = T1s + row * CS + X1 * FG * FG;
+                        const R *trow = T1s + row * CS + X1 * FG * FG + z;
                         R e[7];
 #pragma unroll
                         for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k2 * m1 + nu2];
 #pragma unroll
                         for (int Y2 = 0; Y2 < FG; ++Y2) {
-                            R tv[FG];
+                            const R tv = trow[Y2 * FG];
 #pragma unroll
-                            for (int z = 0; z < FG; ++z) tv[z] = trow[Y2 * FG + z];
-#pragma unroll
-                            for (int X2 = 0; X2 < FG; ++X2)
-#pragma unroll
-                                for (int z = 0; z < FG; ++z) acc[X2][z] += e[X2 - Y2 + 3] * tv[z];
+                            for (int X2 = 0; X2 < FG; ++X2) acc[X2] += e[X2 - Y2 + 3] * tv;
                         }
                     }
-                    R *out = U + (eof[t] + Bp - s0) * CS + X1 * FG * FG;
+                    R *out = U + (eof[t] + Bp - s0) * CS + X1 * FG * FG + z;
 #pragma unroll
-                    for (int X2 = 0; X2 < FG; ++X2)
-#pragma unroll
-                        for (int z = 0; z < FG; ++z) out[X2 * FG + z] = acc[X2][z];
+                    for (int X2 = 0; X2 < FG; ++X2) out[X2 * FG] = acc[X2];
                 }
             }
             __syncthreads();
