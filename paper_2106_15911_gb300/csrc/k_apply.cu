@@ -180,61 +180,74 @@ void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, con
 // S2M at the leaves (Eq. s2m): mu[k][X][a][i] = sum_s St[s][a] sum_{x in X} x[k ls + s][x] Sx[x][i]
 // (double layer: sum over the triangle's three nodes with SK).  CTA per (leaf box, interval
 // chunk, rhs).
+constexpr int kTSB = 32;   // steps per S2M / L2T block
+constexpr int kS2MCK = 6;  // moment groups of 32 per thread (n_kappa <= 192, m_x <= 8)
+
 template <typename R, bool KOP>
 __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncolg, const int *__restrict__ tri,
                                                const R *__restrict__ Stab, const R *__restrict__ St, R *__restrict__ mu,
                                                const int *__restrict__ leaf_start, int nk, int na, int ls, int Et,
-                                               int nint, int nbox, int IB)
+                                               int nint, int nbox)
 {
+    // register-blocked: a CTA covers one leaf box, kTSB steps and one rhs; thread (tg = warp,
+    // kg = lane) accumulates steps 4 tg .. 4 tg + 3 for the moments kg + 32 c (c < ceil(nk / 32))
     extern __shared__ unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
-    constexpr int XCH = 16;
-    constexpr int PER = KOP ? 3 : 1;
-    const int X = blockIdx.x, k0 = blockIdx.y * IB, rhs = blockIdx.z;
-    const int kend = min(nint, k0 + IB), nts = (kend - k0) * ls, t0 = k0 * ls;
+    constexpr int XCH = KOP ? 16 : 32, PER = KOP ? 3 : 1, KC = XCH * PER;
+    const int X = blockIdx.x, rhs = blockIdx.z;
+    const int ipb = kTSB / ls;
+    const int k0 = blockIdx.y * ipb, kend = min(nint, k0 + ipb), nts = (kend - k0) * ls, t0 = k0 * ls;
     const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
-    R *Ws = sm;                        // [nts][XCH*PER]
-    R *Ss = sm + IB * ls * XCH * PER;  // [XCH*PER][nk]
+    R *Ws = sm;              // [kTSB][KC]
+    R *Ss = sm + kTSB * KC;  // [KC][nk]
     const R *xr = xin + (size_t)rhs * Et * ncolg;
-    R acc[8];
+    const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
+    R acc[4][kS2MCK];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = R(0);
-    const int nout = nts * nk;
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < kS2MCK; ++c) acc[r][c] = R(0);
     for (int xb = x0; xb < x1; xb += XCH) {
-        int nx = min(XCH, x1 - xb);
-        for (int e = threadIdx.x; e < nts * XCH * PER; e += blockDim.x) {
-            int ts = e / (XCH * PER), j = e % (XCH * PER);
-            int xi = j / PER, v = j % PER;
+        const int nx = min(XCH, x1 - xb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kTSB * KC; e += blockDim.x) {
+            const int ts = e / KC, j = e % KC, xi = j / PER, v = j % PER;
             R val = R(0);
-            if (xi < nx) {
-                int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
+            if (ts < nts && xi < nx) {
+                const int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
                 val = xr[(size_t)(t0 + ts) * ncolg + col];
             }
             Ws[e] = val;
         }
-        for (int e = threadIdx.x; e < XCH * PER * nk; e += blockDim.x) {
-            int j = e / nk;
+        for (int e = threadIdx.x; e < KC * nk; e += blockDim.x) {
+            const int j = e / nk;
             Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + (e % nk)] : R(0);
         }
         __syncthreads();
+        for (int j = 0; j < KC; ++j) {
+            R w[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            int o = threadIdx.x + q * blockDim.x;
-            if (o < nout) {
-                int ts = o / nk, i = o % nk;
-                R a = acc[q];
-                for (int j = 0; j < XCH * PER; ++j) a += Ws[ts * XCH * PER + j] * Ss[j * nk + i];
-                acc[q] = a;
+            for (int r = 0; r < 4; ++r) w[r] = Ws[(tg * 4 + r) * KC + j];
+#pragma unroll
+            for (int c = 0; c < kS2MCK; ++c) {
+                const int i = kg + 32 * c;
+                if (c < ck && i < nk) {
+                    const R sv = Ss[j * nk + i];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][c] += w[r] * sv;
+                }
             }
         }
-        __syncthreads();
     }
-    R *Ps = sm;  // [nts][nk]
+    __syncthreads();
+    R *Ps = sm;  // [kTSB][nk]
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        int o = threadIdx.x + q * blockDim.x;
-        if (o < nout) Ps[o] = acc[q];
-    }
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < kS2MCK; ++c) {
+            const int i = kg + 32 * c;
+            if (c < ck && i < nk) Ps[(tg * 4 + r) * nk + i] = acc[r][c];
+        }
     __syncthreads();
     const int nmo = (kend - k0) * na * nk;
     for (int o = threadIdx.x; o < nmo; o += blockDim.x) {
@@ -245,30 +258,21 @@ __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncol
     }
 }
 
-static int s2m_chunk(int ls, int nk, int nint)
-{
-    int IB = 2048 / (ls * nk);
-    if (IB < 1) IB = 1;
-    if (IB > 16) IB = 16;
-    if (IB > nint) IB = nint;
-    return IB;
-}
-
 void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
                 const ApplyGeo &g, cudaStream_t st)
 {
     int nint = g.Et / g.ls;
-    int IB = s2m_chunk(g.ls, g.nk, nint);
-    int PER = kop ? 3 : 1;
+    const int ipb = kTSB / g.ls;
+    const int KC = kop ? 48 : 32;
     size_t es = mixed ? 4 : 8;
-    size_t sm1 = (size_t)IB * g.ls * 16 * PER + (size_t)16 * PER * g.nk, sm2 = (size_t)IB * g.ls * g.nk;
+    size_t sm1 = (size_t)kTSB * KC + (size_t)KC * g.nk, sm2 = (size_t)kTSB * g.nk;
     size_t smem = (sm1 > sm2 ? sm1 : sm2) * es;
-    dim3 grd(g.nbox_leaf, (nint + IB - 1) / IB, nrhs);
+    dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
 #define S2M_LAUNCH(R, K)                                                                                          \
     do {                                                                                                          \
         cudaFuncSetAttribute(k_s2m<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
         k_s2m<R, K><<<grd, 256, smem, st>>>((const R *)x, ncolg, g.tri, (const R *)Stab, (const R *)St, (R *)mu_leaf, \
-                                            g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, IB);         \
+                                            g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf);             \
     } while (0)
     if (mixed) {
         if (kop) S2M_LAUNCH(float, true); else S2M_LAUNCH(float, false);
@@ -979,37 +983,57 @@ void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
 template <typename R>
 __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R *__restrict__ Sx, const R *__restrict__ St,
                                                double *__restrict__ f, const int *__restrict__ leaf_start, int nk, int na,
-                                               int ls, int Et, int nint, int nbox, int nt, int IB)
+                                               int ls, int Et, int nint, int nbox, int nt)
 {
+    // a CTA covers one leaf box, kTSB steps and one rhs: Q[ts][nu] = sum_b St[s][b] lam[k][X][b][nu]
+    // in shared memory, then thread (tg = warp, xl = lane) forms steps 4 tg .. 4 tg + 3 for the
+    // triangles xl and xl + 32 of each 64-triangle chunk
     extern __shared__ unsigned char smem_raw[];
-    R *Ls = reinterpret_cast<R *>(smem_raw);  // [nts][nk]
-    constexpr int XCH = 32;
-    const int X = blockIdx.x, k0 = blockIdx.y * IB, rhs = blockIdx.z;
-    const int kend = min(nint, k0 + IB), nts = (kend - k0) * ls, t0 = k0 * ls;
-    R *Sxs = Ls + IB * ls * nk;  // [XCH][nk + 1]
+    R *Qs = reinterpret_cast<R *>(smem_raw);  // [kTSB][nk]
+    constexpr int XCH = 64, SP = XCH + 1;      // Sx chunk stored transposed, rows padded
+    R *Ss = Qs + kTSB * nk;                    // [nk][SP]
+    const int X = blockIdx.x, rhs = blockIdx.z;
+    const int ipb = kTSB / ls;
+    const int k0 = blockIdx.y * ipb, kend = min(nint, k0 + ipb), nts = (kend - k0) * ls, t0 = k0 * ls;
     const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
-    for (int o = threadIdx.x; o < nts * nk; o += blockDim.x) {
-        int ts = o / nk, i = o % nk, kk = ts / ls, s = ts % ls;
-        const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
+    for (int o = threadIdx.x; o < kTSB * nk; o += blockDim.x) {
+        const int ts = o / nk, i = o % nk;
         R v = R(0);
-        for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
-        Ls[o] = v;
+        if (ts < nts) {
+            const int kk = ts / ls, s = ts % ls;
+            const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
+            for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
+        }
+        Qs[o] = v;
     }
+    const int xl = threadIdx.x & 31, tg = threadIdx.x >> 5;
     for (int xb = x0; xb < x1; xb += XCH) {
-        int nx = min(XCH, x1 - xb);
+        const int nx = min(XCH, x1 - xb);
         __syncthreads();
-        for (int e = threadIdx.x; e < XCH * nk; e += blockDim.x) {
-            int xi = e / nk, i = e % nk;
-            Sxs[xi * (nk + 1) + i] = xi < nx ? Sx[(size_t)(xb + xi) * nk + i] : R(0);
+        for (int e = threadIdx.x; e < XCH * nk; e += blockDim.x) {  // coalesced reads along nu
+            const int xi = e / nk, i = e % nk;
+            Ss[i * SP + xi] = xi < nx ? Sx[(size_t)(xb + xi) * nk + i] : R(0);
         }
         __syncthreads();
-        for (int o = threadIdx.x; o < nts * XCH; o += blockDim.x) {
-            int ts = o / XCH, xi = o % XCH;
-            if (xi >= nx) continue;
-            const R *lrow = Ls + ts * nk, *srow = Sxs + xi * (nk + 1);
-            R v = R(0);
-            for (int i = 0; i < nk; ++i) v += lrow[i] * srow[i];
-            f[((size_t)rhs * Et + t0 + ts) * nt + xb + xi] += (double)v;
+        R acc[4][2];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = R(0);
+        for (int i = 0; i < nk; ++i) {
+            const R s0 = Ss[i * SP + xl], s1 = Ss[i * SP + xl + 32];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const R q = Qs[(tg * 4 + r) * nk + i];
+                acc[r][0] += q * s0;
+                acc[r][1] += q * s1;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int ts = tg * 4 + r;
+            if (ts >= nts) continue;
+            double *fr = f + ((size_t)rhs * Et + t0 + ts) * nt + xb;
+            if (xl < nx) fr[xl] += (double)acc[r][0];
+            if (xl + 32 < nx) fr[xl + 32] += (double)acc[r][1];
         }
     }
 }
@@ -1019,18 +1043,18 @@ void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St
 {
     (void)mu_stride;
     int nint = g.Et / g.ls;
-    int IB = s2m_chunk(g.ls, g.nk, nint);
+    const int ipb = kTSB / g.ls;
     size_t es = mixed ? 4 : 8;
-    size_t smem = ((size_t)IB * g.ls * g.nk + 32 * (size_t)(g.nk + 1)) * es;
-    dim3 grd(g.nbox_leaf, (nint + IB - 1) / IB, nrhs);
+    size_t smem = ((size_t)kTSB * g.nk + (size_t)g.nk * 65) * es;
+    dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
     if (mixed) {
         cudaFuncSetAttribute(k_l2t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_l2t<float><<<grd, 256, smem, st>>>((const float *)lam_leaf, (const float *)Sx, (const float *)St, f_int,
-                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, IB);
+                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt);
     } else {
         cudaFuncSetAttribute(k_l2t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_l2t<double><<<grd, 256, smem, st>>>((const double *)lam_leaf, (const double *)Sx, (const double *)St, f_int,
-                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, IB);
+                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt);
     }
 }
 
