@@ -362,6 +362,18 @@ def _profile_case(dev, case):
     return {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
 
 
+def _launches_per_apply(info, nrhs, na=M_T + 1, split_ctas=2 * 152):
+    """Kernels one V_h apply launches (the launch list in profiles/ counts 26 for the bench
+    workload): permute in and out, the 3xTF32 input split (tensor-core nearfield), nearfield,
+    S2M, M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per split level (levels with
+    fewer than two CTAs per SM), L2L (levels 3..p), L2T."""
+    p = info["p"]
+    if p < 2:
+        return 3 + (1 if info["nf_tensor_cores"] & 1 else 0)
+    split = sum(1 for l in range(2, p + 1) if (2 ** l) * na * nrhs < split_ctas)
+    return 2 + (1 if info["nf_tensor_cores"] & 1 else 0) + 1 + 1 + (p - 2) + (p - 1) + split + (p - 2) + 1
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest per-rank value (the slowest replica's time) on every rank."""
     if world <= 1:
@@ -578,7 +590,7 @@ def main():
     if rank == 0 and args.batch > 0:
         batch = _batch_comparison(dev, args.batch)
 
-    launches = 3 * info["p"]  # permute in/out, nearfield, S2M, L2T, (p-2) M2M, (p-1) M2L, (p-2) L2L
+    launches = _launches_per_apply(info, 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
