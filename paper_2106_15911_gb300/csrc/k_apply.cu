@@ -637,7 +637,9 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
 constexpr int FG = 4;  // padded grid extent per direction
 
 constexpr int kM2LThreads = 384;
-constexpr int kM2LSms = 152;  // CTA-count threshold of the split mode (two CTAs per SM on GB300)
+// split mode below this many (interval, node, rhs) CTAs: four per SM of GB300's 152 (at two
+// resident CTAs per SM, fewer than four leave the last wave mostly empty)
+constexpr int kM2LSplitCtas = 4 * 152;
 
 template <typename R>
 __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
@@ -846,7 +848,7 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
         // terms' partial locals fit the workspace
         const size_t nlev = (size_t)nrhs * L.nint * L.nbox * na * g.nk;
         const int nterm = 2 * na;
-        const int split = ((int64_t)L.nint * na * nrhs < 2 * kM2LSms && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
+        const int split = ((int64_t)L.nint * na * nrhs < kM2LSplitCtas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
         dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
         const char *mbf = (const char *)mu + L.mom_off * es * nrhs;
         char *lbf = (char *)lam + L.mom_off * es * nrhs;
