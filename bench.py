@@ -362,11 +362,11 @@ def _profile_case(dev, case):
     return {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
 
 
-def _launches_per_apply(info, nrhs, na=M_T + 1, split_ctas=4 * 152):
-    """Kernels one V_h apply launches (the launch list in profiles/ counts 26 for the bench
-    workload): permute in and out, the 3xTF32 input split (tensor-core nearfield), nearfield,
-    S2M, M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per split level (levels with
-    fewer than two CTAs per SM), L2L (levels 3..p), L2T."""
+def _launches_per_apply(info, nrhs, na=M_T + 1, split_ctas=8 * 152):
+    """Kernels one V_h apply launches: permute in and out, the 3xTF32 input split (tensor-core
+    nearfield), nearfield, S2M, M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per
+    split level (levels with fewer than eight (interval, node) CTAs per SM), L2L (levels 3..p),
+    L2T."""
     p = info["p"]
     if p < 2:
         return 3 + (1 if info["nf_tensor_cores"] & 1 else 0)

@@ -637,9 +637,10 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
 constexpr int FG = 4;  // padded grid extent per direction
 
 constexpr int kM2LThreads = 384;
-// split mode below this many (interval, node, rhs) CTAs: four per SM of GB300's 152 (at two
-// resident CTAs per SM, fewer than four leave the last wave mostly empty)
-constexpr int kM2LSplitCtas = 4 * 152;
+// split mode below this many (interval, node, rhs) CTAs: eight per SM of GB300's 152.  At two
+// resident CTAs per SM and work per CTA that differs by 2x between even and odd intervals, fewer
+// than four waves lose much of the last one; one-term CTAs are uniform and many
+constexpr int kM2LSplitCtas = 8 * 152;
 
 template <typename R>
 __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
@@ -814,11 +815,16 @@ __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R
     }
 }
 
+// lam = sum of the term slices in term order; interval k has nj(k) * na terms (nj = 0 for k < 2,
+// 1 for even k, 2 for odd k): the slices of the other terms are never written and are not read
 template <typename R>
-__global__ void k_m2l_sum_terms(const R *__restrict__ part, int nterm, size_t n, R *__restrict__ lam)
+__global__ void k_m2l_sum_terms(const R *__restrict__ part, int na, size_t n, size_t per_k, int nint,
+                                R *__restrict__ lam)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int k = (int)((i / per_k) % nint);
+    const int nterm = k < 2 ? 0 : (k % 2 == 0 ? na : 2 * na);
     R s = R(0);
     for (int t = 0; t < nterm; ++t) s += part[(size_t)t * n + i];
     lam[i] = s;
@@ -844,25 +850,28 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
     if (mixed && L.G <= FG && fsm <= 200 * 1024 && g.nk * FG <= 2 * kM2LThreads) {
         M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
                   g.kidx, g.kinv, g.eoff};
-        // too few (interval, node) CTAs for two per SM: one CTA per source term as well, when the
-        // terms' partial locals fit the workspace
-        const size_t nlev = (size_t)nrhs * L.nint * L.nbox * na * g.nk;
+        // few (interval, node) CTAs: one CTA per source term as well, when the terms' partial
+        // locals fit the workspace
+        const size_t per_k = (size_t)L.nbox * na * g.nk, nlev = (size_t)nrhs * L.nint * per_k;
         const int nterm = 2 * na;
         const int split = ((int64_t)L.nint * na * nrhs < kM2LSplitCtas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
         dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
         const char *mbf = (const char *)mu + L.mom_off * es * nrhs;
         char *lbf = (char *)lam + L.mom_off * es * nrhs;
-        if (split) cudaMemsetAsync(T1, 0, es * nterm * nlev, st);  // terms a CTA does not cover stay zero
         if (mixed) {
             cudaFuncSetAttribute(k_m2l_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
             k_m2l_fused<float><<<grd, kM2LThreads, fsm, st>>>(A, (const float *)mbf, (const float *)L.E1, (const float *)L.pref,
                                                       (float *)lbf, nrhs, split, (float *)T1);
-            if (split) k_m2l_sum_terms<float><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const float *)T1, nterm, nlev, (float *)lbf);
+            if (split)
+                k_m2l_sum_terms<float><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const float *)T1, na, nlev, per_k,
+                                                                                      L.nint, (float *)lbf);
         } else {
             cudaFuncSetAttribute(k_m2l_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
             k_m2l_fused<double><<<grd, kM2LThreads, fsm, st>>>(A, (const double *)mbf, (const double *)L.E1,
                                                        (const double *)L.pref, (double *)lbf, nrhs, split, (double *)T1);
-            if (split) k_m2l_sum_terms<double><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const double *)T1, nterm, nlev, (double *)lbf);
+            if (split)
+                k_m2l_sum_terms<double><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const double *)T1, na, nlev,
+                                                                                        per_k, L.nint, (double *)lbf);
         }
         return 0;
     }
