@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pFMM matvec space-time DOF/s"
 N_A, ET, M_X, M_T, C_ST = 32, 256, 6, 4, 1.0
+# DRAM bytes (read + write) per stored panel element of one tensor-core nearfield launch, from an
+# ncu capture of the 3072-triangle x 128-step case (None: not captured for the current kernel)
+NF_TC_DRAM_BYTES_PER_ELEMENT = 4.81
 
 
 def _set_size(n_a, et):
@@ -363,15 +366,15 @@ def _profile_case(dev, case):
 
 
 def _launches_per_apply(info, nrhs, na=M_T + 1, split_ctas=8 * 152):
-    """Kernels one V_h apply launches: permute in and out, the 3xTF32 input split (tensor-core
-    nearfield), nearfield, S2M, M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per
+    """Kernels one V_h apply launches: permute in and out, the FP16 input split (max |x| and
+    split; tensor-core nearfield), nearfield, S2M, M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per
     split level (levels with fewer than eight (interval, node) CTAs per SM), L2L (levels 3..p),
     L2T."""
     p = info["p"]
     if p < 2:
-        return 3 + (1 if info["nf_tensor_cores"] & 1 else 0)
+        return 3 + (2 if info["nf_tensor_cores"] & 1 else 0)
     split = sum(1 for l in range(2, p + 1) if (2 ** l) * na * nrhs < split_ctas)
-    return 2 + (1 if info["nf_tensor_cores"] & 1 else 0) + 1 + 1 + (p - 2) + (p - 1) + split + (p - 2) + 1
+    return 2 + (2 if info["nf_tensor_cores"] & 1 else 0) + 1 + 1 + (p - 2) + (p - 1) + split + (p - 2) + 1
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -540,22 +543,22 @@ def main():
     tc = bool(info.get("nf_tensor_cores", 0) & 1)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     if tc:
-        # tcgen05 kind::tf32 with a 3-term split: three TF32 products per useful product; the
-        # TF32 peak is the measured dense BF16 peak x the nominal TF32/BF16 rate ratio (1.1/2.25)
+        # tcgen05 kind::f16 with a 3-term split: three FP16 products per useful product; the FP16
+        # dense rate is the BF16 rate, so the peak is the measured dense BF16 burst peak
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak_tf32 = bf16 * 1.1 / 2.25
+        peak_f16 = bf16
         achieved = 3.0 * flops_nf / (nf_ms * 1e-3) / 1e12
-        # algorithmic HBM bytes: the hi/lo TF32 parts of every stored panel element, read once
-        bytes_nf = 8.0 * info["nearfield_v_elements"]
+        # algorithmic HBM bytes: the hi/lo FP16 parts of every stored panel element, read once
+        bytes_nf = 4.0 * info["nearfield_v_elements"]
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         # DRAM bytes per panel element of this kernel, measured with ncu on the 3072-triangle x
-        # 128-step case (419.7 MB per launch over 44.04M panel elements)
-        traffic = 9.53 * info["nearfield_v_elements"]
-        roofline = {"bound": "tensor", "kernel": "k_nf_apply_tc", "achieved": achieved, "peak": peak_tf32,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tf32, "traffic": traffic,
-                    "peak_source": f"measured bf16 {bf16:.0f} TF x nominal tf32/bf16 ratio (of measured)",
+        # 128-step case
+        traffic = NF_TC_DRAM_BYTES_PER_ELEMENT * info["nearfield_v_elements"] if NF_TC_DRAM_BYTES_PER_ELEMENT else None
+        roofline = {"bound": "tensor", "kernel": "k_nf_apply_tc", "achieved": achieved, "peak": peak_f16,
+                    "unit": "TFLOP/s", "frac": achieved / peak_f16, "traffic": traffic,
+                    "peak_source": f"measured dense bf16 burst {bf16:.0f} TF = the fp16 rate (of measured)",
                     "flops_per_launch_executed": 3.0 * flops_nf, "ms_per_launch": nf_ms,
                     "hbm": {"achieved_gbs": bytes_nf / (nf_ms * 1e-3) / 1e9, "peak_gbs": hbm,
                             "frac": bytes_nf / (nf_ms * 1e-3) / 1e9 / hbm, "bytes_per_launch": bytes_nf}}

@@ -91,8 +91,9 @@ typedef struct pfmm_params {
     int32_t nearfield;  /* PFMM_NEARFIELD_STORED (default) or PFMM_NEARFIELD_ONTHEFLY */
     int32_t quad_regular;  /* Gauss points per direction of the collapsed triangle rule */
     int32_t quad_singular; /* Gauss points per direction of the Sauter-Schwab rule */
-    int32_t nf_engine;  /* PFMM_NF_AUTO: tensor cores (3xTF32 split, mixed mode) where the panel
-                           layout allows, else CUDA cores; PFMM_NF_CUDA_CORES: always CUDA cores */
+    int32_t nf_engine;  /* PFMM_NF_AUTO: tensor cores (scaled two-part FP16 split, FP32 accumulation,
+                           mixed mode) where the panel layout allows, else CUDA cores;
+                           PFMM_NF_CUDA_CORES: always CUDA cores */
 } pfmm_params;
 
 typedef struct pfmm_handle pfmm_handle;

@@ -140,7 +140,7 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// FP32 tensor map, 128-byte swizzle, zero fill out of bounds; dims innermost first
+// FP16 tensor map, 128-byte swizzle, zero fill out of bounds; dims innermost first
 int encode_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims, const uint64_t *strides_bytes,
                const uint32_t *box)
 {
@@ -154,7 +154,7 @@ int encode_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims,
         e[i] = 1;
         if (i > 0) s[i - 1] = strides_bytes[i - 1];
     }
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), d, s, b, e,
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, rank, const_cast<void *>(base), d, s, b, e,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(PFMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -224,10 +224,14 @@ int ensure_workspace(pfmm_handle *H, int nrhs)
     if ((rc = H->alloc((char **)&H->d_T2, H->ws_m2l * H->es, 1))) return rc;
     H->release(H->d_Whi);
     H->release(H->d_Wlo);
+    H->release(H->d_wmax);
     H->d_Whi = H->d_Wlo = nullptr;
+    H->d_wmax = nullptr;
     if (H->tcV || H->tcK) {
         H->w_elems = (size_t)nrhs * H->Et * std::max(H->colsV_u, H->colsK_u);
-        if ((rc = H->alloc(&H->d_Whi, H->w_elems)) || (rc = H->alloc(&H->d_Wlo, H->w_elems))) return rc;
+        if ((rc = H->alloc(&H->d_Whi, H->w_elems)) || (rc = H->alloc(&H->d_Wlo, H->w_elems)) ||
+            (rc = H->alloc(&H->d_wmax, (size_t)nrhs)))
+            return rc;
     }
     H->ws_nrhs = nrhs;
     return PFMM_OK;
@@ -254,17 +258,19 @@ void prof_collect(pfmm_handle *H, int upto_pending)
 int pfmm::ensure_ws(pfmm_handle *H, int nrhs) { return ensure_workspace(H, nrhs); }
 
 // Tensor-core nearfield of op (0: V, 1: K) into fint (zeroed here): splits the FP64 input into
-// TF32 hi/lo parts in whi/wlo ([nrhs][E_t][cols] each), encodes their TMA views and launches.
-int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint,
-                    cudaStream_t st)
+// scaled FP16 hi/lo parts in whi/wlo ([nrhs][E_t][cols] each; per-rhs scale from max |x| in
+// wmax), encodes their TMA views and launches.
+int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned *wmax,
+                    double *fint, cudaStream_t st)
 {
     int rc;
     const int cols = op == 0 ? H->colsV_u : H->colsK_u;
-    launch_split_input(x, op == 0 ? H->d_perm : nullptr, op == 0 ? H->nt : H->nv, cols, nrhs, H->Et, whi, wlo, st);
+    launch_split_input(x, op == 0 ? H->d_perm : nullptr, op == 0 ? H->nt : H->nv, cols, nrhs, H->Et, whi, wlo, wmax,
+                       st);
     const int nint = H->Et / 2;
     uint64_t dims[4] = {(uint64_t)cols, 2, (uint64_t)nint, (uint64_t)nrhs};
-    uint64_t str[3] = {(uint64_t)cols * 4, (uint64_t)cols * 8, (uint64_t)cols * 8 * nint};
-    uint32_t box[4] = {32, 1, 128, 1};
+    uint64_t str[3] = {(uint64_t)cols * 2, (uint64_t)cols * 4, (uint64_t)cols * 4 * nint};
+    uint32_t box[4] = {64, 1, 128, 1};
     CUtensorMap mWhi, mWlo;
     if ((rc = encode_map(&mWhi, whi, 4, dims, str, box)) || (rc = encode_map(&mWlo, wlo, 4, dims, str, box))) return rc;
     CK(cudaMemsetAsync(fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
@@ -273,9 +279,9 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *wh
     P.tiles = H->d_tiles128;
     P.ntiles = H->ntiles128;
     P.nib = (nint + 127) / 128;
-    P.nkb = cols / 32;
+    P.nkb = cols / 64;
     const int tiles = nrhs * P.ntiles * P.nib;
-    // split K into chunks of at most 32 stages (1024 columns): shorter FP32 accumulation in TMEM
+    // split K into chunks of at most 32 stages (2048 columns): shorter FP32 accumulation in TMEM
     // and at least three work items per SM; the FP64 atomics of the partials are cheap
     int ks = std::max((3 * H->nsm + tiles - 1) / tiles, (4 * P.nkb + 31) / 32);
     if (const char *env = std::getenv("PFMM_TC_KSPLIT")) ks = std::atoi(env);  // tuning override
@@ -287,6 +293,8 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *wh
     P.nint = nint;
     P.Et = H->Et;
     P.nt = H->nt;
+    P.a_exp = op == 0 ? H->a_expV : H->a_expK;
+    P.wmax = wmax;
     P.f = fint;
     P.err = H->d_err;
     if (launch_nf_apply_tc(op == 0 ? H->mapAVhi : H->mapAKhi, op == 0 ? H->mapAVlo : H->mapAKlo, mWhi, mWlo, P, H->nsm,
@@ -338,8 +346,9 @@ int pfmm::apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, vo
         int rc = pfmm::run_nf_otf(H, 0, xint, H->nt, ns, 1, 1, 1, fint, st);
         if (rc) return rc;
     } else {
+        NfHalfSplit hs;
         launch_nf_apply(H->mixed, false, H->nf_blocks(0), H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, 1, g,
-                        fint, st, 1, H->nf_blocks_lo(0));
+                        fint, st, 1, H->nf_split(0, &hs));
     }
     launch_permute_out(fint, f, 1, g, st);
     cudaError_t e = cudaGetLastError();
@@ -683,12 +692,15 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             H->colsV_u = t.panels[0].colsV_pad;
             size_t n = (size_t)t.sizeV;
             if ((rc = H->alloc(&H->d_AVhi, n)) || (rc = H->alloc(&H->d_AVlo, n))) return rc;
-            launch_split_panel((const float *)H->d_AV, H->d_AVhi, H->d_AVlo, n, st);
+            H->a_expV = panel_scale_exp((const float *)H->d_AV, n, (unsigned *)H->d_err, st);
+            if (H->a_expV == INT32_MIN) return fail(PFMM_ERR_CUDA, "panel scale");
+            CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), st));
+            launch_split_panel((const float *)H->d_AV, H->d_AVhi, H->d_AVlo, n, H->a_expV, st);
             CK(cudaStreamSynchronize(st));
             H->release(H->d_AV);  // hi + lo represent it; the CUDA-core path reads their sum
             H->d_AV = nullptr;
-            uint64_t dims[2] = {(uint64_t)H->colsV_u, (uint64_t)(n / H->colsV_u)}, str[1] = {(uint64_t)H->colsV_u * 4};
-            uint32_t box[2] = {32, 128};
+            uint64_t dims[2] = {(uint64_t)H->colsV_u, (uint64_t)(n / H->colsV_u)}, str[1] = {(uint64_t)H->colsV_u * 2};
+            uint32_t box[2] = {64, 128};
             if ((rc = encode_map(&H->mapAVhi, H->d_AVhi, 2, dims, str, box)) ||
                 (rc = encode_map(&H->mapAVlo, H->d_AVlo, 2, dims, str, box)))
                 return rc;
@@ -698,12 +710,15 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             H->colsK_u = t.panels[0].colsK_pad;
             size_t n = (size_t)t.sizeK;
             if ((rc = H->alloc(&H->d_AKhi, n)) || (rc = H->alloc(&H->d_AKlo, n))) return rc;
-            launch_split_panel((const float *)H->d_AK, H->d_AKhi, H->d_AKlo, n, st);
+            H->a_expK = panel_scale_exp((const float *)H->d_AK, n, (unsigned *)H->d_err, st);
+            if (H->a_expK == INT32_MIN) return fail(PFMM_ERR_CUDA, "panel scale");
+            CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), st));
+            launch_split_panel((const float *)H->d_AK, H->d_AKhi, H->d_AKlo, n, H->a_expK, st);
             CK(cudaStreamSynchronize(st));
             H->release(H->d_AK);
             H->d_AK = nullptr;
-            uint64_t dims[2] = {(uint64_t)H->colsK_u, (uint64_t)(n / H->colsK_u)}, str[1] = {(uint64_t)H->colsK_u * 4};
-            uint32_t box[2] = {32, 128};
+            uint64_t dims[2] = {(uint64_t)H->colsK_u, (uint64_t)(n / H->colsK_u)}, str[1] = {(uint64_t)H->colsK_u * 2};
+            uint32_t box[2] = {64, 128};
             if ((rc = encode_map(&H->mapAKhi, H->d_AKhi, 2, dims, str, box)) ||
                 (rc = encode_map(&H->mapAKlo, H->d_AKlo, 2, dims, str, box)))
                 return rc;
@@ -795,15 +810,17 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     mark(1);
     const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK) && !H->nf_cuda_cores;
     if (tc) {
-        if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_fint, st))) return rc;
+        if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_wmax, H->d_fint, st))) return rc;
     } else if ((parts & PFMM_PART_NEAR) && H->otf) {
         CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
         if ((rc = pfmm::run_nf_otf(H, op, xin, ncolg, H->Et, H->ls, nrhs, 1 << 30, H->d_fint, st))) return rc;
-    } else if (parts & PFMM_PART_NEAR)
+    } else if (parts & PFMM_PART_NEAR) {
+        NfHalfSplit hs;
         launch_nf_apply(H->mixed, op == 1, H->nf_blocks(op), op == 0 ? H->d_colV : H->d_colK, H->d_tiles, H->ntiles,
-                        H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st, 1 << 30, H->nf_blocks_lo(op));
-    else
+                        H->d_panels, xin, ncolg, nrhs, g, H->d_fint, st, 1 << 30, H->nf_split(op, &hs));
+    } else {
         CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
+    }
     mark(2);
     const int p = H->p;
     bool far = (parts & PFMM_PART_FAR) && p >= 2;
@@ -889,7 +906,7 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     info->n_m2l_pairs = t.n_m2l_pairs;
     // stored blocks: the arithmetic-type panels, or their two FP32 parts once split for tcgen05
     info->nearfield_bytes = h->otf ? h->otf_bytes
-                                   : t.sizeV * (h->tcV ? 8 : (int64_t)h->es) + t.sizeK * (h->tcK ? 8 : (int64_t)h->es);
+                                   : t.sizeV * (h->tcV ? 4 : (int64_t)h->es) + t.sizeK * (h->tcK ? 4 : (int64_t)h->es);
     info->device_bytes = h->dev_bytes;
     info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
     info->nearfield_v_elements = t.sizeV;

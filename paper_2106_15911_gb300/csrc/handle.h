@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -20,7 +21,9 @@ int set_error(int code, const std::string &msg);
 struct pfmm_handle;
 namespace pfmm {
 // tensor-core nearfield of op (0: V, 1: K) into fint; whi/wlo: [nrhs][E_t][cols] FP32 workspaces
-int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, float *whi, float *wlo, double *fint, cudaStream_t st);
+// whi, wlo: FP16 input parts ([nrhs][E_t][cols] each); wmax: nrhs words of scratch
+int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned *wmax, double *fint,
+              cudaStream_t st);
 // size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
 int ensure_ws(pfmm_handle *H, int nrhs);
 // the on-the-fly nearfield of op into fint (+=): arguments of launch_nf_otf for this handle
@@ -78,13 +81,15 @@ struct pfmm_handle {
     // tensor-core nearfield (mixed mode, untruncated panels of equal width, 2 steps per leaf)
     bool tcV = false, tcK = false;
     bool nf_cuda_cores = false;     // engine override chosen by the batch autotuner
-    float *d_AVhi = nullptr, *d_AVlo = nullptr, *d_AKhi = nullptr, *d_AKlo = nullptr;
+    uint16_t *d_AVhi = nullptr, *d_AVlo = nullptr, *d_AKhi = nullptr, *d_AKlo = nullptr;  // FP16 parts
+    int a_expV = 0, a_expK = 0;     // scale exponents of the panels' FP16 split
     CUtensorMap mapAVhi{}, mapAVlo{}, mapAKhi{}, mapAKlo{};
     int colsV_u = 0, colsK_u = 0;  // common padded column count of the panels
     int *d_tiles128 = nullptr;
     int ntiles128 = 0, nsm = 0;
     int *d_err = nullptr;           // bounded-wait error word of the device kernels
-    float *d_Whi = nullptr, *d_Wlo = nullptr;
+    uint16_t *d_Whi = nullptr, *d_Wlo = nullptr;  // FP16 input parts
+    unsigned *d_wmax = nullptr;                    // [ws_nrhs] max |input| per rhs (FP32 bits)
     size_t w_elems = 0;
 
     bool prof = false;
@@ -93,17 +98,23 @@ struct pfmm_handle {
     double acc_ms[8] = {0};
     int n_prof = 0;
 
-    // stored nearfield blocks of op for the CUDA-core engine: the FP32/FP64 panels, or, once
-    // the tensor-core split exists, its hi part (and nf_blocks_lo the lo part, added on load)
-    const void *nf_blocks(int op) const
+    // stored nearfield blocks of op for the CUDA-core engine: the FP32/FP64 panels, or null once
+    // only the tensor-core split exists (nf_split then describes it)
+    const void *nf_blocks(int op) const { return op == 0 ? d_AV : d_AK; }
+    pfmm::NfHalfSplit split_desc(int op) const
     {
-        const void *a = op == 0 ? d_AV : d_AK;
-        return a ? a : (op == 0 ? (const void *)d_AVhi : (const void *)d_AKhi);
+        pfmm::NfHalfSplit s;
+        s.hi = op == 0 ? d_AVhi : d_AKhi;
+        s.lo = op == 0 ? d_AVlo : d_AKlo;
+        s.inv_scale = std::ldexp(1.0f, -(op == 0 ? a_expV : a_expK));
+        return s;
     }
-    const float *nf_blocks_lo(int op) const
+    // the split to read in place of the panels, or null while the panels exist
+    const pfmm::NfHalfSplit *nf_split(int op, pfmm::NfHalfSplit *buf) const
     {
-        if (op == 0) return d_AV ? nullptr : d_AVlo;
-        return d_AK ? nullptr : d_AKlo;
+        if (nf_blocks(op)) return nullptr;
+        *buf = split_desc(op);
+        return buf;
     }
 
     ~pfmm_handle()

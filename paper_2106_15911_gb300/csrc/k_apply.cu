@@ -9,6 +9,8 @@
 //   lam_l                 local contributions, same layout
 // R is the arithmetic type of the FMM passes and of the stored nearfield blocks: double in
 // FP64 mode, float in mixed mode (FP64 output accumulation).
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
                                                     const int *__restrict__ tiles, const PanelGPU *__restrict__ panels,
                                                     const S *__restrict__ x, int ncolg, int Et, int ls, int nint,
                                                     double *__restrict__ f, int nt, int kop, int ndmax,
-                                                    const S *__restrict__ Alo)
+                                                    NfHalfSplit hs)
 {
     constexpr int BM = 64, BN = 64, BK = 16;
     constexpr bool kFloat = sizeof(S) == 4;
@@ -93,8 +95,9 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
     const S *xr = x + (size_t)rhs * Et * ncolg;
     const int *cols = colidx + (kop ? P.colK_at : P.colV_at);
     const int ncp = kop ? P.colsK_pad : P.colsV_pad;
-    A += kop ? P.offK : P.offV;
-    if (Alo) Alo += kop ? P.offK : P.offV;
+    const bool half = hs.hi != nullptr;  // FP32 only
+    const size_t off = kop ? P.offK : P.offV;
+    const __half *Hh = reinterpret_cast<const __half *>(hs.hi), *Hl = reinterpret_cast<const __half *>(hs.lo);
     S acc[4][4];
     double accd[4][4];
 #pragma unroll
@@ -107,14 +110,14 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
     const int nd = min(ls + s + 1, ndmax);
     int ktiles = 0;
     for (int d = 0; d < nd; ++d) {
-        const S *Ad = A + ((size_t)d * P.rows_pad + r0) * ncp;
-        const S *Adl = Alo ? Alo + ((size_t)d * P.rows_pad + r0) * ncp : nullptr;
+        const size_t dbase = off + ((size_t)d * P.rows_pad + r0) * ncp;
         for (int k0 = 0; k0 < ncp; k0 += BK) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 int e = tid + 256 * q;
                 int i = e >> 4, j = e & 15;
-                As[j][i] = Adl ? Ad[(size_t)i * ncp + k0 + j] + Adl[(size_t)i * ncp + k0 + j] : Ad[(size_t)i * ncp + k0 + j];
+                const size_t ia = dbase + (size_t)i * ncp + k0 + j;
+                As[j][i] = half ? S((__half2float(Hh[ia]) + __half2float(Hl[ia])) * hs.inv_scale) : A[ia];
                 int c = e >> 4;
                 int t = ((ib * BN + c) * ls + s);
                 int col = cols[k0 + j];
@@ -164,16 +167,16 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
 
 void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
                      const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
-                     cudaStream_t st, int ndmax, const float *A_lo)
+                     cudaStream_t st, int ndmax, const NfHalfSplit *hs)
 {
     int nint = g.Et / g.ls;
     dim3 grd(ntiles, g.ls * ((nint + 63) / 64), nrhs);
     if (mixed)
         k_nf_apply<float><<<grd, 256, 0, st>>>((const float *)A, colidx, tiles, panels, (const float *)x, ncolg, g.Et,
-                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax, A_lo);
+                                               g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax, hs ? *hs : NfHalfSplit{});
     else
         k_nf_apply<double><<<grd, 256, 0, st>>>((const double *)A, colidx, tiles, panels, (const double *)x, ncolg,
-                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax, nullptr);
+                                                g.Et, g.ls, nint, f_int, g.nt, kop ? 1 : 0, ndmax, NfHalfSplit{});
 }
 
 // ------------------------------------------------------------------------------------------

@@ -1,5 +1,6 @@
 // k_nf_tc.cu -- nearfield apply (Alg. 2, last loop; Eq. eval_sl_nf_block) on the sm_103a
-// tensor cores: tcgen05.mma (kind::tf32) with TMA-staged operands and TMEM accumulators.
+// tensor cores: tcgen05.mma (kind::f16, FP16 operands) with TMA-staged operands and TMEM
+// accumulators.
 //
 // The block-Toeplitz nearfield product of one target leaf box X is a dense GEMM
 //   F[rows][t] += sum_{d} A_d[rows][k] W[t - d][k]      (k: the columns of X's interaction area)
@@ -7,17 +8,25 @@
 // 128 rows x 256 columns: columns 0..127 are the intervals i0..i0+127 at phase s = 0, columns
 // 128..255 the same intervals at s = 1.  W is seen by TMA as a 4D tensor [rhs][interval][phase]
 // [col], so the time shift by d is a coordinate offset, and the causality mask (t - d < 0) is the
-// out-of-bounds zero fill.  FP32 accuracy comes from a 3xTF32 split:
-//   A W ~ A_hi W_hi + A_hi W_lo + A_lo W_hi,   A_hi = rn_tf32(A), A_lo = rn_tf32(A - A_hi)
-//   (same for W), accumulated in FP32 in TMEM over a chunk of the column loop (split K) and
-//   added to the FP64 output with FP64 atomics.
+// out-of-bounds zero fill.  FP32 accuracy comes from a two-part FP16 split with power-of-two
+// scales (FP16 keeps 11 significant bits, as TF32 does, at twice the rate and half the bytes):
+//   A W ~ (A_hi W_hi + A_hi W_lo + A_lo W_hi) / (s_A s_W),
+//   A_hi = rn_f16(s_A A), A_lo = rn_f16(s_A A - A_hi)     (same for W with s_W per rhs),
+// where s_A (per operator, at build) and s_W (per rhs and apply, from max |W|) bring the largest
+// magnitude into [2^14, 2^15): the parts are normal FP16 down to 2^-29 of the maximum, and
+// |A - (A_hi + A_lo) / s_A| <= 2^-22 |A| above that.  The products are accumulated in FP32 in
+// TMEM over a chunk of the column loop (split K), unscaled exactly (powers of two) in FP64 and
+// added to the FP64 output with FP64 atomics.
 // Warp roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues the MMAs,
 // warps 2-5 drain TMEM (each warp reads its 32-lane quadrant).  Two smem stages, two TMEM
 // accumulators (512 columns), persistent CTAs over (tile, K chunk) work items.  Every mbarrier
 // wait gives up after a deadline, sets an error word and lets the CTA finish cleanly.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 
@@ -31,9 +40,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BK = 32;                   // BK fp32 = 128 bytes = one swizzle atom
-constexpr int A_TILE = BM * BK * 4;                // 16 KB
-constexpr int B_HALF = 128 * BK * 4;               // 16 KB (one phase)
+constexpr int BM = 128, BK = 64;                   // BK fp16 = 128 bytes = one swizzle atom
+constexpr int A_TILE = BM * BK * 2;                // 16 KB
+constexpr int B_HALF = 128 * BK * 2;               // 16 KB (one phase)
 constexpr int STAGE_BYTES = 2 * A_TILE + 4 * B_HALF;  // A_hi, A_lo, B_hi (2 halves), B_lo (2 halves)
 constexpr int NSTAGE = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // 2 s per wait
@@ -56,20 +65,19 @@ __device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int x,
         : "memory");
 }
 
-// instruction descriptor: kind::tf32, FP32 accumulate, A and B K-major, M x N
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+// instruction descriptor: kind::f16 with FP16 A and B (format 0), FP32 accumulate, both
+// K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
 {
     return (1u << 4)                      // D format F32
-           | (2u << 7)                    // A format TF32
-           | (2u << 10)                   // B format TF32
            | ((uint32_t)(N >> 3) << 17)   // N / 8
            | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+__device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::
             "r"(dt),
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
@@ -177,7 +185,7 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
         // ---------------- MMA issuer
         if (lane == 0) {
             int g = 0, n = 0;
-            const uint32_t id256 = idesc_tf32(BM, 256), id128 = idesc_tf32(BM, 128);
+            const uint32_t id256 = idesc_f16(BM, 256), id128 = idesc_f16(BM, 128);
             for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x, ++n) {
                 Item I = decode_item(P, it);
                 const int acc = n & 1;
@@ -201,19 +209,19 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
                     const uint32_t a_hi = su32(smem + s * STAGE_BYTES), a_lo = a_hi + A_TILE;
                     const uint32_t b_hi = a_hi + 2 * A_TILE, b_lo = b_hi + 2 * B_HALF;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 8; ++kk) {  // K = 8 tf32 (32 bytes) per MMA
+                    for (int kk = 0; kk < BK / 16; ++kk) {  // K = 16 fp16 (32 bytes) per MMA
                         const uint32_t ko = kk * 32;
                         if (d < 3) {
-                            mma_tf32(dcol, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), id256, first ? 0u : 1u);
+                            mma_f16(dcol, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), id256, first ? 0u : 1u);
                             first = 0;
-                            mma_tf32(dcol, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), id256, 1u);
-                            mma_tf32(dcol, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), id256, 1u);
+                            mma_f16(dcol, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), id256, 1u);
+                            mma_f16(dcol, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), id256, 1u);
                         } else {
                             // d = 3 reaches back only from the second step of an interval
-                            mma_tf32(dcol + 128, sw128_desc(a_hi + ko), sw128_desc(b_hi + B_HALF + ko), id128,
+                            mma_f16(dcol + 128, sw128_desc(a_hi + ko), sw128_desc(b_hi + B_HALF + ko), id128,
                                      first ? 0u : 1u);
-                            mma_tf32(dcol + 128, sw128_desc(a_hi + ko), sw128_desc(b_lo + B_HALF + ko), id128, 1u);
-                            mma_tf32(dcol + 128, sw128_desc(a_lo + ko), sw128_desc(b_hi + B_HALF + ko), id128, 1u);
+                            mma_f16(dcol + 128, sw128_desc(a_hi + ko), sw128_desc(b_lo + B_HALF + ko), id128, 1u);
+                            mma_f16(dcol + 128, sw128_desc(a_lo + ko), sw128_desc(b_hi + B_HALF + ko), id128, 1u);
                             if (first) {
                                 // the phase-0 half starts with no d < 3 stage in this chunk: clear it
                                 first = 0;
@@ -246,6 +254,7 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
             const bool has_any = I.st1 > I.st0;
             const bool has_ph0 = has_any && I.st0 < 3 * P.nkb;
             double *fr = P.f + (size_t)I.rhs * P.Et * P.nt + Pn.row0 + row;
+            const double unscale = ldexp(1.0, -(P.a_exp + w_scale_exp(P.wmax[I.rhs])));
 #pragma unroll 1
             for (int c0 = 0; c0 < 256; c0 += 32) {
                 uint32_t v[32];
@@ -254,7 +263,7 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int c = c0 + j, ph = c >> 7, iv = I.ib * 128 + (c & 127);
-                    if (iv < P.nint) atomicAdd(fr + (size_t)(2 * iv + ph) * P.nt, (double)__uint_as_float(v[j]));
+                    if (iv < P.nint) atomicAdd(fr + (size_t)(2 * iv + ph) * P.nt, (double)__uint_as_float(v[j]) * unscale);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -269,29 +278,47 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------------------------------
-// split kernels: hi = a rounded to nearest TF32, lo = (a - hi) rounded to nearest TF32; both
-// parts are exact TF32 values, so the tensor core reads them unchanged and a - hi - lo is
-// below 2^-22 |a|
-__device__ __forceinline__ float rna_tf32(float x)
+// split kernels: with the scale s = 2^E, hi = rn_f16(s a) and lo = rn_f16(s a - hi).  s a - hi is
+// exact in FP32 (and in FP64 for the input), so a - (hi + lo) / s is one FP16 rounding of the
+// remainder: below 2^-22 |a| while lo is a normal FP16 number.
+
+// largest |a| of n FP32 values into *out as ordered bits (non-negative floats order as integers)
+__global__ void k_absmax_f32(const float *__restrict__ A, size_t n, unsigned *__restrict__ out)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(A[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-__global__ void k_split_panel(const float *__restrict__ A, float *__restrict__ hi, float *__restrict__ lo, size_t n)
+__global__ void k_split_panel(const float *__restrict__ A, __half *__restrict__ hi, __half *__restrict__ lo, size_t n,
+                              float scale)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float a = A[i];
-    float h = rna_tf32(a);
+    const float a = A[i] * scale;
+    const __half h = __float2half_rn(a);
     hi[i] = h;
-    lo[i] = rna_tf32(a - h);
+    lo[i] = __float2half_rn(a - __half2float(h));
+}
+
+// per-rhs max |x| of the FP64 input [rhs][Et][ncol] (rounded to FP32, which moves the scale by
+// at most one binade)
+__global__ void k_absmax_input(const double *__restrict__ x, size_t per_rhs, unsigned *__restrict__ wmax)
+{
+    const double *xr = x + (size_t)blockIdx.y * per_rhs;
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_rhs; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, (float)fabs(xr[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(wmax + blockIdx.y, __float_as_uint(m));
 }
 
 // W split from FP64 input: permutes (V) or pads rows (K) into [rhs][t][ncol_pad]
 __global__ void k_split_input(const double *__restrict__ x, const int *__restrict__ perm, int ncol, int ncol_pad,
-                              float *__restrict__ hi, float *__restrict__ lo, size_t total)
+                              __half *__restrict__ hi, __half *__restrict__ lo, size_t per_rhs, size_t total,
+                              const unsigned *__restrict__ wmax)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
@@ -299,21 +326,41 @@ __global__ void k_split_input(const double *__restrict__ x, const int *__restric
     int c = (int)(i - rt * ncol_pad);
     double v = 0.0;
     if (c < ncol) v = x[rt * ncol + (perm ? perm[c] : c)];
-    float h = rna_tf32((float)v);
+    v = ldexp(v, w_scale_exp(wmax[i / per_rhs]));
+    const __half h = __double2half(v);
     hi[i] = h;
-    lo[i] = rna_tf32((float)(v - (double)h));
+    lo[i] = __double2half(v - (double)__half2float(h));
 }
 
-void launch_split_panel(const float *A, float *hi, float *lo, size_t n, cudaStream_t st)
+int panel_scale_exp(const float *A, size_t n, unsigned *scratch, cudaStream_t st)
 {
-    k_split_panel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, hi, lo, n);
+    if (cudaMemsetAsync(scratch, 0, sizeof(unsigned), st) != cudaSuccess) return INT32_MIN;
+    const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    if (grid > 0) k_absmax_f32<<<grid, 256, 0, st>>>(A, n, scratch);
+    unsigned bits = 0;
+    if (cudaMemcpyAsync(&bits, scratch, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return INT32_MIN;
+    return w_scale_exp(bits);
 }
 
-void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, float *hi,
-                        float *lo, cudaStream_t st)
+void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int a_exp, cudaStream_t st)
 {
-    size_t total = (size_t)nrhs * Et * ncol_pad;
-    k_split_input<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(x, perm, ncol, ncol_pad, hi, lo, total);
+    if (n == 0) return;
+    k_split_panel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, (__half *)hi, (__half *)lo, n,
+                                                              std::ldexp(1.0f, a_exp));
+}
+
+void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, void *hi,
+                        void *lo, unsigned *wmax, cudaStream_t st)
+{
+    cudaMemsetAsync(wmax, 0, sizeof(unsigned) * nrhs, st);
+    const size_t per_in = (size_t)Et * ncol;
+    const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>((per_in + 2047) / 2048, 1216));
+    k_absmax_input<<<dim3(gx, nrhs), 256, 0, st>>>(x, per_in, wmax);
+    const size_t per_rhs = (size_t)Et * ncol_pad, total = (size_t)nrhs * per_rhs;
+    k_split_input<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(x, perm, ncol, ncol_pad, (__half *)hi,
+                                                                   (__half *)lo, per_rhs, total, wmax);
 }
 
 size_t nf_tc_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + 1024 + 256; }

@@ -84,10 +84,15 @@ struct ApplyGeo {
 void launch_permute_in(const double *w, void *w_int, bool to_float, int nrhs, const ApplyGeo &g, cudaStream_t st);
 void launch_permute_out(const double *f_int, double *f, int nrhs, const ApplyGeo &g, cudaStream_t st);
 void launch_cast_to_float(const double *x, float *y, size_t n, cudaStream_t st);
+// FP32 panels held only as the tensor-core engine's FP16 parts: A = (hi + lo) * inv_scale
+struct NfHalfSplit {
+    const uint16_t *hi = nullptr, *lo = nullptr;  // FP16 bit patterns, the stored panels' layout
+    float inv_scale = 1.f;                        // 2^-E of the split's scale (exact)
+};
 void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
                      const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
                      cudaStream_t st, int ndmax = 1 << 30,  // ndmax: only offsets d < ndmax
-                     const float *A_lo = nullptr);         // FP32 only: blocks = A + A_lo
+                     const NfHalfSplit *hs = nullptr);      // FP32 only: blocks from the FP16 parts, A unused
 void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab /*Sx or SK*/, const void *St,
                 void *mu_leaf, int nrhs, const ApplyGeo &g, cudaStream_t st);
 void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,

@@ -4,15 +4,33 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "kernels.h"
 
 namespace pfmm {
+
+constexpr int kScaleExpMax = 100;  // bound on |E| of the power-of-two scales
+
+// Scale exponent E of the FP16 split for a largest magnitude m given by its FP32 bits: 2^E m lies
+// in [2^14, 2^15) (m = 1.f * 2^(b - 127) with biased exponent b, so E = 141 - b); 0 for m = 0,
+// infinite or NaN; clamped to +-kScaleExpMax (subnormal maxima get the bound).
+__host__ __device__ inline int w_scale_exp(unsigned bits)
+{
+    bits &= 0x7fffffffu;
+    const int b = (int)(bits >> 23);
+    if (bits == 0u || b == 255) return 0;
+    const int E = 141 - b;
+    return E > kScaleExpMax ? kScaleExpMax : (E < -kScaleExpMax ? -kScaleExpMax : E);
+}
 
 struct NfTcParams {
     const PanelGPU *panels;
     const int *tiles;   // [ntiles][2] (panel, first row) with 128-row tiles
     int ntiles, nib, ksplit, nkb, nitems, cols_pad, kop;
     int nint, Et, nt;
+    int a_exp;              // scale exponent of the panels' FP16 split
+    const unsigned *wmax;   // [nrhs] FP32 bits of max |W| per rhs (scale of the input split)
     double *f;          // FP64 output [rhs][Et][nt] (internal order), accumulated with atomics
     int *err;           // set non-zero when a bounded wait gave up
 };
@@ -20,8 +38,14 @@ struct NfTcParams {
 size_t nf_tc_smem_bytes();
 int launch_nf_apply_tc(const CUtensorMap &Ahi, const CUtensorMap &Alo, const CUtensorMap &Whi, const CUtensorMap &Wlo,
                        const NfTcParams &P, int nsm, cudaStream_t st);
-void launch_split_panel(const float *A, float *hi, float *lo, size_t n, cudaStream_t st);
-void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, float *hi,
-                        float *lo, cudaStream_t st);
+// scale exponent of n stored FP32 panel values (synchronises st; scratch: one device word);
+// INT32_MIN on a CUDA error
+int panel_scale_exp(const float *A, size_t n, unsigned *scratch, cudaStream_t st);
+// hi/lo FP16 parts ([n] each) of 2^a_exp A
+void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int a_exp, cudaStream_t st);
+// per-rhs max |x| into wmax[nrhs], then the hi/lo FP16 parts [nrhs][Et][ncol_pad] of the scaled,
+// permuted (V) or padded (K) input
+void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, void *hi,
+                        void *lo, unsigned *wmax, cudaStream_t st);
 
 }  // namespace pfmm

@@ -59,13 +59,15 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     if (!H || !w || !f || nrhs < 1) return set_error(PFMM_ERR_INVALID_ARG, "invalid pfmm_apply_V_noalloc arguments");
     cudaStream_t st = (cudaStream_t)stream;
     // carve the static array: permuted input | FP64 output | moments | locals |
-    // [tensor-core input split hi | lo] | M2L T1 | M2L T2
+    // [tensor-core input split hi | lo | max |w| per rhs] | M2L T1 | M2L T2
     const size_t n_in = (size_t)nrhs * H->Et * H->nt;
     const size_t b_x = up256(n_in * H->es), b_f = up256(n_in * sizeof(double));
     const size_t n_mom = (size_t)nrhs * (H->mom_per_rhs > 0 ? H->mom_per_rhs : 1);
     const size_t b_mu = up256(n_mom * H->es);
-    const size_t b_w = (H->tcV && !H->nf_cuda_cores) ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(float)) : 0;
-    const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w;
+    const bool tc = H->tcV && !H->nf_cuda_cores;
+    const size_t b_w = tc ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(uint16_t)) : 0;
+    const size_t b_m = tc ? up256((size_t)nrhs * sizeof(unsigned)) : 0;
+    const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w + b_m;
     const size_t min_chunk = (size_t)nrhs * 2 * H->na * H->na * H->ne * 64;  // M2L: two interval pairs of a 4^3 grid
     size_t need_T = 0;  // elements for the largest single-interval chunk over all levels
     for (int l = 2; l <= H->p; ++l) {
@@ -86,7 +88,8 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     double *fint = (double *)(base + b_x);
     char *mu = (char *)(base + b_x + b_f);
     char *lam = mu + b_mu;
-    float *whi = (float *)(lam + b_mu), *wlo = (float *)(lam + b_mu + b_w);
+    void *whi = lam + b_mu, *wlo = lam + b_mu + b_w;
+    unsigned *wmax = (unsigned *)(lam + b_mu + 2 * b_w);
     const size_t t_bytes = (kScratchBytes - fixed) / 2 / 256 * 256;
     void *T1 = base + fixed, *T2 = base + fixed + t_bytes;
     const size_t ws_elems = t_bytes / H->es;
@@ -112,14 +115,15 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     // every buffer below is fully written before it is read, except the locals of the first two
     // intervals of each level, which launch_m2l clears; nothing depends on the previous call
     launch_permute_in(w, xint, H->mixed, nrhs, g, st);
-    if (H->tcV && !H->nf_cuda_cores) {  // the same nearfield engine as pfmm_apply_V
-        if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, fint, st))) return rc;
+    if (tc) {  // the same nearfield engine as pfmm_apply_V
+        if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, wmax, fint, st))) return rc;
     } else if (H->otf) {
         cudaMemsetAsync(fint, 0, n_in * sizeof(double), st);
         if ((rc = run_nf_otf(H, 0, xint, H->nt, H->Et, H->ls, nrhs, 1 << 30, fint, st))) return rc;
     } else {
+        NfHalfSplit hs;
         launch_nf_apply(H->mixed, false, H->nf_blocks(0), H->d_colV, H->d_tiles, H->ntiles, H->d_panels, xint, H->nt, nrhs,
-                        g, fint, st, 1 << 30, H->nf_blocks_lo(0));
+                        g, fint, st, 1 << 30, H->nf_split(0, &hs));
     }
     const int p = H->p;
     if (p >= 2) {

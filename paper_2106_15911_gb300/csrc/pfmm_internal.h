@@ -16,6 +16,9 @@ constexpr int kMaxMx = 12;
 constexpr int kMaxNa = 12;
 constexpr int kRowTile = 64;  // nearfield panel rows are padded to this
 constexpr int kColTile = 32;  // nearfield panel columns are padded to this
+// columns of panels that index the whole mesh (the tensor-core engine's one column space) are
+// padded to 64: one 128-byte swizzle row of FP16 per K block
+constexpr int kTcColTile = 64;
 
 // ---------------------------------------------------------------------------------------------
 // Host description of one level of the box cluster tree (Section 3.2, Alg. 1).  Every level

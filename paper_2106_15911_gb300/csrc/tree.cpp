@@ -280,7 +280,7 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
             P.colV_at = (int)t.colV.size();
             for (int i = 0; i < nt; ++i) t.colV.push_back(near[t.tri_leaf[i]] ? i : -1);
             P.ncolV = nt;
-            P.colsV_pad = (nt + kColTile - 1) / kColTile * kColTile;
+            P.colsV_pad = (nt + kTcColTile - 1) / kTcColTile * kTcColTile;
             while ((int)t.colV.size() < P.colV_at + P.colsV_pad) t.colV.push_back(-1);
             P.colK_at = (int)t.colK.size();
             for (int nd = 0; nd < nv; ++nd) {
@@ -288,7 +288,7 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
                 t.colK.push_back(nd);
             }
             P.ncolK = nv;
-            P.colsK_pad = (nv + kColTile - 1) / kColTile * kColTile;
+            P.colsK_pad = (nv + kTcColTile - 1) / kTcColTile * kTcColTile;
             while ((int)t.colK.size() < P.colK_at + P.colsK_pad) t.colK.push_back(-1);
             P.offV = offV;
             P.offK = offK;
@@ -304,7 +304,8 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
                 for (int v = 0; v < 3; ++v) nodes.insert(T[3 * t.perm[i] + v]);
             }
         P.ncolV = (int)t.colV.size() - P.colV_at;
-        P.colsV_pad = (P.ncolV + kColTile - 1) / kColTile * kColTile;
+        const int tv = P.ncolV == nt ? kTcColTile : kColTile;
+        P.colsV_pad = (P.ncolV + tv - 1) / tv * tv;
         while ((int)t.colV.size() < P.colV_at + P.colsV_pad) t.colV.push_back(-1);
         P.colK_at = (int)t.colK.size();
         for (int nd : nodes) {
@@ -312,7 +313,8 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
             t.colK.push_back(nd);
         }
         P.ncolK = (int)nodes.size();
-        P.colsK_pad = (P.ncolK + kColTile - 1) / kColTile * kColTile;
+        const int tk = P.ncolK == nv ? kTcColTile : kColTile;
+        P.colsK_pad = (P.ncolK + tk - 1) / tk * tk;
         while ((int)t.colK.size() < P.colK_at + P.colsK_pad) t.colK.push_back(-1);
         P.offV = offV;
         P.offK = offK;
