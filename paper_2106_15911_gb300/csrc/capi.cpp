@@ -695,14 +695,15 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             H->a_expV = panel_scale_exp((const float *)H->d_AV, n, (unsigned *)H->d_err, st);
             if (H->a_expV == INT32_MIN) return fail(PFMM_ERR_CUDA, "panel scale");
             CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), st));
-            launch_split_panel((const float *)H->d_AV, H->d_AVhi, H->d_AVlo, n, H->a_expV, st);
+            launch_split_panel((const float *)H->d_AV, H->d_AVhi, H->d_AVlo, n, H->colsV_u, H->a_expV, st);
             CK(cudaStreamSynchronize(st));
             H->release(H->d_AV);  // hi + lo represent it; the CUDA-core path reads their sum
             H->d_AV = nullptr;
-            uint64_t dims[2] = {(uint64_t)H->colsV_u, (uint64_t)(n / H->colsV_u)}, str[1] = {(uint64_t)H->colsV_u * 2};
-            uint32_t box[2] = {64, 128};
-            if ((rc = encode_map(&H->mapAVhi, H->d_AVhi, 2, dims, str, box)) ||
-                (rc = encode_map(&H->mapAVlo, H->d_AVlo, 2, dims, str, box)))
+            // [block][64 rows][64 columns] view of the 64 x 64 blocks (n is a multiple of 4096)
+            uint64_t dims[3] = {64, 64, (uint64_t)(n / 4096)}, str[2] = {128, 8192};
+            uint32_t box[3] = {64, 64, 1};
+            if ((rc = encode_map(&H->mapAVhi, H->d_AVhi, 3, dims, str, box)) ||
+                (rc = encode_map(&H->mapAVlo, H->d_AVlo, 3, dims, str, box)))
                 return rc;
             H->tcV = true;
         }
@@ -713,14 +714,14 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             H->a_expK = panel_scale_exp((const float *)H->d_AK, n, (unsigned *)H->d_err, st);
             if (H->a_expK == INT32_MIN) return fail(PFMM_ERR_CUDA, "panel scale");
             CK(cudaMemsetAsync(H->d_err, 0, sizeof(int), st));
-            launch_split_panel((const float *)H->d_AK, H->d_AKhi, H->d_AKlo, n, H->a_expK, st);
+            launch_split_panel((const float *)H->d_AK, H->d_AKhi, H->d_AKlo, n, H->colsK_u, H->a_expK, st);
             CK(cudaStreamSynchronize(st));
             H->release(H->d_AK);
             H->d_AK = nullptr;
-            uint64_t dims[2] = {(uint64_t)H->colsK_u, (uint64_t)(n / H->colsK_u)}, str[1] = {(uint64_t)H->colsK_u * 2};
-            uint32_t box[2] = {64, 128};
-            if ((rc = encode_map(&H->mapAKhi, H->d_AKhi, 2, dims, str, box)) ||
-                (rc = encode_map(&H->mapAKlo, H->d_AKlo, 2, dims, str, box)))
+            uint64_t dims[3] = {64, 64, (uint64_t)(n / 4096)}, str[2] = {128, 8192};
+            uint32_t box[3] = {64, 64, 1};
+            if ((rc = encode_map(&H->mapAKhi, H->d_AKhi, 3, dims, str, box)) ||
+                (rc = encode_map(&H->mapAKlo, H->d_AKlo, 3, dims, str, box)))
                 return rc;
             H->tcK = true;
         }

@@ -111,13 +111,18 @@ __global__ void __launch_bounds__(256) k_nf_apply(const S *__restrict__ A, const
     int ktiles = 0;
     for (int d = 0; d < nd; ++d) {
         const size_t dbase = off + ((size_t)d * P.rows_pad + r0) * ncp;
+        const size_t rbase = off / ncp + (size_t)d * P.rows_pad + r0;  // global row (FP16 parts)
         for (int k0 = 0; k0 < ncp; k0 += BK) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 int e = tid + 256 * q;
                 int i = e >> 4, j = e & 15;
-                const size_t ia = dbase + (size_t)i * ncp + k0 + j;
-                As[j][i] = half ? S((__half2float(Hh[ia]) + __half2float(Hl[ia])) * hs.inv_scale) : A[ia];
+                if (half) {
+                    const size_t ia = nf_tiled_index(rbase + i, k0 + j, ncp >> 6);
+                    As[j][i] = S((__half2float(Hh[ia]) + __half2float(Hl[ia])) * hs.inv_scale);
+                } else {
+                    As[j][i] = A[dbase + (size_t)i * ncp + k0 + j];
+                }
                 int c = e >> 4;
                 int t = ((ib * BN + c) * ls + s);
                 int col = cols[k0 + j];

@@ -47,12 +47,13 @@ constexpr int STAGE_BYTES = 2 * A_TILE + 4 * B_HALF;  // A_hi, A_lo, B_hi (2 hal
 constexpr int NSTAGE = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // 2 s per wait
 
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+// 3D tile: the FP16 panel parts seen as [block][64 rows][64 columns]
+__device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
             su32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
         : "memory");
 }
 
@@ -162,11 +163,20 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
                     }
                     const int d = st / P.nkb, kb = st % P.nkb;
                     unsigned char *sA = smem + s * STAGE_BYTES;
-                    const uint32_t bytes = d < 3 ? STAGE_BYTES : 2 * A_TILE + 2 * B_HALF;
+                    // A: the tile's 64-row blocks (the second only where the panel has rows; the
+                    // MMA rows of a skipped half are never written out)
+                    const bool two = I.r0 + 64 < Pn.nrows;
+                    const uint32_t abytes = two ? A_TILE : A_TILE / 2;
+                    const uint32_t bytes = 2 * abytes + (d < 3 ? 4 : 2) * B_HALF;
                     mbar_expect_tx(&full[s], bytes);
-                    const int arow = (int)((P.kop ? Pn.offK : Pn.offV) / P.cols_pad) + d * Pn.rows_pad + I.r0;
-                    tma_2d(sA, &mapAhi, kb * BK, arow, &full[s]);
-                    tma_2d(sA + A_TILE, &mapAlo, kb * BK, arow, &full[s]);
+                    const long long arow = (P.kop ? Pn.offK : Pn.offV) / P.cols_pad + (long long)d * Pn.rows_pad + I.r0;
+                    const int blk = (int)(arow >> 6) * P.nkb + kb;
+                    tma_3d(sA, &mapAhi, 0, 0, blk, &full[s]);
+                    tma_3d(sA + A_TILE, &mapAlo, 0, 0, blk, &full[s]);
+                    if (two) {
+                        tma_3d(sA + A_TILE / 2, &mapAhi, 0, 0, blk + P.nkb, &full[s]);
+                        tma_3d(sA + A_TILE + A_TILE / 2, &mapAlo, 0, 0, blk + P.nkb, &full[s]);
+                    }
                     unsigned char *sB = sA + 2 * A_TILE;
                     for (int ph = (d < 3 ? 0 : 1); ph < 2; ++ph) {
                         // step t = 2 i + ph, source step t - d = 2 (i - q) + phs
@@ -292,15 +302,19 @@ __global__ void k_absmax_f32(const float *__restrict__ A, size_t n, unsigned *__
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
+// row-major FP32 panels [rows][ncp] -> FP16 parts in 64 x 64 blocks
 __global__ void k_split_panel(const float *__restrict__ A, __half *__restrict__ hi, __half *__restrict__ lo, size_t n,
-                              float scale)
+                              int ncp, float scale)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const size_t R = i / ncp;
+    const int c = (int)(i - R * ncp);
+    const size_t o = nf_tiled_index(R, c, ncp >> 6);
     const float a = A[i] * scale;
     const __half h = __float2half_rn(a);
-    hi[i] = h;
-    lo[i] = __float2half_rn(a - __half2float(h));
+    hi[o] = h;
+    lo[o] = __float2half_rn(a - __half2float(h));
 }
 
 // per-rhs max |x| of the FP64 input [rhs][Et][ncol] (rounded to FP32, which moves the scale by
@@ -344,10 +358,10 @@ int panel_scale_exp(const float *A, size_t n, unsigned *scratch, cudaStream_t st
     return w_scale_exp(bits);
 }
 
-void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int a_exp, cudaStream_t st)
+void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int ncp, int a_exp, cudaStream_t st)
 {
     if (n == 0) return;
-    k_split_panel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, (__half *)hi, (__half *)lo, n,
+    k_split_panel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, (__half *)hi, (__half *)lo, n, ncp,
                                                               std::ldexp(1.0f, a_exp));
 }
 

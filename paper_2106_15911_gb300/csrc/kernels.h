@@ -86,9 +86,18 @@ void launch_permute_out(const double *f_int, double *f, int nrhs, const ApplyGeo
 void launch_cast_to_float(const double *x, float *y, size_t n, cudaStream_t st);
 // FP32 panels held only as the tensor-core engine's FP16 parts: A = (hi + lo) * inv_scale
 struct NfHalfSplit {
-    const uint16_t *hi = nullptr, *lo = nullptr;  // FP16 bit patterns, the stored panels' layout
+    const uint16_t *hi = nullptr, *lo = nullptr;  // FP16 bit patterns in 64 x 64 blocks (nf_tiled_index)
     float inv_scale = 1.f;                        // 2^-E of the split's scale (exact)
 };
+// Position of element (R, c) of the FP16 parts.  R is the global panel row (panel element offset /
+// columns + d * rows_pad + r: every panel's step block starts at a multiple of 64 rows) and c the
+// column of a layout with 64 * nkb columns; the parts are stored as contiguous 64-row x 64-column
+// blocks (8 KB, 128-byte rows), block (R / 64, c / 64) at index (R / 64) * nkb + c / 64, so a
+// tensor-core tile half is one contiguous copy.
+__host__ __device__ inline size_t nf_tiled_index(size_t R, int c, int nkb)
+{
+    return (((R >> 6) * (size_t)nkb + (size_t)(c >> 6)) << 12) + ((R & 63) << 6) + (size_t)(c & 63);
+}
 void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, const int *tiles, int ntiles,
                      const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
                      cudaStream_t st, int ndmax = 1 << 30,  // ndmax: only offsets d < ndmax

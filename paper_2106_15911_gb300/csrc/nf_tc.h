@@ -41,8 +41,9 @@ int launch_nf_apply_tc(const CUtensorMap &Ahi, const CUtensorMap &Alo, const CUt
 // scale exponent of n stored FP32 panel values (synchronises st; scratch: one device word);
 // INT32_MIN on a CUDA error
 int panel_scale_exp(const float *A, size_t n, unsigned *scratch, cudaStream_t st);
-// hi/lo FP16 parts ([n] each) of 2^a_exp A
-void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int a_exp, cudaStream_t st);
+// hi/lo FP16 parts ([n] each, 64 x 64 blocks of nf_tiled_index) of 2^a_exp A (row-major, ncp
+// columns, a multiple of 64)
+void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int ncp, int a_exp, cudaStream_t st);
 // per-rhs max |x| into wmax[nrhs], then the hi/lo FP16 parts [nrhs][Et][ncol_pad] of the scaled,
 // permuted (V) or padded (K) input
 void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, void *hi,
