@@ -32,7 +32,7 @@ METRIC = "pFMM matvec space-time DOF/s"
 N_A, ET, M_X, M_T, C_ST = 32, 256, 6, 4, 1.0
 # DRAM bytes (read + write) per stored panel element of one tensor-core nearfield launch, from an
 # ncu capture of the 3072-triangle x 128-step case (None: not captured for the current kernel)
-NF_TC_DRAM_BYTES_PER_ELEMENT = 4.81
+NF_TC_DRAM_BYTES_PER_ELEMENT = 4.79
 
 
 def _set_size(n_a, et):

@@ -260,8 +260,8 @@ int pfmm::ensure_ws(pfmm_handle *H, int nrhs) { return ensure_workspace(H, nrhs)
 // Tensor-core nearfield of op (0: V, 1: K) into fint (zeroed here): splits the FP64 input into
 // scaled FP16 hi/lo parts in whi/wlo ([nrhs][E_t][cols] each; per-rhs scale from max |x| in
 // wmax), encodes their TMA views and launches.
-int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned *wmax,
-                    double *fint, cudaStream_t st)
+int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo,
+                    unsigned long long *wmax, double *fint, cudaStream_t st)
 {
     int rc;
     const int cols = op == 0 ? H->colsV_u : H->colsK_u;

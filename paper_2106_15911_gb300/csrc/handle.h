@@ -22,8 +22,8 @@ struct pfmm_handle;
 namespace pfmm {
 // tensor-core nearfield of op (0: V, 1: K) into fint; whi/wlo: [nrhs][E_t][cols] FP32 workspaces
 // whi, wlo: FP16 input parts ([nrhs][E_t][cols] each); wmax: nrhs words of scratch
-int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned *wmax, double *fint,
-              cudaStream_t st);
+int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned long long *wmax,
+              double *fint, cudaStream_t st);
 // size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
 int ensure_ws(pfmm_handle *H, int nrhs);
 // the on-the-fly nearfield of op into fint (+=): arguments of launch_nf_otf for this handle
@@ -89,7 +89,7 @@ struct pfmm_handle {
     int ntiles128 = 0, nsm = 0;
     int *d_err = nullptr;           // bounded-wait error word of the device kernels
     uint16_t *d_Whi = nullptr, *d_Wlo = nullptr;  // FP16 input parts
-    unsigned *d_wmax = nullptr;                    // [ws_nrhs] max |input| per rhs (FP32 bits)
+    unsigned long long *d_wmax = nullptr;          // [ws_nrhs] max |input| per rhs (FP64 bits)
     size_t w_elems = 0;
 
     bool prof = false;

@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
             const bool has_any = I.st1 > I.st0;
             const bool has_ph0 = has_any && I.st0 < 3 * P.nkb;
             double *fr = P.f + (size_t)I.rhs * P.Et * P.nt + Pn.row0 + row;
-            const double unscale = ldexp(1.0, -(P.a_exp + w_scale_exp(P.wmax[I.rhs])));
+            // 2^-(a_exp + E_W) (|exponent| <= 200) built from its bits
+            const double unscale = __longlong_as_double((long long)(1023 - P.a_exp - f64_scale_exp(P.wmax[I.rhs])) << 52);
 #pragma unroll 1
             for (int c0 = 0; c0 < 256; c0 += 32) {
                 uint32_t v[32];
@@ -317,33 +318,39 @@ __global__ void k_split_panel(const float *__restrict__ A, __half *__restrict__ 
     lo[o] = __float2half_rn(a - __half2float(h));
 }
 
-// per-rhs max |x| of the FP64 input [rhs][Et][ncol] (rounded to FP32, which moves the scale by
-// at most one binade)
-__global__ void k_absmax_input(const double *__restrict__ x, size_t per_rhs, unsigned *__restrict__ wmax)
+// per-rhs max |x| of the FP64 input [rhs][Et][ncol], on the bits (non-negative doubles order as
+// unsigned integers; no FP64 arithmetic)
+__global__ void k_absmax_input(const double *__restrict__ x, size_t per_rhs, unsigned long long *__restrict__ wmax)
 {
-    const double *xr = x + (size_t)blockIdx.y * per_rhs;
-    float m = 0.f;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_rhs; i += (size_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, (float)fabs(xr[i]));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(wmax + blockIdx.y, __float_as_uint(m));
+    const unsigned long long *xr = reinterpret_cast<const unsigned long long *>(x) + (size_t)blockIdx.y * per_rhs;
+    unsigned long long m = 0ull;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_rhs; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long v = xr[i] & 0x7fffffffffffffffull;
+        m = v > m ? v : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(wmax + blockIdx.y, m);
 }
 
-// W split from FP64 input: permutes (V) or pads rows (K) into [rhs][t][ncol_pad]
+// W split from FP64 input: permutes (V) or pads rows (K) into [rhs][t][ncol_pad].  x is rounded
+// once to FP32 (2^-24 relative), scaled exactly by 2^E in FP32 and split there.
 __global__ void k_split_input(const double *__restrict__ x, const int *__restrict__ perm, int ncol, int ncol_pad,
                               __half *__restrict__ hi, __half *__restrict__ lo, size_t per_rhs, size_t total,
-                              const unsigned *__restrict__ wmax)
+                              const unsigned long long *__restrict__ wmax)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     size_t rt = i / ncol_pad;
     int c = (int)(i - rt * ncol_pad);
-    double v = 0.0;
-    if (c < ncol) v = x[rt * ncol + (perm ? perm[c] : c)];
-    v = ldexp(v, w_scale_exp(wmax[i / per_rhs]));
-    const __half h = __double2half(v);
+    float v = 0.f;
+    if (c < ncol) v = (float)x[rt * ncol + (perm ? perm[c] : c)];
+    v *= __int_as_float((127 + f64_scale_exp(wmax[i / per_rhs])) << 23);  // 2^E, |E| <= 100
+    const __half h = __float2half_rn(v);
     hi[i] = h;
-    lo[i] = __double2half(v - (double)__half2float(h));
+    lo[i] = __float2half_rn(v - __half2float(h));
 }
 
 int panel_scale_exp(const float *A, size_t n, unsigned *scratch, cudaStream_t st)
@@ -355,7 +362,7 @@ int panel_scale_exp(const float *A, size_t n, unsigned *scratch, cudaStream_t st
     if (cudaMemcpyAsync(&bits, scratch, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return INT32_MIN;
-    return w_scale_exp(bits);
+    return f32_scale_exp(bits);
 }
 
 void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int ncp, int a_exp, cudaStream_t st)
@@ -366,9 +373,9 @@ void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int ncp, i
 }
 
 void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, void *hi,
-                        void *lo, unsigned *wmax, cudaStream_t st)
+                        void *lo, unsigned long long *wmax, cudaStream_t st)
 {
-    cudaMemsetAsync(wmax, 0, sizeof(unsigned) * nrhs, st);
+    cudaMemsetAsync(wmax, 0, sizeof(unsigned long long) * nrhs, st);
     const size_t per_in = (size_t)Et * ncol;
     const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>((per_in + 2047) / 2048, 1216));
     k_absmax_input<<<dim3(gx, nrhs), 256, 0, st>>>(x, per_in, wmax);

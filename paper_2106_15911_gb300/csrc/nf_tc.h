@@ -12,15 +12,24 @@ namespace pfmm {
 
 constexpr int kScaleExpMax = 100;  // bound on |E| of the power-of-two scales
 
-// Scale exponent E of the FP16 split for a largest magnitude m given by its FP32 bits: 2^E m lies
-// in [2^14, 2^15) (m = 1.f * 2^(b - 127) with biased exponent b, so E = 141 - b); 0 for m = 0,
-// infinite or NaN; clamped to +-kScaleExpMax (subnormal maxima get the bound).
-__host__ __device__ inline int w_scale_exp(unsigned bits)
+// Scale exponents E of the FP16 split for a largest magnitude m: 2^E m lies in [2^14, 2^15); 0 for
+// m = 0, infinite or NaN; clamped to +-kScaleExpMax (subnormal maxima get the bound).
+// From the FP32 bits of m (panels): m = 1.f * 2^(b - 127) with biased exponent b, E = 141 - b.
+__host__ __device__ inline int f32_scale_exp(unsigned bits)
 {
     bits &= 0x7fffffffu;
     const int b = (int)(bits >> 23);
     if (bits == 0u || b == 255) return 0;
     const int E = 141 - b;
+    return E > kScaleExpMax ? kScaleExpMax : (E < -kScaleExpMax ? -kScaleExpMax : E);
+}
+// From the FP64 bits of m (input): m = 1.f * 2^(b - 1023), E = 1037 - b.
+__host__ __device__ inline int f64_scale_exp(unsigned long long bits)
+{
+    bits &= 0x7fffffffffffffffull;
+    const int b = (int)(bits >> 52);
+    if (bits == 0ull || b == 2047) return 0;
+    const int E = 1037 - b;
     return E > kScaleExpMax ? kScaleExpMax : (E < -kScaleExpMax ? -kScaleExpMax : E);
 }
 
@@ -30,7 +39,7 @@ struct NfTcParams {
     int ntiles, nib, ksplit, nkb, nitems, cols_pad, kop;
     int nint, Et, nt;
     int a_exp;              // scale exponent of the panels' FP16 split
-    const unsigned *wmax;   // [nrhs] FP32 bits of max |W| per rhs (scale of the input split)
+    const unsigned long long *wmax;  // [nrhs] FP64 bits of max |W| per rhs (scale of the input split)
     double *f;          // FP64 output [rhs][Et][nt] (internal order), accumulated with atomics
     int *err;           // set non-zero when a bounded wait gave up
 };
@@ -47,6 +56,6 @@ void launch_split_panel(const float *A, void *hi, void *lo, size_t n, int ncp, i
 // per-rhs max |x| into wmax[nrhs], then the hi/lo FP16 parts [nrhs][Et][ncol_pad] of the scaled,
 // permuted (V) or padded (K) input
 void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad, int nrhs, int Et, void *hi,
-                        void *lo, unsigned *wmax, cudaStream_t st);
+                        void *lo, unsigned long long *wmax, cudaStream_t st);
 
 }  // namespace pfmm

@@ -66,7 +66,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     const size_t b_mu = up256(n_mom * H->es);
     const bool tc = H->tcV && !H->nf_cuda_cores;
     const size_t b_w = tc ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(uint16_t)) : 0;
-    const size_t b_m = tc ? up256((size_t)nrhs * sizeof(unsigned)) : 0;
+    const size_t b_m = tc ? up256((size_t)nrhs * sizeof(unsigned long long)) : 0;
     const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w + b_m;
     const size_t min_chunk = (size_t)nrhs * 2 * H->na * H->na * H->ne * 64;  // M2L: two interval pairs of a 4^3 grid
     size_t need_T = 0;  // elements for the largest single-interval chunk over all levels
@@ -89,7 +89,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     char *mu = (char *)(base + b_x + b_f);
     char *lam = mu + b_mu;
     void *whi = lam + b_mu, *wlo = lam + b_mu + b_w;
-    unsigned *wmax = (unsigned *)(lam + b_mu + 2 * b_w);
+    unsigned long long *wmax = (unsigned long long *)(lam + b_mu + 2 * b_w);
     const size_t t_bytes = (kScratchBytes - fixed) / 2 / 256 * 256;
     void *T1 = base + fixed, *T2 = base + fixed + t_bytes;
     const size_t ws_elems = t_bytes / H->es;

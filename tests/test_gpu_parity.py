@@ -150,7 +150,7 @@ def test_config2_sampled_rows(cfg2, op_id):
     assert _rel(f32, ref, rows) <= 1e-5
 
 
-# ---- tensor-core nearfield (3xTF32 split, mixed mode) ------------------------------------------
+# ---- tensor-core nearfield (scaled FP16 hi/lo split, mixed mode) -------------------------------
 @pytest.mark.parametrize("n_a,Et,kw", [(4, 16, dict(m_t=4, m_x=4, c_st=1.0)), (8, 64, dict(m_t=4, m_x=6, c_st=1.0)),
                                        (4, 512, dict(m_t=3, m_x=3, c_st=1.0))])
 def test_tensor_core_nearfield_matches_cuda_cores_and_oracle(n_a, Et, kw):
@@ -175,6 +175,31 @@ def test_tensor_core_nearfield_matches_cuda_cores_and_oracle(n_a, Et, kw):
             assert _rel(res[P.PFMM_NF_AUTO][r], res[P.PFMM_NF_CUDA_CORES][r]) <= 1e-5
     for o in ops.values():
         o.close()
+
+
+def test_tensor_core_split_scales_are_exact_powers_of_two():
+    """The FP16 split scales each rhs by 2^E from its own max |x| and unscales exactly: an input
+    multiplied by 2^k (any k within the FP32 range) gives the same FP16 parts, so the nearfield
+    of 2^k x is 2^k times that of x up to the order of the FP64 output additions; an all-zero rhs
+    gives zeros, whatever the other right-hand sides hold."""
+    V, T = cube_mesh(8)
+    Et = 64
+    op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_MIXED)
+    assert op.info()["nf_tensor_cores"] == 3
+    w = random_density(Et, T.shape[0], 1, seed=31)[0]
+    g = random_density(Et, V.shape[0], 1, seed=32)[0]
+    for apply, x in ((op.V, w), (op.K, g)):
+        # one call (the split-K chunking depends on the number of right-hand sides)
+        k = [-80, 0, 80]
+        xs = np.stack([np.ldexp(x, k[0]), x, np.ldexp(x, k[2]), np.zeros_like(x)])
+        out = apply(torch.tensor(xs, device=DEV), parts=P.PFMM_PART_NEAR).cpu().numpy()
+        P.pfmm_check(op.h)
+        base = out[1]
+        assert np.max(np.abs(base)) > 0
+        for r in (0, 2):
+            assert np.max(np.abs(np.ldexp(out[r], -k[r]) - base)) <= 1e-13 * np.max(np.abs(base))
+        assert not np.any(out[3])
+    op.close()
 
 
 def test_dense_column_layout_with_holes():
