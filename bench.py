@@ -244,12 +244,14 @@ def _batch_comparison(dev, n_problems, seed=3, tol=3e-3):
             "m_x_histogram": {str(m): mx.count(m) for m in sorted(set(mx))}}
 
 
-def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
+def _config5(dev, n_rhs=4, n_record=2, tol=1e-6, solve=True):
     """Large combined run: cube-sphere 49152 triangles x 1024 steps (50.3M space-time DOF),
     m_x 6, m_t 4, mixed precision with the stored (dense-column, tensor-core) nearfield, learned
     preconditioner retrained at this size on residuals recorded by mixed FGMRES(30) runs, then
     n_rhs heat-source data sets solved with FGMRES(30) + the network (and one without it) to
-    `tol` in the mixed operator; device memory is sampled after every stage (cap 180 GB)."""
+    `tol` in the mixed operator; device memory is sampled after every stage (cap 180 GB).
+    solve=False: the build and the matvecs only (1 and n_rhs right-hand sides, phase times of one
+    single-rhs apply)."""
     import torch
 
     from paper_2106_15911_gb300 import pfmm as P
@@ -271,15 +273,30 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
     track()
     w = torch.randn((n_rhs, Et, nt), dtype=torch.float64, device=dev)
     f = torch.empty_like(w)
-    P.pfmm_apply_V(opm.h, w, f, n_rhs, None)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    P.pfmm_apply_V(opm.h, w, f, n_rhs, None)
-    e1.record()
+    mv_ms = {}
+    for nr in (1, n_rhs):
+        P.pfmm_apply_V(opm.h, w, f, nr, None)
+        e0.record()
+        P.pfmm_apply_V(opm.h, w, f, nr, None)
+        e1.record()
+        torch.cuda.synchronize()
+        mv_ms[str(nr)] = e0.elapsed_time(e1)
+    P.pfmm_set_profiling(opm.h, True)
+    P.pfmm_apply_V(opm.h, w, f, 1, None)
     torch.cuda.synchronize()
-    mv_ms = e0.elapsed_time(e1)
+    ph, nph = P.pfmm_phase_times(opm.h)
+    P.pfmm_set_profiling(opm.h, False)
+    phases = {k: v / max(nph, 1) for k, v in ph.items()}
     track()
     del w, f
+    head = {"workload": f"cube-sphere {nt} tri x {Et} steps ({nt * Et} DOF), m_x 6, m_t 4, mixed, stored nearfield",
+            "build_s": build_s, "nearfield_GB": info["nearfield_bytes"] / 1e9, "nf_tensor_cores": info["nf_tensor_cores"],
+            "matvec_ms_nrhs": mv_ms, "matvec_dofs_per_s": n_rhs * nt * Et / (mv_ms[str(n_rhs)] * 1e-3),
+            "phases_ms_1rhs": phases}
+    if not solve:
+        opm.close()
+        return dict(head, peak_device_GB=peak[0], device_total_GB=total / 1e9, cap_GB=180)
 
     def datum(seed):
         return torch.tensor(heat_source_datum(V, 1.0, Et, shell_sources(1, seed=seed))[None], device=dev)
@@ -318,14 +335,12 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6):
     track()
     net.close()
     opm.close()
-    return {"workload": f"cube-sphere {nt} tri x {Et} steps ({nt * Et} DOF), m_x 6, m_t 4, mixed, stored nearfield",
-            "build_s": build_s, "nearfield_GB": info["nearfield_bytes"] / 1e9, "nf_tensor_cores": info["nf_tensor_cores"],
-            "matvec_ms_nrhs": {str(n_rhs): mv_ms}, "matvec_dofs_per_s": n_rhs * nt * Et / (mv_ms * 1e-3),
+    return dict(head, **{
             "record": {"data_sets": n_record, "residuals": used, "seconds": rec_s},
             "train": {"steps": 1000, "seconds": train_s, "loss_first": float(hist[:10].mean()),
                       "loss_last": float(hist[-50:].mean()), "compile_s": compile_s},
             "solve_tol": tol, "learned": solves, "plain_first_rhs": plain,
-            "peak_device_GB": peak[0], "device_total_GB": total / 1e9, "cap_GB": 180}
+            "peak_device_GB": peak[0], "device_total_GB": total / 1e9, "cap_GB": 180})
 
 
 def _profile_case(dev, case):
@@ -430,6 +445,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
     ap.add_argument("--solve-sets", type=int, default=32, help="held-out data sets of the solver comparison")
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
+    ap.add_argument("--config5-matvec", action="store_true",
+                    help="with --config5: the build and matvecs only (no recording, training or solves)")
     ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf"], default=None,
                     help="profiling only: run one small case of a kernel outside the matvec and exit")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
@@ -455,7 +472,7 @@ def main():
     dev = torch.device("cuda", local)
     if args.config5:
         if rank == 0:
-            print(json.dumps({"config5": _config5(dev)}), flush=True)
+            print(json.dumps({"config5": _config5(dev, solve=not args.config5_matvec)}), flush=True)
         return 0
     if args.profile_case:
         if rank == 0:
