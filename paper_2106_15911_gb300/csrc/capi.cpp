@@ -571,9 +571,10 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
     // ---- nearfield blocks (Eq. eval_sl_nf_block)
     {
         std::vector<PanelGPU> pg(t.panels.size());
-        std::vector<int> tiles;
+        std::vector<int> tiles, box_tiles(t.panels.size() + 1, 0);  // panel i = leaf box i
         for (size_t i = 0; i < t.panels.size(); ++i) {
             const Panel &P = t.panels[i];
+            box_tiles[i] = (int)tiles.size() / 2;
             pg[i] = PanelGPU{(int)i, P.row0, P.nrows, P.rows_pad, P.ncolV, P.colsV_pad, P.ncolK, P.colsK_pad,
                              (long long)P.offV, (long long)P.offK, P.colV_at, P.colK_at};
             for (int r0 = 0; r0 < P.nrows; r0 += kRowTile) {
@@ -582,6 +583,7 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
             }
         }
         H->ntiles = (int)tiles.size() / 2;
+        box_tiles[t.panels.size()] = H->ntiles;
         std::vector<int> sing(12 * t.sing.size(), 0);
         for (size_t i = 0; i < t.sing.size(); ++i) {
             const SingularPair &s = t.sing[i];
@@ -592,6 +594,7 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         int *d_sing = nullptr;
         H->otf = prm->nearfield == PFMM_NEARFIELD_ONTHEFLY;
         if ((rc = upload(H, &H->d_panels, pg, st)) || (rc = upload(H, &H->d_tiles, tiles, st)) ||
+            (rc = upload(H, &H->d_box_tiles, box_tiles, st)) ||
             (rc = upload(H, &H->d_colV, t.colV, st)) || (rc = upload(H, &d_sing, sing, st)))
             return rc;
         if (!H->otf) {
@@ -778,6 +781,11 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     g.kinv = H->d_kinv;
     g.ne = H->ne;
     g.eoff = H->d_eoff;
+    if ((int)t.panels.size() == g.nbox_leaf) {  // one row panel per leaf box: its 64-row tiles
+        g.tiles = H->d_tiles;
+        g.ntiles = H->ntiles;
+        g.box_tiles = H->d_box_tiles;
+    }
     EvSet *ev = nullptr;
     if (H->prof) {
         if (H->evs.empty()) {
@@ -828,7 +836,7 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     char *mu = (char *)H->d_mu, *lam = (char *)H->d_lam;
     if (far) {
         launch_s2m(H->mixed, op == 1, xin, ncolg, op == 0 ? H->d_Sx : H->d_SK, H->d_St,
-                   mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st);
+                   mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st, H->d_T1, H->ws_m2l);
     }
     mark(3);
     if (far)

@@ -58,6 +58,7 @@ struct pfmm_handle {
     std::vector<pfmm::DevLevel> dl;
     void *d_AV = nullptr, *d_AK = nullptr;
     int *d_colV = nullptr, *d_colK = nullptr, *d_kmap = nullptr, *d_tiles = nullptr;
+    int *d_box_tiles = nullptr;  // [leaf boxes + 1] first 64-row tile of each leaf box
     pfmm::PanelGPU *d_panels = nullptr;
     int ntiles = 0;
     int64_t mom_per_rhs = 0;

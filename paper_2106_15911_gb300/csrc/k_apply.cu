@@ -266,9 +266,129 @@ __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncol
     }
 }
 
-void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
-                const ApplyGeo &g, cudaStream_t st)
+// Balanced S2M in two stages (leaf boxes hold from a few to several hundred triangles):
+// stage 1, CTA per (64-row tile of a leaf box, kTSB steps, rhs): the spatial moments of the
+// tile's triangles, P[tile][t][i] = sum_{x in tile} x[t][x] Sx[x][i], same register blocking as
+// k_s2m; stage 2, thread per moment: mu[k][X][a][i] = sum_s St[s][a] sum_{tiles of X} P[tile][k ls + s][i]
+// in tile order (deterministic).
+template <typename R, bool KOP>
+__global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int ncolg, const int *__restrict__ tri,
+                                                    const R *__restrict__ Stab, R *__restrict__ part,
+                                                    const int *__restrict__ tiles, int ntiles,
+                                                    const int *__restrict__ leaf_start, int nk, int Et)
 {
+    extern __shared__ unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    constexpr int XCH = KOP ? 16 : 32, PER = KOP ? 3 : 1, KC = XCH * PER;
+    const int tile = blockIdx.x, rhs = blockIdx.z;
+    const int X = tiles[2 * tile];
+    const int x0 = leaf_start[X] + tiles[2 * tile + 1], x1 = min(x0 + 64, leaf_start[X + 1]);
+    const int t0 = blockIdx.y * kTSB, nts = min(kTSB, Et - t0);
+    R *Ws = sm;              // [kTSB][KC]
+    R *Ss = sm + kTSB * KC;  // [KC][nk]
+    const R *xr = xin + (size_t)rhs * Et * ncolg;
+    const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
+    R acc[4][kS2MCK];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < kS2MCK; ++c) acc[r][c] = R(0);
+    for (int xb = x0; xb < x1; xb += XCH) {
+        const int nx = min(XCH, x1 - xb);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kTSB * KC; e += blockDim.x) {
+            const int ts = e / KC, j = e % KC, xi = j / PER, v = j % PER;
+            R val = R(0);
+            if (ts < nts && xi < nx) {
+                const int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
+                val = xr[(size_t)(t0 + ts) * ncolg + col];
+            }
+            Ws[e] = val;
+        }
+        for (int e = threadIdx.x; e < KC * nk; e += blockDim.x) {
+            const int j = e / nk;
+            Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + (e % nk)] : R(0);
+        }
+        __syncthreads();
+        for (int j = 0; j < KC; ++j) {
+            R w[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) w[r] = Ws[(tg * 4 + r) * KC + j];
+#pragma unroll
+            for (int c = 0; c < kS2MCK; ++c) {
+                const int i = kg + 32 * c;
+                if (c < ck && i < nk) {
+                    const R sv = Ss[j * nk + i];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][c] += w[r] * sv;
+                }
+            }
+        }
+    }
+    R *pt = part + (((size_t)rhs * ntiles + tile) * Et + t0) * nk;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int ts = tg * 4 + r;
+        if (ts >= nts) continue;
+#pragma unroll
+        for (int c = 0; c < kS2MCK; ++c) {
+            const int i = kg + 32 * c;
+            if (c < ck && i < nk) pt[(size_t)ts * nk + i] = acc[r][c];
+        }
+    }
+}
+
+template <typename R>
+__global__ void k_s2m_time(const R *__restrict__ part, const R *__restrict__ St, R *__restrict__ mu,
+                           const int *__restrict__ box_tiles, int ntiles, int nk, int na, int ls, int Et, int nint,
+                           int nbox, size_t total)
+{
+    const size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= total) return;
+    const int i = (int)(o % nk);
+    size_t r_ = o / nk;
+    const int a = (int)(r_ % na);
+    r_ /= na;
+    const int X = (int)(r_ % nbox);
+    r_ /= nbox;
+    const int k = (int)(r_ % nint), rhs = (int)(r_ / nint);
+    R v = R(0);
+    for (int tl = box_tiles[X]; tl < box_tiles[X + 1]; ++tl) {
+        const R *pt = part + (((size_t)rhs * ntiles + tl) * Et + (size_t)k * ls) * nk + i;
+        for (int s = 0; s < ls; ++s) v += St[s * na + a] * pt[(size_t)s * nk];
+    }
+    mu[o] = v;
+}
+
+void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
+                const ApplyGeo &g, cudaStream_t st, void *ws, size_t ws_elems)
+{
+    if (ws && g.tiles && (size_t)nrhs * g.ntiles * g.Et * g.nk <= ws_elems) {
+        const int KC = kop ? 48 : 32;
+        const size_t smem = ((size_t)kTSB * KC + (size_t)KC * g.nk) * (mixed ? 4 : 8);
+        const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs);
+        const int nint = g.Et / g.ls;
+        const size_t total = (size_t)nrhs * nint * g.nbox_leaf * g.na * g.nk;
+        const unsigned gb = (unsigned)((total + 255) / 256);
+#define S2M_TILE_LAUNCH(R, K)                                                                                          \
+    do {                                                                                                               \
+        cudaFuncSetAttribute(k_s2m_tile<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
+        k_s2m_tile<R, K><<<grd, 256, smem, st>>>((const R *)x, ncolg, g.tri, (const R *)Stab, (R *)ws, g.tiles,         \
+                                                 g.ntiles, g.leaf_start, g.nk, g.Et);                                  \
+        k_s2m_time<R><<<gb, 256, 0, st>>>((const R *)ws, (const R *)St, (R *)mu_leaf, g.box_tiles, g.ntiles, g.nk,     \
+                                          g.na, g.ls, g.Et, nint, g.nbox_leaf, total);                                 \
+    } while (0)
+        if (mixed) {
+            if (kop) S2M_TILE_LAUNCH(float, true);
+            else S2M_TILE_LAUNCH(float, false);
+        } else {
+            if (kop) S2M_TILE_LAUNCH(double, true);
+            else S2M_TILE_LAUNCH(double, false);
+        }
+#undef S2M_TILE_LAUNCH
+        return;
+    }
+
     int nint = g.Et / g.ls;
     const int ipb = kTSB / g.ls;
     const int KC = kop ? 48 : 32;
@@ -1002,19 +1122,21 @@ void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
 template <typename R>
 __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R *__restrict__ Sx, const R *__restrict__ St,
                                                double *__restrict__ f, const int *__restrict__ leaf_start, int nk, int na,
-                                               int ls, int Et, int nint, int nbox, int nt)
+                                               int ls, int Et, int nint, int nbox, int nt, const int *__restrict__ tiles)
 {
-    // a CTA covers one leaf box, kTSB steps and one rhs: Q[ts][nu] = sum_b St[s][b] lam[k][X][b][nu]
-    // in shared memory, then thread (tg = warp, xl = lane) forms steps 4 tg .. 4 tg + 3 for the
-    // triangles xl and xl + 32 of each 64-triangle chunk
+    // a CTA covers one 64-row tile of a leaf box (tiles: (box, first row); without a tile list, the
+    // whole box), kTSB steps and one rhs: Q[ts][nu] = sum_b St[s][b] lam[k][X][b][nu] in shared
+    // memory, then thread (tg = warp, xl = lane) forms steps 4 tg .. 4 tg + 3 for the triangles xl
+    // and xl + 32 of each 64-triangle chunk
     extern __shared__ unsigned char smem_raw[];
     R *Qs = reinterpret_cast<R *>(smem_raw);  // [kTSB][nk]
     constexpr int XCH = 64, SP = XCH + 1;      // Sx chunk stored transposed, rows padded
     R *Ss = Qs + kTSB * nk;                    // [nk][SP]
-    const int X = blockIdx.x, rhs = blockIdx.z;
+    const int X = tiles ? tiles[2 * blockIdx.x] : blockIdx.x, rhs = blockIdx.z;
     const int ipb = kTSB / ls;
     const int k0 = blockIdx.y * ipb, kend = min(nint, k0 + ipb), nts = (kend - k0) * ls, t0 = k0 * ls;
-    const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
+    const int x0 = leaf_start[X] + (tiles ? tiles[2 * blockIdx.x + 1] : 0);
+    const int x1 = tiles ? min(x0 + 64, leaf_start[X + 1]) : leaf_start[X + 1];
     for (int o = threadIdx.x; o < kTSB * nk; o += blockDim.x) {
         const int ts = o / nk, i = o % nk;
         R v = R(0);
@@ -1065,15 +1187,16 @@ void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St
     const int ipb = kTSB / g.ls;
     size_t es = mixed ? 4 : 8;
     size_t smem = ((size_t)kTSB * g.nk + (size_t)g.nk * 65) * es;
-    dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
+    // one CTA per 64-row tile (balanced over leaf boxes of different sizes)
+    dim3 grd(g.tiles ? g.ntiles : g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
     if (mixed) {
         cudaFuncSetAttribute(k_l2t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_l2t<float><<<grd, 256, smem, st>>>((const float *)lam_leaf, (const float *)Sx, (const float *)St, f_int,
-                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt);
+                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles);
     } else {
         cudaFuncSetAttribute(k_l2t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_l2t<double><<<grd, 256, smem, st>>>((const double *)lam_leaf, (const double *)Sx, (const double *)St, f_int,
-                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt);
+                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles);
     }
 }
 

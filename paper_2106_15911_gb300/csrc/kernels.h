@@ -78,6 +78,9 @@ struct ApplyGeo {
     const int *kinv;       // [(m+1)^3] -> graded index
     int ne;                // C(m_x+4, 4): budget-indexed entries of the separable M2L intermediates
     const int *eoff;       // [nk] offset of the budget range of each triple
+    const int *tiles;      // [ntiles][2] (leaf box, first row) of the 64-row tiles of every leaf box
+    int ntiles;
+    const int *box_tiles;  // [nbox_p + 1] first tile of each leaf box (tiles are box-major)
 };
 
 // R: arithmetic/storage type of the FMM passes (double or float)
@@ -102,8 +105,10 @@ void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, con
                      const PanelGPU *panels, const void *x, int ncolg, int nrhs, const ApplyGeo &g, double *f_int,
                      cudaStream_t st, int ndmax = 1 << 30,  // ndmax: only offsets d < ndmax
                      const NfHalfSplit *hs = nullptr);      // FP32 only: blocks from the FP16 parts, A unused
+// ws: scratch of ws_elems elements of the arithmetic type for the per-tile partial moments (the
+// M2L workspace, idle at this point); too small: one CTA per whole leaf box instead
 void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab /*Sx or SK*/, const void *St,
-                void *mu_leaf, int nrhs, const ApplyGeo &g, cudaStream_t st);
+                void *mu_leaf, int nrhs, const ApplyGeo &g, cudaStream_t st, void *ws = nullptr, size_t ws_elems = 0);
 void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
 int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,

@@ -112,6 +112,11 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     g.kinv = H->d_kinv;
     g.ne = H->ne;
     g.eoff = H->d_eoff;
+    if ((int)H->tree.panels.size() == g.nbox_leaf) {  // one row panel per leaf box: its 64-row tiles
+        g.tiles = H->d_tiles;
+        g.ntiles = H->ntiles;
+        g.box_tiles = H->d_box_tiles;
+    }
     // every buffer below is fully written before it is read, except the locals of the first two
     // intervals of each level, which launch_m2l clears; nothing depends on the previous call
     launch_permute_in(w, xint, H->mixed, nrhs, g, st);
@@ -127,7 +132,8 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     }
     const int p = H->p;
     if (p >= 2) {
-        launch_s2m(H->mixed, false, xint, H->nt, H->d_Sx, H->d_St, mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st);
+        launch_s2m(H->mixed, false, xint, H->nt, H->d_Sx, H->d_St, mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st, T1,
+                   ws_elems);
         for (int l = p - 1; l >= 2; --l) launch_m2m(H->mixed, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
         for (int l = 2; l <= p; ++l)
             if (launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, T1, T2, ws_elems, st))
