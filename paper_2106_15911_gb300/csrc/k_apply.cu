@@ -189,6 +189,25 @@ void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, con
 // (double layer: sum over the triangle's three nodes with SK).  CTA per (leaf box, interval
 // chunk, rhs).
 constexpr int kTSB = 32;   // steps per S2M / L2T block
+constexpr int kTSP = kTSB + 4;  // padded row of kTSB steps (16-byte aligned rows)
+
+// four consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void lds4(const float *p, float (&w)[4])
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    w[0] = v.x;
+    w[1] = v.y;
+    w[2] = v.z;
+    w[3] = v.w;
+}
+__device__ __forceinline__ void lds4(const double *p, double (&w)[4])
+{
+    const double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    w[0] = a.x;
+    w[1] = a.y;
+    w[2] = b.x;
+    w[3] = b.y;
+}
 constexpr int kS2MCK = 6;  // moment groups of 32 per thread (n_kappa <= 192, m_x <= 8)
 
 template <typename R, bool KOP>
@@ -277,15 +296,15 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
                                                     const int *__restrict__ tiles, int ntiles,
                                                     const int *__restrict__ leaf_start, int nk, int Et)
 {
-    extern __shared__ unsigned char smem_raw[];
-    R *sm = reinterpret_cast<R *>(smem_raw);
+    extern __shared__ __align__(16) unsigned char s2m_raw[];
+    R *sm = reinterpret_cast<R *>(s2m_raw);
     constexpr int XCH = KOP ? 16 : 32, PER = KOP ? 3 : 1, KC = XCH * PER;
     const int tile = blockIdx.x, rhs = blockIdx.z;
     const int X = tiles[2 * tile];
     const int x0 = leaf_start[X] + tiles[2 * tile + 1], x1 = min(x0 + 64, leaf_start[X + 1]);
     const int t0 = blockIdx.y * kTSB, nts = min(kTSB, Et - t0);
-    R *Ws = sm;              // [kTSB][KC]
-    R *Ss = sm + kTSB * KC;  // [KC][nk]
+    R *Ws = sm;              // [KC][kTSP]: a thread's four steps are one vector load
+    R *Ss = sm + KC * kTSP;  // [KC][nk]
     const R *xr = xin + (size_t)rhs * Et * ncolg;
     const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
     R acc[4][kS2MCK];
@@ -303,7 +322,7 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
                 const int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
                 val = xr[(size_t)(t0 + ts) * ncolg + col];
             }
-            Ws[e] = val;
+            Ws[j * kTSP + ts] = val;
         }
         for (int e = threadIdx.x; e < KC * nk; e += blockDim.x) {
             const int j = e / nk;
@@ -312,8 +331,7 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
         __syncthreads();
         for (int j = 0; j < KC; ++j) {
             R w[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) w[r] = Ws[(tg * 4 + r) * KC + j];
+            lds4(Ws + j * kTSP + tg * 4, w);
 #pragma unroll
             for (int c = 0; c < kS2MCK; ++c) {
                 const int i = kg + 32 * c;
@@ -365,7 +383,7 @@ void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab
 {
     if (ws && g.tiles && (size_t)nrhs * g.ntiles * g.Et * g.nk <= ws_elems) {
         const int KC = kop ? 48 : 32;
-        const size_t smem = ((size_t)kTSB * KC + (size_t)KC * g.nk) * (mixed ? 4 : 8);
+        const size_t smem = ((size_t)KC * kTSP + (size_t)KC * g.nk) * (mixed ? 4 : 8);
         const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs);
         const int nint = g.Et / g.ls;
         const size_t total = (size_t)nrhs * nint * g.nbox_leaf * g.na * g.nk;
@@ -1128,10 +1146,10 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
     // whole box), kTSB steps and one rhs: Q[ts][nu] = sum_b St[s][b] lam[k][X][b][nu] in shared
     // memory, then thread (tg = warp, xl = lane) forms steps 4 tg .. 4 tg + 3 for the triangles xl
     // and xl + 32 of each 64-triangle chunk
-    extern __shared__ unsigned char smem_raw[];
-    R *Qs = reinterpret_cast<R *>(smem_raw);  // [kTSB][nk]
+    extern __shared__ __align__(16) unsigned char l2t_raw[];
+    R *Qs = reinterpret_cast<R *>(l2t_raw);  // [nk][kTSP]: a thread's four steps are one vector load
     constexpr int XCH = 64, SP = XCH + 1;      // Sx chunk stored transposed, rows padded
-    R *Ss = Qs + kTSB * nk;                    // [nk][SP]
+    R *Ss = Qs + kTSP * nk;                    // [nk][SP]
     const int X = tiles ? tiles[2 * blockIdx.x] : blockIdx.x, rhs = blockIdx.z;
     const int ipb = kTSB / ls;
     const int k0 = blockIdx.y * ipb, kend = min(nint, k0 + ipb), nts = (kend - k0) * ls, t0 = k0 * ls;
@@ -1145,7 +1163,7 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
             const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
             for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
         }
-        Qs[o] = v;
+        Qs[i * kTSP + ts] = v;
     }
     const int xl = threadIdx.x & 31, tg = threadIdx.x >> 5;
     for (int xb = x0; xb < x1; xb += XCH) {
@@ -1161,11 +1179,12 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
         for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = R(0);
         for (int i = 0; i < nk; ++i) {
             const R s0 = Ss[i * SP + xl], s1 = Ss[i * SP + xl + 32];
+            R q[4];
+            lds4(Qs + i * kTSP + tg * 4, q);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const R q = Qs[(tg * 4 + r) * nk + i];
-                acc[r][0] += q * s0;
-                acc[r][1] += q * s1;
+                acc[r][0] += q[r] * s0;
+                acc[r][1] += q[r] * s1;
             }
         }
 #pragma unroll
@@ -1186,7 +1205,7 @@ void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St
     int nint = g.Et / g.ls;
     const int ipb = kTSB / g.ls;
     size_t es = mixed ? 4 : 8;
-    size_t smem = ((size_t)kTSB * g.nk + (size_t)g.nk * 65) * es;
+    size_t smem = ((size_t)kTSP * g.nk + (size_t)g.nk * 65) * es;
     // one CTA per 64-row tile (balanced over leaf boxes of different sizes)
     dim3 grd(g.tiles ? g.ntiles : g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
     if (mixed) {
