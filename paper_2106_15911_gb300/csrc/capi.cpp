@@ -850,7 +850,9 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     if (far)
         for (int l = 3; l <= p; ++l) launch_l2l(H->mixed, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
     mark(6);
-    if (far) launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, H->d_fint, nrhs, g, 0, st);
+    if (far)
+        launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, H->d_fint, nrhs, g, 0, st, H->d_T1,
+                   H->ws_m2l);
     mark(7);
     launch_permute_out(H->d_fint, f, nrhs, g, st);
     mark(8);

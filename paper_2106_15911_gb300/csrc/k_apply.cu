@@ -356,26 +356,56 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
     }
 }
 
+// stage 2: thread per (rhs, interval k) [grid x] and (box X, moment i) [grid y, x threads]; each
+// partial is read once and weighted for every time node a (registers)
 template <typename R>
 __global__ void k_s2m_time(const R *__restrict__ part, const R *__restrict__ St, R *__restrict__ mu,
                            const int *__restrict__ box_tiles, int ntiles, int nk, int na, int ls, int Et, int nint,
-                           int nbox, size_t total)
+                           int nbox)
 {
-    const size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= total) return;
-    const int i = (int)(o % nk);
-    size_t r_ = o / nk;
-    const int a = (int)(r_ % na);
-    r_ /= na;
-    const int X = (int)(r_ % nbox);
-    r_ /= nbox;
-    const int k = (int)(r_ % nint), rhs = (int)(r_ / nint);
-    R v = R(0);
+    const int xi = blockIdx.y * blockDim.x + threadIdx.x;
+    if (xi >= nbox * nk) return;
+    const int X = xi / nk, i = xi - X * nk;
+    const int k = blockIdx.x % nint, rhs = blockIdx.x / nint;
+    R v[kMaxNa];
+#pragma unroll
+    for (int a = 0; a < kMaxNa; ++a) v[a] = R(0);
     for (int tl = box_tiles[X]; tl < box_tiles[X + 1]; ++tl) {
         const R *pt = part + (((size_t)rhs * ntiles + tl) * Et + (size_t)k * ls) * nk + i;
-        for (int s = 0; s < ls; ++s) v += St[s * na + a] * pt[(size_t)s * nk];
+        for (int s = 0; s < ls; ++s) {
+            const R pv = pt[(size_t)s * nk];
+#pragma unroll
+            for (int a = 0; a < kMaxNa; ++a)
+                if (a < na) v[a] += St[s * na + a] * pv;
+        }
     }
-    mu[o] = v;
+    R *mo = mu + ((((size_t)rhs * nint + k) * nbox + X) * na) * nk + i;
+#pragma unroll
+    for (int a = 0; a < kMaxNa; ++a)
+        if (a < na) mo[(size_t)a * nk] = v[a];
+}
+
+// L2T's temporal factor for every (step, leaf box): Q[rhs][t][X][nu] = sum_b St[s][b] lam[k][X][b][nu],
+// t = k ls + s; thread per (rhs, k) [grid x] and (X, nu)
+template <typename R>
+__global__ void k_l2t_time(const R *__restrict__ lam, const R *__restrict__ St, R *__restrict__ Q, int nk, int na,
+                           int ls, int Et, int nint, int nbox)
+{
+    const int xi = blockIdx.y * blockDim.x + threadIdx.x;
+    if (xi >= nbox * nk) return;
+    const int X = xi / nk, i = xi - X * nk;
+    const int k = blockIdx.x % nint, rhs = blockIdx.x / nint;
+    R lv[kMaxNa];
+    const R *lp = lam + ((((size_t)rhs * nint + k) * nbox + X) * na) * nk + i;
+#pragma unroll
+    for (int b = 0; b < kMaxNa; ++b) lv[b] = b < na ? lp[(size_t)b * nk] : R(0);
+    for (int s = 0; s < ls; ++s) {
+        R v = R(0);
+#pragma unroll
+        for (int b = 0; b < kMaxNa; ++b)
+            if (b < na) v += St[s * na + b] * lv[b];
+        Q[(((size_t)rhs * Et + (size_t)k * ls + s) * nbox + X) * nk + i] = v;
+    }
 }
 
 void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
@@ -386,15 +416,14 @@ void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab
         const size_t smem = ((size_t)KC * kTSP + (size_t)KC * g.nk) * (mixed ? 4 : 8);
         const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs);
         const int nint = g.Et / g.ls;
-        const size_t total = (size_t)nrhs * nint * g.nbox_leaf * g.na * g.nk;
-        const unsigned gb = (unsigned)((total + 255) / 256);
+        const dim3 g2((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
 #define S2M_TILE_LAUNCH(R, K)                                                                                          \
     do {                                                                                                               \
         cudaFuncSetAttribute(k_s2m_tile<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
         k_s2m_tile<R, K><<<grd, 256, smem, st>>>((const R *)x, ncolg, g.tri, (const R *)Stab, (R *)ws, g.tiles,         \
                                                  g.ntiles, g.leaf_start, g.nk, g.Et);                                  \
-        k_s2m_time<R><<<gb, 256, 0, st>>>((const R *)ws, (const R *)St, (R *)mu_leaf, g.box_tiles, g.ntiles, g.nk,     \
-                                          g.na, g.ls, g.Et, nint, g.nbox_leaf, total);                                 \
+        k_s2m_time<R><<<g2, 256, 0, st>>>((const R *)ws, (const R *)St, (R *)mu_leaf, g.box_tiles, g.ntiles, g.nk,     \
+                                          g.na, g.ls, g.Et, nint, g.nbox_leaf);                                        \
     } while (0)
         if (mixed) {
             if (kop) S2M_TILE_LAUNCH(float, true);
@@ -1140,7 +1169,8 @@ void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
 template <typename R>
 __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R *__restrict__ Sx, const R *__restrict__ St,
                                                double *__restrict__ f, const int *__restrict__ leaf_start, int nk, int na,
-                                               int ls, int Et, int nint, int nbox, int nt, const int *__restrict__ tiles)
+                                               int ls, int Et, int nint, int nbox, int nt, const int *__restrict__ tiles,
+                                               const R *__restrict__ Qg)
 {
     // a CTA covers one 64-row tile of a leaf box (tiles: (box, first row); without a tile list, the
     // whole box), kTSB steps and one rhs: Q[ts][nu] = sum_b St[s][b] lam[k][X][b][nu] in shared
@@ -1159,9 +1189,13 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
         const int ts = o / nk, i = o % nk;
         R v = R(0);
         if (ts < nts) {
-            const int kk = ts / ls, s = ts % ls;
-            const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
-            for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
+            if (Qg) {  // precomputed by k_l2t_time
+                v = Qg[(((size_t)rhs * Et + t0 + ts) * nbox + X) * nk + i];
+            } else {
+                const int kk = ts / ls, s = ts % ls;
+                const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
+                for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
+            }
         }
         Qs[i * kTSP + ts] = v;
     }
@@ -1199,23 +1233,34 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
 }
 
 void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
-                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st, void *ws, size_t ws_elems)
 {
     (void)mu_stride;
     int nint = g.Et / g.ls;
+    // temporal factor once per (step, box) in the workspace when it fits (else per CTA)
+    const bool qg = ws && (size_t)nrhs * g.Et * g.nbox_leaf * g.nk <= ws_elems;
+    const dim3 gq((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
     const int ipb = kTSB / g.ls;
     size_t es = mixed ? 4 : 8;
     size_t smem = ((size_t)kTSP * g.nk + (size_t)g.nk * 65) * es;
     // one CTA per 64-row tile (balanced over leaf boxes of different sizes)
     dim3 grd(g.tiles ? g.ntiles : g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
     if (mixed) {
+        if (qg)
+            k_l2t_time<float><<<gq, 256, 0, st>>>((const float *)lam_leaf, (const float *)St, (float *)ws, g.nk, g.na,
+                                                  g.ls, g.Et, nint, g.nbox_leaf);
         cudaFuncSetAttribute(k_l2t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_l2t<float><<<grd, 256, smem, st>>>((const float *)lam_leaf, (const float *)Sx, (const float *)St, f_int,
-                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles);
+                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles,
+                                             qg ? (const float *)ws : nullptr);
     } else {
+        if (qg)
+            k_l2t_time<double><<<gq, 256, 0, st>>>((const double *)lam_leaf, (const double *)St, (double *)ws, g.nk,
+                                                   g.na, g.ls, g.Et, nint, g.nbox_leaf);
         cudaFuncSetAttribute(k_l2t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_l2t<double><<<grd, 256, smem, st>>>((const double *)lam_leaf, (const double *)Sx, (const double *)St, f_int,
-                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles);
+                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles,
+                                              qg ? (const double *)ws : nullptr);
     }
 }
 

@@ -115,8 +115,10 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
                void *T1, void *T2, size_t ws_elems, cudaStream_t st);
 void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
+// ws: scratch (ws_elems elements of the arithmetic type) for the temporal factor of every (step,
+// leaf box), the M2L workspace idle at this point; too small: computed per CTA
 void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
-                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
+                const ApplyGeo &g, int64_t mu_stride, cudaStream_t st, void *ws = nullptr, size_t ws_elems = 0);
 void launch_apply_M(const double *g_in, double *f, const int *tri_user, const double *area, int nrhs, int nt, int nv,
                     int Et, double h, cudaStream_t st);
 

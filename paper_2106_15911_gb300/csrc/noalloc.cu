@@ -139,7 +139,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
             if (launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, T1, T2, ws_elems, st))
                 return set_error(PFMM_ERR_OOM, "static scratch too small for one M2L interval");
         for (int l = 3; l <= p; ++l) launch_l2l(H->mixed, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
-        launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, fint, nrhs, g, 0, st);
+        launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, fint, nrhs, g, 0, st, T1, ws_elems);
     }
     launch_permute_out(fint, f, nrhs, g, st);
     cudaError_t e = cudaGetLastError();
