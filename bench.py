@@ -382,14 +382,17 @@ def _profile_case(dev, case):
 
 def _launches_per_apply(info, nrhs, na=M_T + 1, split_ctas=8 * 152):
     """Kernels one V_h apply launches: permute in and out, the FP16 input split (max |x| and
-    split; tensor-core nearfield), nearfield, S2M, M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per
-    split level (levels with fewer than eight (interval, node) CTAs per SM), L2L (levels 3..p),
-    L2T."""
+    split; tensor-core nearfield), nearfield, S2M (per-tile moments and their temporal sum),
+    M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per split level (levels with fewer
+    than eight (interval, node) CTAs per SM), L2L (levels 3..p), L2T (temporal factor and
+    per-tile evaluation).  The two-stage S2M / L2T forms are the ones taken when the M2L
+    workspace holds their intermediates, as it does for the bench workload."""
     p = info["p"]
+    tc = 2 if info["nf_tensor_cores"] & 1 else 0
     if p < 2:
-        return 3 + (2 if info["nf_tensor_cores"] & 1 else 0)
+        return 3 + tc
     split = sum(1 for l in range(2, p + 1) if (2 ** l) * na * nrhs < split_ctas)
-    return 2 + (2 if info["nf_tensor_cores"] & 1 else 0) + 1 + 1 + (p - 2) + (p - 1) + split + (p - 2) + 1
+    return 2 + tc + 1 + 2 + (p - 2) + (p - 1) + split + (p - 2) + 2
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
