@@ -8,7 +8,10 @@
 // 128 rows x 256 columns: columns 0..127 are the intervals i0..i0+127 at phase s = 0, columns
 // 128..255 the same intervals at s = 1.  W is seen by TMA as a 4D tensor [rhs][interval][phase]
 // [col], so the time shift by d is a coordinate offset, and the causality mask (t - d < 0) is the
-// out-of-bounds zero fill.  FP32 accuracy comes from a two-part FP16 split with power-of-two
+// out-of-bounds zero fill.  A comes from the FP16 parts stored as contiguous 64-row x 64-column
+// blocks (nf_tiled_index): each 64-row half of a tile's K block is one 8 KB TMA copy of a 3D view
+// [block][64][64], and the half past a panel's last row is not copied (its MMA rows are never
+// written out).  FP32 accuracy comes from a two-part FP16 split with power-of-two
 // scales (FP16 keeps 11 significant bits, as TF32 does, at twice the rate and half the bytes):
 //   A W ~ (A_hi W_hi + A_hi W_lo + A_lo W_hi) / (s_A s_W),
 //   A_hi = rn_f16(s_A A), A_lo = rn_f16(s_A A - A_hi)     (same for W with s_W per rhs),
