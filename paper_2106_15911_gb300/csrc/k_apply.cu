@@ -1005,6 +1005,159 @@ __global__ void k_m2l_sum_terms(const R *__restrict__ part, int na, size_t n, si
     lam[i] = s;
 }
 
+// M2L for grids of 5^3 .. 8^3 cells (FP32), one CTA per (target interval k, time node b, target
+// x-slab X1, rhs) over all source terms (J, a) of the interaction list.  The three directional
+// passes of k_m2l_fused restricted to one X1: pass 1 streams the source x-slabs Y1 within the
+// interaction radius through shared memory (the moments of one slab, cells (Y2, Y3)) and adds
+// their budget chains into T1(X1, Y2, Y3); pass 2 (registers: X2) and pass 3 (registers: X3)
+// need only this slab of T1 and T2.  The locals of the slab's cells (X2, X3) accumulate in
+// shared memory over the terms, so each is written once (no partials).  Same arithmetic as the
+// three-pass kernels; cells beyond G are empty.
+constexpr int SG = 8;  // padded grid extent per direction
+constexpr int kM2LSlabThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kM2LSlabThreads, 1) k_m2l_slab(M2LArgs A, const R *__restrict__ mu,
+                                                                  const R *__restrict__ E1, const R *__restrict__ pref,
+                                                                  R *__restrict__ lam)
+{
+    extern __shared__ __align__(16) unsigned char slab_raw[];
+    constexpr int SC = SG * SG, SCS = SC + 1, NO = 2 * SG - 1;
+    const int G = A.G, nk = A.nk, ne = A.ne, mx = A.mx, m1 = mx + 1, na = A.na, esz = m1 * m1;
+    R *Ms = reinterpret_cast<R *>(slab_raw);  // [nk][SCS]  moments of one source slab Y1, cells (Y2, Y3)
+    R *T1s = Ms + nk * SCS;                    // [ne][SCS]  cells (Y2, Y3) at X1
+    R *T2s = T1s + ne * SCS;                   // [ne][SCS]  cells (X2, Y3) at X1
+    R *Ls = T2s + ne * SCS;                    // [nk][SCS]  locals, cells (X2, X3) at X1
+    R *Es = Ls + nk * SCS;                     // [NO][m1][m1] offsets -(SG-1)..SG-1, zero outside the radius
+    int *kid = reinterpret_cast<int *>(Es + NO * esz);
+    int *kin = kid + nk;
+    int *eof = kin + m1 * m1 * m1;
+    int *cbx = eof + nk;  // [SG^3] padded cell -> box or -1
+    const int X1 = blockIdx.x % G, kb = blockIdx.x / G;
+    const int k = kb / na, b = kb % na, rhs = blockIdx.y;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+        kid[i] = A.kidx[3 * i] | (A.kidx[3 * i + 1] << 8) | (A.kidx[3 * i + 2] << 16);
+        eof[i] = A.eoff[i];
+    }
+    for (int i = threadIdx.x; i < m1 * m1 * m1; i += blockDim.x) kin[i] = A.kinv[i];
+    for (int i = threadIdx.x; i < SG * SC; i += blockDim.x) {
+        const int x = i / SC, y = (i / SG) % SG, z = i % SG;
+        cbx[i] = (x < G && y < G && z < G) ? A.cellbox[(x * G + y) * G + z] : -1;
+    }
+    for (int i = threadIdx.x; i < nk * SCS; i += blockDim.x) Ls[i] = R(0);
+    int js[2], nj = 0;
+    if (k >= 2) {
+        if (k % 2 == 0) { js[0] = k - 2; nj = 1; }
+        else { js[0] = k - 3; js[1] = k - 2; nj = 2; }
+    }
+    const int no = 2 * G - 1;
+    const int y_lo = max(0, X1 - A.ntr), y_hi = min(G - 1, X1 + A.ntr);
+    for (int jj = 0; jj < nj; ++jj) {
+        const int J = js[jj], D = k - J;
+        const R *mJ = mu + ((size_t)rhs * A.nint + J) * A.nbox * na * nk;
+        for (int a = 0; a < na; ++a) {
+            __syncthreads();  // the previous term's passes are done with Es, T1s, T2s
+            const R *Eab = E1 + (size_t)(((D - 2) * na + a) * na + b) * no * esz;
+            for (int i = threadIdx.x; i < NO * esz; i += blockDim.x) {
+                const int o = i / esz - (SG - 1);  // offset X - Y
+                Es[i] = (o >= -(G - 1) && o <= G - 1 && (o < 0 ? -o : o) <= A.ntr) ? Eab[(o + G - 1) * esz + i % esz]
+                                                                                      : R(0);
+            }
+            for (int i = threadIdx.x; i < ne * SCS; i += blockDim.x) T1s[i] = R(0);
+            const R coef = pref[((D - 2) * na + a) * na + b];
+            // pass 1 (direction x): unit = (triple (nu1, k2, k3), cell (Y2, Y3)); per source slab Y1
+            // the budget chain over B is added into T1 (the cumulative budget)
+            for (int Y1 = y_lo; Y1 <= y_hi; ++Y1) {
+                __syncthreads();  // Ms free, Es and T1s ready
+                for (int i = threadIdx.x; i < nk * SC; i += blockDim.x) {  // consecutive threads: consecutive kappa
+                    const int c = i / nk, ik = i % nk, box = cbx[Y1 * SC + c];
+                    Ms[ik * SCS + c] = box >= 0 ? mJ[((size_t)box * na + a) * nk + ik] : R(0);
+                }
+                __syncthreads();
+                const R *Eo = Es + (X1 - Y1 + SG - 1) * esz;
+                for (int u = threadIdx.x; u < nk * SC; u += blockDim.x) {
+                    const int c = u % SC, t = u / SC, tk = kid[t];
+                    const int nu1 = tk & 255, k2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + k2 + k3;
+                    R acc = R(0);
+                    for (int B = s0; B <= mx; ++B) {
+                        const int k1 = B - s0;
+                        acc += Eo[k1 * m1 + nu1] * Ms[kin[(k1 * m1 + k2) * m1 + k3] * SCS + c];
+                        T1s[(eof[t] + k1) * SCS + c] += acc;
+                    }
+                }
+            }
+            __syncthreads();
+            // pass 2 (direction y): unit = (triple (nu1, nu2, k3), Y3); registers: cells X2
+            for (int u = threadIdx.x; u < nk * SG; u += blockDim.x) {
+                const int Y3 = u % SG, t = u / SG, tk = kid[t];
+                const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + nu2 + k3;
+                for (int Bp = s0; Bp <= mx; ++Bp) {
+                    R acc[SG];
+#pragma unroll
+                    for (int x = 0; x < SG; ++x) acc[x] = R(0);
+                    for (int k2 = 0; k2 <= Bp - s0; ++k2) {
+                        const int row = eof[kin[(nu1 * m1 + k2) * m1 + k3]] + (Bp - nu2 - nu1 - k2 - k3);
+                        const R *trow = T1s + row * SCS + Y3;
+                        R e[NO];
+#pragma unroll
+                        for (int o = 0; o < NO; ++o) e[o] = Es[o * esz + k2 * m1 + nu2];
+#pragma unroll
+                        for (int Y2 = 0; Y2 < SG; ++Y2) {
+                            const R tv = trow[Y2 * SG];
+#pragma unroll
+                            for (int X2 = 0; X2 < SG; ++X2) acc[X2] += e[X2 - Y2 + SG - 1] * tv;
+                        }
+                    }
+                    R *out = T2s + (eof[t] + Bp - s0) * SCS + Y3;
+#pragma unroll
+                    for (int X2 = 0; X2 < SG; ++X2) out[X2 * SG] = acc[X2];
+                }
+            }
+            __syncthreads();
+            // pass 3 (direction z): item = (nu, X2); registers: cells X3; locals += coef * sum
+            for (int it = threadIdx.x; it < nk * SG; it += blockDim.x) {
+                const int X2 = it % SG, iv = it / SG, tk = kid[iv];
+                const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, nu3 = tk >> 16, smax = mx - nu1 - nu2 - nu3;
+                R acc[SG];
+#pragma unroll
+                for (int x = 0; x < SG; ++x) acc[x] = R(0);
+                for (int k3 = 0; k3 <= smax; ++k3) {
+                    const int row = eof[kin[(nu1 * m1 + nu2) * m1 + k3]] + (mx - nu3 - nu1 - nu2 - k3);
+                    const R *trow = T2s + row * SCS + X2 * SG;
+                    R e[NO];
+#pragma unroll
+                    for (int o = 0; o < NO; ++o) e[o] = Es[o * esz + k3 * m1 + nu3];
+#pragma unroll
+                    for (int Y3 = 0; Y3 < SG; ++Y3) {
+                        const R tv = trow[Y3];
+#pragma unroll
+                        for (int X3 = 0; X3 < SG; ++X3) acc[X3] += e[X3 - Y3 + SG - 1] * tv;
+                    }
+                }
+                R *lrow = Ls + iv * SCS + X2 * SG;
+#pragma unroll
+                for (int X3 = 0; X3 < SG; ++X3) lrow[X3] += coef * acc[X3];
+            }
+        }
+    }
+    __syncthreads();
+    // the locals of the non-empty target boxes of this slab (intervals 0 and 1: zeros)
+    R *lk = lam + ((size_t)rhs * A.nint + k) * A.nbox * na * nk;
+    for (int i = threadIdx.x; i < nk * SC; i += blockDim.x) {
+        const int c = i / nk, iv = i % nk, X2 = c / SG, X3 = c % SG;
+        if (X2 >= G || X3 >= G) continue;
+        const int box = cbx[X1 * SC + c];
+        if (box >= 0) lk[((size_t)box * na + b) * nk + iv] = Ls[iv * SCS + c];
+    }
+}
+
+size_t m2l_slab_smem(int nk, int ne, int mx, size_t es)
+{
+    const int SCS = SG * SG + 1, m1 = mx + 1;
+    return es * ((size_t)(2 * nk + 2 * ne) * SCS + (size_t)(2 * SG - 1) * m1 * m1) +
+           4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + SG * SG * SG);
+}
+
 size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
 {
     (void)G;
@@ -1048,6 +1201,16 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
                 k_m2l_sum_terms<double><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const double *)T1, na, nlev,
                                                                                         per_k, L.nint, (double *)lbf);
         }
+        return 0;
+    }
+    const size_t ssm = m2l_slab_smem(g.nk, g.ne, g.mx, es);
+    if (mixed && L.G > FG && L.G <= SG && ssm <= 220 * 1024 && g.nk <= 256) {
+        M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
+                  g.kidx, g.kinv, g.eoff};
+        cudaFuncSetAttribute(k_m2l_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+        k_m2l_slab<float><<<dim3((unsigned)(L.nint * na * L.G), nrhs), kM2LSlabThreads, ssm, st>>>(
+            A, (const float *)((const char *)mu + L.mom_off * es * nrhs), (const float *)L.E1, (const float *)L.pref,
+            (float *)((char *)lam + L.mom_off * es * nrhs));
         return 0;
     }
     const size_t per_pair = (size_t)nrhs * na * na * G3 * g.ne;

@@ -103,6 +103,31 @@ def test_mixed_precision_within_1e5_of_fp64_oracle():
     errs, _ = _case(V, T, 64, nrhs=2, precision=P.PFMM_MIXED, tol=1e-5, m_t=4, m_x=6, c_st=1.0)
 
 
+@pytest.mark.parametrize("mesh,n_a,Et,kw", [
+    (cube_sphere_mesh, 16, 64, dict(m_t=4, m_x=5, c_st=0.1, n_tr=6)),  # 8^3 at levels 4, 5; radius 6
+    (cube_mesh, 12, 32, dict(m_t=4, m_x=6, c_st=0.1)),                # 8^3 at the leaf level; radius 7
+])
+def test_mixed_m2l_on_8_cubed_grids_matches_fp64(mesh, n_a, Et, kw):
+    """Levels with 5^3 .. 8^3 cells run the slab M2L in mixed precision (one CTA per target
+    x-slab); the FP64 handle runs the three-pass kernels.  The far field (S2M .. L2T) of the two
+    agrees to FP32 accuracy, for V and K and two right-hand sides."""
+    V, T = mesh(n_a)
+    opm = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, **kw)
+    opd = P.Operator(V, T, 1.0, Et, precision=P.PFMM_FP64, **kw)
+    info = opm.info()
+    assert any(2 ** info["lx"][l] == 8 for l in range(2, info["p"] + 1))
+    w = torch.tensor(random_density(Et, T.shape[0], 2, seed=51), device=DEV)
+    g = torch.tensor(random_density(Et, V.shape[0], 2, seed=52), device=DEV)
+    for op_m, op_d, x in ((opm.V, opd.V, w), (opm.K, opd.K, g)):
+        fm = op_m(x, parts=P.PFMM_PART_FAR).cpu().numpy()
+        fd = op_d(x, parts=P.PFMM_PART_FAR).cpu().numpy()
+        assert np.max(np.abs(fd)) > 0
+        assert _rel(fm, fd) <= 1e-5, _rel(fm, fd)
+    P.pfmm_check(opm.h)
+    opm.close()
+    opd.close()
+
+
 def test_errors_are_reported_not_crashed():
     V, T = cube_mesh(2)
     op = P.Operator(V, T, 1.0, 8)
