@@ -930,7 +930,8 @@ int estimate_scale(pfmm_mpnn *N, pfmm_handle *H, const double *R, const double *
     std::vector<float> a(ns), b(ns);
     cudaMemcpyAsync(a.data(), N->scale, ns * sizeof(float), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(b.data(), N->en2, ns * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_status("output scale estimate");
+    cudaStreamSynchronize(st);
+    if ((rc = cuda_status("output scale estimate"))) return rc;  // failed copies or launches above too
     double sr = 0, st2 = 0;
     for (int i = 0; i < ns; ++i) {
         sr += a[i];
@@ -1071,9 +1072,11 @@ int pfmm_mpnn_create(const pfmm_mesh *mesh, int32_t width, int32_t layers, uint6
     cudaMemset(N->m1, 0, N->nparam * sizeof(float));
     cudaMemset(N->m2, 0, N->nparam * sizeof(float));
     k_to_bf16<<<nblk(N->nparam), 256>>>(N->p32, N->p16, N->nparam);
-    if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaDeviceSynchronize();
+    // any failed upload, memset or launch above is still the last error here
+    if (const int rc = cuda_status("network initialisation")) {
         delete N;
-        return cuda_status("network initialisation");
+        return rc;
     }
     *out = N;
     return PFMM_OK;
@@ -1100,8 +1103,8 @@ int pfmm_mpnn_set_params(pfmm_mpnn *net, const float *host, int64_t n)
     cudaMemset(net->m2, 0, n * sizeof(float));
     net->adam_t = 0;
     k_to_bf16<<<nblk(n), 256>>>(net->p32, net->p16, n);
-    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_status("parameter upload");
-    return PFMM_OK;
+    cudaDeviceSynchronize();
+    return cuda_status("parameter upload");  // a failed upload, memset or launch above included
 }
 
 int pfmm_mpnn_set_output_scale(pfmm_mpnn *net, float c)
@@ -1163,8 +1166,8 @@ int pfmm_mpnn_loss_grad(pfmm_mpnn *net, pfmm_handle *h, const double *R, const d
     if ((rc = loss_grad(net, h, R, E, slices, nslices, st))) return rc;
     if (loss) cudaMemcpyAsync(loss, net->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (grad) cudaMemcpyAsync(grad, net->grad, net->nparam * sizeof(float), cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_status("loss / gradient download");
-    return PFMM_OK;
+    cudaStreamSynchronize(st);
+    return cuda_status("loss / gradient download");  // a failed copy included
 }
 
 int pfmm_mpnn_train(pfmm_mpnn *net, pfmm_handle *h, const double *R, const double *E, int64_t nvec, int32_t steps,
