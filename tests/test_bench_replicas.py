@@ -46,3 +46,16 @@ def test_two_replicas_max_time_and_aggregate_throughput():
 def test_single_rank_needs_no_collective():
     assert bench.max_over_ranks(4.0, 1, None) == 4.0
     assert bench.replicas_throughput(10.0, 2.0, 1) == pytest.approx(5000.0)
+
+
+def test_launches_per_apply_matches_the_launch_list():
+    """The bench's `gpu_launches` claim counts the kernels of one V_h apply from the tree depth:
+    the 12288-triangle x 256-step workload (7 levels, tensor-core nearfield, every M2L level
+    split) launches 31, as the ncu launch list of that workload shows; without the tensor-core
+    engine the input max and split are not launched; a tree without far field launches the
+    permutes and the nearfield only."""
+    assert bench._launches_per_apply({"p": 7, "nf_tensor_cores": 3}, 1) == 31
+    assert bench._launches_per_apply({"p": 7, "nf_tensor_cores": 0}, 1) == 29
+    # more right-hand sides fill the coarse levels: levels with >= 8 CTAs per SM are not split
+    assert bench._launches_per_apply({"p": 7, "nf_tensor_cores": 3}, 2) == 30
+    assert bench._launches_per_apply({"p": 1, "nf_tensor_cores": 0}, 1) == 3
