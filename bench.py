@@ -346,7 +346,9 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6, solve=True):
 def _profile_case(dev, case):
     """Small cases for ncu captures of kernels the matvec does not launch: the learned
     preconditioner's layers (`mpnn`), its compiled form (`mpnn_compiled`), the on-the-fly
-    nearfield (`otf`).  3072-triangle cube; 128 steps (network) or 32 steps (on-the-fly)."""
+    nearfield (`otf`), the slab M2L of 8^3 grids (`m2l_slab`).  3072-triangle cube; 128 steps
+    (network) or 32 steps (on-the-fly); 1728-triangle cube x 32 steps with an 8^3 leaf grid
+    (c_st 0.1, interaction radius 7) for the slab M2L, far field only."""
     import numpy as np
     import torch
 
@@ -365,6 +367,12 @@ def _profile_case(dev, case):
         v = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
         z = torch.empty_like(v)
         run = lambda: net.apply(v, z)  # noqa: E731
+    elif case == "m2l_slab":
+        V, T = cube_mesh(12)
+        Et = 32
+        op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=0.1, precision=P.PFMM_MIXED)
+        w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
+        run = lambda: op.V(w, parts=P.PFMM_PART_FAR)  # noqa: E731
     else:
         Et = 32
         op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_MIXED,
@@ -450,7 +458,7 @@ def main():
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
     ap.add_argument("--config5-matvec", action="store_true",
                     help="with --config5: the build and matvecs only (no recording, training or solves)")
-    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf"], default=None,
+    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab"], default=None,
                     help="profiling only: run one small case of a kernel outside the matvec and exit")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
