@@ -4,9 +4,11 @@ Workload (the single large problem): surface of the unit cube, 32 x 32 squares p
 into 12288 flat triangles, 256 uniform steps on [0, 1] (3,145,728 space-time DOFs), Chebyshev
 degree 6 in space, Lagrange degree 4 in time, c_st = 1, temporal leaves of 2 steps.  A step is
 one f = V_h w (the product every GMRES iteration applies), w ~ N(0,1) seeded.  The nearfield
-blocks and tables are built before the timed region (assembly).
+blocks and tables are built before the timed region (assembly).  The headline value is the
+FP64 product (the paper's precision); the mixed-precision product of the same workload is
+reported beside it with its error against FP64 and against the CPU oracle.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
 
 Prints one JSON line.  Under torchrun (N > 1) each rank runs its own replica of the problem
 (the matvec does not shard on one box: replicas only), timing is the max over ranks and value
@@ -30,9 +32,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pFMM matvec space-time DOF/s"
 N_A, ET, M_X, M_T, C_ST = 32, 256, 6, 4, 1.0
-# DRAM bytes (read + write) per stored panel element of one tensor-core nearfield launch, from an
-# ncu capture of the 3072-triangle x 128-step case (None: not captured for the current kernel)
-NF_TC_DRAM_BYTES_PER_ELEMENT = 4.79
 
 
 def _set_size(n_a, et):
@@ -73,23 +72,106 @@ def _clocks_summary(samples):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_sample(n_targets=16, nthreads=0):
-    """Time the CPU oracle (plain FP64 pFMM of Alg. 2) on a bounded sample: the rows of
-    ``n_targets`` triangles (all 256 steps) of the same workload."""
-    import oracle as O
-    from paper_2106_15911_gb300.inputs import cube_mesh, random_density, sample_triangles
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
-    V, T = cube_mesh(N_A)
-    P = O.make_problem(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST)
-    w = random_density(ET, T.shape[0], 1, seed=1234)[0]
-    tg = sample_triangles(T.shape[0], n_targets, seed=7)
+
+def _oracle_rows(V, T, Et, w, rows, nthreads=0, near=None):
+    """The CPU oracle's V_h w on the sampled target rows: the nearfield rows as stored blocks
+    (assembled before the timer, as the paper assembles before its GMRES iterations) times w over
+    the nearfield offsets, plus the far field of the oracle's pFMM (Alg. 2: whole-mesh S2M and M2M,
+    then M2L / L2L / L2T on the boxes of the sampled rows).  Returns the rows of f, the timings and
+    the assembled blocks (for reuse)."""
+    import oracle as O
+
+    P_ = O.make_problem(V, T, 1.0, Et, m_t=M_T, m_x=M_X, c_st=C_ST)
     t0 = time.perf_counter()
-    O.pfmm_apply(P, 0, w, targets=tg, nthreads=nthreads)
-    dt = time.perf_counter() - t0
-    cores = nthreads if nthreads > 0 else (os.cpu_count() or 1)
-    return dict(value=n_targets * ET / dt, unit="space-time DOF/s", cores=cores, kind="oracle",
-                sample=f"rows of {n_targets} seeded target triangles x {ET} steps of V_h w (full S2M/M2M, "
-                       f"M2L/L2L/L2T on their box chains, their nearfield rows); {dt:.1f} s"), dt
+    if near is None:
+        near = O.assemble_V_rows(V, T, 1.0 / Et, rows, nd=4, nthreads=nthreads)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fn = O.toeplitz_rows_apply(near, w, leaf_steps=2)
+    t_near = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ff = O.pfmm_apply(P_, 0, w, targets=rows, parts=2, nthreads=nthreads)[:, rows]
+    t_far = time.perf_counter() - t0
+    return dict(f=fn + ff, t_assembly=t_asm, t_near=t_near, t_far=t_far), near
+
+
+def _cpu_baseline(V, T, Et, w, every=64, nthreads=0):
+    """cpu_baseline: the oracle's matvec (stored nearfield rows, pFMM far field) on every
+    `every`-th target triangle (all Et steps) of the workload, in space-time DOF/s of the sampled
+    rows; plus the far field's fixed whole-mesh cost (one target row) for context."""
+    import oracle as O
+
+    rows = np.arange(0, T.shape[0], every, dtype=np.int32)
+    r, near = _oracle_rows(V, T, Et, w, rows, nthreads)
+    P_ = O.make_problem(V, T, 1.0, Et, m_t=M_T, m_x=M_X, c_st=C_ST)
+    t0 = time.perf_counter()
+    O.pfmm_apply(P_, 0, w, targets=rows[:1], parts=2, nthreads=nthreads)
+    t_fixed = time.perf_counter() - t0
+    t = r["t_near"] + r["t_far"]
+    cores = nthreads if nthreads > 0 else _host_cores()
+    cb = dict(value=len(rows) * Et / t, unit="space-time DOF/s", cores=cores, kind="oracle",
+              sample=f"V_h w on every {every}th target triangle ({len(rows)} rows x {Et} steps): nearfield rows as "
+                     f"stored blocks (assembled outside the timer, {r['t_assembly']:.1f} s) x w, plus the oracle pFMM "
+                     f"far field of those rows; {t:.1f} s",
+              near_s=r["t_near"], far_s=r["t_far"], far_fixed_one_row_s=t_fixed, assembly_s=r["t_assembly"])
+    return cb, rows, r["f"]
+
+
+def _dense_rows_error(V, T, Et, w, outs, n_rows=8, nthreads=0):
+    """Error of each GPU output against the dense Galerkin V_h (every step offset, no FMM
+    approximation) on n_rows sampled target triangles (the oracle's plain definition, Section 2)."""
+    import oracle as O
+    from paper_2106_15911_gb300.inputs import sample_triangles
+
+    rows = sample_triangles(T.shape[0], n_rows, seed=64)
+    blocks = np.concatenate([O.assemble_V_rows(V, T, 1.0 / Et, rows, d0=d0, nd=min(64, Et - d0), nthreads=nthreads)
+                             for d0 in range(0, Et, 64)])
+    ref = O.toeplitz_rows_apply(blocks, w)
+    den = np.max(np.abs(ref))
+    return {k: float(np.max(np.abs(v[:, rows] - ref)) / den) for k, v in outs.items()}, len(rows)
+
+
+def phase_rooflines(phases, info, es, nt, Et, mx, mt, peaks):
+    """Algorithmic work per apply of every phase (the formulas of the design doc's kernel table), the
+    rate it achieved in its measured phase time, and the fraction of the relevant peak.
+    peaks: hbm_gbs, fp64_tflops, fp32_tflops (and fp16_tflops for a tensor-core nearfield)."""
+    from math import comb
+
+    nk, na = comb(mx + 3, 3), mt + 1
+    p = info["p"]
+    nleaf = info["nbox"][p] * (Et // 2)
+    dof = nt * Et
+    fma = peaks["fp64_tflops"] if es == 8 else peaks["fp32_tflops"]
+    out = {}
+
+    def put(name, flops, byts, ms, fpeak):
+        if not ms or ms <= 0:
+            return
+        d = {"ms": ms, "flops": flops, "bytes": byts, "tflops": flops / (ms * 1e-3) / 1e12,
+             "gbs": byts / (ms * 1e-3) / 1e9}
+        d["frac_fp"] = d["tflops"] / fpeak
+        d["frac_hbm"] = d["gbs"] / peaks["hbm_gbs"]
+        d["bound"] = "fp" if d["frac_fp"] >= d["frac_hbm"] else "hbm"
+        out[name] = d
+
+    s2m_f = 2.0 * Et * nt * nk + 2.0 * nleaf * 2 * na * nk
+    put("s2m", s2m_f, es * dof + es * nt * nk + es * nleaf * na * nk, phases.get("s2m"), fma)
+    put("l2t", s2m_f, 16.0 * dof + es * nt * nk + es * nleaf * na * nk, phases.get("l2t"), fma)
+    if p >= 2:
+        put("m2l", 2.0 * 3 * comb(mx + 4, 4) * na * na * info["n_m2l_pairs"],
+            2.0 * es * sum(info["nbox"][l] * 2 ** l for l in range(2, p + 1)) * na * nk, phases.get("m2l"), fma)
+    nel = info["nearfield_v_elements"]
+    nf_flops = 2.0 * (nel / 4) * (Et // 2) * 7  # 2 sum_t |D(t)| nnz(A_d): |D| = 3, 4 on the two steps
+    tc = bool(info.get("nf_tensor_cores", 0) & 1) and es == 4
+    put("nearfield", nf_flops, nel * (4 if tc else es) + 16.0 * dof, phases.get("nearfield"),
+        peaks.get("fp16_tflops", fma) if tc else fma)
+    return out
 
 
 def _solve_comparison(dev, n_train=256, n_test=32):
@@ -388,21 +470,6 @@ def _profile_case(dev, case):
     return {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
 
 
-def _launches_per_apply(info, nrhs, na=M_T + 1, split_ctas=8 * 152):
-    """Kernels one V_h apply launches: permute in and out, the FP16 input split (max |x| and
-    split; tensor-core nearfield), nearfield, S2M (per-tile moments and their temporal sum),
-    M2M (levels p-1..2), M2L (levels 2..p) plus one term sum per split level (levels with fewer
-    than eight (interval, node) CTAs per SM), L2L (levels 3..p), L2T (temporal factor and
-    per-tile evaluation).  The two-stage S2M / L2T forms are the ones taken when the M2L
-    workspace holds their intermediates, as it does for the bench workload."""
-    p = info["p"]
-    tc = 2 if info["nf_tensor_cores"] & 1 else 0
-    if p < 2:
-        return 3 + tc
-    split = sum(1 for l in range(2, p + 1) if (2 ** l) * na * nrhs < split_ctas)
-    return 2 + tc + 1 + 2 + (p - 2) + (p - 1) + split + (p - 2) + 2
-
-
 def max_over_ranks(x: float, world: int, device) -> float:
     """The largest per-rank value (the slowest replica's time) on every rank."""
     if world <= 1:
@@ -422,26 +489,54 @@ def replicas_throughput(units_per_rank: float, ms_step: float, world: int) -> fl
 
 
 def reference_arm(args, rank, world):
+    """The oracle (plain CPU FP64 pFMM of Alg. 2, nearfield rows stored) on the same workload:
+    each step is V_h w on a bounded sample of target rows (every 384th triangle, 32 rows x 256
+    steps), the nearfield rows assembled once before the steps."""
     if rank != 0:
         return 0
+    from paper_2106_15911_gb300.inputs import cube_mesh, random_density
+
+    V, T = cube_mesh(N_A)
+    nt = T.shape[0]
+    w = random_density(ET, nt, 1, seed=1234)[0]
+    rows = np.arange(0, nt, 384, dtype=np.int32)
+    near = None
     vals, tot = [], 0.0
-    for _ in range(args.warmup):
-        _oracle_sample()
-    for _ in range(args.steps):
-        cb, dt = _oracle_sample()
-        vals.append(cb["value"])
-        tot += dt
+    for i in range(args.warmup + args.steps):
+        r, near = _oracle_rows(V, T, ET, w, rows, near=near)
+        if i >= args.warmup:
+            dt = r["t_near"] + r["t_far"]
+            vals.append(len(rows) * ET / dt)
+            tot += dt
     v = statistics.mean(vals)
-    cb["value"] = v
+    cb = {"value": v, "unit": "space-time DOF/s", "cores": _host_cores(), "kind": "oracle",
+          "sample": f"V_h w on every 384th target triangle ({len(rows)} rows x {ET} steps) per step: stored "
+                    f"nearfield rows x w plus the oracle pFMM far field of those rows"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "space-time DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"cube {N_A}x{N_A} faces ({12 * N_A * N_A} tri) x {ET} steps",
-                                             "m_x": M_X, "m_t": M_T, "c_st": C_ST},
-            "cpu_baseline": cb, "e2e": {"value": v, "unit": "space-time DOF/s", "h2d_bytes_per_step": 0,
-                                          "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": _config_dict(nt), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "space-time DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _config_dict(nt, world=1):
+    return {"workload": f"cube {N_A}x{N_A} faces ({nt} tri) x {ET} steps, V_h matvec", "dofs": nt * ET,
+            "m_x": M_X, "m_t": M_T, "c_st": C_ST, "leaf_steps": 2, "n_tr": "derived (no truncation)",
+            "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"}
+
+
+def _peaks(P, stream):
+    pk = {}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+    src = "of measured" if pk else "of fallback"
+    return {"hbm_gbs": float(pk.get("hbm_gbs", 6800.0)), "fp16_tflops": float(pk.get("bf16_tflops", 1900.0)),
+            "fp64_tflops": P.pfmm_probe_fma_rate(True, stream), "fp32_tflops": P.pfmm_probe_fma_rate(False, stream),
+            "source": f"HBM and FP16 (= dense BF16 burst) {src} MEASURED_PEAKS.json; FP64 / FP32 FMA rates measured "
+                      f"by pfmm_probe_fma_rate in this run"}
 
 
 def main():
@@ -449,10 +544,12 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64",
+                    help="precision of the headline value (the other one is reported beside it)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--other-steps", type=int, default=10, help="timed steps of the other precision (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dense-rows", type=int, default=8, help="rows of the dense-oracle error check (0: skip)")
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
     ap.add_argument("--solve-sets", type=int, default=32, help="held-out data sets of the solver comparison")
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
@@ -493,37 +590,41 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     V, T = cube_mesh(N_A)
-    nt, nv = T.shape[0], V.shape[0]
+    nt = T.shape[0]
     dof = nt * ET
     stream = torch.cuda.current_stream()
-    prec = P.PFMM_MIXED if args.precision == "mixed" else P.PFMM_FP64
+    head = P.PFMM_FP64 if args.precision == "fp64" else P.PFMM_MIXED
+    other = P.PFMM_MIXED if head == P.PFMM_FP64 else P.PFMM_FP64
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    t_build = time.perf_counter()
-    op = P.Operator(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST, precision=prec)
-    torch.cuda.synchronize()
-    t_build = time.perf_counter() - t_build
+    def build(prec):
+        t0 = time.perf_counter()
+        o = P.Operator(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST, precision=prec)
+        torch.cuda.synchronize()
+        return o, time.perf_counter() - t0
+
+    op, t_build = build(head)
     info = op.info()
     w = torch.tensor(random_density(ET, nt, 1, seed=1234 + rank), device=dev)
     f = torch.empty_like(w)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def run_device_timed(steps, warm, opx, prof):
+    def run_device_timed(steps, warm, opx, fx):
         P.pfmm_set_profiling(opx.h, False)
         for _ in range(warm):
-            P.pfmm_apply_V(opx.h, w, f, 1, stream)
+            P.pfmm_apply_V(opx.h, w, fx, 1, stream)
         P.pfmm_phase_times(opx.h)
-        P.pfmm_set_profiling(opx.h, prof)
+        P.pfmm_set_profiling(opx.h, True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         for i in range(steps):
             flush.zero_()
             ev[i][0].record(stream)
-            P.pfmm_apply_V(opx.h, w, f, 1, stream)
+            P.pfmm_apply_V(opx.h, w, fx, 1, stream)
             ev[i][1].record(stream)
         barrier()
         ms = [a.elapsed_time(b) for a, b in ev]
@@ -535,11 +636,12 @@ def main():
     stop, samples = threading.Event(), []
     th = threading.Thread(target=_clock_sampler, args=(stop, samples), daemon=True)
     th.start()
-    ms, phases = run_device_timed(args.steps, args.warmup, op, prof=True)
+    ms, phases = run_device_timed(args.steps, args.warmup, op, f)
     stop.set()
     th.join(timeout=5)
     ms_step = max_over_ranks(statistics.mean(ms), world, dev)
     value = replicas_throughput(dof, ms_step, world)
+    launches = P.pfmm_count_apply_kernels(op.h, 0, w, f, 1)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     wh = torch.tensor(random_density(ET, nt, 1, seed=99 + rank)).pin_memory()
@@ -562,57 +664,63 @@ def main():
     e2e = {"value": replicas_throughput(dof, e2e_ms, world), "unit": "space-time DOF/s", "h2d_bytes_per_step": 8 * dof,
            "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_ms}
 
-    # ---- roofline of the dominant kernel (nearfield apply): algorithmic work per launch
-    ls = 2
-    nint = ET // ls
-    flops_nf = 2.0 * nt * nt * nint * sum(ls + s + 1 for s in range(ls))  # 2 * E_x^2 * sum_t |D(t)|
-    nf_ms = phases["nearfield"]
-    fp64 = prec == P.PFMM_FP64
-    tc = bool(info.get("nf_tensor_cores", 0) & 1)
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    # ---- rooflines: every phase from its algorithmic work; the dominant kernel is the nearfield
+    peaks = _peaks(P, stream)
+    es = 8 if head == P.PFMM_FP64 else 4
+    rl = phase_rooflines(phases, info, es, nt, ET, M_X, M_T, peaks)
+    nf = rl["nearfield"]
+    tc = head == P.PFMM_MIXED and bool(info["nf_tensor_cores"] & 1)
     if tc:
-        # tcgen05 kind::f16 with a 3-term split: three FP16 products per useful product; the FP16
-        # dense rate is the BF16 rate, so the peak is the measured dense BF16 burst peak
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak_f16 = bf16
-        achieved = 3.0 * flops_nf / (nf_ms * 1e-3) / 1e12
-        # algorithmic HBM bytes: the hi/lo FP16 parts of every stored panel element, read once
-        bytes_nf = 4.0 * info["nearfield_v_elements"]
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        # DRAM bytes per panel element of this kernel, measured with ncu on the 3072-triangle x
-        # 128-step case
-        traffic = NF_TC_DRAM_BYTES_PER_ELEMENT * info["nearfield_v_elements"] if NF_TC_DRAM_BYTES_PER_ELEMENT else None
-        roofline = {"bound": "tensor", "kernel": "k_nf_apply_tc", "achieved": achieved, "peak": peak_f16,
-                    "unit": "TFLOP/s", "frac": achieved / peak_f16, "traffic": traffic,
-                    "peak_source": f"measured dense bf16 burst {bf16:.0f} TF = the fp16 rate (of measured)",
-                    "flops_per_launch_executed": 3.0 * flops_nf, "ms_per_launch": nf_ms,
-                    "hbm": {"achieved_gbs": bytes_nf / (nf_ms * 1e-3) / 1e9, "peak_gbs": hbm,
-                            "frac": bytes_nf / (nf_ms * 1e-3) / 1e9 / hbm, "bytes_per_launch": bytes_nf}}
+        roofline = {"bound": "hbm", "kernel": "k_nf_apply_tc", "achieved": nf["gbs"], "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": nf["frac_hbm"], "traffic": None,
+                    "peak_source": "measured copy rate (of measured)", "bytes_per_launch": nf["bytes"],
+                    "ms_per_launch": nf["ms"], "tensor": {"algorithmic_tflops": nf["tflops"],
+                                                          "frac_of_fp16_peak": nf["frac_fp"]}}
     else:
-        peak_meas = P.pfmm_probe_fma_rate(fp64, stream)
-        peak_nominal = sm_count * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
-        roofline = {"bound": "alu", "kernel": "k_nf_apply", "achieved": flops_nf / (nf_ms * 1e-3) / 1e12,
-                    "peak": peak_meas, "unit": "TFLOP/s", "frac": flops_nf / (nf_ms * 1e-3) / 1e12 / peak_meas,
-                    "traffic": None, "peak_source": f"measured {'FP64' if fp64 else 'FP32'} FMA probe "
-                                                    f"(nominal FP32 {peak_nominal:.1f} at 2070 MHz)",
-                    "flops_per_launch": flops_nf, "ms_per_launch": nf_ms}
+        roofline = {"bound": "alu", "kernel": "k_nf_apply<double>" if es == 8 else "k_nf_apply<float>",
+                    "achieved": nf["tflops"], "peak": peaks["fp64_tflops"] if es == 8 else peaks["fp32_tflops"],
+                    "unit": "TFLOP/s", "frac": nf["frac_fp"], "traffic": None,
+                    "peak_source": "FMA rate measured in this run by pfmm_probe_fma_rate (independent FMA chains)",
+                    "flops_per_launch": nf["flops"], "ms_per_launch": nf["ms"],
+                    "hbm": {"achieved_gbs": nf["gbs"], "frac": nf["frac_hbm"], "bytes_per_launch": nf["bytes"]}}
 
-    # ---- FP64 mode of the same workload (context; the other half of the workload's comparison)
-    fp64_line = None
-    if not fp64 and args.fp64_steps > 0:
-        op64 = P.Operator(V, T, 1.0, ET, m_t=M_T, m_x=M_X, c_st=C_ST, precision=P.PFMM_FP64)
-        ms64, ph64 = run_device_timed(args.fp64_steps, 1, op64, prof=True)
-        with torch.no_grad():
-            P.pfmm_apply_V(op64.h, w, fd, 1, stream)
-            P.pfmm_apply_V(op.h, w, f, 1, stream)
-            torch.cuda.synchronize()
-            rel = float((f - fd).abs().max() / fd.abs().max())
-        fp64_line = {"value": dof / (statistics.mean(ms64) * 1e-3), "ms_per_step": statistics.mean(ms64),
-                     "phases_ms": ph64, "mixed_vs_fp64_rel_maxnorm": rel,
-                     "fp64_fma_tflops": P.pfmm_probe_fma_rate(True, stream)}
-        op64.close()
+    # ---- the other precision of the same workload, and the errors between them
+    other_line = None
+    fo = torch.empty_like(f)
+    P.pfmm_apply_V(op.h, w, f, 1, stream)
+    torch.cuda.synchronize()
+    if args.other_steps > 0:
+        op2, t_build2 = build(other)
+        ms2, ph2 = run_device_timed(args.other_steps, 1, op2, fo)
+        P.pfmm_apply_V(op2.h, w, fo, 1, stream)
+        torch.cuda.synchronize()
+        f64, fmx = (f, fo) if head == P.PFMM_FP64 else (fo, f)
+        rel = float((fmx - f64).abs().max() / f64.abs().max())
+        info2 = op2.info()
+        other_line = {"precision": "mixed" if other == P.PFMM_MIXED else "fp64",
+                      "value": dof / (statistics.mean(ms2) * 1e-3), "ms_per_step": statistics.mean(ms2),
+                      "phases_ms": ph2, "build_s": t_build2, "mixed_vs_fp64_rel_maxnorm": rel,
+                      "rooflines": phase_rooflines(ph2, info2, 8 if other == P.PFMM_FP64 else 4, nt, ET, M_X, M_T,
+                                                   peaks),
+                      "nf_tensor_cores": info2["nf_tensor_cores"]}
+        op2.close()
+
+    # ---- oracle: cpu_baseline (a matvec on every 64th target row) and parity on those rows
+    cpu, parity = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            wn = w[0].cpu().numpy()
+            outs = {("fp64" if head == P.PFMM_FP64 else "mixed"): f[0].cpu().numpy()}
+            if other_line:
+                outs[other_line["precision"]] = fo[0].cpu().numpy()
+            cpu, rows, fref = _cpu_baseline(V, T, ET, wn)
+            den = np.max(np.abs(fref))
+            parity = {"rows": int(len(rows)), "vs_oracle_pfmm": {k: float(np.max(np.abs(v[:, rows] - fref)) / den)
+                                                                  for k, v in outs.items()}}
+            if args.dense_rows > 0:
+                parity["vs_dense_oracle"], parity["dense_rows"] = _dense_rows_error(V, T, ET, wn, outs, args.dense_rows)
+        except Exception as e:  # the baseline is context; the line still prints
+            cpu = {"value": None, "error": str(e)}
 
     solve = None
     if rank == 0 and not args.no_solve:
@@ -621,25 +729,17 @@ def main():
     if rank == 0 and args.batch > 0:
         batch = _batch_comparison(dev, args.batch)
 
-    launches = _launches_per_apply(info, 1)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            cpu, _ = _oracle_sample()
-        except Exception as e:  # the baseline is context; the line still prints
-            cpu = {"value": None, "error": str(e)}
     if rank == 0:
+        cfg = _config_dict(nt, world)
+        cfg.update({"precision": args.precision, "build_s": t_build,
+                    "nearfield_GB": info["nearfield_bytes"] / 1e9})
         line = {"metric": METRIC, "value": value, "unit": "space-time DOF/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if not fp64 else "f64", "data": "synthetic",
-                "config": {"workload": f"cube {N_A}x{N_A} faces ({nt} tri) x {ET} steps, V_h matvec",
-                           "dofs": dof, "m_x": M_X, "m_t": M_T, "c_st": C_ST, "precision": args.precision,
-                           "l2": "flushed (256 MB write) between timed steps; nearfield blocks "
-                                 f"{info['nearfield_bytes'] / 1e9:.2f} GB > L2",
-                           "parallelism": f"replicas x{world}", "build_s": t_build},
-                "phases_ms": phases, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches * args.steps, "clocks": _clocks_summary(samples), "fp64": fp64_line,
-                "solve": solve, "batch": batch}
+                "vs_baseline": None, "dtype": "f64" if head == P.PFMM_FP64 else "f32", "data": "synthetic",
+                "config": cfg, "phases_ms": phases, "roofline": roofline, "phase_rooflines": rl, "peaks": peaks,
+                "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "launches_per_apply": launches, "clocks": _clocks_summary(samples),
+                ("mixed" if other == P.PFMM_MIXED else "fp64"): other_line, "solve": solve, "batch": batch}
         print(json.dumps(line), flush=True)
     op.close()
     if world > 1:

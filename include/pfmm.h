@@ -48,8 +48,12 @@ extern "C" {
 
 /* precision modes */
 #define PFMM_FP64 0   /* every phase in FP64 */
-#define PFMM_MIXED 1  /* FP32 storage and FP32 arithmetic for the nearfield apply and the FMM
-                         passes; FP64 singular quadrature, FP64 output accumulation */
+#define PFMM_MIXED 1  /* FP32 regular-pair quadrature and FP32 FMM passes; FP64 singular
+                         quadrature; FP64 output accumulation.  The stored nearfield is applied
+                         on the tensor cores (default engine) as three FP16 products of scaled
+                         hi/lo parts with FP32 accumulation (about 2^-22 relative, as FP32), or
+                         in FP32 on the CUDA cores (PFMM_NF_CUDA_CORES, or where the panel layout
+                         does not suit the tensor cores) */
 
 /* nearfield modes */
 #define PFMM_NEARFIELD_STORED 0    /* nearfield blocks assembled once at build time */
@@ -111,7 +115,15 @@ typedef struct pfmm_info {
     int64_t nearfield_v_elements; /* stored V nearfield entries (all panels, all step offsets) */
     int32_t nf_dense_columns;     /* 1: the panels share one column space (all triangles / nodes,
                                      zero where the source is not near), 0: compact per panel */
+    int32_t m2l_engine[32];       /* M2L kernel of level l (l = 2 .. p; 0 elsewhere): PFMM_M2L_* */
 } pfmm_info;
+
+/* M2L kernels (pfmm_info.m2l_engine): the three separable passes through a global workspace
+ * (FP64, grids beyond 8^3 or high degrees), the fused kernel (FP32, grids of at most 4^3 cells,
+ * m_x <= 7), the slab kernel (FP32, grids of 5^3 .. 8^3 cells, m_x <= 6). */
+#define PFMM_M2L_THREE_PASS 1
+#define PFMM_M2L_FUSED 2
+#define PFMM_M2L_SLAB 3
 
 /* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,
  * leaf_steps = 2, leaf_tris = 16, FP64, stored nearfield, quad_regular = 3,
@@ -150,6 +162,14 @@ int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies);
 
 int pfmm_get_info(const pfmm_handle *h, pfmm_info *info);
 
+/* Measurement utility (not part of the paper's method): the number of kernels one
+ * pfmm_apply_parts(h, op, x, f, nrhs, parts) launches.  The apply is captured into a CUDA graph
+ * on a private stream (nothing executes; x and f are device buffers of the apply's sizes, not
+ * read or written) and its kernel nodes are counted into *kernels.  Sizes the handle's
+ * workspaces for nrhs first (may allocate). */
+int pfmm_count_apply_kernels(pfmm_handle *h, int32_t op, const double *x, double *f, int32_t nrhs, int32_t parts,
+                             int64_t *kernels);
+
 /* Synchronise the device and report whether a bounded wait inside a kernel of this handle gave
  * up since the last check (PFMM_ERR_TIMEOUT; the result of that apply is invalid), or a CUDA
  * error is pending (PFMM_ERR_CUDA).  Clears the flag.  PFMM_OK otherwise. */
@@ -173,7 +193,11 @@ int pfmm_probe_fma_rate(int32_t fp64, double *tflops, void *stream);
  *   PFMM_ERR_OOM with a message naming the bytes needed when the workspaces of this handle and
  *   nrhs do not fit in 64 MiB (the separable-M2L intermediates are processed in chunks that fit).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.  All calls share the
+ * that device current); make that first call before any stream capture.  With lazy module
+ * loading (the CUDA runtime's default, CUDA_MODULE_LOADING=LAZY) that first lookup is also when
+ * the module holding the array is loaded and its 64 MiB are committed on the device, so make the
+ * first call at start-up, while memory is known to be free; if the device has no room then, the
+ * call returns PFMM_ERR_OOM.  All calls share the
  * one array: calls whose work overlaps on the GPU (other streams, other threads, other handles)
  * race on it and must be serialised by the caller.  The array keeps the last call's contents;
  * each call writes every workspace before reading it. */

@@ -65,6 +65,7 @@ def lib():
             L.orc_pair_integral.argtypes = [pd, pi, pi, i, i, d, d, pd, i, i, pd]
             L.orc_assemble_V.argtypes = [i, pd, i, pi, d, d, i, i, i, i, pd, i]
             L.orc_assemble_K.argtypes = [i, pd, i, pi, d, d, i, i, i, i, pd, i]
+            L.orc_assemble_V_rows.argtypes = [i, pd, i, pi, d, d, i, i, i, i, pi, i, pd, i]
             L.orc_assemble_M.argtypes = [i, pd, i, pi, d, pd]
             L.orc_tree_info.argtypes = [ctypes.POINTER(Problem), pi, pi, pi, pd, pi, pi, pd]
             L.orc_pfmm_apply.argtypes = [ctypes.POINTER(Problem), i, pd, pd, pi, i, i, i]
@@ -157,6 +158,36 @@ def assemble_V(V, T, h, alpha=1.0, d0=0, nd=1, n_r=3, n_s=6, nthreads=0):
     rc = lib().orc_assemble_V(V.shape[0], _pd(V), T.shape[0], _pi(T), h, alpha, d0, nd, n_r, n_s, _pd(out), nthreads)
     assert rc == 0
     return out
+
+
+def assemble_V_rows(V, T, h, rows, alpha=1.0, d0=0, nd=1, n_r=3, n_s=6, nthreads=0):
+    """Rows of the Toeplitz blocks for the listed target triangles: A_d[rows[i]][y],
+    d = d0 .. d0+nd-1, shape [nd, len(rows), nt] (nd <= 64 per call)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.int32)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.zeros((nd, rows.shape[0], T.shape[0]))
+    rc = lib().orc_assemble_V_rows(V.shape[0], _pd(V), T.shape[0], _pi(T), h, alpha, d0, nd, n_r, n_s, _pi(rows),
+                                   rows.shape[0], _pd(out), nthreads)
+    assert rc == 0
+    return out
+
+
+def toeplitz_rows_apply(blocks, x, leaf_steps=None):
+    """f[k][i] = sum_{d} blocks[d][i] . x[k-d] for row blocks [nd, nrows, ncol] and x [Et, ncol]:
+    the sampled rows of the block lower triangular Toeplitz product, shape [Et, nrows].  Without
+    leaf_steps every d < min(k+1, nd) enters (blocks beyond nd are zero); with leaf_steps = ls only
+    the pFMM nearfield offsets of step k on a uniform-depth tree do, d <= ls + (k mod ls) (the
+    source steps of leaf intervals I_{i-1} and I_i, Eq. 03:ILtemp)."""
+    Et = x.shape[0]
+    f = np.zeros((Et, blocks.shape[1]))
+    for k in range(Et):
+        dmax = min(k + 1, blocks.shape[0])
+        if leaf_steps:
+            dmax = min(dmax, leaf_steps + k % leaf_steps + 1)
+        for d in range(dmax):
+            f[k] += blocks[d] @ x[k - d]
+    return f
 
 
 def assemble_K(V, T, h, alpha=1.0, d0=0, nd=1, n_r=3, n_s=6, nthreads=0):

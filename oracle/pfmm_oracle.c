@@ -525,6 +525,29 @@ int orc_assemble_V(int nv, const double *V, int nt, const int *T, double h, doub
     return 0;
 }
 
+/* The rows of the listed target triangles only: out_V[d][i][y] = V[(k, rows[i]), (k - d, y)],
+ * d = d0 .. d0+nd-1 (same entries as orc_assemble_V, for a sample of rows). */
+int orc_assemble_V_rows(int nv, const double *V, int nt, const int *T, double h, double alpha, int d0, int nd,
+                        int n_r, int n_s, const int *rows, int nrows, double *out, int nthreads)
+{
+    (void)nv;
+    if (nd > 64) return -1;
+    for (int i = 0; i < nrows; ++i)
+        if (rows[i] < 0 || rows[i] >= nt) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for collapse(2) schedule(dynamic, 64)
+#endif
+    for (int i = 0; i < nrows; ++i) {
+        for (int y = 0; y < nt; ++y) {
+            double e[64];
+            or_pair_entries(V, T + 3 * rows[i], T + 3 * y, ORK_V, d0, nd, h, alpha, n_r, n_s, e);
+            for (int j = 0; j < nd; ++j) out[((size_t)j * nrows + i) * nt + y] = e[j];
+        }
+    }
+    return 0;
+}
+
 int orc_assemble_K(int nv, const double *V, int nt, const int *T, double h, double alpha, int d0, int nd, int n_r,
                    int n_s, double *out, int nthreads)
 {

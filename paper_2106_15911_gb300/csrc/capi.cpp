@@ -284,7 +284,6 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
     // split K into chunks of at most 32 stages (2048 columns): shorter FP32 accumulation in TMEM
     // and at least three work items per SM; the FP64 atomics of the partials are cheap
     int ks = std::max((3 * H->nsm + tiles - 1) / tiles, (4 * P.nkb + 31) / 32);
-    if (const char *env = std::getenv("PFMM_TC_KSPLIT")) ks = std::atoi(env);  // tuning override
     ks = std::max(1, std::min(ks, 4 * P.nkb / 8));
     P.ksplit = ks;
     P.nitems = tiles * ks;
@@ -340,6 +339,7 @@ int pfmm::apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, vo
     g.Et = ns;
     g.ls = 1;
     g.perm = H->d_perm;
+    g.nsm = H->nsm;
     launch_permute_in(x, xint, H->mixed, 1, g, st);
     if (H->otf) {
         cudaMemsetAsync(fint, 0, sizeof(double) * ns * (size_t)H->nt, st);
@@ -781,6 +781,7 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     g.kinv = H->d_kinv;
     g.ne = H->ne;
     g.eoff = H->d_eoff;
+    g.nsm = H->nsm;
     if ((int)t.panels.size() == g.nbox_leaf) {  // one row panel per leaf box: its 64-row tiles
         g.tiles = H->d_tiles;
         g.ntiles = H->ntiles;
@@ -865,6 +866,42 @@ int pfmm_apply_parts(pfmm_handle *h, int32_t op, const double *x, double *f, int
     return apply_impl(h, op, x, f, nrhs, parts, (cudaStream_t)stream);
 }
 
+int pfmm_count_apply_kernels(pfmm_handle *h, int32_t op, const double *x, double *f, int32_t nrhs, int32_t parts,
+                             int64_t *kernels)
+{
+    if (!h || !x || !f || !kernels || nrhs < 1 || (op != 0 && op != 1) || parts < 1 || parts > 3)
+        return fail(PFMM_ERR_INVALID_ARG, "invalid pfmm_count_apply_kernels arguments");
+    *kernels = 0;
+    int rc = ensure_workspace(h, nrhs);  // no allocation may happen inside the capture
+    if (rc) return rc;
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const bool prof = h->prof;
+    h->prof = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        rc = apply_impl(h, op, x, f, nrhs, parts, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    h->prof = prof;
+    size_t n = 0;
+    if (e == cudaSuccess && !rc && graph) e = cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && !rc && n) e = cudaGraphGetNodes(graph, nodes.data(), &n);
+    int64_t k = 0;
+    for (size_t i = 0; e == cudaSuccess && !rc && i < n; ++i) {
+        cudaGraphNodeType t;
+        if ((e = cudaGraphNodeGetType(nodes[i], &t)) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, std::string("apply capture: ") + cudaGetErrorString(e));
+    *kernels = k;
+    return PFMM_OK;
+}
+
 int pfmm_apply_V(pfmm_handle *h, const double *w, double *f, int32_t nrhs, void *stream)
 {
     return apply_impl(h, 0, w, f, nrhs, PFMM_PART_ALL, (cudaStream_t)stream);
@@ -922,6 +959,10 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
     info->nearfield_v_elements = t.sizeV;
     info->nf_dense_columns = t.dense_cols ? 1 : 0;
+    for (int l = 2; l <= h->p && l < 32 && l < (int)h->dl.size(); ++l) {
+        const int e = pfmm::m2l_engine(h->mixed, h->dl[l].G, h->nk, h->ne, h->mx);
+        info->m2l_engine[l] = e == pfmm::kM2LFused ? PFMM_M2L_FUSED : (e == pfmm::kM2LSlab ? PFMM_M2L_SLAB : PFMM_M2L_THREE_PASS);
+    }
     return PFMM_OK;
 }
 

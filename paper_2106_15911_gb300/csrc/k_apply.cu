@@ -812,10 +812,10 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
 constexpr int FG = 4;  // padded grid extent per direction
 
 constexpr int kM2LThreads = 384;
-// split mode below this many (interval, node, rhs) CTAs: eight per SM of GB300's 152.  At two
-// resident CTAs per SM and work per CTA that differs by 2x between even and odd intervals, fewer
-// than four waves lose much of the last one; one-term CTAs are uniform and many
-constexpr int kM2LSplitCtas = 8 * 152;
+// split mode below this many (interval, node, rhs) CTAs per SM: eight.  At two resident CTAs per
+// SM and work per CTA that differs by 2x between even and odd intervals, fewer than four waves
+// lose much of the last one; one-term CTAs are uniform and many
+constexpr int kM2LSplitCtasPerSm = 8;
 
 template <typename R>
 __global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
@@ -1166,6 +1166,18 @@ size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
            4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
 }
 
+// Which M2L kernel a level takes: the fused kernel for FP32 grids of at most 4^3 cells whose
+// intermediates fit its shared memory (m_x <= 7), the slab kernel for FP32 grids of 5^3 .. 8^3
+// cells with m_x <= 6 (its per-thread arrays and shared memory are sized for that), else the
+// three separable passes through the global workspace (FP64, larger grids or degrees).
+int m2l_engine(bool mixed, int G, int nk, int ne, int mx)
+{
+    if (!mixed) return kM2LThreePass;
+    if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4) <= 200 * 1024 && nk * FG <= 2 * kM2LThreads) return kM2LFused;
+    if (G > FG && G <= SG && mx <= 6 && m2l_slab_smem(nk, ne, mx, 4) <= 220 * 1024 && nk <= 256) return kM2LSlab;
+    return kM2LThreePass;
+}
+
 // Runs the three passes over chunks of target intervals so that the intermediates fit the
 // workspace (ws_elems elements of R for each of T1 and T2).
 int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
@@ -1174,15 +1186,17 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
     (void)l;
     const size_t es = mixed ? 4 : 8;
     const int G3 = L.G * L.G * L.G, na = g.na;
+    const int engine = m2l_engine(mixed, L.G, g.nk, g.ne, g.mx);
     const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es);
-    if (mixed && L.G <= FG && fsm <= 200 * 1024 && g.nk * FG <= 2 * kM2LThreads) {
+    if (engine == kM2LFused) {
         M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
                   g.kidx, g.kinv, g.eoff};
         // few (interval, node) CTAs: one CTA per source term as well, when the terms' partial
         // locals fit the workspace
         const size_t per_k = (size_t)L.nbox * na * g.nk, nlev = (size_t)nrhs * L.nint * per_k;
         const int nterm = 2 * na;
-        const int split = ((int64_t)L.nint * na * nrhs < kM2LSplitCtas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
+        const int64_t split_ctas = (int64_t)kM2LSplitCtasPerSm * (g.nsm > 0 ? g.nsm : 152);
+        const int split = ((int64_t)L.nint * na * nrhs < split_ctas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
         dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
         const char *mbf = (const char *)mu + L.mom_off * es * nrhs;
         char *lbf = (char *)lam + L.mom_off * es * nrhs;
@@ -1204,7 +1218,7 @@ int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, 
         return 0;
     }
     const size_t ssm = m2l_slab_smem(g.nk, g.ne, g.mx, es);
-    if (mixed && L.G > FG && L.G <= SG && ssm <= 220 * 1024 && g.nk <= 256) {
+    if (engine == kM2LSlab) {
         M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
                   g.kidx, g.kinv, g.eoff};
         cudaFuncSetAttribute(k_m2l_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);

@@ -81,6 +81,7 @@ struct ApplyGeo {
     const int *tiles;      // [ntiles][2] (leaf box, first row) of the 64-row tiles of every leaf box
     int ntiles;
     const int *box_tiles;  // [nbox_p + 1] first tile of each leaf box (tiles are box-major)
+    int nsm;               // streaming multiprocessors of the device (grid sizing)
 };
 
 // R: arithmetic/storage type of the FMM passes (double or float)
@@ -113,6 +114,9 @@ void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, cons
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
 int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
                void *T1, void *T2, size_t ws_elems, cudaStream_t st);
+// M2L kernel of a level with a G^3 grid (launch_m2l's choice): only kM2LThreePass uses T1 / T2
+enum { kM2LThreePass = 0, kM2LFused = 1, kM2LSlab = 2 };
+int m2l_engine(bool mixed, int G, int nk, int ne, int mx);
 void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
 // ws: scratch (ws_elems elements of the arithmetic type) for the temporal factor of every (step,

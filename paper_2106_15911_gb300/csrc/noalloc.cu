@@ -40,9 +40,15 @@ int scratch_base(unsigned char **out)
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
+        // with lazy module loading (the runtime's default) this first lookup also loads the module
+        // that holds the array, which is when its 64 MiB are committed on this device: a failure
+        // for lack of memory is reported as PFMM_ERR_OOM
         e = cudaGetSymbolAddress(&p, g_pfmm_scratch);
-        if (e != cudaSuccess || !p)
-            return pfmm::set_error(PFMM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return pfmm::set_error(e == cudaErrorMemoryAllocation ? PFMM_ERR_OOM : PFMM_ERR_CUDA,
+                                   std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+        }
         g_scratch_addr[dev] = (unsigned char *)p;
     }
     *out = g_scratch_addr[dev];
@@ -68,15 +74,18 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     const size_t b_w = tc ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(uint16_t)) : 0;
     const size_t b_m = tc ? up256((size_t)nrhs * sizeof(unsigned long long)) : 0;
     const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w + b_m;
-    const size_t min_chunk = (size_t)nrhs * 2 * H->na * H->na * H->ne * 64;  // M2L: two interval pairs of a 4^3 grid
-    size_t need_T = 0;  // elements for the largest single-interval chunk over all levels
+    // elements of T1 (and of T2) for the largest single-interval chunk of the levels whose M2L
+    // takes the three separable passes (the fused and slab kernels keep their intermediates in
+    // shared memory; the fused kernel's split mode and the two-stage S2M / L2T use T1 only when
+    // it is large enough and fall back otherwise)
+    size_t need_T = 0;
     for (int l = 2; l <= H->p; ++l) {
         const DevLevel &L = H->dl[l];
+        if (m2l_engine(H->mixed, L.G, H->nk, H->ne, H->mx) != kM2LThreePass) continue;
         int maxpairs = 0;
         for (int k = 0; k < L.nint; ++k) maxpairs = std::max(maxpairs, L.kptr_host[k + 1] - L.kptr_host[k]);
         need_T = std::max(need_T, (size_t)nrhs * maxpairs * H->na * H->na * L.G * L.G * L.G * H->ne);
     }
-    need_T = std::max(need_T, min_chunk);
     if (fixed + 2 * up256(need_T * H->es) > kScratchBytes)
         return set_error(PFMM_ERR_OOM, "pfmm_apply_V_noalloc needs " + std::to_string(fixed + 2 * up256(need_T * H->es)) +
                                            " bytes of scratch; the static scratch holds " +
@@ -112,6 +121,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     g.kinv = H->d_kinv;
     g.ne = H->ne;
     g.eoff = H->d_eoff;
+    g.nsm = H->nsm;
     if ((int)H->tree.panels.size() == g.nbox_leaf) {  // one row panel per leaf box: its 64-row tiles
         g.tiles = H->d_tiles;
         g.ntiles = H->ntiles;

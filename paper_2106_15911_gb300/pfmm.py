@@ -23,6 +23,7 @@ PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_NEARFIELD_STORED, PFMM_NEARFIELD_ONTHEFLY = 0, 1
 PFMM_PART_NEAR, PFMM_PART_FAR, PFMM_PART_ALL = 1, 2, 3
 PFMM_NF_AUTO, PFMM_NF_CUDA_CORES = 0, 1
+PFMM_M2L_THREE_PASS, PFMM_M2L_FUSED, PFMM_M2L_SLAB = 1, 2, 3
 
 
 class pfmm_mesh(ctypes.Structure):
@@ -42,7 +43,8 @@ class pfmm_info(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("lx", ctypes.c_int32 * 32), ("nbox", ctypes.c_int32 * 32),
                 ("pad", ctypes.c_double * 32), ("n_m2l_pairs", ctypes.c_int32), ("nearfield_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("nf_tensor_cores", ctypes.c_int32),
-                ("nearfield_v_elements", ctypes.c_int64), ("nf_dense_columns", ctypes.c_int32)]
+                ("nearfield_v_elements", ctypes.c_int64), ("nf_dense_columns", ctypes.c_int32),
+                ("m2l_engine", ctypes.c_int32 * 32)]
 
 
 class pfmm_solve_opts(ctypes.Structure):
@@ -78,6 +80,7 @@ SIGNATURES = {
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
     "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
+    "pfmm_count_apply_kernels": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_int64)]),
     "pfmm_default_solve_opts": (ctypes.c_int, [ctypes.POINTER(pfmm_solve_opts)]),
     "pfmm_solve": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, ctypes.POINTER(pfmm_solve_opts),
                                   ctypes.POINTER(pfmm_solve_info), _VP]),
@@ -218,6 +221,13 @@ def pfmm_apply_parts(h, op: int, x, f, nrhs: int, parts: int, stream=None):
     _check(lib().pfmm_apply_parts(h, int(op), _ptr(x), _ptr(f), int(nrhs), int(parts), _stream(stream)))
 
 
+def pfmm_count_apply_kernels(h, op: int, x, f, nrhs: int, parts: int = PFMM_PART_ALL) -> int:
+    """Kernels one pfmm_apply_parts call launches (counted in a captured graph, nothing runs)."""
+    n = ctypes.c_int64()
+    _check(lib().pfmm_count_apply_kernels(h, int(op), _ptr(x), _ptr(f), int(nrhs), int(parts), ctypes.byref(n)))
+    return n.value
+
+
 def pfmm_set_profiling(h, on: bool):
     _check(lib().pfmm_set_profiling(h, 1 if on else 0))
 
@@ -238,7 +248,8 @@ def pfmm_get_info(h) -> dict:
     n = i.p + 1
     return dict(p=i.p, lx=list(i.lx[:n]), nbox=list(i.nbox[:n]), pad=list(i.pad[:n]), n_m2l_pairs=i.n_m2l_pairs,
                 nearfield_bytes=i.nearfield_bytes, device_bytes=i.device_bytes, nf_tensor_cores=i.nf_tensor_cores,
-                nearfield_v_elements=i.nearfield_v_elements, nf_dense_columns=i.nf_dense_columns)
+                nearfield_v_elements=i.nearfield_v_elements, nf_dense_columns=i.nf_dense_columns,
+                m2l_engine=list(i.m2l_engine[:n]))
 
 
 def pfmm_check(h):

@@ -48,14 +48,25 @@ def test_single_rank_needs_no_collective():
     assert bench.replicas_throughput(10.0, 2.0, 1) == pytest.approx(5000.0)
 
 
-def test_launches_per_apply_matches_the_launch_list():
-    """The bench's `gpu_launches` claim counts the kernels of one V_h apply from the tree depth:
-    the 12288-triangle x 256-step workload (7 levels, tensor-core nearfield, every M2L level
-    split) launches 31, as the ncu launch list of that workload shows; without the tensor-core
-    engine the input max and split are not launched; a tree without far field launches the
-    permutes and the nearfield only."""
-    assert bench._launches_per_apply({"p": 7, "nf_tensor_cores": 3}, 1) == 31
-    assert bench._launches_per_apply({"p": 7, "nf_tensor_cores": 0}, 1) == 29
-    # more right-hand sides fill the coarse levels: levels with >= 8 CTAs per SM are not split
-    assert bench._launches_per_apply({"p": 7, "nf_tensor_cores": 3}, 2) == 30
-    assert bench._launches_per_apply({"p": 1, "nf_tensor_cores": 0}, 1) == 3
+def test_phase_rooflines_follow_the_algorithmic_work():
+    """Per-phase rooflines of the bench line: the nearfield of the 12288-triangle x 256-step
+    workload does 2 x 12288^2 x 128 x 7 flops (the d = 0..2 / 0..3 offsets of the two steps of
+    each leaf interval) on 4 x 12288^2 stored FP64 entries; M2L counts 2 x 3 x C(m_x+4, 4) x
+    (m_t+1)^2 flops per box pair; fractions divide by the given peaks."""
+    info = {"p": 7, "nbox": [1, 1, 1, 1, 8, 8, 56, 56], "n_m2l_pairs": 1000,
+            "nearfield_v_elements": 4 * 12288 * 12288, "nf_tensor_cores": 0}
+    peaks = {"hbm_gbs": 1000.0, "fp64_tflops": 1.0, "fp32_tflops": 50.0}
+    rl = bench.phase_rooflines({"nearfield": 100.0, "m2l": 2.0, "s2m": 1.0, "l2t": 1.0}, info, 8, 12288, 256, 6, 4,
+                               peaks)
+    nf = rl["nearfield"]
+    assert nf["flops"] == 2.0 * 12288 ** 2 * 128 * 7
+    assert nf["bytes"] == 8.0 * 4 * 12288 ** 2 + 16.0 * 12288 * 256
+    assert nf["tflops"] == pytest.approx(nf["flops"] / 0.1 / 1e12)
+    assert nf["frac_fp"] == pytest.approx(nf["tflops"] / 1.0) and nf["bound"] == "fp"
+    assert rl["m2l"]["flops"] == 2.0 * 3 * 210 * 25 * 1000
+    assert rl["s2m"]["frac_hbm"] == pytest.approx(rl["s2m"]["gbs"] / 1000.0)
+    # mixed precision with the tensor-core nearfield: 4 bytes per element, the FP16 peak
+    info["nf_tensor_cores"] = 3
+    rl = bench.phase_rooflines({"nearfield": 1.0}, info, 4, 12288, 256, 6, 4, dict(peaks, fp16_tflops=2000.0))
+    assert rl["nearfield"]["bytes"] == 4.0 * 4 * 12288 ** 2 + 16.0 * 12288 * 256
+    assert rl["nearfield"]["frac_fp"] == pytest.approx(rl["nearfield"]["tflops"] / 2000.0)

@@ -115,7 +115,9 @@ def test_mixed_m2l_on_8_cubed_grids_matches_fp64(mesh, n_a, Et, kw):
     opm = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, **kw)
     opd = P.Operator(V, T, 1.0, Et, precision=P.PFMM_FP64, **kw)
     info = opm.info()
-    assert any(2 ** info["lx"][l] == 8 for l in range(2, info["p"] + 1))
+    lv8 = [l for l in range(2, info["p"] + 1) if 2 ** info["lx"][l] == 8]
+    assert lv8 and all(info["m2l_engine"][l] == P.PFMM_M2L_SLAB for l in lv8), info["m2l_engine"]
+    assert all(opd.info()["m2l_engine"][l] == P.PFMM_M2L_THREE_PASS for l in lv8)
     w = torch.tensor(random_density(Et, T.shape[0], 2, seed=51), device=DEV)
     g = torch.tensor(random_density(Et, V.shape[0], 2, seed=52), device=DEV)
     for op_m, op_d, x in ((opm.V, opd.V, w), (opm.K, opd.K, g)):
@@ -123,6 +125,40 @@ def test_mixed_m2l_on_8_cubed_grids_matches_fp64(mesh, n_a, Et, kw):
         fd = op_d(x, parts=P.PFMM_PART_FAR).cpu().numpy()
         assert np.max(np.abs(fd)) > 0
         assert _rel(fm, fd) <= 1e-5, _rel(fm, fd)
+    P.pfmm_check(opm.h)
+    opm.close()
+    opd.close()
+
+
+@pytest.mark.parametrize("mesh,n_a,Et,kw,engine8", [
+    (cube_mesh, 12, 32, dict(m_t=4, m_x=6, c_st=0.1), P.PFMM_M2L_SLAB),                 # 8^3 leaf grid, radius 7
+    (cube_sphere_mesh, 16, 64, dict(m_t=4, m_x=5, c_st=0.1, n_tr=6), P.PFMM_M2L_SLAB),  # padded boxes, radius 6
+    (cube_mesh, 12, 32, dict(m_t=4, m_x=7, c_st=0.1), P.PFMM_M2L_THREE_PASS),           # m_x = 7: three passes
+])
+def test_8_cubed_grids_match_oracle(mesh, n_a, Et, kw, engine8):
+    """Trees whose finest levels hold 8^3 grids of boxes (the shape of the 49152-triangle
+    cube-sphere): the far field and the whole product of the mixed handle (slab M2L on the 8^3
+    levels) within 1e-5, and of the FP64 handle (three separable passes) within 1e-12, of the
+    oracle's pFMM (Alg. 2, literal Eq. m2l) on 8 sampled target triangles, V and K."""
+    V, T = mesh(n_a)
+    opm = P.Operator(V, T, 1.0, Et, precision=P.PFMM_MIXED, **kw)
+    opd = P.Operator(V, T, 1.0, Et, precision=P.PFMM_FP64, **kw)
+    info = opm.info()
+    lv8 = [l for l in range(2, info["p"] + 1) if 2 ** info["lx"][l] == 8]
+    assert lv8 and all(info["m2l_engine"][l] == engine8 for l in lv8), info["m2l_engine"]
+    Pr = O.make_problem(V, T, 1.0, Et, **kw)
+    rows = sample_triangles(T.shape[0], 8, seed=61)
+    w = random_density(Et, T.shape[0], 1, seed=62)
+    g = random_density(Et, V.shape[0], 1, seed=63)
+    for op_id, x in ((0, w), (1, g)):
+        xt = torch.tensor(x, device=DEV)
+        for parts in (P.PFMM_PART_FAR, P.PFMM_PART_ALL):
+            ref = O.pfmm_apply(Pr, op_id, x[0], targets=rows, parts=parts)
+            fm = (opm.V(xt, parts=parts) if op_id == 0 else opm.K(xt, parts=parts)).cpu().numpy()[0]
+            fd = (opd.V(xt, parts=parts) if op_id == 0 else opd.K(xt, parts=parts)).cpu().numpy()[0]
+            assert np.max(np.abs(ref[:, rows])) > 0
+            assert _rel(fd, ref, rows) <= 1e-12, (op_id, parts, _rel(fd, ref, rows))
+            assert _rel(fm, ref, rows) <= 1e-5, (op_id, parts, _rel(fm, ref, rows))
     P.pfmm_check(opm.h)
     opm.close()
     opd.close()
@@ -166,13 +202,26 @@ def test_config2_sampled_rows(cfg2, op_id):
     V, T, Et, ops, Pr = cfg2
     ncol = T.shape[0] if op_id == 0 else V.shape[0]
     x = random_density(Et, ncol, 1, seed=2025 + op_id)
-    rows = sample_triangles(T.shape[0], 6, seed=11 + op_id)
+    rows = sample_triangles(T.shape[0], 12, seed=11 + op_id)
     ref = O.pfmm_apply(Pr, op_id, x[0], targets=rows)
     xt = torch.tensor(x, device=DEV)
     f64 = (ops[P.PFMM_FP64].V(xt) if op_id == 0 else ops[P.PFMM_FP64].K(xt)).cpu().numpy()[0]
     f32 = (ops[P.PFMM_MIXED].V(xt) if op_id == 0 else ops[P.PFMM_MIXED].K(xt)).cpu().numpy()[0]
     assert _rel(f64, ref, rows) <= 1e-12
     assert _rel(f32, ref, rows) <= 1e-5
+
+
+def test_config2_kernel_count(cfg2):
+    """pfmm_count_apply_kernels (a captured graph of one apply) counts the kernels the bench
+    claims per step: 31 for the mixed V_h apply of the 12288-triangle x 256-step workload, as the
+    ncu launch list of that workload shows; the count does not depend on the call."""
+    V, T, Et, ops, Pr = cfg2
+    x = torch.zeros((1, Et, T.shape[0]), dtype=torch.float64, device=DEV)
+    f = torch.empty_like(x)
+    assert P.pfmm_count_apply_kernels(ops[P.PFMM_MIXED].h, 0, x, f, 1) == 31
+    n64 = P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1)
+    assert n64 >= 20 and n64 == P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1)
+    assert P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1, P.PFMM_PART_NEAR) <= 4
 
 
 # ---- tensor-core nearfield (scaled FP16 hi/lo split, mixed mode) -------------------------------

@@ -89,3 +89,22 @@ def test_K_steady_state_gauss_law():
     u = math.sqrt(3.0) / (2 * math.sqrt((Tend - h)))
     tail = math.erf(u) - 2 * u * math.exp(-u * u) / math.sqrt(math.pi)
     assert np.max(np.abs(rows + 0.5)) < 2e-3 + 4 * tail
+
+
+def test_sampled_rows_match_the_full_blocks_and_the_pfmm_nearfield():
+    """The row-sampled assembly returns exactly the listed rows of the full Toeplitz blocks, and
+    their product restricted to the nearfield offsets (d <= ls + k mod ls) equals the nearfield
+    part of the oracle's pFMM (Alg. 2, last loop) on those rows; with all offsets it equals the
+    dense product."""
+    V, T = cube_mesh(2)
+    Et, h = 16, 1.0 / 16
+    rows = np.array([0, 5, 11, 30, 47])
+    A = O.assemble_V(V, T, h, nd=Et)
+    R = O.assemble_V_rows(V, T, h, rows, nd=Et)
+    assert np.array_equal(A[:, rows, :], R)
+    x = np.random.default_rng(3).standard_normal((Et, T.shape[0]))
+    assert np.allclose(O.toeplitz_rows_apply(R, x), O.toeplitz_apply(A, x)[:, rows], rtol=0, atol=1e-14)
+    Pr = O.make_problem(V, T, 1.0, Et, m_t=3, m_x=3, c_st=1.0)
+    near = O.pfmm_apply(Pr, 0, x, targets=rows, parts=1)[:, rows]
+    mine = O.toeplitz_rows_apply(R[:4], x, leaf_steps=2)
+    assert np.max(np.abs(mine - near)) <= 1e-14 * np.max(np.abs(near))

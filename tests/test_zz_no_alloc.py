@@ -15,11 +15,21 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-@pytest.mark.parametrize("precision", [P.PFMM_FP64, P.PFMM_MIXED])
-def test_noalloc_matches_apply_V_on_two_calls(precision):
-    V, T = cube_mesh(4)
-    Et, nrhs = 16, 2
-    op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=4, c_st=0.25, precision=precision)
+@pytest.mark.parametrize("precision,n_a,Et,kw", [
+    (P.PFMM_FP64, 4, 16, dict(m_t=4, m_x=4, c_st=0.25)),
+    (P.PFMM_MIXED, 4, 16, dict(m_t=4, m_x=4, c_st=0.25)),
+    (P.PFMM_MIXED, 4, 16, dict(m_t=4, m_x=4, c_st=1.0)),   # tensor-core nearfield, parts in the array
+    (P.PFMM_MIXED, 12, 32, dict(m_t=4, m_x=6, c_st=0.1)),  # 8^3 leaf grid: slab M2L, no T1 / T2 needed
+])
+def test_noalloc_matches_apply_V_on_two_calls(precision, n_a, Et, kw):
+    V, T = cube_mesh(n_a)
+    nrhs = 2
+    op = P.Operator(V, T, 1.0, Et, precision=precision, **kw)
+    if precision == P.PFMM_MIXED and kw["c_st"] == 1.0:
+        assert op.info()["nf_tensor_cores"] & 1
+    if n_a == 12:
+        info = op.info()
+        assert P.PFMM_M2L_SLAB in info["m2l_engine"]
     for seed in (11, 12):  # two calls in a row: the second must not see the first's contents
         w = torch.tensor(random_density(Et, T.shape[0], nrhs, seed=seed), device=DEV)
         ref = torch.empty_like(w)
