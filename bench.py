@@ -138,9 +138,11 @@ def _dense_rows_error(V, T, Et, w, outs, n_rows=8, nthreads=0):
 
 
 def phase_rooflines(phases, info, es, nt, Et, mx, mt, peaks):
-    """Algorithmic work per apply of every phase (the formulas of the design doc's kernel table), the
-    rate it achieved in its measured phase time, and the fraction of the relevant peak.
-    peaks: hbm_gbs, fp64_tflops, fp32_tflops (and fp16_tflops for a tensor-core nearfield)."""
+    """Algorithmic work per apply of every phase, the rate it achieved in its measured phase time
+    and the fraction of the relevant peak.  S2M / L2T: 2 E_t E_x n_kappa + 4 (leaves) n_a n_kappa
+    flops; M2L: the separable passes' flops reported by the library (info m2l_flops); nearfield:
+    2 sum_t |D(t)| nnz(A_d) flops on the stored elements.  peaks: hbm_gbs, fp64_tflops,
+    fp32_tflops (and fp16_tflops for a tensor-core nearfield)."""
     from math import comb
 
     nk, na = comb(mx + 3, 3), mt + 1
@@ -164,7 +166,7 @@ def phase_rooflines(phases, info, es, nt, Et, mx, mt, peaks):
     put("s2m", s2m_f, es * dof + es * nt * nk + es * nleaf * na * nk, phases.get("s2m"), fma)
     put("l2t", s2m_f, 16.0 * dof + es * nt * nk + es * nleaf * na * nk, phases.get("l2t"), fma)
     if p >= 2:
-        put("m2l", 2.0 * 3 * comb(mx + 4, 4) * na * na * info["n_m2l_pairs"],
+        put("m2l", info["m2l_flops"],
             2.0 * es * sum(info["nbox"][l] * 2 ** l for l in range(2, p + 1)) * na * nk, phases.get("m2l"), fma)
     nel = info["nearfield_v_elements"]
     nf_flops = 2.0 * (nel / 4) * (Et // 2) * 7  # 2 sum_t |D(t)| nnz(A_d): |D| = 3, 4 on the two steps

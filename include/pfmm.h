@@ -116,6 +116,10 @@ typedef struct pfmm_info {
     int32_t nf_dense_columns;     /* 1: the panels share one column space (all triangles / nodes,
                                      zero where the source is not near), 0: compact per panel */
     int32_t m2l_engine[32];       /* M2L kernel of level l (l = 2 .. p; 0 elsewhere): PFMM_M2L_* */
+    double m2l_flops;             /* flops of one rhs's M2L in the separable form (Eq. m2l with
+                                     Eq. exp_coeffs_3d applied one direction at a time over the
+                                     full box grid of every level, all interval pairs of Eq.
+                                     03:ILtemp and time nodes): 2 x FMAs of the three passes */
 } pfmm_info;
 
 /* M2L kernels (pfmm_info.m2l_engine): the three separable passes through a global workspace

@@ -14,6 +14,7 @@
 #include "handle.h"
 #include "kernels.h"
 #include "nf_tc.h"
+#include "nf_crt.h"
 #include "pfmm_internal.h"
 
 using namespace pfmm;
@@ -233,6 +234,16 @@ int ensure_workspace(pfmm_handle *H, int nrhs)
             (rc = H->alloc(&H->d_wmax, (size_t)nrhs)))
             return rc;
     }
+    H->release(H->d_Wres);
+    H->release(H->d_res8);
+    H->d_Wres = nullptr;
+    H->d_res8 = nullptr;
+    if (H->crtV || H->crtK) {
+        const size_t nw = (size_t)kCrtModuli * nrhs * H->Et * std::max(H->colsV_u, H->colsK_u);
+        if ((rc = H->alloc(&H->d_Wres, nw)) || (rc = H->alloc(&H->d_res8, (size_t)kCrtModuli * n_in)) ||
+            (!H->d_wmax && (rc = H->alloc(&H->d_wmax, (size_t)nrhs))))
+            return rc;
+    }
     H->ws_nrhs = nrhs;
     return PFMM_OK;
 }
@@ -299,6 +310,43 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
     if (launch_nf_apply_tc(op == 0 ? H->mapAVhi : H->mapAKhi, op == 0 ? H->mapAVlo : H->mapAKlo, mWhi, mWlo, P, H->nsm,
                            st))
         return fail(PFMM_ERR_CUDA, std::string("tensor-core nearfield launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return PFMM_OK;
+}
+
+// FP64 exact nearfield: residues of x, the residue products on the tensor cores, their FP64
+// combination into fint (every element written)
+int pfmm::run_nf_crt(pfmm_handle *H, int op, const double *x, int nrhs, double *fint, cudaStream_t st)
+{
+    int rc;
+    const int cols = op == 0 ? H->colsV_u : H->colsK_u, b = op == 0 ? H->crt_bV : H->crt_bK;
+    launch_crt_split_input(x, op == 0 ? H->d_perm : nullptr, op == 0 ? H->nt : H->nv, cols, nrhs, H->Et, b, H->d_Wres,
+                           H->d_wmax, st);
+    const int nint = H->Et / 2;
+    uint64_t dims[5] = {(uint64_t)cols, 2, (uint64_t)nint, (uint64_t)nrhs, (uint64_t)kCrtModuli};
+    uint64_t str[4] = {(uint64_t)cols * 2, (uint64_t)cols * 4, (uint64_t)cols * 4 * nint,
+                       (uint64_t)cols * 4 * nint * nrhs};
+    uint32_t box[5] = {64, 1, 128, 1, 1};
+    CUtensorMap mW;
+    if ((rc = encode_map(&mW, H->d_Wres, 5, dims, str, box))) return rc;
+    NfCrtParams P{};
+    P.panels = H->d_panels;
+    P.tiles = H->d_tiles128;
+    P.ntiles = H->ntiles128;
+    P.nib = (nint + 127) / 128;
+    P.nkb = cols / 64;
+    P.nrhs = nrhs;
+    P.nitems = (kCrtModuli / 2) * nrhs * P.ntiles * P.nib;
+    P.cols_pad = cols;
+    P.kop = op;
+    P.nint = nint;
+    P.Et = H->Et;
+    P.nt = H->nt;
+    P.res = H->d_res8;
+    P.err = H->d_err;
+    if (launch_nf_apply_crt(op == 0 ? H->mapAVres : H->mapAKres, mW, P, H->nsm, st))
+        return fail(PFMM_ERR_CUDA, std::string("FP64 tensor-core nearfield launch: ") +
+                                       cudaGetErrorString(cudaGetLastError()));
+    launch_crt_combine(H->d_res8, nrhs, H->Et, H->nt, op == 0 ? H->d_rexpV : H->d_rexpK, H->d_wmax, b, fint, st);
     return PFMM_OK;
 }
 
@@ -375,6 +423,60 @@ int pfmm_default_params(pfmm_params *p)
     p->quad_regular = 3;
     p->quad_singular = 6;
     p->nf_engine = PFMM_NF_AUTO;
+    return PFMM_OK;
+}
+
+// FP64 mode on panels that span all columns: per-row exponents and the residues of the scaled,
+// rounded panels for the exact tensor-core nearfield.  Skipped (CUDA-core FP64 engine kept) when
+// the residues (32 bytes per stored element) would not leave room on the device.
+static int build_crt(pfmm_handle *H, const Tree &t, bool fullV, bool fullK, cudaStream_t st)
+{
+    using namespace pfmm;
+    if (crt_upload_constants(st)) return fail(PFMM_ERR_CUDA, "CRT constants upload failed");
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t need = (fullV ? (size_t)t.sizeV : 0) * 2 * kCrtModuli + (fullK ? (size_t)t.sizeK : 0) * 2 * kCrtModuli;
+    if (need > free_b / 10 * 7) return PFMM_OK;
+    const int nd = H->nd, npanel = (int)t.panels.size();
+    unsigned long long *rowmax = nullptr;
+    int rc;
+    if ((rc = H->alloc(&rowmax, (size_t)H->nt))) return rc;
+    for (int op = 0; op < 2; ++op) {
+        if (!(op == 0 ? fullV : fullK)) continue;
+        const int cols = op == 0 ? t.panels[0].colsV_pad : t.panels[0].colsK_pad;
+        const size_t n = op == 0 ? (size_t)t.sizeV : (size_t)t.sizeK;
+        const int b = crt_bits(4ll * cols);
+        int *rexp = nullptr, *rexpR = nullptr;
+        uint16_t *res = nullptr;
+        if ((rc = H->alloc(&rexp, (size_t)H->nt)) || (rc = H->alloc(&rexpR, n / cols)) ||
+            (rc = H->alloc(&res, n * kCrtModuli)))
+            return rc;
+        const double *A = (const double *)(op == 0 ? H->d_AV : H->d_AK);
+        launch_crt_row_exps(A, H->d_panels, npanel, op, nd, cols, b, rowmax, H->nt, rexp, rexpR, st);
+        launch_crt_split_panel(A, rexpR, n, cols, res, st);
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        H->release(rexpR);
+        // [modulus][block][64 rows][64 columns]
+        uint64_t dims[4] = {64, 64, (uint64_t)(n / 4096), (uint64_t)kCrtModuli}, str[3] = {128, 8192, (n / 4096) * 8192};
+        uint32_t box[4] = {64, 64, 1, 1};
+        if (op == 0) {
+            H->colsV_u = cols;
+            H->crt_bV = b;
+            H->d_AVres = res;
+            H->d_rexpV = rexp;
+            if ((rc = encode_map(&H->mapAVres, res, 4, dims, str, box))) return rc;
+            H->crtV = true;
+        } else {
+            H->colsK_u = cols;
+            H->crt_bK = b;
+            H->d_AKres = res;
+            H->d_rexpK = rexp;
+            if ((rc = encode_map(&H->mapAKres, res, 4, dims, str, box))) return rc;
+            H->crtK = true;
+        }
+    }
+    H->release(rowmax);
     return PFMM_OK;
 }
 
@@ -666,8 +768,9 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         int cc_major = 0, cc_minor = 0;
         CK(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, dev));
         CK(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
-        bool eligible = !H->otf && H->mixed && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 &&
-                        encode_fn();
+        // tensor cores for the stored panels when every panel spans all columns: the FP16 split
+        // (mixed mode) or the exact residue arithmetic (FP64 mode)
+        bool eligible = !H->otf && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 && encode_fn();
         bool fullV = eligible, fullK = eligible;
         for (const Panel &P : t.panels) {
             fullV = fullV && P.ncolV == nt && P.colsV_pad == t.panels[0].colsV_pad;
@@ -690,6 +793,10 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
                 }
             H->ntiles128 = (int)t128.size() / 2;
             if ((rc = upload(H, &H->d_tiles128, t128, st))) return rc;
+        }
+        if (!H->mixed && (fullV || fullK)) {
+            if ((rc = build_crt(H, t, fullV, fullK, st))) return rc;
+            fullV = fullK = false;
         }
         if (fullV) {
             H->colsV_u = t.panels[0].colsV_pad;
@@ -819,8 +926,11 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     }
     mark(1);
     const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK) && !H->nf_cuda_cores;
+    const bool crt = (parts & PFMM_PART_NEAR) && (op == 0 ? H->crtV : H->crtK) && !H->nf_cuda_cores;
     if (tc) {
         if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_wmax, H->d_fint, st))) return rc;
+    } else if (crt) {
+        if ((rc = pfmm::run_nf_crt(H, op, x, nrhs, H->d_fint, st))) return rc;
     } else if ((parts & PFMM_PART_NEAR) && H->otf) {
         CK(cudaMemsetAsync(H->d_fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
         if ((rc = pfmm::run_nf_otf(H, op, xin, ncolg, H->Et, H->ls, nrhs, 1 << 30, H->d_fint, st))) return rc;
@@ -956,9 +1066,26 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     info->nearfield_bytes = h->otf ? h->otf_bytes
                                    : t.sizeV * (h->tcV ? 4 : (int64_t)h->es) + t.sizeK * (h->tcK ? 4 : (int64_t)h->es);
     info->device_bytes = h->dev_bytes;
-    info->nf_tensor_cores = (h->tcV ? 1 : 0) | (h->tcK ? 2 : 0);
+    info->nf_tensor_cores = (h->tcV || h->crtV ? 1 : 0) | (h->tcK || h->crtK ? 2 : 0);
+    if (h->crtV || h->crtK)
+        info->nearfield_bytes += (h->crtV ? t.sizeV : 0) * 2 * pfmm::kCrtModuli + (h->crtK ? t.sizeK : 0) * 2 * pfmm::kCrtModuli;
     info->nearfield_v_elements = t.sizeV;
     info->nf_dense_columns = t.dense_cols ? 1 : 0;
+    // separable M2L work per level: pass 1 over cells (X1, Y2, Y3) and the budget chains of every
+    // triple (ne entries), pass 2 over cells (X1, X2, Y3) and C(m_x+5, 5) (budget, k2) pairs, pass 3
+    // over the non-empty target boxes and ne (nu, k3) pairs; each sums over the R cells of one
+    // direction within the interaction radius (R averaged over the target coordinate)
+    double c5 = 1.0;
+    for (int i = 1; i <= 5; ++i) c5 = c5 * (h->mx + i) / i;
+    for (int l = 2; l <= h->p && l < (int)h->dl.size(); ++l) {
+        const pfmm::DevLevel &L = h->dl[l];
+        double R = 0.0;
+        for (int X = 0; X < L.G; ++X) R += std::min(L.G - 1, X + L.ntr) - std::max(0, X - L.ntr) + 1;
+        R /= L.G;
+        const double pairs = L.kptr_host.empty() ? 0.0 : (double)L.kptr_host[L.nint], na2 = (double)h->na * h->na;
+        const double G3 = (double)L.G * L.G * L.G;
+        info->m2l_flops += 2.0 * pairs * na2 * R * (G3 * h->ne + G3 * c5 + (double)L.nbox * h->ne);
+    }
     for (int l = 2; l <= h->p && l < 32 && l < (int)h->dl.size(); ++l) {
         const int e = pfmm::m2l_engine(h->mixed, h->dl[l].G, h->nk, h->ne, h->mx);
         info->m2l_engine[l] = e == pfmm::kM2LFused ? PFMM_M2L_FUSED : (e == pfmm::kM2LSlab ? PFMM_M2L_SLAB : PFMM_M2L_THREE_PASS);

@@ -24,6 +24,8 @@ namespace pfmm {
 // whi, wlo: FP16 input parts ([nrhs][E_t][cols] each); wmax: nrhs words of scratch
 int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned long long *wmax,
               double *fint, cudaStream_t st);
+// FP64 mode: exact residue-arithmetic nearfield of op on the tensor cores into fint (overwritten)
+int run_nf_crt(pfmm_handle *H, int op, const double *x, int nrhs, double *fint, cudaStream_t st);
 // size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
 int ensure_ws(pfmm_handle *H, int nrhs);
 // the on-the-fly nearfield of op into fint (+=): arguments of launch_nf_otf for this handle
@@ -89,6 +91,14 @@ struct pfmm_handle {
     int *d_tiles128 = nullptr;
     int ntiles128 = 0, nsm = 0;
     int *d_err = nullptr;           // bounded-wait error word of the device kernels
+    // FP64 mode, exact residue-arithmetic nearfield on the tensor cores (k_nf_crt.cu)
+    bool crtV = false, crtK = false;
+    int crt_bV = 0, crt_bK = 0;                       // fixed-point bits of the operands
+    uint16_t *d_AVres = nullptr, *d_AKres = nullptr;  // FP16 residues [16][panel elements]
+    int *d_rexpV = nullptr, *d_rexpK = nullptr;       // row scale exponents by triangle
+    CUtensorMap mapAVres{}, mapAKres{};
+    uint16_t *d_Wres = nullptr;                       // input residues [16][nrhs][E_t][cols]
+    unsigned char *d_res8 = nullptr;                  // output residues [16][nrhs][E_t][E_x]
     uint16_t *d_Whi = nullptr, *d_Wlo = nullptr;  // FP16 input parts
     unsigned long long *d_wmax = nullptr;          // [ws_nrhs] max |input| per rhs (FP64 bits)
     size_t w_elems = 0;

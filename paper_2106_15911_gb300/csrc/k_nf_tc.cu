@@ -387,6 +387,12 @@ void launch_split_input(const double *x, const int *perm, int ncol, int ncol_pad
                                                                    (__half *)lo, per_rhs, total, wmax);
 }
 
+void launch_absmax_input(const double *x, size_t per_rhs, int nrhs, unsigned grid_x, unsigned long long *wmax,
+                         cudaStream_t st)
+{
+    k_absmax_input<<<dim3(grid_x, nrhs), 256, 0, st>>>(x, per_rhs, wmax);
+}
+
 size_t nf_tc_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + 1024 + 256; }
 
 int launch_nf_apply_tc(const CUtensorMap &Ahi, const CUtensorMap &Alo, const CUtensorMap &Whi, const CUtensorMap &Wlo,

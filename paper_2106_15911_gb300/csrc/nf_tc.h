@@ -44,6 +44,9 @@ struct NfTcParams {
     int *err;           // set non-zero when a bounded wait gave up
 };
 
+// per-rhs max |x| of x [nrhs][per_rhs] FP64 into wmax (FP64 bits, accumulated with atomicMax: zero it first)
+void launch_absmax_input(const double *x, size_t per_rhs, int nrhs, unsigned grid_x, unsigned long long *wmax,
+                         cudaStream_t st);
 size_t nf_tc_smem_bytes();
 int launch_nf_apply_tc(const CUtensorMap &Ahi, const CUtensorMap &Alo, const CUtensorMap &Whi, const CUtensorMap &Wlo,
                        const NfTcParams &P, int nsm, cudaStream_t st);

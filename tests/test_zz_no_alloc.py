@@ -39,7 +39,11 @@ def test_noalloc_matches_apply_V_on_two_calls(precision, n_a, Et, kw):
         torch.cuda.synchronize()
         a, b = out.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a))
-        assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= 1e-12
+        # FP64: the same arithmetic up to summation order; mixed: the two entry points may take
+        # different S2M / L2T forms (the two-stage form needs a workspace that the static array
+        # offers and the per-handle one may not), which add in different FP32 orders
+        tol = 1e-12 if precision == P.PFMM_FP64 else 1e-6
+        assert np.max(np.abs(a - b)) / np.max(np.abs(b)) <= tol
     op.close()
 
 
