@@ -428,9 +428,9 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6, solve=True):
 
 
 def _profile_case(dev, case):
-    """Small cases for ncu captures of kernels the matvec does not launch: the learned
-    preconditioner's layers (`mpnn`), its compiled form (`mpnn_compiled`), the on-the-fly
-    nearfield (`otf`), the slab M2L of 8^3 grids (`m2l_slab`).  3072-triangle cube; 128 steps
+    """Small cases for ncu captures: the learned preconditioner's layers (`mpnn`), its compiled
+    form (`mpnn_compiled`), the on-the-fly nearfield (`otf`), the slab M2L of 8^3 grids
+    (`m2l_slab`), the FP64 residue-arithmetic nearfield (`crt`, 3072 triangles x 128 steps).  3072-triangle cube; 128 steps
     (network) or 32 steps (on-the-fly); 1728-triangle cube x 32 steps with an 8^3 leaf grid
     (c_st 0.1, interaction radius 7) for the slab M2L, far field only."""
     import numpy as np
@@ -451,6 +451,11 @@ def _profile_case(dev, case):
         v = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
         z = torch.empty_like(v)
         run = lambda: net.apply(v, z)  # noqa: E731
+    elif case == "crt":
+        Et = 128
+        op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_FP64)
+        w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
+        run = lambda: op.V(w, parts=P.PFMM_PART_NEAR)  # noqa: E731
     elif case == "m2l_slab":
         V, T = cube_mesh(12)
         Et = 32
@@ -557,7 +562,7 @@ def main():
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
     ap.add_argument("--config5-matvec", action="store_true",
                     help="with --config5: the build and matvecs only (no recording, training or solves)")
-    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab"], default=None,
+    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt"], default=None,
                     help="profiling only: run one small case of a kernel outside the matvec and exit")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
@@ -672,7 +677,21 @@ def main():
     rl = phase_rooflines(phases, info, es, nt, ET, M_X, M_T, peaks)
     nf = rl["nearfield"]
     tc = head == P.PFMM_MIXED and bool(info["nf_tensor_cores"] & 1)
-    if tc:
+    crt = head == P.PFMM_FP64 and bool(info["nf_tensor_cores"] & 1)
+    if crt:
+        # FP64 nearfield as exact residue products on the tensor cores: 16 FP16 products per
+        # product of the method, 16 FP16 residues (32 bytes) per stored element read from HBM
+        nel = info["nearfield_v_elements"]
+        byts = 32.0 * nel + 16.0 * dof
+        gbs = byts / (nf["ms"] * 1e-3) / 1e9
+        executed = 16.0 * nf["flops"] / (nf["ms"] * 1e-3) / 1e12
+        roofline = {"bound": "hbm", "kernel": "k_nf_apply_crt", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": "measured copy rate (of measured)", "bytes_per_launch": byts,
+                    "ms_per_launch": nf["ms"],
+                    "tensor": {"executed_fp16_tflops": executed, "frac_of_fp16_peak": executed / peaks["fp16_tflops"]},
+                    "method_fp64_tflops": nf["tflops"], "fp64_pipe_tflops": peaks["fp64_tflops"]}
+    elif tc:
         roofline = {"bound": "hbm", "kernel": "k_nf_apply_tc", "achieved": nf["gbs"], "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": nf["frac_hbm"], "traffic": None,
                     "peak_source": "measured copy rate (of measured)", "bytes_per_launch": nf["bytes"],

@@ -221,7 +221,9 @@ def test_config2_kernel_count(cfg2):
     assert P.pfmm_count_apply_kernels(ops[P.PFMM_MIXED].h, 0, x, f, 1) == 31
     n64 = P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1)
     assert n64 >= 20 and n64 == P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1)
-    assert P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1, P.PFMM_PART_NEAR) <= 4
+    # FP64 nearfield alone: permute in, input max and residues, residue products, combination,
+    # permute out
+    assert P.pfmm_count_apply_kernels(ops[P.PFMM_FP64].h, 0, x, f, 1, P.PFMM_PART_NEAR) == 6
 
 
 # ---- tensor-core nearfield (scaled FP16 hi/lo split, mixed mode) -------------------------------
