@@ -47,7 +47,7 @@ extern "C" {
 #define PFMM_ERR_UNSUPPORTED (-7)  /* a valid request this build does not implement */
 
 /* precision modes */
-#define PFMM_FP64 0   /* every phase in FP64 */
+#define PFMM_FP64 0   /* FP64 accuracy in every phase (see pfmm_params.fp64_native for how) */
 #define PFMM_MIXED 1  /* FP32 regular-pair quadrature and FP32 FMM passes; FP64 singular
                          quadrature; FP64 output accumulation.  The stored nearfield is applied
                          on the tensor cores (default engine) as three FP16 products of scaled
@@ -95,9 +95,15 @@ typedef struct pfmm_params {
     int32_t nearfield;  /* PFMM_NEARFIELD_STORED (default) or PFMM_NEARFIELD_ONTHEFLY */
     int32_t quad_regular;  /* Gauss points per direction of the collapsed triangle rule */
     int32_t quad_singular; /* Gauss points per direction of the Sauter-Schwab rule */
-    int32_t nf_engine;  /* PFMM_NF_AUTO: tensor cores (scaled two-part FP16 split, FP32 accumulation,
-                           mixed mode) where the panel layout allows, else CUDA cores;
-                           PFMM_NF_CUDA_CORES: always CUDA cores */
+    int32_t nf_engine;  /* PFMM_NF_AUTO: tensor cores where the panel layout allows (mixed mode: the
+                           scaled two-part FP16 split with FP32 accumulation; FP64 mode: exact
+                           integer products modulo 16 primes, combined by the Chinese remainder
+                           theorem), else CUDA cores; PFMM_NF_CUDA_CORES: always CUDA cores */
+    int32_t fp64_native;/* FP64 mode only.  0 (default): FP64-accurate arithmetic on the fast units --
+                           the nearfield as exact residue products on the tensor cores (see
+                           nf_engine) and the FMM passes in double-FP32 arithmetic (pairs of FP32
+                           numbers, about 48 significant bits, on the FP32 pipe); 1: every phase on
+                           the FP64 pipe (reference mode, about 50x slower on GB300) */
 } pfmm_params;
 
 typedef struct pfmm_handle pfmm_handle;
@@ -131,7 +137,8 @@ typedef struct pfmm_info {
 
 /* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,
  * leaf_steps = 2, leaf_tris = 16, FP64, stored nearfield, quad_regular = 3,
- * quad_singular = 6, nf_engine = PFMM_NF_AUTO.  Returns PFMM_OK or PFMM_ERR_INVALID_ARG (p NULL). */
+ * quad_singular = 6, nf_engine = PFMM_NF_AUTO, fp64_native = 0.  Returns PFMM_OK or
+ * PFMM_ERR_INVALID_ARG (p NULL). */
 int pfmm_default_params(pfmm_params *p);
 
 /* Build the box cluster tree (Section 3.2, Alg. 1), the nearfield and interaction lists

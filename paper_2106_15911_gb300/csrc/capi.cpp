@@ -171,10 +171,15 @@ int upload(pfmm_handle *H, T_ **dst, const std::vector<T_> &src, cudaStream_t st
     return PFMM_OK;
 }
 
-// upload a host FP64 table in the handle's arithmetic type R
+// upload a host FP64 table in the arithmetic type of the handle's FMM passes (FP32, FP64, or
+// double-FP32 pairs converted in place)
 int upload_R(pfmm_handle *H, void **dst, const std::vector<double> &src, cudaStream_t st)
 {
-    if (!H->mixed) return upload(H, (double **)dst, src, st);
+    if (!H->mixed) {
+        int rc = upload(H, (double **)dst, src, st);
+        if (!rc && H->fprec == 2) launch_to_df64((double *)*dst, src.size(), st);
+        return rc;
+    }
     std::vector<float> f(src.begin(), src.end());
     return upload(H, (float **)dst, f, st);
 }
@@ -183,6 +188,7 @@ int upload_R(pfmm_handle *H, void **dst, const std::vector<double> &src, cudaStr
 int device_to_R(pfmm_handle *H, void **dst, double *src, size_t n, cudaStream_t st)
 {
     if (!H->mixed) {
+        if (H->fprec == 2) launch_to_df64(src, n, st);
         *dst = src;
         return PFMM_OK;
     }
@@ -423,6 +429,7 @@ int pfmm_default_params(pfmm_params *p)
     p->quad_regular = 3;
     p->quad_singular = 6;
     p->nf_engine = PFMM_NF_AUTO;
+    p->fp64_native = 0;
     return PFMM_OK;
 }
 
@@ -497,6 +504,7 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         return fail(PFMM_ERR_UNSUPPORTED, "the on-the-fly nearfield supports leaf_steps <= 4");
     H->mixed = prm->precision == PFMM_MIXED;
     H->es = H->mixed ? 4 : 8;
+    H->fprec = H->mixed ? 1 : (prm->fp64_native ? 0 : 2);
     std::string err;
     int rc = build_tree(*mesh, *prm, H->tree, err);
     if (rc) return fail(rc, err);
@@ -770,7 +778,8 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         CK(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
         // tensor cores for the stored panels when every panel spans all columns: the FP16 split
         // (mixed mode) or the exact residue arithmetic (FP64 mode)
-        bool eligible = !H->otf && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 && encode_fn();
+        bool eligible = !H->otf && H->ls == 2 && prm->nf_engine == PFMM_NF_AUTO && cc_major == 10 && encode_fn() &&
+                        (H->mixed || !prm->fp64_native);
         bool fullV = eligible, fullK = eligible;
         for (const Panel &P : t.panels) {
             fullV = fullV && P.ncolV == nt && P.colsV_pad == t.panels[0].colsV_pad;
@@ -946,23 +955,23 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     bool far = (parts & PFMM_PART_FAR) && p >= 2;
     char *mu = (char *)H->d_mu, *lam = (char *)H->d_lam;
     if (far) {
-        launch_s2m(H->mixed, op == 1, xin, ncolg, op == 0 ? H->d_Sx : H->d_SK, H->d_St,
+        launch_s2m(H->fprec, op == 1, xin, ncolg, op == 0 ? H->d_Sx : H->d_SK, H->d_St,
                    mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st, H->d_T1, H->ws_m2l);
     }
     mark(3);
     if (far)
-        for (int l = p - 1; l >= 2; --l) launch_m2m(H->mixed, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
+        for (int l = p - 1; l >= 2; --l) launch_m2m(H->fprec, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
     mark(4);
     if (far)
         for (int l = 2; l <= p; ++l)
-            if (launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, H->d_T1, H->d_T2, H->ws_m2l, st))
+            if (launch_m2l(H->fprec, H->dl[l], l, mu, lam, nrhs, g, H->d_T1, H->d_T2, H->ws_m2l, st))
                 return fail(PFMM_ERR_OOM, "M2L workspace too small for one interval");
     mark(5);
     if (far)
-        for (int l = 3; l <= p; ++l) launch_l2l(H->mixed, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
+        for (int l = 3; l <= p; ++l) launch_l2l(H->fprec, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
     mark(6);
     if (far)
-        launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, H->d_fint, nrhs, g, 0, st, H->d_T1,
+        launch_l2t(H->fprec, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, H->d_fint, nrhs, g, 0, st, H->d_T1,
                    H->ws_m2l);
     mark(7);
     launch_permute_out(H->d_fint, f, nrhs, g, st);
@@ -1087,7 +1096,7 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
         info->m2l_flops += 2.0 * pairs * na2 * R * (G3 * h->ne + G3 * c5 + (double)L.nbox * h->ne);
     }
     for (int l = 2; l <= h->p && l < 32 && l < (int)h->dl.size(); ++l) {
-        const int e = pfmm::m2l_engine(h->mixed, h->dl[l].G, h->nk, h->ne, h->mx);
+        const int e = pfmm::m2l_engine(h->fprec, h->dl[l].G, h->nk, h->ne, h->mx);
         info->m2l_engine[l] = e == pfmm::kM2LFused ? PFMM_M2L_FUSED : (e == pfmm::kM2LSlab ? PFMM_M2L_SLAB : PFMM_M2L_THREE_PASS);
     }
     return PFMM_OK;

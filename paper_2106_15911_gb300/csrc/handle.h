@@ -48,6 +48,7 @@ struct pfmm_handle {
     pfmm_params prm{};
     pfmm::Tree tree;
     bool mixed = false;
+    int fprec = 0;  // arithmetic of the FMM passes: 0 FP64, 1 FP32 (mixed), 2 double-FP32 (FP64 mode)
     int ls = 2, nd = 4, na = 0, nk = 0, mx = 0, p = 0;
     size_t es = 8;  // bytes of R
     std::vector<void *> allocs;

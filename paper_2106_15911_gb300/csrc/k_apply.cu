@@ -7,13 +7,16 @@
 //   mu_l[r][k][b][a][i]   moments of level l: interval k, spatial box b, time node a, graded
 //                         multi-index i (all kappa with |kappa| <= q come first)
 //   lam_l                 local contributions, same layout
-// R is the arithmetic type of the FMM passes and of the stored nearfield blocks: double in
-// FP64 mode, float in mixed mode (FP64 output accumulation).
+// R is the arithmetic type of the FMM passes: float in mixed mode, df64 (double-FP32, about 48
+// significant bits on the FP32 pipe) in FP64 mode, or double when native FP64 passes are asked for;
+// outputs accumulate in FP64.  The stored nearfield blocks are float (mixed) or double (FP64).
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 
+#include "df64.cuh"
 #include "device_math.cuh"
 #include "kernels.h"
 
@@ -66,6 +69,20 @@ __global__ void k_cast(const double *__restrict__ x, float *__restrict__ y, size
 void launch_cast_to_float(const double *x, float *y, size_t n, cudaStream_t st)
 {
     k_cast<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, n);
+}
+
+__global__ void k_to_df64(double *__restrict__ x, size_t n)
+{
+    size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < n) {
+        const df64 v(x[gid]);
+        reinterpret_cast<float2 *>(x)[gid] = make_float2(v.hi, v.lo);
+    }
+}
+
+void launch_to_df64(double *x, size_t n, cudaStream_t st)
+{
+    if (n) k_to_df64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -210,8 +227,8 @@ __device__ __forceinline__ void lds4(const double *p, double (&w)[4])
 }
 constexpr int kS2MCK = 6;  // moment groups of 32 per thread (n_kappa <= 192, m_x <= 8)
 
-template <typename R, bool KOP>
-__global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncolg, const int *__restrict__ tri,
+template <typename R, typename XT, bool KOP>
+__global__ void __launch_bounds__(256) k_s2m(const XT *__restrict__ xin, int ncolg, const int *__restrict__ tri,
                                                const R *__restrict__ Stab, const R *__restrict__ St, R *__restrict__ mu,
                                                const int *__restrict__ leaf_start, int nk, int na, int ls, int Et,
                                                int nint, int nbox)
@@ -227,7 +244,7 @@ __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncol
     const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
     R *Ws = sm;              // [kTSB][KC]
     R *Ss = sm + kTSB * KC;  // [KC][nk]
-    const R *xr = xin + (size_t)rhs * Et * ncolg;
+    const XT *xr = xin + (size_t)rhs * Et * ncolg;
     const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
     R acc[4][kS2MCK];
 #pragma unroll
@@ -242,7 +259,7 @@ __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncol
             R val = R(0);
             if (ts < nts && xi < nx) {
                 const int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
-                val = xr[(size_t)(t0 + ts) * ncolg + col];
+                val = R(xr[(size_t)(t0 + ts) * ncolg + col]);
             }
             Ws[e] = val;
         }
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncol
                 if (c < ck && i < nk) {
                     const R sv = Ss[j * nk + i];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[r][c] += w[r] * sv;
+                    for (int r = 0; r < 4; ++r) mac(acc[r][c], w[r], sv);
                 }
             }
         }
@@ -290,8 +307,8 @@ __global__ void __launch_bounds__(256) k_s2m(const R *__restrict__ xin, int ncol
 // tile's triangles, P[tile][t][i] = sum_{x in tile} x[t][x] Sx[x][i], same register blocking as
 // k_s2m; stage 2, thread per moment: mu[k][X][a][i] = sum_s St[s][a] sum_{tiles of X} P[tile][k ls + s][i]
 // in tile order (deterministic).
-template <typename R, bool KOP>
-__global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int ncolg, const int *__restrict__ tri,
+template <typename R, typename XT, bool KOP>
+__global__ void __launch_bounds__(256) k_s2m_tile(const XT *__restrict__ xin, int ncolg, const int *__restrict__ tri,
                                                     const R *__restrict__ Stab, R *__restrict__ part,
                                                     const int *__restrict__ tiles, int ntiles,
                                                     const int *__restrict__ leaf_start, int nk, int Et)
@@ -305,7 +322,7 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
     const int t0 = blockIdx.y * kTSB, nts = min(kTSB, Et - t0);
     R *Ws = sm;              // [KC][kTSP]: a thread's four steps are one vector load
     R *Ss = sm + KC * kTSP;  // [KC][nk]
-    const R *xr = xin + (size_t)rhs * Et * ncolg;
+    const XT *xr = xin + (size_t)rhs * Et * ncolg;
     const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
     R acc[4][kS2MCK];
 #pragma unroll
@@ -320,7 +337,7 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
             R val = R(0);
             if (ts < nts && xi < nx) {
                 const int col = KOP ? tri[3 * (xb + xi) + v] : xb + xi;
-                val = xr[(size_t)(t0 + ts) * ncolg + col];
+                val = R(xr[(size_t)(t0 + ts) * ncolg + col]);
             }
             Ws[j * kTSP + ts] = val;
         }
@@ -338,7 +355,7 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const R *__restrict__ xin, int
                 if (c < ck && i < nk) {
                     const R sv = Ss[j * nk + i];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[r][c] += w[r] * sv;
+                    for (int r = 0; r < 4; ++r) mac(acc[r][c], w[r], sv);
                 }
             }
         }
@@ -376,7 +393,7 @@ __global__ void k_s2m_time(const R *__restrict__ part, const R *__restrict__ St,
             const R pv = pt[(size_t)s * nk];
 #pragma unroll
             for (int a = 0; a < kMaxNa; ++a)
-                if (a < na) v[a] += St[s * na + a] * pv;
+                if (a < na) mac(v[a], St[s * na + a], pv);
         }
     }
     R *mo = mu + ((((size_t)rhs * nint + k) * nbox + X) * na) * nk + i;
@@ -403,58 +420,43 @@ __global__ void k_l2t_time(const R *__restrict__ lam, const R *__restrict__ St, 
         R v = R(0);
 #pragma unroll
         for (int b = 0; b < kMaxNa; ++b)
-            if (b < na) v += St[s * na + b] * lv[b];
+            if (b < na) mac(v, St[s * na + b], lv[b]);
         Q[(((size_t)rhs * Et + (size_t)k * ls + s) * nbox + X) * nk + i] = v;
     }
 }
 
-void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
+void launch_s2m(int prec, bool kop, const void *x, int ncolg, const void *Stab, const void *St, void *mu_leaf, int nrhs,
                 const ApplyGeo &g, cudaStream_t st, void *ws, size_t ws_elems)
 {
-    if (ws && g.tiles && (size_t)nrhs * g.ntiles * g.Et * g.nk <= ws_elems) {
-        const int KC = kop ? 48 : 32;
-        const size_t smem = ((size_t)KC * kTSP + (size_t)KC * g.nk) * (mixed ? 4 : 8);
-        const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs);
-        const int nint = g.Et / g.ls;
-        const dim3 g2((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
-#define S2M_TILE_LAUNCH(R, K)                                                                                          \
-    do {                                                                                                               \
-        cudaFuncSetAttribute(k_s2m_tile<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
-        k_s2m_tile<R, K><<<grd, 256, smem, st>>>((const R *)x, ncolg, g.tri, (const R *)Stab, (R *)ws, g.tiles,         \
-                                                 g.ntiles, g.leaf_start, g.nk, g.Et);                                  \
-        k_s2m_time<R><<<g2, 256, 0, st>>>((const R *)ws, (const R *)St, (R *)mu_leaf, g.box_tiles, g.ntiles, g.nk,     \
-                                          g.na, g.ls, g.Et, nint, g.nbox_leaf);                                        \
-    } while (0)
-        if (mixed) {
-            if (kop) S2M_TILE_LAUNCH(float, true);
-            else S2M_TILE_LAUNCH(float, false);
-        } else {
-            if (kop) S2M_TILE_LAUNCH(double, true);
-            else S2M_TILE_LAUNCH(double, false);
+    const size_t es = prec == 1 ? 4 : 8;
+    const int nint = g.Et / g.ls;
+    dispatch_prec(prec, [&](auto tag) {
+        using R = decltype(tag);
+        // input in the arithmetic type, or FP64 converted on load for the double-FP32 passes
+        using XT = typename std::conditional<std::is_same<R, df64>::value, double, R>::type;
+        if (ws && g.tiles && (size_t)nrhs * g.ntiles * g.Et * g.nk <= ws_elems) {
+            const int KC = kop ? 48 : 32;
+            const size_t smem = ((size_t)KC * kTSP + (size_t)KC * g.nk) * es;
+            const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs);
+            const dim3 g2((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
+            auto kt = kop ? k_s2m_tile<R, XT, true> : k_s2m_tile<R, XT, false>;
+            cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            kt<<<grd, 256, smem, st>>>((const XT *)x, ncolg, g.tri, (const R *)Stab, (R *)ws, g.tiles, g.ntiles,
+                                       g.leaf_start, g.nk, g.Et);
+            k_s2m_time<R><<<g2, 256, 0, st>>>((const R *)ws, (const R *)St, (R *)mu_leaf, g.box_tiles, g.ntiles, g.nk,
+                                              g.na, g.ls, g.Et, nint, g.nbox_leaf);
+            return;
         }
-#undef S2M_TILE_LAUNCH
-        return;
-    }
-
-    int nint = g.Et / g.ls;
-    const int ipb = kTSB / g.ls;
-    const int KC = kop ? 48 : 32;
-    size_t es = mixed ? 4 : 8;
-    size_t sm1 = (size_t)kTSB * KC + (size_t)KC * g.nk, sm2 = (size_t)kTSB * g.nk;
-    size_t smem = (sm1 > sm2 ? sm1 : sm2) * es;
-    dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
-#define S2M_LAUNCH(R, K)                                                                                          \
-    do {                                                                                                          \
-        cudaFuncSetAttribute(k_s2m<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                \
-        k_s2m<R, K><<<grd, 256, smem, st>>>((const R *)x, ncolg, g.tri, (const R *)Stab, (const R *)St, (R *)mu_leaf, \
-                                            g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf);             \
-    } while (0)
-    if (mixed) {
-        if (kop) S2M_LAUNCH(float, true); else S2M_LAUNCH(float, false);
-    } else {
-        if (kop) S2M_LAUNCH(double, true); else S2M_LAUNCH(double, false);
-    }
-#undef S2M_LAUNCH
+        const int ipb = kTSB / g.ls;
+        const int KC = kop ? 48 : 32;
+        const size_t sm1 = (size_t)kTSB * KC + (size_t)KC * g.nk, sm2 = (size_t)kTSB * g.nk;
+        const size_t smem = (sm1 > sm2 ? sm1 : sm2) * es;
+        const dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
+        auto kb = kop ? k_s2m<R, XT, true> : k_s2m<R, XT, false>;
+        cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kb<<<grd, 256, smem, st>>>((const XT *)x, ncolg, g.tri, (const R *)Stab, (const R *)St, (R *)mu_leaf,
+                                   g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf);
+    });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -618,43 +620,32 @@ __global__ void __launch_bounds__(256) k_l2l_st(const R *__restrict__ lam_p, R *
     }
 }
 
-void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
+void launch_m2m(int prec, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
 {
     (void)l;
     (void)mu_stride;
-    size_t total = (size_t)nrhs * par.nint * par.nbox * g.na * g.nk;
-    unsigned blocks = (unsigned)((total + 127) / 128);
-    size_t es = mixed ? 4 : 8;
+    const size_t total = (size_t)nrhs * par.nint * par.nbox * g.na * g.nk;
+    const unsigned blocks = (unsigned)((total + 127) / 128);
+    const size_t es = prec == 1 ? 4 : 8;
     char *base = (char *)mu;
     const int m1 = g.mx + 1;
-    if (ch.st) {
-        size_t smem = es * ((size_t)16 * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
-        dim3 grd(par.nint * par.nbox * g.na, nrhs);
-        if (mixed) {
-            cudaFuncSetAttribute(k_m2m_st<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_m2m_st<float><<<grd, 256, smem, st>>>((const float *)(base + ch.mom_off * es * nrhs),
-                                                    (float *)(base + par.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
-                                                    ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx, g.kinv,
-                                                    g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
-        } else {
-            cudaFuncSetAttribute(k_m2m_st<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_m2m_st<double><<<grd, 256, smem, st>>>((const double *)(base + ch.mom_off * es * nrhs),
-                                                     (double *)(base + par.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
-                                                     ch.octant, (const double *)ch.qx, (const double *)qt, g.kidx,
-                                                     g.kinv, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
+    dispatch_prec(prec, [&](auto tag) {
+        using R = decltype(tag);
+        const R *mc = (const R *)(base + ch.mom_off * es * nrhs);
+        R *mp = (R *)(base + par.mom_off * es * nrhs);
+        if (ch.st) {
+            const size_t smem = es * ((size_t)16 * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
+            const dim3 grd(par.nint * par.nbox * g.na, nrhs);
+            cudaFuncSetAttribute(k_m2m_st<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_m2m_st<R><<<grd, 256, smem, st>>>(mc, mp, par.ch_ptr, par.ch_idx, ch.octant, (const R *)ch.qx,
+                                                (const R *)qt, g.kidx, g.kinv, g.na, g.nk, g.mx, par.nint, par.nbox,
+                                                ch.nbox);
+            return;
         }
-        return;
-    }
-    if (mixed)
-        k_m2m<float><<<blocks, 128, 0, st>>>((const float *)(base + ch.mom_off * es * nrhs), (float *)(base + par.mom_off * es * nrhs),
-                                             par.ch_ptr, par.ch_idx, ch.octant, (const float *)ch.qx, (const float *)qt,
-                                             g.kidx, g.kinv, ch.st, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox, nrhs);
-    else
-        k_m2m<double><<<blocks, 128, 0, st>>>((const double *)(base + ch.mom_off * es * nrhs),
-                                              (double *)(base + par.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
-                                              ch.octant, (const double *)ch.qx, (const double *)qt, g.kidx, g.kinv,
-                                              ch.st, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox, nrhs);
+        k_m2m<R><<<blocks, 128, 0, st>>>(mc, mp, par.ch_ptr, par.ch_idx, ch.octant, (const R *)ch.qx, (const R *)qt,
+                                         g.kidx, g.kinv, ch.st, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox, nrhs);
+    });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -715,7 +706,7 @@ __global__ void k_m2l_s1(M2LArgs A, const R *__restrict__ mu, const R *__restric
         for (int Y1 = y_lo; Y1 <= y_hi; ++Y1) {
             int box = A.cellbox[(Y1 * G + Y2) * G + Y3];
             if (box < 0) continue;
-            acc += E[((X1 - Y1 + G - 1) * m1 + k1) * m1 + nu1] * mJ[((size_t)box * na + a) * A.nk + im];
+            mac(acc, E[((X1 - Y1 + G - 1) * m1 + k1) * m1 + nu1], mJ[((size_t)box * na + a) * A.nk + im]);
         }
         out[B - s0] = acc;
     }
@@ -748,7 +739,7 @@ __global__ void k_m2l_s2(M2LArgs A, const R *__restrict__ E1, const R *__restric
             const R *Tc = Tin + (size_t)((X1 * G + Y2) * G + Y3) * A.ne;
             for (int k2 = 0; k2 <= Bp - s0; ++k2) {
                 int t1 = A.kinv[(nu1 * m1 + k2) * m1 + k3];
-                acc += Ey[k2 * m1 + nu2] * Tc[A.eoff[t1] + (Bp - nu2 - nu1 - k2 - k3)];
+                mac(acc, Ey[k2 * m1 + nu2], Tc[A.eoff[t1] + (Bp - nu2 - nu1 - k2 - k3)]);
             }
         }
         out[Bp - s0] = acc;
@@ -790,7 +781,7 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
                 const R *Tc = Tin + (size_t)((X1 * G + X2) * G + Y3) * A.ne;
                 for (int k3 = 0; k3 <= smax; ++k3) {
                     int t2 = A.kinv[(nu1 * m1 + nu2) * m1 + k3];
-                    s += Ez[k3 * m1 + nu3] * Tc[A.eoff[t2] + (A.mx - nu3 - nu1 - nu2 - k3)];
+                    mac(s, Ez[k3 * m1 + nu3], Tc[A.eoff[t2] + (A.mx - nu3 - nu1 - nu2 - k3)]);
                 }
             }
             val += pref[((D - 2) * na + a) * na + b] * s;
@@ -1166,13 +1157,14 @@ size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
            4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
 }
 
-// Which M2L kernel a level takes: the fused kernel for FP32 grids of at most 4^3 cells whose
-// intermediates fit its shared memory (m_x <= 7), the slab kernel for FP32 grids of 5^3 .. 8^3
-// cells with m_x <= 6 (its per-thread arrays and shared memory are sized for that), else the
-// three separable passes through the global workspace (FP64, larger grids or degrees).
-int m2l_engine(bool mixed, int G, int nk, int ne, int mx)
+// Which M2L kernel a level takes (prec: 0 FP64, 1 FP32, 2 double-FP32): the fused kernel for FP32
+// grids of at most 4^3 cells whose intermediates fit its shared memory (m_x <= 7), the slab kernel
+// for FP32 grids of 5^3 .. 8^3 cells with m_x <= 6 (its per-thread arrays and shared memory are
+// sized for that), else the three separable passes through the global workspace (the 8-byte
+// formats, larger grids or degrees).
+int m2l_engine(int prec, int G, int nk, int ne, int mx)
 {
-    if (!mixed) return kM2LThreePass;
+    if (prec != 1) return kM2LThreePass;
     if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4) <= 200 * 1024 && nk * FG <= 2 * kM2LThreads) return kM2LFused;
     if (G > FG && G <= SG && mx <= 6 && m2l_slab_smem(nk, ne, mx, 4) <= 220 * 1024 && nk <= 256) return kM2LSlab;
     return kM2LThreePass;
@@ -1180,87 +1172,75 @@ int m2l_engine(bool mixed, int G, int nk, int ne, int mx)
 
 // Runs the three passes over chunks of target intervals so that the intermediates fit the
 // workspace (ws_elems elements of R for each of T1 and T2).
-int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
+int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
                void *T1, void *T2, size_t ws_elems, cudaStream_t st)
 {
     (void)l;
-    const size_t es = mixed ? 4 : 8;
+    const size_t es = prec == 1 ? 4 : 8;
     const int G3 = L.G * L.G * L.G, na = g.na;
-    const int engine = m2l_engine(mixed, L.G, g.nk, g.ne, g.mx);
-    const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es);
-    if (engine == kM2LFused) {
-        M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
-                  g.kidx, g.kinv, g.eoff};
-        // few (interval, node) CTAs: one CTA per source term as well, when the terms' partial
-        // locals fit the workspace
-        const size_t per_k = (size_t)L.nbox * na * g.nk, nlev = (size_t)nrhs * L.nint * per_k;
-        const int nterm = 2 * na;
-        const int64_t split_ctas = (int64_t)kM2LSplitCtasPerSm * (g.nsm > 0 ? g.nsm : 152);
-        const int split = ((int64_t)L.nint * na * nrhs < split_ctas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
-        dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
-        const char *mbf = (const char *)mu + L.mom_off * es * nrhs;
-        char *lbf = (char *)lam + L.mom_off * es * nrhs;
-        if (mixed) {
-            cudaFuncSetAttribute(k_m2l_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            k_m2l_fused<float><<<grd, kM2LThreads, fsm, st>>>(A, (const float *)mbf, (const float *)L.E1, (const float *)L.pref,
-                                                      (float *)lbf, nrhs, split, (float *)T1);
-            if (split)
-                k_m2l_sum_terms<float><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const float *)T1, na, nlev, per_k,
-                                                                                      L.nint, (float *)lbf);
-        } else {
-            cudaFuncSetAttribute(k_m2l_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            k_m2l_fused<double><<<grd, kM2LThreads, fsm, st>>>(A, (const double *)mbf, (const double *)L.E1,
-                                                       (const double *)L.pref, (double *)lbf, nrhs, split, (double *)T1);
-            if (split)
-                k_m2l_sum_terms<double><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const double *)T1, na, nlev,
-                                                                                        per_k, L.nint, (double *)lbf);
-        }
-        return 0;
-    }
-    const size_t ssm = m2l_slab_smem(g.nk, g.ne, g.mx, es);
-    if (engine == kM2LSlab) {
-        M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
-                  g.kidx, g.kinv, g.eoff};
-        cudaFuncSetAttribute(k_m2l_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
-        k_m2l_slab<float><<<dim3((unsigned)(L.nint * na * L.G), nrhs), kM2LSlabThreads, ssm, st>>>(
-            A, (const float *)((const char *)mu + L.mom_off * es * nrhs), (const float *)L.E1, (const float *)L.pref,
-            (float *)((char *)lam + L.mom_off * es * nrhs));
-        return 0;
-    }
-    const size_t per_pair = (size_t)nrhs * na * na * G3 * g.ne;
+    const int engine = m2l_engine(prec, L.G, g.nk, g.ne, g.mx);
     const char *mb = (const char *)mu + L.mom_off * es * nrhs;
     char *lb = (char *)lam + L.mom_off * es * nrhs;
-    // intervals 0 and 1 have no interaction list: their locals start at zero
-    for (int r = 0; r < nrhs; ++r)
-        cudaMemsetAsync(lb + es * (size_t)r * L.nint * L.nbox * na * g.nk, 0,
-                        es * (size_t)L.nbox * na * g.nk * std::min(2, L.nint), st);
-    int k = 2;
-    while (k < L.nint) {
-        // largest chunk [k, k1) whose problem pairs fit the workspace
-        int k1 = k, p0 = L.kptr_host[k];
-        while (k1 < L.nint && (size_t)(L.kptr_host[k1 + 1] - p0) * per_pair <= ws_elems) k1++;
-        if (k1 == k) return -1;  // a single interval does not fit: workspace too small
-        int npair = L.kptr_host[k1] - p0;
-        M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk + p0, L.pJ + p0,
-                  npair, g.kidx, g.kinv, g.eoff};
-        size_t n12 = (size_t)nrhs * npair * na * na * G3 * g.nk;
-        unsigned b12 = (unsigned)((n12 + 127) / 128);
-        size_t n3 = (size_t)nrhs * (k1 - k) * L.nbox * na * g.nk;
-        unsigned b3 = (unsigned)((n3 + 127) / 128);
-        if (mixed) {
-            k_m2l_s1<float><<<b12, 128, 0, st>>>(A, (const float *)mb, (const float *)L.E1, (float *)T1, nrhs);
-            k_m2l_s2<float><<<b12, 128, 0, st>>>(A, (const float *)L.E1, (const float *)T1, (float *)T2, nrhs);
-            k_m2l_s3<float><<<b3, 128, 0, st>>>(A, (const float *)L.E1, (const float *)L.pref, (const float *)T2,
-                                                (float *)lb, L.kptr, p0, k, k1, nrhs);
-        } else {
-            k_m2l_s1<double><<<b12, 128, 0, st>>>(A, (const double *)mb, (const double *)L.E1, (double *)T1, nrhs);
-            k_m2l_s2<double><<<b12, 128, 0, st>>>(A, (const double *)L.E1, (const double *)T1, (double *)T2, nrhs);
-            k_m2l_s3<double><<<b3, 128, 0, st>>>(A, (const double *)L.E1, (const double *)L.pref, (const double *)T2,
-                                                 (double *)lb, L.kptr, p0, k, k1, nrhs);
+    int rc = 0;
+    dispatch_prec(prec, [&](auto tag) {
+        using R = decltype(tag);
+        if (engine == kM2LFused) {
+            const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es);
+            M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
+                      g.kidx, g.kinv, g.eoff};
+            // few (interval, node) CTAs: one CTA per source term as well, when the terms' partial
+            // locals fit the workspace
+            const size_t per_k = (size_t)L.nbox * na * g.nk, nlev = (size_t)nrhs * L.nint * per_k;
+            const int nterm = 2 * na;
+            const int64_t split_ctas = (int64_t)kM2LSplitCtasPerSm * (g.nsm > 0 ? g.nsm : 152);
+            const int split = ((int64_t)L.nint * na * nrhs < split_ctas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
+            const dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
+            cudaFuncSetAttribute(k_m2l_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            k_m2l_fused<R><<<grd, kM2LThreads, fsm, st>>>(A, (const R *)mb, (const R *)L.E1, (const R *)L.pref, (R *)lb,
+                                                         nrhs, split, (R *)T1);
+            if (split)
+                k_m2l_sum_terms<R><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const R *)T1, na, nlev, per_k,
+                                                                                  L.nint, (R *)lb);
+            return;
         }
-        k = k1;
-    }
-    return 0;
+        if (engine == kM2LSlab) {
+            const size_t ssm = m2l_slab_smem(g.nk, g.ne, g.mx, es);
+            M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
+                      g.kidx, g.kinv, g.eoff};
+            cudaFuncSetAttribute(k_m2l_slab<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm);
+            k_m2l_slab<R><<<dim3((unsigned)(L.nint * na * L.G), nrhs), kM2LSlabThreads, ssm, st>>>(
+                A, (const R *)mb, (const R *)L.E1, (const R *)L.pref, (R *)lb);
+            return;
+        }
+        const size_t per_pair = (size_t)nrhs * na * na * G3 * g.ne;
+        // intervals 0 and 1 have no interaction list: their locals start at zero
+        for (int r = 0; r < nrhs; ++r)
+            cudaMemsetAsync(lb + es * (size_t)r * L.nint * L.nbox * na * g.nk, 0,
+                            es * (size_t)L.nbox * na * g.nk * std::min(2, L.nint), st);
+        int k = 2;
+        while (k < L.nint) {
+            // largest chunk [k, k1) whose problem pairs fit the workspace
+            int k1 = k, p0 = L.kptr_host[k];
+            while (k1 < L.nint && (size_t)(L.kptr_host[k1 + 1] - p0) * per_pair <= ws_elems) k1++;
+            if (k1 == k) {  // a single interval does not fit: workspace too small
+                rc = -1;
+                return;
+            }
+            const int npair = L.kptr_host[k1] - p0;
+            M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk + p0, L.pJ + p0,
+                      npair, g.kidx, g.kinv, g.eoff};
+            const size_t n12 = (size_t)nrhs * npair * na * na * G3 * g.nk;
+            const unsigned b12 = (unsigned)((n12 + 127) / 128);
+            const size_t n3 = (size_t)nrhs * (k1 - k) * L.nbox * na * g.nk;
+            const unsigned b3 = (unsigned)((n3 + 127) / 128);
+            k_m2l_s1<R><<<b12, 128, 0, st>>>(A, (const R *)mb, (const R *)L.E1, (R *)T1, nrhs);
+            k_m2l_s2<R><<<b12, 128, 0, st>>>(A, (const R *)L.E1, (const R *)T1, (R *)T2, nrhs);
+            k_m2l_s3<R><<<b3, 128, 0, st>>>(A, (const R *)L.E1, (const R *)L.pref, (const R *)T2, (R *)lb, L.kptr, p0, k,
+                                            k1, nrhs);
+            k = k1;
+        }
+    });
+    return rc;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1305,40 +1285,31 @@ __global__ void k_l2l(const R *__restrict__ lam_p, R *__restrict__ lam_c, const 
     lam_c[gid] += acc;
 }
 
-void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
+void launch_l2l(int prec, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st)
 {
     (void)l;
     (void)mu_stride;
-    size_t total = (size_t)nrhs * ch.nint * ch.nbox * g.na * g.nk;
-    unsigned blocks = (unsigned)((total + 127) / 128);
-    size_t es = mixed ? 4 : 8;
+    const size_t total = (size_t)nrhs * ch.nint * ch.nbox * g.na * g.nk;
+    const unsigned blocks = (unsigned)((total + 127) / 128);
+    const size_t es = prec == 1 ? 4 : 8;
     char *base = (char *)lam;
     const int m1 = g.mx + 1;
-    if (ch.st) {
-        size_t smem = es * ((size_t)2 * g.na * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
-        dim3 grd(par.nint * par.nbox * 8, nrhs);  // one CTA per (parent, child slot); empty slots exit
-        if (mixed)
-            k_l2l_st<float><<<grd, 256, smem, st>>>((const float *)(base + par.mom_off * es * nrhs),
-                                                    (float *)(base + ch.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
-                                                    ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx, g.kinv,
-                                                    g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
-        else
-            k_l2l_st<double><<<grd, 256, smem, st>>>((const double *)(base + par.mom_off * es * nrhs),
-                                                     (double *)(base + ch.mom_off * es * nrhs), par.ch_ptr, par.ch_idx,
-                                                     ch.octant, (const double *)ch.qx, (const double *)qt, g.kidx,
-                                                     g.kinv, g.na, g.nk, g.mx, par.nint, par.nbox, ch.nbox);
-        return;
-    }
-    if (mixed)
-        k_l2l<float><<<blocks, 128, 0, st>>>((const float *)(base + par.mom_off * es * nrhs), (float *)(base + ch.mom_off * es * nrhs),
-                                             ch.parent, ch.octant, (const float *)ch.qx, (const float *)qt, g.kidx,
-                                             g.kinv, ch.st, g.na, g.nk, g.mx, ch.nint, ch.nbox, par.nbox, nrhs);
-    else
-        k_l2l<double><<<blocks, 128, 0, st>>>((const double *)(base + par.mom_off * es * nrhs),
-                                              (double *)(base + ch.mom_off * es * nrhs), ch.parent, ch.octant,
-                                              (const double *)ch.qx, (const double *)qt, g.kidx, g.kinv, ch.st, g.na,
-                                              g.nk, g.mx, ch.nint, ch.nbox, par.nbox, nrhs);
+    dispatch_prec(prec, [&](auto tag) {
+        using R = decltype(tag);
+        const R *lp = (const R *)(base + par.mom_off * es * nrhs);
+        R *lc = (R *)(base + ch.mom_off * es * nrhs);
+        if (ch.st) {
+            const size_t smem = es * ((size_t)2 * g.na * g.nk + 2 * m1 * m1) + 4 * (size_t)m1 * m1 * m1;
+            const dim3 grd(par.nint * par.nbox * 8, nrhs);  // one CTA per (parent, child slot); empty slots exit
+            k_l2l_st<R><<<grd, 256, smem, st>>>(lp, lc, par.ch_ptr, par.ch_idx, ch.octant, (const R *)ch.qx,
+                                                (const R *)qt, g.kidx, g.kinv, g.na, g.nk, g.mx, par.nint, par.nbox,
+                                                ch.nbox);
+            return;
+        }
+        k_l2l<R><<<blocks, 128, 0, st>>>(lp, lc, ch.parent, ch.octant, (const R *)ch.qx, (const R *)qt, g.kidx,
+                                         g.kinv, ch.st, g.na, g.nk, g.mx, ch.nint, ch.nbox, par.nbox, nrhs);
+    });
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1394,8 +1365,8 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
             lds4(Qs + i * kTSP + tg * 4, q);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                acc[r][0] += q[r] * s0;
-                acc[r][1] += q[r] * s1;
+                mac(acc[r][0], q[r], s0);
+                mac(acc[r][1], q[r], s1);
             }
         }
 #pragma unroll
@@ -1403,42 +1374,34 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
             const int ts = tg * 4 + r;
             if (ts >= nts) continue;
             double *fr = f + ((size_t)rhs * Et + t0 + ts) * nt + xb;
-            if (xl < nx) fr[xl] += (double)acc[r][0];
-            if (xl + 32 < nx) fr[xl + 32] += (double)acc[r][1];
+            if (xl < nx) fr[xl] += as_double(acc[r][0]);
+            if (xl + 32 < nx) fr[xl + 32] += as_double(acc[r][1]);
         }
     }
 }
 
-void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
+void launch_l2t(int prec, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st, void *ws, size_t ws_elems)
 {
     (void)mu_stride;
-    int nint = g.Et / g.ls;
+    const int nint = g.Et / g.ls;
     // temporal factor once per (step, box) in the workspace when it fits (else per CTA)
     const bool qg = ws && (size_t)nrhs * g.Et * g.nbox_leaf * g.nk <= ws_elems;
     const dim3 gq((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
     const int ipb = kTSB / g.ls;
-    size_t es = mixed ? 4 : 8;
-    size_t smem = ((size_t)kTSP * g.nk + (size_t)g.nk * 65) * es;
+    const size_t es = prec == 1 ? 4 : 8;
+    const size_t smem = ((size_t)kTSP * g.nk + (size_t)g.nk * 65) * es;
     // one CTA per 64-row tile (balanced over leaf boxes of different sizes)
-    dim3 grd(g.tiles ? g.ntiles : g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
-    if (mixed) {
+    const dim3 grd(g.tiles ? g.ntiles : g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
+    dispatch_prec(prec, [&](auto tag) {
+        using R = decltype(tag);
         if (qg)
-            k_l2t_time<float><<<gq, 256, 0, st>>>((const float *)lam_leaf, (const float *)St, (float *)ws, g.nk, g.na,
-                                                  g.ls, g.Et, nint, g.nbox_leaf);
-        cudaFuncSetAttribute(k_l2t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_l2t<float><<<grd, 256, smem, st>>>((const float *)lam_leaf, (const float *)Sx, (const float *)St, f_int,
-                                             g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles,
-                                             qg ? (const float *)ws : nullptr);
-    } else {
-        if (qg)
-            k_l2t_time<double><<<gq, 256, 0, st>>>((const double *)lam_leaf, (const double *)St, (double *)ws, g.nk,
-                                                   g.na, g.ls, g.Et, nint, g.nbox_leaf);
-        cudaFuncSetAttribute(k_l2t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_l2t<double><<<grd, 256, smem, st>>>((const double *)lam_leaf, (const double *)Sx, (const double *)St, f_int,
-                                              g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles,
-                                              qg ? (const double *)ws : nullptr);
-    }
+            k_l2t_time<R><<<gq, 256, 0, st>>>((const R *)lam_leaf, (const R *)St, (R *)ws, g.nk, g.na, g.ls, g.Et, nint,
+                                              g.nbox_leaf);
+        cudaFuncSetAttribute(k_l2t<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_l2t<R><<<grd, 256, smem, st>>>((const R *)lam_leaf, (const R *)Sx, (const R *)St, f_int, g.leaf_start, g.nk,
+                                         g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles, qg ? (const R *)ws : nullptr);
+    });
 }
 
 // ------------------------------------------------------------------------------------------

@@ -84,10 +84,13 @@ struct ApplyGeo {
     int nsm;               // streaming multiprocessors of the device (grid sizing)
 };
 
-// R: arithmetic/storage type of the FMM passes (double or float)
+// prec of the FMM launchers: 0 FP64, 1 FP32 (mixed mode), 2 double-FP32 (FP64 mode); every
+// moment, local and table buffer holds 8-byte elements in modes 0 and 2, 4-byte ones in mode 1
 void launch_permute_in(const double *w, void *w_int, bool to_float, int nrhs, const ApplyGeo &g, cudaStream_t st);
 void launch_permute_out(const double *f_int, double *f, int nrhs, const ApplyGeo &g, cudaStream_t st);
 void launch_cast_to_float(const double *x, float *y, size_t n, cudaStream_t st);
+// rewrite n FP64 values in place as double-FP32 pairs (hi, lo) of the same 8 bytes
+void launch_to_df64(double *x, size_t n, cudaStream_t st);
 // FP32 panels held only as the tensor-core engine's FP16 parts: A = (hi + lo) * inv_scale
 struct NfHalfSplit {
     const uint16_t *hi = nullptr, *lo = nullptr;  // FP16 bit patterns in 64 x 64 blocks (nf_tiled_index)
@@ -108,20 +111,20 @@ void launch_nf_apply(bool mixed, bool kop, const void *A, const int *colidx, con
                      const NfHalfSplit *hs = nullptr);      // FP32 only: blocks from the FP16 parts, A unused
 // ws: scratch of ws_elems elements of the arithmetic type for the per-tile partial moments (the
 // M2L workspace, idle at this point); too small: one CTA per whole leaf box instead
-void launch_s2m(bool mixed, bool kop, const void *x, int ncolg, const void *Stab /*Sx or SK*/, const void *St,
+void launch_s2m(int prec, bool kop, const void *x, int ncolg, const void *Stab /*Sx or SK*/, const void *St,
                 void *mu_leaf, int nrhs, const ApplyGeo &g, cudaStream_t st, void *ws = nullptr, size_t ws_elems = 0);
-void launch_m2m(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
+void launch_m2m(int prec, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *mu, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
-int launch_m2l(bool mixed, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
+int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
                void *T1, void *T2, size_t ws_elems, cudaStream_t st);
 // M2L kernel of a level with a G^3 grid (launch_m2l's choice): only kM2LThreePass uses T1 / T2
 enum { kM2LThreePass = 0, kM2LFused = 1, kM2LSlab = 2 };
-int m2l_engine(bool mixed, int G, int nk, int ne, int mx);
-void launch_l2l(bool mixed, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
+int m2l_engine(int prec, int G, int nk, int ne, int mx);
+void launch_l2l(int prec, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
 // ws: scratch (ws_elems elements of the arithmetic type) for the temporal factor of every (step,
 // leaf box), the M2L workspace idle at this point; too small: computed per CTA
-void launch_l2t(bool mixed, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
+void launch_l2t(int prec, const void *lam_leaf, const void *Sx, const void *St, double *f_int, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st, void *ws = nullptr, size_t ws_elems = 0);
 void launch_apply_M(const double *g_in, double *f, const int *tri_user, const double *area, int nrhs, int nt, int nv,
                     int Et, double h, cudaStream_t st);

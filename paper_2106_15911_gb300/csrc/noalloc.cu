@@ -81,7 +81,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     size_t need_T = 0;
     for (int l = 2; l <= H->p; ++l) {
         const DevLevel &L = H->dl[l];
-        if (m2l_engine(H->mixed, L.G, H->nk, H->ne, H->mx) != kM2LThreePass) continue;
+        if (m2l_engine(H->fprec, L.G, H->nk, H->ne, H->mx) != kM2LThreePass) continue;
         int maxpairs = 0;
         for (int k = 0; k < L.nint; ++k) maxpairs = std::max(maxpairs, L.kptr_host[k + 1] - L.kptr_host[k]);
         need_T = std::max(need_T, (size_t)nrhs * maxpairs * H->na * H->na * L.G * L.G * L.G * H->ne);
@@ -142,14 +142,14 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     }
     const int p = H->p;
     if (p >= 2) {
-        launch_s2m(H->mixed, false, xint, H->nt, H->d_Sx, H->d_St, mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st, T1,
+        launch_s2m(H->fprec, false, xint, H->nt, H->d_Sx, H->d_St, mu + H->dl[p].mom_off * H->es * nrhs, nrhs, g, st, T1,
                    ws_elems);
-        for (int l = p - 1; l >= 2; --l) launch_m2m(H->mixed, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
+        for (int l = p - 1; l >= 2; --l) launch_m2m(H->fprec, H->dl[l], H->dl[l + 1], l, H->d_qt, mu, nrhs, g, 0, st);
         for (int l = 2; l <= p; ++l)
-            if (launch_m2l(H->mixed, H->dl[l], l, mu, lam, nrhs, g, T1, T2, ws_elems, st))
+            if (launch_m2l(H->fprec, H->dl[l], l, mu, lam, nrhs, g, T1, T2, ws_elems, st))
                 return set_error(PFMM_ERR_OOM, "static scratch too small for one M2L interval");
-        for (int l = 3; l <= p; ++l) launch_l2l(H->mixed, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
-        launch_l2t(H->mixed, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, fint, nrhs, g, 0, st, T1, ws_elems);
+        for (int l = 3; l <= p; ++l) launch_l2l(H->fprec, H->dl[l - 1], H->dl[l], l, H->d_qt, lam, nrhs, g, 0, st);
+        launch_l2t(H->fprec, lam + H->dl[p].mom_off * H->es * nrhs, H->d_Sx, H->d_St, fint, nrhs, g, 0, st, T1, ws_elems);
     }
     launch_permute_out(fint, f, nrhs, g, st);
     cudaError_t e = cudaGetLastError();

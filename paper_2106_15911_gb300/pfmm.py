@@ -36,7 +36,8 @@ class pfmm_params(ctypes.Structure):
     _fields_ = [("m_t", ctypes.c_int32), ("m_x", ctypes.c_int32), ("c_st", ctypes.c_double),
                 ("n_tr", ctypes.c_int32), ("eps_tr", ctypes.c_double), ("leaf_steps", ctypes.c_int32),
                 ("leaf_tris", ctypes.c_int32), ("precision", ctypes.c_int32), ("nearfield", ctypes.c_int32),
-                ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32), ("nf_engine", ctypes.c_int32)]
+                ("quad_regular", ctypes.c_int32), ("quad_singular", ctypes.c_int32), ("nf_engine", ctypes.c_int32),
+                ("fp64_native", ctypes.c_int32)]
 
 
 class pfmm_info(ctypes.Structure):

@@ -68,3 +68,29 @@ def test_fp64_tensor_core_nearfield_scales_exactly():
         assert np.array_equal(np.ldexp(out[2], -200), out[1])
         assert not np.any(out[3])
     op.close()
+
+
+@pytest.mark.parametrize("mesh,n_a,Et,kw", [
+    (cube_mesh, 8, 64, dict(m_t=4, m_x=6, c_st=1.0)),                   # tensor-core nearfield, 4^3 grids
+    (cube_mesh, 4, 32, dict(m_t=5, m_x=6, c_st=0.25)),                  # space-time M2M / L2L
+    (cube_sphere_mesh, 16, 64, dict(m_t=4, m_x=5, c_st=0.1, n_tr=6)),   # 8^3 grids, padded boxes
+])
+def test_fp64_mode_matches_native_fp64(mesh, n_a, Et, kw):
+    """The FP64 mode's default arithmetic (exact residue nearfield, double-FP32 FMM passes) and
+    the native FP64 reference mode (fp64_native = 1, every phase on the FP64 pipe) agree within
+    1e-13 of the largest output, for V and K, far field and whole product."""
+    V, T = mesh(n_a)
+    op = P.Operator(V, T, 1.0, Et, **kw)
+    opn = P.Operator(V, T, 1.0, Et, fp64_native=1, **kw)
+    assert opn.info()["nf_tensor_cores"] == 0
+    w = torch.tensor(random_density(Et, T.shape[0], 2, seed=81), device=DEV)
+    g = torch.tensor(random_density(Et, V.shape[0], 2, seed=82), device=DEV)
+    for apply, apply_n, x in ((op.V, opn.V, w), (op.K, opn.K, g)):
+        for parts in (P.PFMM_PART_FAR, P.PFMM_PART_ALL):
+            a = apply(x, parts=parts).cpu().numpy()
+            b = apply_n(x, parts=parts).cpu().numpy()
+            assert np.max(np.abs(b)) > 0
+            assert _rel(a, b) <= 1e-13, (parts, _rel(a, b))
+    P.pfmm_check(op.h)
+    op.close()
+    opn.close()
