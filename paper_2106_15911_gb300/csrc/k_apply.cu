@@ -809,7 +809,7 @@ constexpr int kM2LThreads = 384;
 constexpr int kM2LSplitCtasPerSm = 8;
 
 template <typename R>
-__global__ void __launch_bounds__(kM2LThreads, 2) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
+__global__ void __launch_bounds__(kM2LThreads, sizeof(R) == 4 ? 2 : 1) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
                                                                 const R *__restrict__ E1, const R *__restrict__ pref,
                                                                 R *__restrict__ lam, int nrhs, int split,
                                                                 R *__restrict__ part)
@@ -1158,12 +1158,17 @@ size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
 }
 
 // Which M2L kernel a level takes (prec: 0 FP64, 1 FP32, 2 double-FP32): the fused kernel for FP32
-// grids of at most 4^3 cells whose intermediates fit its shared memory (m_x <= 7), the slab kernel
+// grids of at most 4^3 cells whose intermediates fit its shared memory (m_x <= 7; double-FP32:
+// m_x <= 6 at one CTA per SM), the slab kernel
 // for FP32 grids of 5^3 .. 8^3 cells with m_x <= 6 (its per-thread arrays and shared memory are
 // sized for that), else the three separable passes through the global workspace (the 8-byte
 // formats, larger grids or degrees).
 int m2l_engine(int prec, int G, int nk, int ne, int mx)
 {
+    // double-FP32: the fused kernel at one CTA per SM when its 8-byte intermediates fit the
+    // 227 KB of shared memory a CTA may hold (m_x <= 6)
+    if (prec == 2 && G <= FG && m2l_fused_smem(G, nk, ne, mx, 8) <= 227 * 1024 && nk * FG <= 2 * kM2LThreads)
+        return kM2LFused;
     if (prec != 1) return kM2LThreePass;
     if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4) <= 200 * 1024 && nk * FG <= 2 * kM2LThreads) return kM2LFused;
     if (G > FG && G <= SG && mx <= 6 && m2l_slab_smem(nk, ne, mx, 4) <= 220 * 1024 && nk <= 256) return kM2LSlab;
