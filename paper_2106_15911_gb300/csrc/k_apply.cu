@@ -225,27 +225,30 @@ __device__ __forceinline__ void lds4(const double *p, double (&w)[4])
     w[2] = b.x;
     w[3] = b.y;
 }
-constexpr int kS2MCK = 6;  // moment groups of 32 per thread (n_kappa <= 192, m_x <= 8)
+constexpr int kS2MCK = 6;  // moment groups of 32 per thread: a CTA covers a chunk of 192 moments
+constexpr int kS2MChunk = 32 * kS2MCK;
 
 template <typename R, typename XT, bool KOP>
 __global__ void __launch_bounds__(256) k_s2m(const XT *__restrict__ xin, int ncolg, const int *__restrict__ tri,
                                                const R *__restrict__ Stab, const R *__restrict__ St, R *__restrict__ mu,
                                                const int *__restrict__ leaf_start, int nk, int na, int ls, int Et,
-                                               int nint, int nbox)
+                                               int nint, int nbox, int nchk)
 {
-    // register-blocked: a CTA covers one leaf box, kTSB steps and one rhs; thread (tg = warp,
-    // kg = lane) accumulates steps 4 tg .. 4 tg + 3 for the moments kg + 32 c (c < ceil(nk / 32))
+    // register-blocked: a CTA covers one leaf box, kTSB steps, one chunk of at most 192 moments
+    // (grid z = rhs x chunk) and one rhs; thread (tg = warp, kg = lane) accumulates steps
+    // 4 tg .. 4 tg + 3 for the moments i0 + kg + 32 c of the chunk
     extern __shared__ unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     constexpr int XCH = KOP ? 16 : 32, PER = KOP ? 3 : 1, KC = XCH * PER;
-    const int X = blockIdx.x, rhs = blockIdx.z;
+    const int X = blockIdx.x, rhs = blockIdx.z / nchk, i0 = (blockIdx.z % nchk) * kS2MChunk;
+    const int nkc = min(nk - i0, kS2MChunk);
     const int ipb = kTSB / ls;
     const int k0 = blockIdx.y * ipb, kend = min(nint, k0 + ipb), nts = (kend - k0) * ls, t0 = k0 * ls;
     const int x0 = leaf_start[X], x1 = leaf_start[X + 1];
     R *Ws = sm;              // [kTSB][KC]
-    R *Ss = sm + kTSB * KC;  // [KC][nk]
+    R *Ss = sm + kTSB * KC;  // [KC][nkc]
     const XT *xr = xin + (size_t)rhs * Et * ncolg;
-    const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
+    const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nkc + 31) / 32;
     R acc[4][kS2MCK];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -263,9 +266,9 @@ __global__ void __launch_bounds__(256) k_s2m(const XT *__restrict__ xin, int nco
             }
             Ws[e] = val;
         }
-        for (int e = threadIdx.x; e < KC * nk; e += blockDim.x) {
-            const int j = e / nk;
-            Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + (e % nk)] : R(0);
+        for (int e = threadIdx.x; e < KC * nkc; e += blockDim.x) {
+            const int j = e / nkc;
+            Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + i0 + (e % nkc)] : R(0);
         }
         __syncthreads();
         for (int j = 0; j < KC; ++j) {
@@ -275,8 +278,8 @@ __global__ void __launch_bounds__(256) k_s2m(const XT *__restrict__ xin, int nco
 #pragma unroll
             for (int c = 0; c < kS2MCK; ++c) {
                 const int i = kg + 32 * c;
-                if (c < ck && i < nk) {
-                    const R sv = Ss[j * nk + i];
+                if (c < ck && i < nkc) {
+                    const R sv = Ss[j * nkc + i];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) mac(acc[r][c], w[r], sv);
                 }
@@ -284,21 +287,21 @@ __global__ void __launch_bounds__(256) k_s2m(const XT *__restrict__ xin, int nco
         }
     }
     __syncthreads();
-    R *Ps = sm;  // [kTSB][nk]
+    R *Ps = sm;  // [kTSB][nkc]
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < kS2MCK; ++c) {
             const int i = kg + 32 * c;
-            if (c < ck && i < nk) Ps[(tg * 4 + r) * nk + i] = acc[r][c];
+            if (c < ck && i < nkc) Ps[(tg * 4 + r) * nkc + i] = acc[r][c];
         }
     __syncthreads();
-    const int nmo = (kend - k0) * na * nk;
+    const int nmo = (kend - k0) * na * nkc;
     for (int o = threadIdx.x; o < nmo; o += blockDim.x) {
-        int kk = o / (na * nk), a = (o / nk) % na, i = o % nk;
+        int kk = o / (na * nkc), a = (o / nkc) % na, i = o % nkc;
         R v = R(0);
-        for (int s = 0; s < ls; ++s) v += St[s * na + a] * Ps[((kk * ls) + s) * nk + i];
-        mu[((((size_t)rhs * nint + k0 + kk) * nbox + X) * na + a) * nk + i] = v;
+        for (int s = 0; s < ls; ++s) v += St[s * na + a] * Ps[((kk * ls) + s) * nkc + i];
+        mu[((((size_t)rhs * nint + k0 + kk) * nbox + X) * na + a) * nk + i0 + i] = v;
     }
 }
 
@@ -311,19 +314,20 @@ template <typename R, typename XT, bool KOP>
 __global__ void __launch_bounds__(256) k_s2m_tile(const XT *__restrict__ xin, int ncolg, const int *__restrict__ tri,
                                                     const R *__restrict__ Stab, R *__restrict__ part,
                                                     const int *__restrict__ tiles, int ntiles,
-                                                    const int *__restrict__ leaf_start, int nk, int Et)
+                                                    const int *__restrict__ leaf_start, int nk, int Et, int nchk)
 {
     extern __shared__ __align__(16) unsigned char s2m_raw[];
     R *sm = reinterpret_cast<R *>(s2m_raw);
     constexpr int XCH = KOP ? 16 : 32, PER = KOP ? 3 : 1, KC = XCH * PER;
-    const int tile = blockIdx.x, rhs = blockIdx.z;
+    const int tile = blockIdx.x, rhs = blockIdx.z / nchk, i0 = (blockIdx.z % nchk) * kS2MChunk;
+    const int nkc = min(nk - i0, kS2MChunk);
     const int X = tiles[2 * tile];
     const int x0 = leaf_start[X] + tiles[2 * tile + 1], x1 = min(x0 + 64, leaf_start[X + 1]);
     const int t0 = blockIdx.y * kTSB, nts = min(kTSB, Et - t0);
     R *Ws = sm;              // [KC][kTSP]: a thread's four steps are one vector load
-    R *Ss = sm + KC * kTSP;  // [KC][nk]
+    R *Ss = sm + KC * kTSP;  // [KC][nkc]
     const XT *xr = xin + (size_t)rhs * Et * ncolg;
-    const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nk + 31) / 32;
+    const int kg = threadIdx.x & 31, tg = threadIdx.x >> 5, ck = (nkc + 31) / 32;
     R acc[4][kS2MCK];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -341,9 +345,9 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const XT *__restrict__ xin, in
             }
             Ws[j * kTSP + ts] = val;
         }
-        for (int e = threadIdx.x; e < KC * nk; e += blockDim.x) {
-            const int j = e / nk;
-            Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + (e % nk)] : R(0);
+        for (int e = threadIdx.x; e < KC * nkc; e += blockDim.x) {
+            const int j = e / nkc;
+            Ss[e] = (j / PER < nx) ? Stab[(size_t)(xb * PER + j) * nk + i0 + (e % nkc)] : R(0);
         }
         __syncthreads();
         for (int j = 0; j < KC; ++j) {
@@ -352,8 +356,8 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const XT *__restrict__ xin, in
 #pragma unroll
             for (int c = 0; c < kS2MCK; ++c) {
                 const int i = kg + 32 * c;
-                if (c < ck && i < nk) {
-                    const R sv = Ss[j * nk + i];
+                if (c < ck && i < nkc) {
+                    const R sv = Ss[j * nkc + i];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) mac(acc[r][c], w[r], sv);
                 }
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(256) k_s2m_tile(const XT *__restrict__ xin, in
 #pragma unroll
         for (int c = 0; c < kS2MCK; ++c) {
             const int i = kg + 32 * c;
-            if (c < ck && i < nk) pt[(size_t)ts * nk + i] = acc[r][c];
+            if (c < ck && i < nkc) pt[(size_t)ts * nk + i0 + i] = acc[r][c];
         }
     }
 }
@@ -434,28 +438,29 @@ void launch_s2m(int prec, bool kop, const void *x, int ncolg, const void *Stab, 
         using R = decltype(tag);
         // input in the arithmetic type, or FP64 converted on load for the double-FP32 passes
         using XT = typename std::conditional<std::is_same<R, df64>::value, double, R>::type;
+        const int nchk = (g.nk + kS2MChunk - 1) / kS2MChunk, nkc = std::min(g.nk, kS2MChunk);
         if (ws && g.tiles && (size_t)nrhs * g.ntiles * g.Et * g.nk <= ws_elems) {
             const int KC = kop ? 48 : 32;
-            const size_t smem = ((size_t)KC * kTSP + (size_t)KC * g.nk) * es;
-            const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs);
+            const size_t smem = ((size_t)KC * kTSP + (size_t)KC * nkc) * es;
+            const dim3 grd(g.ntiles, (g.Et + kTSB - 1) / kTSB, nrhs * nchk);
             const dim3 g2((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
             auto kt = kop ? k_s2m_tile<R, XT, true> : k_s2m_tile<R, XT, false>;
             cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             kt<<<grd, 256, smem, st>>>((const XT *)x, ncolg, g.tri, (const R *)Stab, (R *)ws, g.tiles, g.ntiles,
-                                       g.leaf_start, g.nk, g.Et);
+                                       g.leaf_start, g.nk, g.Et, nchk);
             k_s2m_time<R><<<g2, 256, 0, st>>>((const R *)ws, (const R *)St, (R *)mu_leaf, g.box_tiles, g.ntiles, g.nk,
                                               g.na, g.ls, g.Et, nint, g.nbox_leaf);
             return;
         }
         const int ipb = kTSB / g.ls;
         const int KC = kop ? 48 : 32;
-        const size_t sm1 = (size_t)kTSB * KC + (size_t)KC * g.nk, sm2 = (size_t)kTSB * g.nk;
+        const size_t sm1 = (size_t)kTSB * KC + (size_t)KC * nkc, sm2 = (size_t)kTSB * nkc;
         const size_t smem = (sm1 > sm2 ? sm1 : sm2) * es;
-        const dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
+        const dim3 grd(g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs * nchk);
         auto kb = kop ? k_s2m<R, XT, true> : k_s2m<R, XT, false>;
         cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kb<<<grd, 256, smem, st>>>((const XT *)x, ncolg, g.tri, (const R *)Stab, (const R *)St, (R *)mu_leaf,
-                                   g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf);
+                                   g.leaf_start, g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, nchk);
     });
 }
 
@@ -1323,30 +1328,32 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R *__restrict__ Sx, const R *__restrict__ St,
                                                double *__restrict__ f, const int *__restrict__ leaf_start, int nk, int na,
                                                int ls, int Et, int nint, int nbox, int nt, const int *__restrict__ tiles,
-                                               const R *__restrict__ Qg)
+                                               const R *__restrict__ Qg, int i0, int nkc)
 {
+    // the multi-indices nu = i0 .. i0 + nkc - 1 (one launch per chunk when n_kappa is large; the
+    // launches add into f one after the other)
     // a CTA covers one 64-row tile of a leaf box (tiles: (box, first row); without a tile list, the
     // whole box), kTSB steps and one rhs: Q[ts][nu] = sum_b St[s][b] lam[k][X][b][nu] in shared
     // memory, then thread (tg = warp, xl = lane) forms steps 4 tg .. 4 tg + 3 for the triangles xl
     // and xl + 32 of each 64-triangle chunk
     extern __shared__ __align__(16) unsigned char l2t_raw[];
-    R *Qs = reinterpret_cast<R *>(l2t_raw);  // [nk][kTSP]: a thread's four steps are one vector load
+    R *Qs = reinterpret_cast<R *>(l2t_raw);  // [nkc][kTSP]: a thread's four steps are one vector load
     constexpr int XCH = 64, SP = XCH + 1;      // Sx chunk stored transposed, rows padded
-    R *Ss = Qs + kTSP * nk;                    // [nk][SP]
+    R *Ss = Qs + kTSP * nkc;                   // [nkc][SP]
     const int X = tiles ? tiles[2 * blockIdx.x] : blockIdx.x, rhs = blockIdx.z;
     const int ipb = kTSB / ls;
     const int k0 = blockIdx.y * ipb, kend = min(nint, k0 + ipb), nts = (kend - k0) * ls, t0 = k0 * ls;
     const int x0 = leaf_start[X] + (tiles ? tiles[2 * blockIdx.x + 1] : 0);
     const int x1 = tiles ? min(x0 + 64, leaf_start[X + 1]) : leaf_start[X + 1];
-    for (int o = threadIdx.x; o < kTSB * nk; o += blockDim.x) {
-        const int ts = o / nk, i = o % nk;
+    for (int o = threadIdx.x; o < kTSB * nkc; o += blockDim.x) {
+        const int ts = o / nkc, i = o % nkc;
         R v = R(0);
         if (ts < nts) {
             if (Qg) {  // precomputed by k_l2t_time
-                v = Qg[(((size_t)rhs * Et + t0 + ts) * nbox + X) * nk + i];
+                v = Qg[(((size_t)rhs * Et + t0 + ts) * nbox + X) * nk + i0 + i];
             } else {
                 const int kk = ts / ls, s = ts % ls;
-                const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i;
+                const R *lp = lam + ((((size_t)rhs * nint + k0 + kk) * nbox + X) * na) * nk + i0 + i;
                 for (int b = 0; b < na; ++b) v += St[s * na + b] * lp[(size_t)b * nk];
             }
         }
@@ -1356,15 +1363,15 @@ __global__ void __launch_bounds__(256) k_l2t(const R *__restrict__ lam, const R 
     for (int xb = x0; xb < x1; xb += XCH) {
         const int nx = min(XCH, x1 - xb);
         __syncthreads();
-        for (int e = threadIdx.x; e < XCH * nk; e += blockDim.x) {  // coalesced reads along nu
-            const int xi = e / nk, i = e % nk;
-            Ss[i * SP + xi] = xi < nx ? Sx[(size_t)(xb + xi) * nk + i] : R(0);
+        for (int e = threadIdx.x; e < XCH * nkc; e += blockDim.x) {  // coalesced reads along nu
+            const int xi = e / nkc, i = e % nkc;
+            Ss[i * SP + xi] = xi < nx ? Sx[(size_t)(xb + xi) * nk + i0 + i] : R(0);
         }
         __syncthreads();
         R acc[4][2];
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = R(0);
-        for (int i = 0; i < nk; ++i) {
+        for (int i = 0; i < nkc; ++i) {
             const R s0 = Ss[i * SP + xl], s1 = Ss[i * SP + xl + 32];
             R q[4];
             lds4(Qs + i * kTSP + tg * 4, q);
@@ -1395,7 +1402,9 @@ void launch_l2t(int prec, const void *lam_leaf, const void *Sx, const void *St, 
     const dim3 gq((unsigned)(nrhs * nint), (unsigned)((g.nbox_leaf * g.nk + 255) / 256));
     const int ipb = kTSB / g.ls;
     const size_t es = prec == 1 ? 4 : 8;
-    const size_t smem = ((size_t)kTSP * g.nk + (size_t)g.nk * 65) * es;
+    constexpr int kL2TChunk = 256;  // multi-indices per launch: the shared memory of a CTA bounds it
+    const int nkc_max = std::min(g.nk, kL2TChunk);
+    const size_t smem = ((size_t)kTSP * nkc_max + (size_t)nkc_max * 65) * es;
     // one CTA per 64-row tile (balanced over leaf boxes of different sizes)
     const dim3 grd(g.tiles ? g.ntiles : g.nbox_leaf, (nint + ipb - 1) / ipb, nrhs);
     dispatch_prec(prec, [&](auto tag) {
@@ -1404,8 +1413,10 @@ void launch_l2t(int prec, const void *lam_leaf, const void *Sx, const void *St, 
             k_l2t_time<R><<<gq, 256, 0, st>>>((const R *)lam_leaf, (const R *)St, (R *)ws, g.nk, g.na, g.ls, g.Et, nint,
                                               g.nbox_leaf);
         cudaFuncSetAttribute(k_l2t<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_l2t<R><<<grd, 256, smem, st>>>((const R *)lam_leaf, (const R *)Sx, (const R *)St, f_int, g.leaf_start, g.nk,
-                                         g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles, qg ? (const R *)ws : nullptr);
+        for (int i0 = 0; i0 < g.nk; i0 += kL2TChunk)
+            k_l2t<R><<<grd, 256, smem, st>>>((const R *)lam_leaf, (const R *)Sx, (const R *)St, f_int, g.leaf_start,
+                                             g.nk, g.na, g.ls, g.Et, nint, g.nbox_leaf, g.nt, g.tiles,
+                                             qg ? (const R *)ws : nullptr, i0, std::min(kL2TChunk, g.nk - i0));
     });
 }
 

@@ -164,6 +164,30 @@ def test_8_cubed_grids_match_oracle(mesh, n_a, Et, kw, engine8):
     opd.close()
 
 
+@pytest.mark.parametrize("n_a,Et,m_x,kw", [
+    (4, 32, 9, dict(m_t=4, c_st=0.25)),               # 220 moments: S2M / L2T over two moment chunks
+    (4, 32, 12, dict(m_t=4, c_st=0.25)),              # 455 moments: three S2M chunks, two L2T launches
+    (8, 256, 12, dict(m_t=4, c_st=4.1, n_tr=2)),      # the paper's large-run parameters (Section 5)
+])
+def test_high_degrees_match_oracle(n_a, Et, m_x, kw):
+    """Degrees up to the ABI's m_x = 12 (Section 5 runs m_x = 12, m_t = 4, c_st = 4.1, n_tr = 2):
+    FP64 within 1e-12 and mixed within 1e-5 of the oracle on 6 sampled target triangles, V and K."""
+    V, T = cube_mesh(n_a)
+    Pr = O.make_problem(V, T, 1.0, Et, m_x=m_x, **kw)
+    rows = sample_triangles(T.shape[0], 6, seed=5)
+    w = random_density(Et, T.shape[0], 1, seed=91)
+    g = random_density(Et, V.shape[0], 1, seed=92)
+    refs = {0: O.pfmm_apply(Pr, 0, w[0], targets=rows), 1: O.pfmm_apply(Pr, 1, g[0], targets=rows)}
+    for prec, tol in ((P.PFMM_FP64, 1e-12), (P.PFMM_MIXED, 1e-5)):
+        op = P.Operator(V, T, 1.0, Et, m_x=m_x, precision=prec, **kw)
+        fV = op.V(torch.tensor(w, device=DEV)).cpu().numpy()[0]
+        fK = op.K(torch.tensor(g, device=DEV)).cpu().numpy()[0]
+        P.pfmm_check(op.h)
+        op.close()
+        assert _rel(fV, refs[0], rows) <= tol, (prec, _rel(fV, refs[0], rows))
+        assert _rel(fK, refs[1], rows) <= tol, (prec, _rel(fK, refs[1], rows))
+
+
 def test_errors_are_reported_not_crashed():
     V, T = cube_mesh(2)
     op = P.Operator(V, T, 1.0, 8)
