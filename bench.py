@@ -427,6 +427,61 @@ def _config5(dev, n_rhs=4, n_record=2, tol=1e-6, solve=True):
             "peak_device_GB": peak[0], "device_total_GB": total / 1e9, "cap_GB": 180})
 
 
+def _paper_scale(dev, steps=5, dense_rows=4):
+    """The parameter set of the paper's large distributed run (Section 5, Tab. mpi: m_x = 12,
+    m_t = 4, c_st = 4.1, n_tr = 2) on its 12288 x 1024 shape: the unit-cube surface, 32 x 32
+    squares per face, 1024 steps on [0, 1] (12.6M space-time DOF).  Mixed and FP64 V_h matvecs
+    (build time, phases, throughput) and the truncation error of both against the dense Galerkin
+    V_h of the oracle on sampled rows (the paper quotes 1.5 s per GMRES iteration on 256 CPU nodes
+    for this shape, context only)."""
+    import torch
+
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_mesh, random_density
+
+    V, T = cube_mesh(32)
+    Et, nt = 1024, T.shape[0]
+    kw = dict(m_t=4, m_x=12, c_st=4.1, n_tr=2)
+    w = torch.tensor(random_density(Et, nt, 1, seed=4100), device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out, res = {}, {}
+    for name, prec in (("mixed", P.PFMM_MIXED), ("fp64", P.PFMM_FP64)):
+        t0 = time.perf_counter()
+        op = P.Operator(V, T, 1.0, Et, precision=prec, **kw)
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        info = op.info()
+        f = torch.empty_like(w)
+        for _ in range(2):
+            P.pfmm_apply_V(op.h, w, f, 1, None)
+        e0.record()
+        for _ in range(steps):
+            P.pfmm_apply_V(op.h, w, f, 1, None)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        P.pfmm_set_profiling(op.h, True)
+        P.pfmm_apply_V(op.h, w, f, 1, None)
+        ph, n = P.pfmm_phase_times(op.h)
+        P.pfmm_set_profiling(op.h, False)
+        res[name] = f[0].cpu().numpy()
+        out[name] = {"build_s": build_s, "ms_per_matvec": ms, "dofs_per_s": nt * Et / (ms * 1e-3),
+                     "phases_ms": {k: v / max(n, 1) for k, v in ph.items()}, "tree_lx": info["lx"],
+                     "nearfield_GB": info["nearfield_bytes"] / 1e9, "nf_tensor_cores": info["nf_tensor_cores"],
+                     "nf_dense_columns": info["nf_dense_columns"], "m2l_engine": info["m2l_engine"],
+                     "m2l_gflop": info["m2l_flops"] / 1e9}
+        op.close()
+        torch.cuda.empty_cache()
+    rel = float(np.max(np.abs(res["mixed"] - res["fp64"])) / np.max(np.abs(res["fp64"])))
+    dense = None
+    if dense_rows > 0:
+        dense, nr = _dense_rows_error(V, T, Et, w[0].cpu().numpy(), res, dense_rows)
+        dense["rows"] = nr
+    return {"workload": f"cube 32x32 faces ({nt} tri) x {Et} steps, m_x 12, m_t 4, c_st 4.1, n_tr 2 (Section 5 "
+                        f"parameters)", **out, "mixed_vs_fp64_rel_maxnorm": rel, "vs_dense_oracle": dense,
+            "paper": "1.5 s per GMRES iteration on 256 Salomon nodes (Tab. mpi), CPU cluster, context only"}
+
+
 def _profile_case(dev, case):
     """Small cases for ncu captures: the learned preconditioner's layers (`mpnn`), its compiled
     form (`mpnn_compiled`), the on-the-fly nearfield (`otf`), the slab M2L of 8^3 grids
@@ -560,6 +615,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="skip the solver comparison")
     ap.add_argument("--solve-sets", type=int, default=32, help="held-out data sets of the solver comparison")
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="run only the paper's large-run parameters (m_x 12, c_st 4.1, n_tr 2) on 12288 x 1024")
     ap.add_argument("--config5-matvec", action="store_true",
                     help="with --config5: the build and matvecs only (no recording, training or solves)")
     ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt"], default=None,
@@ -592,6 +649,10 @@ def main():
     if args.profile_case:
         if rank == 0:
             print(json.dumps(_profile_case(dev, args.profile_case)), flush=True)
+        return 0
+    if args.paper_scale:
+        if rank == 0:
+            print(json.dumps({"paper_scale": _paper_scale(dev)}), flush=True)
         return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
