@@ -214,6 +214,24 @@ int pfmm_probe_fma_rate(int32_t fp64, double *tflops, void *stream);
  * each call writes every workspace before reading it. */
 int pfmm_apply_V_noalloc(pfmm_handle *h, const double *w, double *f, int32_t nrhs, void *stream);
 
+/* Representation formula (Section 2): the solution at interior space-time points,
+ *   u(x, t) = (V~ w)(x, t) - (W g)(x, t),
+ *   V~ w = int_0^t int_Gamma G_alpha(x - y, t - tau) w(y, tau) ds_y dtau,
+ *   W g  = int_0^t int_Gamma alpha dG_alpha/dn_y(x - y, t - tau) g(y, tau) ds_y dtau,
+ * for the discrete densities of Eq. 02:linear:system: w piecewise constant on the space-time
+ * elements (the solution of pfmm_solve, direct formulation) and g piecewise constant in time,
+ * piecewise linear in space (the projected Dirichlet datum); with g = NULL only V~ w (the
+ * indirect formulation's single-layer ansatz).  The time integrals are exact (first time
+ * antiderivatives of the heat kernel); the space integrals use the handle's regular collapsed
+ * Gauss rule (quad_regular^2 points per triangle), so points should keep a distance of a few
+ * element sizes from Gamma for that rule to be accurate.  Direct summation over all elements in
+ * FP64 (no FMM): cost np x E_x x quad_regular^2 x E_t per rhs.
+ *   w: device [nrhs][E_t][E_x], g: device [nrhs][E_t][N_v] or NULL, points: device [npoints][4] =
+ *   (x, y, z, t) with t > 0 (t <= 0 gives 0; steps beyond E_t do not exist), u: device
+ *   [nrhs][npoints] (overwritten).  Enqueued on `stream`; returns without synchronising. */
+int pfmm_eval_repr(pfmm_handle *h, const double *w, const double *g, const double *points, int32_t npoints,
+                   double *u, int32_t nrhs, void *stream);
+
 /* ---- solver ------------------------------------------------------------------------------ */
 #define PFMM_DIRECT 0    /* V_h w = (1/2 M_h + K_h) g  (Section 2, Eq. 02:linear:system) */
 #define PFMM_INDIRECT 1  /* V_h w = M_h g              (single-layer ansatz) */

@@ -69,6 +69,9 @@ def lib():
             L.orc_assemble_M.argtypes = [i, pd, i, pi, d, pd]
             L.orc_tree_info.argtypes = [ctypes.POINTER(Problem), pi, pi, pi, pd, pi, pi, pd]
             L.orc_pfmm_apply.argtypes = [ctypes.POINTER(Problem), i, pd, pd, pi, i, i, i]
+            L.orc_H1.restype = d
+            L.orc_H1.argtypes = [d, d, d]
+            L.orc_repr_eval.argtypes = [ctypes.POINTER(Problem), pd, pd, pd, i, pd, i]
             L.orc_E1.restype = d
             L.orc_E1.argtypes = [i, i, d, d, i]
             L.orc_qt.restype = d
@@ -263,6 +266,26 @@ def pfmm_apply(P, op, x, targets=None, parts=3, nthreads=0):
     if rc:
         raise ValueError("oracle pfmm failed")
     return f
+
+
+def H1(r, s, alpha=1.0):
+    """int_0^s G(r, q) / (2 q) dq (the time integral of the double-layer kernel's factor)."""
+    return lib().orc_H1(r, s, alpha)
+
+
+def repr_eval(P, w, g, points, nthreads=0):
+    """Representation formula u = V~ w - W g (Section 2) at points [np][4] = (x, y, z, t) for the
+    discrete data w [Et][nt] (p0 in space and time) and g [Et][nv] (p1 in space, p0 in time; None:
+    single-layer potential only)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 4)
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    u = np.zeros(pts.shape[0])
+    rc = lib().orc_repr_eval(ctypes.byref(P), _pd(w), _pd(gg) if gg is not None else None, _pd(pts), pts.shape[0],
+                             _pd(u), nthreads)
+    if rc:
+        raise ValueError("oracle representation formula failed")
+    return u
 
 
 def interaction_list(k):

@@ -1302,3 +1302,78 @@ double orc_cheb_node(int k, int m) { return or_cheb_node(k, m); }
 int orc_sizeof_problem(void) { return (int)sizeof(orc_problem); }
 int orc_interaction_list(int k, int *js) { return or_interaction_list(k, js); }
 int orc_nearfield_list(int k, int *js) { return or_nearfield_list(k, js); }
+
+/* ======================================================================================
+ * 9. Representation formula (Section 2): for (x, t) in Omega x (0, T)
+ *      u(x, t) = (V~ w)(x, t) - (W u)(x, t),
+ *    V~ w = int_0^t int_Gamma G(x - y, t - tau) w(y, tau),
+ *    W u  = int_0^t int_Gamma alpha dG/dn_y(x - y, t - tau) u(y, tau),
+ *    with the discrete data of Eq. 02:linear:system: w_h piecewise constant on the space-time
+ *    elements, u = g_h piecewise constant in time and piecewise linear (nodal) in space.
+ *    Time: over step j the integrals of G(r, t - tau) and of G(r, t - tau) / (2 (t - tau)) are
+ *    differences of the first antiderivatives in s = t - tau,
+ *      G1(r, s) = int_0^s G(r, q) dq = erfc(u) / (4 pi alpha r),
+ *      H1(r, s) = int_0^s G(r, q) / (2 q) dq = [erfc(u) + 2 u exp(-u^2) / sqrt(pi)] / (4 pi r^3),
+ *    u = r / (2 sqrt(alpha s)), taken as 0 for s <= 0 (causality); the double-layer integrand is
+ *    (x - y).n_y G / (2 s).  Space: the collapsed Gauss rule with n_r x n_r points per triangle
+ *    (the points must not lie on Gamma).
+ * ====================================================================================== */
+
+double orc_H1(double r, double s, double alpha)
+{
+    if (s <= 0.0) return 0.0;
+    double u = r / (2.0 * sqrt(alpha * s));
+    return (erfc(u) + 2.0 * u * exp(-u * u) / sqrt(OR_PI)) / (4.0 * OR_PI * r * r * r);
+}
+
+/* u[p] for the points pts[p] = (x, y, z, t), p < np; w: [Et][nt], g: [Et][nv] or NULL (single-layer
+ * potential only) */
+int orc_repr_eval(const orc_problem *P, const double *w, const double *g, const double *pts, int np, double *u,
+                  int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    or_trirule *R = (or_trirule *)malloc(sizeof(or_trirule));
+    if (!R) return -1;
+    or_make_trirule(P->n_r, R);
+    const double h = P->Tend / P->Et, alpha = P->alpha;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int p = 0; p < np; ++p) {
+        const double *x = pts + 4 * p, t = pts[4 * p + 3];
+        double acc = 0.0;
+        for (int tr = 0; tr < P->nt; ++tr) {
+            const int *tv = P->T + 3 * tr;
+            const double *P0 = P->V + 3 * tv[0], *P1 = P->V + 3 * tv[1], *P2 = P->V + 3 * tv[2];
+            const double jac = 2.0 * or_tri_area(P0, P1, P2);
+            double n[3];
+            or_tri_normal(P0, P1, P2, n);
+            for (int q = 0; q < R->n; ++q) {
+                double y[3];
+                or_chi(P0, P1, P2, R->s1[q], R->s2[q], y);
+                const double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+                const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                const double dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+                const double phi[3] = {1.0 - R->s1[q], R->s1[q] - R->s2[q], R->s2[q]};
+                for (int j = 1; j <= P->Et; ++j) {
+                    const double s0 = t - (j - 1) * h, s1 = t - j * h;  /* tau = t_{j-1}, t_j */
+                    if (s0 <= 0.0) break;
+                    const double dG = orc_G1(r, s0, alpha) - orc_G1(r, s1, alpha);
+                    double v = w[(size_t)(j - 1) * P->nt + tr] * dG;
+                    if (g) {
+                        const double dH = orc_H1(r, s0, alpha) - orc_H1(r, s1, alpha);
+                        double gy = 0.0;
+                        for (int c = 0; c < 3; ++c) gy += g[(size_t)(j - 1) * P->nv + tv[c]] * phi[c];
+                        v -= dn * dH * gy;
+                    }
+                    acc += R->w[q] * jac * v;
+                }
+            }
+        }
+        u[p] = acc;
+    }
+    free(R);
+    return 0;
+}

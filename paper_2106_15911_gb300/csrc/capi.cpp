@@ -743,6 +743,8 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         gls.insert(gls.end(), gw.begin(), gw.end());
         double *d_rreg = nullptr, *d_gls = nullptr;
         if ((rc = upload(H, &d_rreg, rreg, st)) || (rc = upload(H, &d_gls, gls, st))) return rc;
+        H->d_rule_reg = d_rreg;
+        H->nq_reg = prm->quad_regular * prm->quad_regular;
         NfQuadArgs a{};
         a.verts = H->d_verts;
         a.tri = H->d_tri_int;
@@ -1056,6 +1058,18 @@ int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies)
     }
     if (n_applies) *n_applies = h->n_prof;
     h->n_prof = 0;
+    return PFMM_OK;
+}
+
+int pfmm_eval_repr(pfmm_handle *h, const double *w, const double *g, const double *points, int32_t npoints,
+                   double *u, int32_t nrhs, void *stream)
+{
+    if (!h || !w || !points || !u || npoints < 0 || nrhs < 1)
+        return fail(PFMM_ERR_INVALID_ARG, "invalid pfmm_eval_repr arguments");
+    if (!h->d_rule_reg) return fail(PFMM_ERR_UNSUPPORTED, "handle has no quadrature rule");
+    launch_repr(h->d_verts, h->d_tri_user, h->nt, h->nv, h->d_rule_reg, h->nq_reg, w, g, points, npoints, nrhs, h->Et,
+                h->h, h->alpha, u, (cudaStream_t)stream);
+    CK(cudaGetLastError());
     return PFMM_OK;
 }
 

@@ -55,6 +55,8 @@ struct pfmm_handle {
     int64_t dev_bytes = 0;
 
     double *d_verts = nullptr, *d_area = nullptr;
+    double *d_rule_reg = nullptr;  // collapsed Gauss rule of the regular quadrature: s1[nq], s2[nq], w[nq]
+    int nq_reg = 0;
     int *d_tri_int = nullptr, *d_tri_user = nullptr, *d_perm = nullptr, *d_tri_leaf = nullptr, *d_leaf_start = nullptr,
         *d_leaf_grid = nullptr, *d_kidx = nullptr, *d_kinv = nullptr;
     void *d_Sx = nullptr, *d_SK = nullptr, *d_St = nullptr, *d_qt = nullptr;

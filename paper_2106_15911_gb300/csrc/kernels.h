@@ -128,5 +128,10 @@ void launch_l2t(int prec, const void *lam_leaf, const void *Sx, const void *St, 
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st, void *ws = nullptr, size_t ws_elems = 0);
 void launch_apply_M(const double *g_in, double *f, const int *tri_user, const double *area, int nrhs, int nt, int nv,
                     int Et, double h, cudaStream_t st);
+// representation formula u[rhs][p] = V~ w - W g at the points pts [np][4] = (x, y, z, t)
+// (caller's triangle and node order; g may be null: single-layer potential only)
+void launch_repr(const double *verts, const int *tri, int nt, int nv, const double *rule, int nq, const double *w,
+                 const double *g, const double *pts, int np, int nrhs, int Et, double h, double alpha, double *u,
+                 cudaStream_t st);
 
 }  // namespace pfmm

@@ -81,6 +81,7 @@ SIGNATURES = {
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
     "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
+    "pfmm_eval_repr": (ctypes.c_int, [_VP, _DP, _DP, _DP, _I, _DP, _I, _VP]),
     "pfmm_count_apply_kernels": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_int64)]),
     "pfmm_default_solve_opts": (ctypes.c_int, [ctypes.POINTER(pfmm_solve_opts)]),
     "pfmm_solve": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, ctypes.POINTER(pfmm_solve_opts),
@@ -220,6 +221,12 @@ def pfmm_apply_V_noalloc(h, w, f, nrhs: int, stream=None):
 
 def pfmm_apply_parts(h, op: int, x, f, nrhs: int, parts: int, stream=None):
     _check(lib().pfmm_apply_parts(h, int(op), _ptr(x), _ptr(f), int(nrhs), int(parts), _stream(stream)))
+
+
+def pfmm_eval_repr(h, w, g, points, u, nrhs: int, stream=None):
+    """u[rhs][p] = (V~ w - W g)(points[p]) (Section 2); g may be None (single layer only)."""
+    _check(lib().pfmm_eval_repr(h, _ptr(w), _ptr(g), _ptr(points), int(points.shape[0]), _ptr(u), int(nrhs),
+                                _stream(stream)))
 
 
 def pfmm_count_apply_kernels(h, op: int, x, f, nrhs: int, parts: int = PFMM_PART_ALL) -> int:
