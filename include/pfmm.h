@@ -232,6 +232,28 @@ int pfmm_apply_V_noalloc(pfmm_handle *h, const double *w, double *f, int32_t nrh
 int pfmm_eval_repr(pfmm_handle *h, const double *w, const double *g, const double *points, int32_t npoints,
                    double *u, int32_t nrhs, void *stream);
 
+/* ---- temporal decomposition over several GPUs (Section 4) ----------------------------------
+ * The space-time FMM shards by time: every cluster of the binary temporal tree (levels 0 ..
+ * `levels`, 2^l clusters on level l, the leaf intervals on the last level) has one owner rank,
+ * which runs the FMM operations of all space-time boxes attached to it.  Owners follow the three
+ * rules of Section 4.1 (levels >= ceil(log2 nranks): consecutive ranks in ascending order, as
+ * evenly as possible; the level above: the owner of the left child; coarser levels: from each of
+ * 2^l consecutive rank groups the rank with the fewest clusters so far).  The messages of one
+ * distributed matrix-vector product (Section 4.2) are one-directional per cluster: moments to
+ * the owners of the parent (M2M, levels >= 3) and of the M2L targets k + 2 and, for even k, k + 3
+ * (Eq. 03:ILtemp, levels >= 2); locals to the owners of the two children (L2L, levels 2 ..
+ * levels - 1); the input of a leaf interval to the owner of the next one (nearfield halo).
+ * Host logic only (no device work); this build runs one GPU per process and uses it to plan. */
+#define PFMM_MSG_MOMENTS 0
+#define PFMM_MSG_LOCALS 1
+#define PFMM_MSG_INPUT 2
+/* owner[(1 << l) - 1 + k] = rank owning cluster k of level l (array of 2^(levels+1) - 1 ints). */
+int pfmm_shard_owners(int32_t levels, int32_t nranks, int32_t *owner);
+/* The messages as rows (kind, level, interval, source rank, destination rank), in the order of a
+ * bottom-up sweep over the levels; at most `cap` rows are written to msgs [cap][5], *count gets
+ * the total (call with cap = 0 to size the array). */
+int pfmm_shard_messages(int32_t levels, int32_t nranks, int32_t *msgs, int64_t cap, int64_t *count);
+
 /* ---- solver ------------------------------------------------------------------------------ */
 #define PFMM_DIRECT 0    /* V_h w = (1/2 M_h + K_h) g  (Section 2, Eq. 02:linear:system) */
 #define PFMM_INDIRECT 1  /* V_h w = M_h g              (single-layer ansatz) */

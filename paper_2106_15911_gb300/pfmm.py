@@ -82,6 +82,9 @@ SIGNATURES = {
     "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
     "pfmm_eval_repr": (ctypes.c_int, [_VP, _DP, _DP, _DP, _I, _DP, _I, _VP]),
+    "pfmm_shard_owners": (ctypes.c_int, [_I, _I, ctypes.POINTER(ctypes.c_int32)]),
+    "pfmm_shard_messages": (ctypes.c_int, [_I, _I, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "pfmm_count_apply_kernels": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, _I, ctypes.POINTER(ctypes.c_int64)]),
     "pfmm_default_solve_opts": (ctypes.c_int, [ctypes.POINTER(pfmm_solve_opts)]),
     "pfmm_solve": (ctypes.c_int, [_VP, _I, _DP, _DP, _I, ctypes.POINTER(pfmm_solve_opts),
@@ -227,6 +230,30 @@ def pfmm_eval_repr(h, w, g, points, u, nrhs: int, stream=None):
     """u[rhs][p] = (V~ w - W g)(points[p]) (Section 2); g may be None (single layer only)."""
     _check(lib().pfmm_eval_repr(h, _ptr(w), _ptr(g), _ptr(points), int(points.shape[0]), _ptr(u), int(nrhs),
                                 _stream(stream)))
+
+
+PFMM_MSG_MOMENTS, PFMM_MSG_LOCALS, PFMM_MSG_INPUT = 0, 1, 2
+
+
+def pfmm_shard_owners(levels: int, nranks: int):
+    """Owner rank of every temporal cluster: a list per level l = 0 .. levels of 2^l ranks."""
+    import numpy as np
+
+    o = np.zeros((1 << (levels + 1)) - 1, np.int32)
+    _check(lib().pfmm_shard_owners(int(levels), int(nranks), o.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return [o[(1 << l) - 1:(1 << (l + 1)) - 1].tolist() for l in range(levels + 1)]
+
+
+def pfmm_shard_messages(levels: int, nranks: int):
+    """Messages of a distributed product: int array [n][5] of (kind, level, interval, src, dst)."""
+    import numpy as np
+
+    n = ctypes.c_int64()
+    _check(lib().pfmm_shard_messages(int(levels), int(nranks), None, 0, ctypes.byref(n)))
+    m = np.zeros((max(n.value, 1), 5), np.int32)
+    _check(lib().pfmm_shard_messages(int(levels), int(nranks), m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     n.value, ctypes.byref(n)))
+    return m[:n.value]
 
 
 def pfmm_count_apply_kernels(h, op: int, x, f, nrhs: int, parts: int = PFMM_PART_ALL) -> int:
