@@ -485,7 +485,7 @@ def _paper_scale(dev, steps=5, dense_rows=4):
 def _profile_case(dev, case):
     """Small cases for ncu captures: the learned preconditioner's layers (`mpnn`), its compiled
     form (`mpnn_compiled`), the on-the-fly nearfield (`otf`), the slab M2L of 8^3 grids
-    (`m2l_slab`), the FP64 residue-arithmetic nearfield (`crt`, 3072 triangles x 128 steps).  3072-triangle cube; 128 steps
+    (`m2l_slab`), the FP64 residue-arithmetic nearfield (`crt`, 3072 triangles x 256 steps).  3072-triangle cube; 128 steps
     (network) or 32 steps (on-the-fly); 1728-triangle cube x 32 steps with an 8^3 leaf grid
     (c_st 0.1, interaction radius 7) for the slab M2L, far field only."""
     import numpy as np
@@ -507,7 +507,7 @@ def _profile_case(dev, case):
         z = torch.empty_like(v)
         run = lambda: net.apply(v, z)  # noqa: E731
     elif case == "crt":
-        Et = 128
+        Et = 256
         op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_FP64)
         w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
         run = lambda: op.V(w, parts=P.PFMM_PART_NEAR)  # noqa: E731

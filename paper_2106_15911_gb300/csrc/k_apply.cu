@@ -795,17 +795,19 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
     lam[((((size_t)rhs * A.nint + k) * A.nbox + box) * na + b) * A.nk + iv] = val;
 }
 
-// Fused M2L for grids of at most 4^3 cells (FP32): one CTA per (target interval k, time node b,
-// rhs) keeps the source moments of all cells, the intermediates T1, T2 of all cells and the
-// target locals in shared memory.  Every thread owns one multi-index triple and one grid
-// coordinate and keeps a 4 x 4 block of cells in registers, so each step of its list does 64
-// FMAs from 16 moment / intermediate loads and 7 coefficient loads.  Coefficients beyond the
+// Fused M2L for grids of at most 4^3 cells: one CTA per (target interval k, time node b, rhs)
+// keeps the source moments of all cells, the intermediates T1, T2 of all cells and the target
+// locals in shared memory.  The grid is padded to FG^3 cells (FG = 4, or 2 for levels with G <= 2,
+// whose CTAs then need an eighth of the shared memory and work).  Every thread owns one
+// multi-index triple and one grid coordinate and keeps an FG x FG block of cells in registers, so
+// each step of its list does FG^3 FMAs from FG^2 moment / intermediate loads and 7 coefficient
+// loads.  Coefficients beyond the
 // interaction radius are zeroed once per (J, a), which applies Eq. 03:Iarea without branches.
 // Same arithmetic as the three-pass kernels (cells with G < 4 are padded with empty cells).
 // Split mode (levels with too few intervals to fill the GPU): one CTA per (k, b, source term)
 // with source term = (J, a) of the interaction list; each term's locals go to its own slice of a
 // workspace and k_m2l_sum_terms adds the slices in a fixed order (deterministic).
-constexpr int FG = 4;  // padded grid extent per direction
+constexpr int FGMax = 4;  // padded grid extent per direction: 4, or 2 for the coarse levels (G <= 2)
 
 constexpr int kM2LThreads = 384;
 // split mode below this many (interval, node, rhs) CTAs per SM: eight.  At two resident CTAs per
@@ -813,8 +815,8 @@ constexpr int kM2LThreads = 384;
 // lose much of the last one; one-term CTAs are uniform and many
 constexpr int kM2LSplitCtasPerSm = 8;
 
-template <typename R>
-__global__ void __launch_bounds__(kM2LThreads, sizeof(R) == 4 ? 2 : 1) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
+template <typename R, int FG>
+__global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2 : 1)) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
                                                                 const R *__restrict__ E1, const R *__restrict__ pref,
                                                                 R *__restrict__ lam, int nrhs, int split,
                                                                 R *__restrict__ part)
@@ -1154,10 +1156,12 @@ size_t m2l_slab_smem(int nk, int ne, int mx, size_t es)
            4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + SG * SG * SG);
 }
 
+// padded grid extent of the fused kernel for a G^3 grid
+int m2l_fused_fg(int G) { return G <= 2 ? 2 : FGMax; }
+
 size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
 {
-    (void)G;
-    const int CS = FG * FG * FG + 1, m1 = mx + 1;
+    const int FG = m2l_fused_fg(G), CS = FG * FG * FG + 1, m1 = mx + 1;
     return es * ((size_t)2 * std::max(ne, nk) * CS + (size_t)7 * m1 * m1) +
            4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
 }
@@ -1172,11 +1176,12 @@ int m2l_engine(int prec, int G, int nk, int ne, int mx)
 {
     // double-FP32: the fused kernel at one CTA per SM when its 8-byte intermediates fit the
     // 227 KB of shared memory a CTA may hold (m_x <= 6)
+    const int FG = m2l_fused_fg(G);
     if (prec == 2 && G <= FG && m2l_fused_smem(G, nk, ne, mx, 8) <= 227 * 1024 && nk * FG <= 2 * kM2LThreads)
         return kM2LFused;
     if (prec != 1) return kM2LThreePass;
     if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4) <= 200 * 1024 && nk * FG <= 2 * kM2LThreads) return kM2LFused;
-    if (G > FG && G <= SG && mx <= 6 && m2l_slab_smem(nk, ne, mx, 4) <= 220 * 1024 && nk <= 256) return kM2LSlab;
+    if (G > FGMax && G <= SG && mx <= 6 && m2l_slab_smem(nk, ne, mx, 4) <= 220 * 1024 && nk <= 256) return kM2LSlab;
     return kM2LThreePass;
 }
 
@@ -1205,9 +1210,10 @@ int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, in
             const int64_t split_ctas = (int64_t)kM2LSplitCtasPerSm * (g.nsm > 0 ? g.nsm : 152);
             const int split = ((int64_t)L.nint * na * nrhs < split_ctas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
             const dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
-            cudaFuncSetAttribute(k_m2l_fused<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            k_m2l_fused<R><<<grd, kM2LThreads, fsm, st>>>(A, (const R *)mb, (const R *)L.E1, (const R *)L.pref, (R *)lb,
-                                                         nrhs, split, (R *)T1);
+            auto kf = m2l_fused_fg(L.G) == 2 ? k_m2l_fused<R, 2> : k_m2l_fused<R, FGMax>;
+            cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            kf<<<grd, kM2LThreads, fsm, st>>>(A, (const R *)mb, (const R *)L.E1, (const R *)L.pref, (R *)lb, nrhs,
+                                              split, (R *)T1);
             if (split)
                 k_m2l_sum_terms<R><<<(unsigned)((nlev + 255) / 256), 256, 0, st>>>((const R *)T1, na, nlev, per_k,
                                                                                   L.nint, (R *)lb);
