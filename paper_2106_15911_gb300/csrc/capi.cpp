@@ -349,7 +349,7 @@ int pfmm::run_nf_crt(pfmm_handle *H, int op, const double *x, int nrhs, double *
     P.nt = H->nt;
     P.res = H->d_res8;
     P.err = H->d_err;
-    if (launch_nf_apply_crt(op == 0 ? H->mapAVres : H->mapAKres, mW, P, H->nsm, st))
+    if (launch_nf_apply_crt(op == 0 ? H->mapAVres : H->mapAKres, mW, P, H->nsm, st, H->crt_form))
         return fail(PFMM_ERR_CUDA, std::string("FP64 tensor-core nearfield launch: ") +
                                        cudaGetErrorString(cudaGetLastError()));
     launch_crt_combine(H->d_res8, nrhs, H->Et, H->nt, op == 0 ? H->d_rexpV : H->d_rexpK, H->d_wmax, b, fint, st);
@@ -430,6 +430,43 @@ int pfmm_default_params(pfmm_params *p)
     p->quad_singular = 6;
     p->nf_engine = PFMM_NF_AUTO;
     p->fp64_native = 0;
+    return PFMM_OK;
+}
+
+// The faster of the two forms of the FP64 tensor-core nearfield (one row tile and two moduli per
+// work item, or two row tiles sharing each input stage), timed with CUDA events on this handle's
+// V product of a zero input (the work does not depend on the values).
+static int tune_crt_form(pfmm_handle *H, cudaStream_t st)
+{
+    int rc = ensure_workspace(H, 1);
+    if (rc) return rc;
+    double *x = nullptr;
+    if ((rc = H->alloc(&x, (size_t)H->Et * H->nt))) return rc;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * H->Et * H->nt, st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int form = 1; form <= 2; ++form) {
+        H->crt_form = form;
+        if ((rc = pfmm::run_nf_crt(H, 0, x, 1, H->d_fint, st))) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2 && !rc; ++r) rc = pfmm::run_nf_crt(H, 0, x, 1, H->d_fint, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && ms < best) {
+            best = ms;
+            H->crt_best_form = form;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    H->crt_form = H->crt_best_form;
+    H->release(x);
+    if (rc) return rc;
+    CK(cudaGetLastError());
     return PFMM_OK;
 }
 
@@ -849,6 +886,7 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(st));
+    if (H->crtV && (rc = tune_crt_form(H, st))) return rc;
     return PFMM_OK;
 }
 

@@ -314,6 +314,229 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_crt(const __grid_constant__
 }
 
 // ------------------------------------------------------------------------------------------
+// Two row tiles per CTA: the W stage (32 KB) feeds the MMAs of two 128-row tiles, so every byte
+// brought from L2 / HBM serves twice the tensor work of the form above.  A work item is (modulus,
+// pair of row tiles, interval block, rhs); the two tiles' accumulators take all 512 TMEM columns,
+// so the epilogue's reduction after each 1024-column chunk pauses the MMAs (about 900 of 16000
+// cycles).  Warps: 0 TMA, 1 MMA, 2..9 epilogue (warp w serves tile (w - 2) / 4 and TMEM lane
+// quadrant w % 4).  Three 64 KB stages.
+constexpr int STAGE2 = 2 * A_TILE + 2 * B_HALF;  // 64 KB
+constexpr int NSTAGE2 = 3;
+constexpr int kCrt2Threads = 320;
+
+struct CItem2 {
+    int m, rhs, ib;
+    int panel[2], r0[2];
+    bool has1;
+};
+
+__device__ __forceinline__ CItem2 decode_citem2(const NfCrtParams &P, int it)
+{
+    const int ntp = (P.ntiles + 1) / 2, per_m = ntp * P.nib * P.nrhs;
+    CItem2 I;
+    I.m = it / per_m;  // modulus-major: consecutive CTAs share the modulus (its W residues stay in L2)
+    int r_ = it % per_m;
+    I.rhs = r_ / (ntp * P.nib);
+    r_ %= ntp * P.nib;
+    I.ib = r_ % P.nib;
+    const int tp = r_ / P.nib;
+    const int t0 = 2 * tp, t1 = 2 * tp + 1;
+    I.panel[0] = P.tiles[2 * t0];
+    I.r0[0] = P.tiles[2 * t0 + 1];
+    I.has1 = t1 < P.ntiles;
+    I.panel[1] = I.has1 ? P.tiles[2 * t1] : I.panel[0];
+    I.r0[1] = I.has1 ? P.tiles[2 * t1 + 1] : I.r0[0];
+    return I;
+}
+
+__global__ void __launch_bounds__(kCrt2Threads, 1) k_nf_apply_crt2(const __grid_constant__ CUtensorMap mapA,
+                                                                   const __grid_constant__ CUtensorMap mapW,
+                                                                   NfCrtParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + NSTAGE2 * STAGE2);
+    uint64_t *empty = full + NSTAGE2;
+    uint64_t *tfull = empty + NSTAGE2;
+    uint64_t *tempty = tfull + 1;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE2; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 256);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    uint64_t deadline = gtimer() + kTimeoutNs;  // renewed per chunk: each wait is bounded by 2 s
+    const int nst = 4 * P.nkb;
+    const int nch = (nst + CHUNK - 1) / CHUNK;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int g = 0;
+            for (int it = blockIdx.x; it < P.nitems && !s_abort; it += gridDim.x) {
+                const CItem2 I = decode_citem2(P, it);
+                bool two[2];
+                long long rbase[2];
+                int rpad[2];
+                for (int q = 0; q < 2; ++q) {
+                    const PanelGPU &Pn = P.panels[I.panel[q]];
+                    two[q] = I.r0[q] + 64 < Pn.nrows;
+                    rbase[q] = (P.kop ? Pn.offK : Pn.offV) / P.cols_pad + I.r0[q];
+                    rpad[q] = Pn.rows_pad;
+                }
+                for (int ch = 0; ch < nch && !s_abort; ++ch) {
+                    deadline = gtimer() + kTimeoutNs;
+                    const int st1 = min(nst, (ch + 1) * CHUNK);
+                    for (int st = ch * CHUNK; st < st1; ++st, ++g) {
+                        const int s = g % NSTAGE2;
+                        if (!mbar_wait(&empty[s], ((g / NSTAGE2) & 1) ^ 1, deadline)) {
+                            atomicExch(P.err, 21);
+                            s_abort = 1;
+                            break;
+                        }
+                        const int d = st / P.nkb, kb = st % P.nkb;
+                        unsigned char *sA = smem + s * STAGE2;
+                        uint32_t bytes = (d < 3 ? 2 : 1) * B_HALF;
+                        for (int q = 0; q < (I.has1 ? 2 : 1); ++q) bytes += two[q] ? A_TILE : A_TILE / 2;
+                        mbar_expect_tx(&full[s], bytes);
+                        for (int q = 0; q < (I.has1 ? 2 : 1); ++q) {
+                            const int blk = (int)((rbase[q] + (long long)d * rpad[q]) >> 6) * P.nkb + kb;
+                            tma_4d(sA + q * A_TILE, &mapA, 0, 0, blk, I.m, &full[s]);
+                            if (two[q]) tma_4d(sA + q * A_TILE + A_TILE / 2, &mapA, 0, 0, blk + P.nkb, I.m, &full[s]);
+                        }
+                        unsigned char *sB = sA + 2 * A_TILE;
+                        for (int ph = (d < 3 ? 0 : 1); ph < 2; ++ph) {
+                            const int phs = ((ph - d) % 2 + 2) % 2, q = (phs - (ph - d)) / 2;
+                            tma_5d(sB + ph * B_HALF, &mapW, kb * BK, phs, I.ib * 128 - q, I.rhs, I.m, &full[s]);
+                        }
+                    }
+                }
+            }
+            const uint64_t dl2 = gtimer() + kTimeoutNs / 20;
+            for (int j = (g > NSTAGE2 ? g - NSTAGE2 : 0); j < g; ++j)
+                mbar_wait(&full[j % NSTAGE2], (j / NSTAGE2) & 1, dl2);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int g = 0, u = 0;
+            const uint32_t id256 = idesc_f16(BM, 256), id128 = idesc_f16(BM, 128);
+            for (int it = blockIdx.x; it < P.nitems && !s_abort; it += gridDim.x) {
+                const CItem2 I = decode_citem2(P, it);
+                for (int ch = 0; ch < nch && !s_abort; ++ch, ++u) {
+                    deadline = gtimer() + kTimeoutNs;
+                    if (!mbar_wait(tempty, (u & 1) ^ 1, deadline)) {
+                        atomicExch(P.err, 22);
+                        s_abort = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int st1 = min(nst, (ch + 1) * CHUNK);
+                    for (int st = ch * CHUNK; st < st1; ++st, ++g) {
+                        const int s = g % NSTAGE2;
+                        if (!mbar_wait(&full[s], (g / NSTAGE2) & 1, deadline)) {
+                            atomicExch(P.err, 23);
+                            s_abort = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const int d = st / P.nkb;
+                        const uint32_t a0 = su32(smem + s * STAGE2), b0 = a0 + 2 * A_TILE;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t ko = kk * 32;
+                            const uint32_t accf = (ch == 0 && st == 0 && kk == 0) ? 0u : 1u;
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                if (q == 1 && !I.has1) break;
+                                const uint32_t aq = a0 + q * A_TILE + ko, dq = tmem + q * 256;
+                                if (d < 3)
+                                    mma_f16(dq, sw128_desc(aq), sw128_desc(b0 + ko), id256, accf);
+                                else
+                                    mma_f16(dq + 128, sw128_desc(aq), sw128_desc(b0 + B_HALF + ko), id128, 1u);
+                            }
+                        }
+                        mma_commit(&empty[s]);
+                    }
+                    mma_commit(tfull);
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9; tile (warp - 2) / 4, TMEM lane quadrant warp % 4
+        const int quad = warp & 3, tq = (warp - 2) >> 2;
+        const int row_l = quad * 32 + lane;
+        int u = 0;
+        for (int it = blockIdx.x; it < P.nitems && !s_abort; it += gridDim.x) {
+            const CItem2 I = decode_citem2(P, it);
+            const bool active = tq == 0 || I.has1;
+            const PanelGPU &Pn = P.panels[I.panel[tq]];
+            const int row = I.r0[tq] + row_l;
+            const bool row_ok = active && row < Pn.nrows;
+            const float p = (float)c_p[I.m], invp = c_invp[I.m];
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + tq * 256;
+            unsigned char *out = P.res + ((size_t)I.m * P.nrhs + I.rhs) * P.Et * (size_t)P.nt + Pn.row0 + row;
+            for (int ch = 0; ch < nch && !s_abort; ++ch, ++u) {
+                deadline = gtimer() + kTimeoutNs;
+                if (!mbar_wait(tfull, u & 1, deadline)) {
+                    atomicExch(P.err, 24);
+                    s_abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const bool last = ch == nch - 1;
+                if (active) {
+#pragma unroll 1
+                    for (int c0 = 0; c0 < 256; c0 += 32) {
+                        uint32_t v[32];
+                        tmem_ld32(tbase + c0, v);
+                        if (!last) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = __float_as_uint(mod_small(__uint_as_float(v[j]), p, invp));
+                            tmem_st32(tbase + c0, v);
+                        } else if (row_ok) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int c = c0 + j, ph = c >> 7, iv = I.ib * 128 + (c & 127);
+                                float r = mod_small(__uint_as_float(v[j]), p, invp);
+                                r = r < 0.f ? r + p : r;
+                                r = r < 0.f ? r + p : r;
+                                r = r >= p ? r - p : r;
+                                if (iv < P.nint) out[(size_t)(2 * iv + ph) * P.nt] = (unsigned char)(int)r;
+                            }
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(tempty);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // scaling and residues
 
 // largest |A| of every target row over the step offsets and columns of its panel, as FP64 bits
@@ -546,8 +769,19 @@ void launch_crt_combine(const unsigned char *res, int nrhs, int Et, int nt, cons
 
 size_t nf_crt_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + 1024 + 256; }
 
-int launch_nf_apply_crt(const CUtensorMap &A, const CUtensorMap &W, const NfCrtParams &P, int nsm, cudaStream_t st)
+int launch_nf_apply_crt(const CUtensorMap &A, const CUtensorMap &W, const NfCrtParams &P, int nsm, cudaStream_t st,
+                        int form)
 {
+    if (form == 2) {  // two row tiles per CTA, one modulus per item
+        NfCrtParams Q = P;
+        Q.nitems = kCrtModuli * ((P.ntiles + 1) / 2) * P.nib * P.nrhs;
+        const size_t smem = (size_t)NSTAGE2 * STAGE2 + 1024 + 256;
+        cudaError_t e = cudaFuncSetAttribute(k_nf_apply_crt2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return -1;
+        const int grid = Q.nitems < nsm ? Q.nitems : nsm;
+        k_nf_apply_crt2<<<grid, kCrt2Threads, smem, st>>>(A, W, Q);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
     const size_t smem = nf_crt_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_nf_apply_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -1;

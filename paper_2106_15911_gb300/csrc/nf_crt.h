@@ -41,6 +41,9 @@ void launch_crt_split_input(const double *x, const int *perm, int ncol, int ncol
 void launch_crt_combine(const unsigned char *res, int nrhs, int Et, int nt, const int *rowexp,
                         const unsigned long long *wmax, int b, double *f, cudaStream_t st);
 size_t nf_crt_smem_bytes();
-int launch_nf_apply_crt(const CUtensorMap &A, const CUtensorMap &W, const NfCrtParams &P, int nsm, cudaStream_t st);
+// form 1: one row tile and two moduli per CTA work item; form 2: two row tiles sharing each W
+// stage, one modulus per item (P.nitems is recomputed for it)
+int launch_nf_apply_crt(const CUtensorMap &A, const CUtensorMap &W, const NfCrtParams &P, int nsm, cudaStream_t st,
+                        int form);
 
 }  // namespace pfmm
