@@ -104,6 +104,9 @@ typedef struct pfmm_params {
                            nf_engine) and the FMM passes in double-FP32 arithmetic (pairs of FP32
                            numbers, about 48 significant bits, on the FP32 pipe); 1: every phase on
                            the FP64 pipe (reference mode, about 50x slower on GB300) */
+    int32_t nf_form;    /* FP64 tensor-core nearfield kernel form: 0 (default) the faster of the two,
+                           timed at build; 1 one 128-row tile and two moduli per work item; 2 two
+                           row tiles sharing each input stage, one modulus per item */
 } pfmm_params;
 
 typedef struct pfmm_handle pfmm_handle;
@@ -122,6 +125,7 @@ typedef struct pfmm_info {
     int32_t nf_dense_columns;     /* 1: the panels share one column space (all triangles / nodes,
                                      zero where the source is not near), 0: compact per panel */
     int32_t m2l_engine[32];       /* M2L kernel of level l (l = 2 .. p; 0 elsewhere): PFMM_M2L_* */
+    int32_t nf_form;              /* form of the FP64 tensor-core nearfield kernel in use (0: none) */
     double m2l_flops;             /* flops of one rhs's M2L in the separable form (Eq. m2l with
                                      Eq. exp_coeffs_3d applied one direction at a time over the
                                      full box grid of every level, all interval pairs of Eq.
@@ -137,7 +141,7 @@ typedef struct pfmm_info {
 
 /* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,
  * leaf_steps = 2, leaf_tris = 16, FP64, stored nearfield, quad_regular = 3,
- * quad_singular = 6, nf_engine = PFMM_NF_AUTO, fp64_native = 0.  Returns PFMM_OK or
+ * quad_singular = 6, nf_engine = PFMM_NF_AUTO, fp64_native = 0, nf_form = 0.  Returns PFMM_OK or
  * PFMM_ERR_INVALID_ARG (p NULL). */
 int pfmm_default_params(pfmm_params *p);
 

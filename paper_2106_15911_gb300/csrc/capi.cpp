@@ -430,6 +430,7 @@ int pfmm_default_params(pfmm_params *p)
     p->quad_singular = 6;
     p->nf_engine = PFMM_NF_AUTO;
     p->fp64_native = 0;
+    p->nf_form = 0;
     return PFMM_OK;
 }
 
@@ -886,7 +887,8 @@ static int build_impl(const pfmm_mesh *mesh, const pfmm_params *prm, cudaStream_
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(st));
-    if (H->crtV && (rc = tune_crt_form(H, st))) return rc;
+    if (H->crtV && (prm->nf_form == 1 || prm->nf_form == 2)) H->crt_form = prm->nf_form;
+    else if (H->crtV && (rc = tune_crt_form(H, st))) return rc;
     return PFMM_OK;
 }
 
@@ -1128,6 +1130,7 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
                                    : t.sizeV * (h->tcV ? 4 : (int64_t)h->es) + t.sizeK * (h->tcK ? 4 : (int64_t)h->es);
     info->device_bytes = h->dev_bytes;
     info->nf_tensor_cores = (h->tcV || h->crtV ? 1 : 0) | (h->tcK || h->crtK ? 2 : 0);
+    info->nf_form = h->crtV || h->crtK ? h->crt_form : 0;
     if (h->crtV || h->crtK)
         info->nearfield_bytes += (h->crtV ? t.sizeV : 0) * 2 * pfmm::kCrtModuli + (h->crtK ? t.sizeK : 0) * 2 * pfmm::kCrtModuli;
     info->nearfield_v_elements = t.sizeV;

@@ -26,11 +26,13 @@ def _rel(a, b):
     (cube_mesh, 4, 512, dict(m_t=3, m_x=3, c_st=1.0)),      # 256 leaf intervals: two interval blocks
     (cube_sphere_mesh, 16, 64, dict(m_t=4, m_x=5, c_st=0.1, n_tr=6)),  # dense columns with holes
 ])
-def test_fp64_tensor_core_nearfield(mesh, n_a, Et, kw):
+@pytest.mark.parametrize("form", [1, 2])
+def test_fp64_tensor_core_nearfield(mesh, n_a, Et, kw, form):
     V, T = mesh(n_a)
-    op = P.Operator(V, T, 1.0, Et, **kw)
+    op = P.Operator(V, T, 1.0, Et, nf_form=form, **kw)
     opc = P.Operator(V, T, 1.0, Et, nf_engine=P.PFMM_NF_CUDA_CORES, **kw)
     assert op.info()["nf_tensor_cores"] == 3 and opc.info()["nf_tensor_cores"] == 0
+    assert op.info()["nf_form"] == form
     Pr = O.make_problem(V, T, 1.0, Et, **kw)
     w = random_density(Et, T.shape[0], 2, seed=71)
     g = random_density(Et, V.shape[0], 2, seed=72)
@@ -50,13 +52,15 @@ def test_fp64_tensor_core_nearfield(mesh, n_a, Et, kw):
     opc.close()
 
 
-def test_fp64_tensor_core_nearfield_scales_exactly():
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_fp64_tensor_core_nearfield_scales_exactly(form):
     """Scales are powers of two per right-hand side, so 2^k x gives the same integers and
-    exactly 2^k times the result; a zero right-hand side gives zeros."""
+    exactly 2^k times the result; a zero right-hand side gives zeros (either kernel form, and
+    the one the build-time timing picks)."""
     V, T = cube_mesh(8)
     Et = 64
-    op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0)
-    assert op.info()["nf_tensor_cores"] == 3
+    op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, nf_form=form)
+    assert op.info()["nf_tensor_cores"] == 3 and op.info()["nf_form"] in ((form,) if form else (1, 2))
     w = random_density(Et, T.shape[0], 1, seed=73)[0]
     g = random_density(Et, V.shape[0], 1, seed=74)[0]
     for apply, x in ((op.V, w), (op.K, g)):
