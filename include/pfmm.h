@@ -138,6 +138,7 @@ typedef struct pfmm_info {
 #define PFMM_M2L_THREE_PASS 1
 #define PFMM_M2L_FUSED 2
 #define PFMM_M2L_SLAB 3
+#define PFMM_M2L_FUSED_SLICED 4  /* the fused kernel forming T2 one nu1 at a time (FP32, m_x = 8) */
 
 /* Fill *p with defaults: m_t = 4, m_x = 4, c_st = 1, n_tr = -1, eps_tr = 1e-12,
  * leaf_steps = 2, leaf_tris = 16, FP64, stored nearfield, quad_regular = 3,

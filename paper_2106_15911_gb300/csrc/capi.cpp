@@ -1152,7 +1152,9 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     }
     for (int l = 2; l <= h->p && l < 32 && l < (int)h->dl.size(); ++l) {
         const int e = pfmm::m2l_engine(h->fprec, h->dl[l].G, h->nk, h->ne, h->mx);
-        info->m2l_engine[l] = e == pfmm::kM2LFused ? PFMM_M2L_FUSED : (e == pfmm::kM2LSlab ? PFMM_M2L_SLAB : PFMM_M2L_THREE_PASS);
+        info->m2l_engine[l] = e == pfmm::kM2LFused ? PFMM_M2L_FUSED
+                              : e == pfmm::kM2LFusedSliced ? PFMM_M2L_FUSED_SLICED
+                              : (e == pfmm::kM2LSlab ? PFMM_M2L_SLAB : PFMM_M2L_THREE_PASS);
     }
     return PFMM_OK;
 }

@@ -815,8 +815,8 @@ constexpr int kM2LThreads = 384;
 // lose much of the last one; one-term CTAs are uniform and many
 constexpr int kM2LSplitCtasPerSm = 8;
 
-template <typename R, int FG>
-__global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2 : 1)) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
+template <typename R, int FG, bool SL>
+__global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 && !SL ? 2 : 1)) k_m2l_fused(M2LArgs A, const R *__restrict__ mu,
                                                                 const R *__restrict__ E1, const R *__restrict__ pref,
                                                                 R *__restrict__ lam, int nrhs, int split,
                                                                 R *__restrict__ part)
@@ -824,13 +824,18 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2
     extern __shared__ unsigned char smem_raw[];
     constexpr int C3 = FG * FG * FG, CS = C3 + 1;  // cell rows are padded by one (bank spread)
     const int G = A.G, nk = A.nk, ne = A.ne, mx = A.mx, m1 = mx + 1, na = A.na, esz = m1 * m1;
+    // SL (sliced): T2 is formed and consumed one value of nu1 at a time, so U needs only nk rows
+    // (the largest slice, nu1 = 0, has C(m_x+3, 3) = nk budget entries); the shared memory of
+    // degrees whose full T2 would not fit
+    const int nu_rows = SL ? nk : max(ne, nk);
     R *T1s = reinterpret_cast<R *>(smem_raw);  // [ne][CS]  cells (X1, Y2, Y3)
-    R *U = T1s + ne * CS;                      // [ne][CS]  moments [nk][CS] in pass 1, then T2 (X1, X2, Y3)
-    R *Es = U + ne * CS;                       // [7][m1][m1] offsets -3..3, zero outside the radius
+    R *U = T1s + ne * CS;                      // [nu_rows][CS]  moments [nk][CS] in pass 1, then T2 (X1, X2, Y3)
+    R *Es = U + nu_rows * CS;                  // [7][m1][m1] offsets -3..3, zero outside the radius
     int *kid = reinterpret_cast<int *>(Es + 7 * esz);
     int *kin = kid + nk;
     int *eof = kin + m1 * m1 * m1;
     int *cbx = eof + nk;                       // [C3] padded cell -> box or -1
+    int *eofs = cbx + C3;                      // SL: offset of a triple's budget range within its nu1 slice
     const int nterm = split ? 2 * na : 1;  // source terms per CTA group: (J index, a)
     const int kb = blockIdx.x / nterm, term = blockIdx.x % nterm;
     const int k = kb / na, b = kb % na, rhs = blockIdx.y;
@@ -842,6 +847,15 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2
     for (int i = threadIdx.x; i < C3; i += blockDim.x) {
         int x = i / (FG * FG), y = (i / FG) % FG, z = i % FG;
         cbx[i] = (x < G && y < G && z < G) ? A.cellbox[(x * G + y) * G + z] : -1;
+    }
+    if (SL && threadIdx.x == 0) {
+        int off[kMaxMx + 1];
+        for (int v = 0; v <= mx; ++v) off[v] = 0;
+        for (int t = 0; t < nk; ++t) {
+            const int n1 = A.kidx[3 * t], s0 = n1 + A.kidx[3 * t + 1] + A.kidx[3 * t + 2];
+            eofs[t] = off[n1];
+            off[n1] += mx - s0 + 1;
+        }
     }
     // target locals of this thread's pass-3 items (nu, X1), cells (X1, X2, X3), kept in registers
     R lamr[2][FG][FG];
@@ -904,10 +918,13 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2
                 }
             }
             __syncthreads();
+            for (int sl = 0; sl < (SL ? m1 : 1); ++sl) {
+            if (SL && sl > 0) __syncthreads();  // the previous slice's pass 3 is done with U
             // pass 2 (direction y): unit = (triple (nu1, nu2, k3), X1, Y3); registers: cells X2; T2 -> U
             for (int u = threadIdx.x; u < nitems * FG; u += blockDim.x) {
                 const int z = u % FG, X1 = (u / FG) % FG, t = u / (FG * FG), tk = kid[t];
                 const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + nu2 + k3;
+                if (SL && nu1 != sl) continue;
                 for (int Bp = s0; Bp <= mx; ++Bp) {
                     R acc[FG];
 #pragma unroll
@@ -925,7 +942,7 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2
                             for (int X2 = 0; X2 < FG; ++X2) acc[X2] += e[X2 - Y2 + 3] * tv;
                         }
                     }
-                    R *out = U + (eof[t] + Bp - s0) * CS + X1 * FG * FG + z;
+                    R *out = U + ((SL ? eofs[t] : eof[t]) + Bp - s0) * CS + X1 * FG * FG + z;
 #pragma unroll
                     for (int X2 = 0; X2 < FG; ++X2) out[X2 * FG] = acc[X2];
                 }
@@ -938,13 +955,15 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2
                 if (it >= nitems) break;
                 const int iv = it / FG, X1 = it % FG, tk = kid[iv];
                 const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, nu3 = tk >> 16, smax = mx - nu1 - nu2 - nu3;
+                if (SL && nu1 != sl) continue;
                 R acc[FG][FG];
 #pragma unroll
                 for (int y = 0; y < FG; ++y)
 #pragma unroll
                     for (int z = 0; z < FG; ++z) acc[y][z] = R(0);
                 for (int k3 = 0; k3 <= smax; ++k3) {
-                    const int row = eof[kin[(nu1 * m1 + nu2) * m1 + k3]] + (mx - nu3 - nu1 - nu2 - k3);
+                    const int t2 = kin[(nu1 * m1 + nu2) * m1 + k3];
+                    const int row = (SL ? eofs[t2] : eof[t2]) + (mx - nu3 - nu1 - nu2 - k3);
                     const R *trow = U + row * CS + X1 * FG * FG;
                     R e[7];
 #pragma unroll
@@ -965,6 +984,7 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 ? 2
 #pragma unroll
                     for (int X3 = 0; X3 < FG; ++X3) lamr[q][X2][X3] += coef * acc[X2][X3];
             }
+            }  // slices
         }
     }
     // write the locals of the non-empty target boxes (intervals 0 and 1 get zeros); split mode:
@@ -1159,11 +1179,12 @@ size_t m2l_slab_smem(int nk, int ne, int mx, size_t es)
 // padded grid extent of the fused kernel for a G^3 grid
 int m2l_fused_fg(int G) { return G <= 2 ? 2 : FGMax; }
 
-size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
+size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es, bool sliced)
 {
     const int FG = m2l_fused_fg(G), CS = FG * FG * FG + 1, m1 = mx + 1;
-    return es * ((size_t)2 * std::max(ne, nk) * CS + (size_t)7 * m1 * m1) +
-           4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
+    const size_t urows = sliced ? (size_t)nk : (size_t)std::max(ne, nk);
+    return es * (((size_t)ne + urows) * CS + (size_t)7 * m1 * m1) +
+           4 * ((size_t)3 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
 }
 
 // Which M2L kernel a level takes (prec: 0 FP64, 1 FP32, 2 double-FP32): the fused kernel for FP32
@@ -1171,16 +1192,20 @@ size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es)
 // m_x <= 6 at one CTA per SM), the slab kernel
 // for FP32 grids of 5^3 .. 8^3 cells with m_x <= 6 (its per-thread arrays and shared memory are
 // sized for that), else the three separable passes through the global workspace (the 8-byte
-// formats, larger grids or degrees).
+// formats, larger grids or degrees).  FP32 degrees whose full T2 does not fit the fused kernel
+// (m_x = 8) take its sliced form (T2 one nu1 value at a time).
 int m2l_engine(int prec, int G, int nk, int ne, int mx)
 {
     // double-FP32: the fused kernel at one CTA per SM when its 8-byte intermediates fit the
     // 227 KB of shared memory a CTA may hold (m_x <= 6)
     const int FG = m2l_fused_fg(G);
-    if (prec == 2 && G <= FG && m2l_fused_smem(G, nk, ne, mx, 8) <= 227 * 1024 && nk * FG <= 2 * kM2LThreads)
+    if (prec == 2 && G <= FG && m2l_fused_smem(G, nk, ne, mx, 8, false) <= 227 * 1024 && nk * FG <= 2 * kM2LThreads)
         return kM2LFused;
     if (prec != 1) return kM2LThreePass;
-    if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4) <= 200 * 1024 && nk * FG <= 2 * kM2LThreads) return kM2LFused;
+    if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4, false) <= 200 * 1024 && nk * FG <= 2 * kM2LThreads)
+        return kM2LFused;
+    if (G <= FG && m2l_fused_smem(G, nk, ne, mx, 4, true) <= 227 * 1024 && nk * FG <= 2 * kM2LThreads)
+        return kM2LFusedSliced;
     if (G > FGMax && G <= SG && mx <= 6 && m2l_slab_smem(nk, ne, mx, 4) <= 220 * 1024 && nk <= 256) return kM2LSlab;
     return kM2LThreePass;
 }
@@ -1199,8 +1224,9 @@ int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, in
     int rc = 0;
     dispatch_prec(prec, [&](auto tag) {
         using R = decltype(tag);
-        if (engine == kM2LFused) {
-            const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es);
+        if (engine == kM2LFused || engine == kM2LFusedSliced) {
+            const bool sl = engine == kM2LFusedSliced;
+            const size_t fsm = m2l_fused_smem(L.G, g.nk, g.ne, g.mx, es, sl);
             M2LArgs A{L.G, L.ntr, na, g.nk, g.mx, g.ne, L.nint, L.nbox, L.cellbox, L.boxcell, L.pk, L.pJ, 0,
                       g.kidx, g.kinv, g.eoff};
             // few (interval, node) CTAs: one CTA per source term as well, when the terms' partial
@@ -1210,7 +1236,8 @@ int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, in
             const int64_t split_ctas = (int64_t)kM2LSplitCtasPerSm * (g.nsm > 0 ? g.nsm : 152);
             const int split = ((int64_t)L.nint * na * nrhs < split_ctas && (size_t)nterm * nlev <= ws_elems) ? 1 : 0;
             const dim3 grd(L.nint * na * (split ? nterm : 1), nrhs);
-            auto kf = m2l_fused_fg(L.G) == 2 ? k_m2l_fused<R, 2> : k_m2l_fused<R, FGMax>;
+            auto kf = m2l_fused_fg(L.G) == 2 ? (sl ? k_m2l_fused<R, 2, true> : k_m2l_fused<R, 2, false>)
+                                             : (sl ? k_m2l_fused<R, FGMax, true> : k_m2l_fused<R, FGMax, false>);
             cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
             kf<<<grd, kM2LThreads, fsm, st>>>(A, (const R *)mb, (const R *)L.E1, (const R *)L.pref, (R *)lb, nrhs,
                                               split, (R *)T1);

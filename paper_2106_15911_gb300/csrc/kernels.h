@@ -118,7 +118,7 @@ void launch_m2m(int prec, const DevLevel &par, const DevLevel &ch, int l, const 
 int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
                void *T1, void *T2, size_t ws_elems, cudaStream_t st);
 // M2L kernel of a level with a G^3 grid (launch_m2l's choice): only kM2LThreePass uses T1 / T2
-enum { kM2LThreePass = 0, kM2LFused = 1, kM2LSlab = 2 };
+enum { kM2LThreePass = 0, kM2LFused = 1, kM2LSlab = 2, kM2LFusedSliced = 3 };
 int m2l_engine(int prec, int G, int nk, int ne, int mx);
 void launch_l2l(int prec, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);

@@ -23,7 +23,7 @@ PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_NEARFIELD_STORED, PFMM_NEARFIELD_ONTHEFLY = 0, 1
 PFMM_PART_NEAR, PFMM_PART_FAR, PFMM_PART_ALL = 1, 2, 3
 PFMM_NF_AUTO, PFMM_NF_CUDA_CORES = 0, 1
-PFMM_M2L_THREE_PASS, PFMM_M2L_FUSED, PFMM_M2L_SLAB = 1, 2, 3
+PFMM_M2L_THREE_PASS, PFMM_M2L_FUSED, PFMM_M2L_SLAB, PFMM_M2L_FUSED_SLICED = 1, 2, 3, 4
 
 
 class pfmm_mesh(ctypes.Structure):
