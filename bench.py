@@ -814,7 +814,8 @@ def main():
     if rank == 0:
         cfg = _config_dict(nt, world)
         cfg.update({"precision": args.precision, "build_s": t_build,
-                    "nearfield_GB": info["nearfield_bytes"] / 1e9})
+                    "nearfield_GB": info["nearfield_bytes"] / 1e9, "nf_form": info["nf_form"],
+                    "nf_form_ms_at_build": info["nf_form_ms"], "m2l_engine": info["m2l_engine"]})
         line = {"metric": METRIC, "value": value, "unit": "space-time DOF/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if head == P.PFMM_FP64 else "f32", "data": "synthetic",

@@ -126,6 +126,7 @@ typedef struct pfmm_info {
                                      zero where the source is not near), 0: compact per panel */
     int32_t m2l_engine[32];       /* M2L kernel of level l (l = 2 .. p; 0 elsewhere): PFMM_M2L_* */
     int32_t nf_form;              /* form of the FP64 tensor-core nearfield kernel in use (0: none) */
+    double nf_form_ms[2];         /* build-time timing of forms 1 and 2 (ms per V product; 0 if not timed) */
     double m2l_flops;             /* flops of one rhs's M2L in the separable form (Eq. m2l with
                                      Eq. exp_coeffs_3d applied one direction at a time over the
                                      full box grid of every level, all interval pairs of Eq.

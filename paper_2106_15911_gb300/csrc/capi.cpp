@@ -457,6 +457,7 @@ static int tune_crt_form(pfmm_handle *H, cudaStream_t st)
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc) H->crt_form_ms[form - 1] = ms / 2;
         if (!rc && ms < best) {
             best = ms;
             H->crt_best_form = form;
@@ -1131,6 +1132,8 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
     info->device_bytes = h->dev_bytes;
     info->nf_tensor_cores = (h->tcV || h->crtV ? 1 : 0) | (h->tcK || h->crtK ? 2 : 0);
     info->nf_form = h->crtV || h->crtK ? h->crt_form : 0;
+    info->nf_form_ms[0] = h->crt_form_ms[0];
+    info->nf_form_ms[1] = h->crt_form_ms[1];
     if (h->crtV || h->crtK)
         info->nearfield_bytes += (h->crtV ? t.sizeV : 0) * 2 * pfmm::kCrtModuli + (h->crtK ? t.sizeK : 0) * 2 * pfmm::kCrtModuli;
     info->nearfield_v_elements = t.sizeV;

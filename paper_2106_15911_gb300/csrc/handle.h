@@ -98,6 +98,7 @@ struct pfmm_handle {
     bool crtV = false, crtK = false;
     int crt_bV = 0, crt_bK = 0;                       // fixed-point bits of the operands
     int crt_form = 1, crt_best_form = 1;              // kernel form (1: two moduli, 2: two row tiles per item)
+    double crt_form_ms[2] = {0, 0};                   // build-time timing of the two forms
     uint16_t *d_AVres = nullptr, *d_AKres = nullptr;  // FP16 residues [16][panel elements]
     int *d_rexpV = nullptr, *d_rexpK = nullptr;       // row scale exponents by triangle
     CUtensorMap mapAVres{}, mapAKres{};

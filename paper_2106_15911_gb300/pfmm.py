@@ -45,7 +45,8 @@ class pfmm_info(ctypes.Structure):
                 ("pad", ctypes.c_double * 32), ("n_m2l_pairs", ctypes.c_int32), ("nearfield_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("nf_tensor_cores", ctypes.c_int32),
                 ("nearfield_v_elements", ctypes.c_int64), ("nf_dense_columns", ctypes.c_int32),
-                ("m2l_engine", ctypes.c_int32 * 32), ("nf_form", ctypes.c_int32), ("m2l_flops", ctypes.c_double)]
+                ("m2l_engine", ctypes.c_int32 * 32), ("nf_form", ctypes.c_int32),
+                ("nf_form_ms", ctypes.c_double * 2), ("m2l_flops", ctypes.c_double)]
 
 
 class pfmm_solve_opts(ctypes.Structure):
@@ -284,7 +285,8 @@ def pfmm_get_info(h) -> dict:
     return dict(p=i.p, lx=list(i.lx[:n]), nbox=list(i.nbox[:n]), pad=list(i.pad[:n]), n_m2l_pairs=i.n_m2l_pairs,
                 nearfield_bytes=i.nearfield_bytes, device_bytes=i.device_bytes, nf_tensor_cores=i.nf_tensor_cores,
                 nearfield_v_elements=i.nearfield_v_elements, nf_dense_columns=i.nf_dense_columns,
-                m2l_engine=list(i.m2l_engine[:n]), nf_form=i.nf_form, m2l_flops=i.m2l_flops)
+                m2l_engine=list(i.m2l_engine[:n]), nf_form=i.nf_form, nf_form_ms=list(i.nf_form_ms),
+                m2l_flops=i.m2l_flops)
 
 
 def pfmm_check(h):
