@@ -69,15 +69,6 @@ __device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int x,
         : "memory");
 }
 
-// L2 prefetch of a 4D tile (no shared memory, no barrier): the A tiles are streamed from HBM once,
-// so requesting them a whole chunk ahead turns the stage loads' HBM latency into L2 latency
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap *map, int x, int y, int z, int w)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"((uint64_t)map),
-                 "r"(x), "r"(y), "r"(z), "r"(w)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tma_5d(void *dst, const CUtensorMap *map, int x, int y, int z, int w, int v,
                                        uint64_t *bar)
 {
@@ -198,31 +189,6 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_crt(const __grid_constant__
                         deadline = gtimer() + kTimeoutNs;
                         const int m = I.m0 + slot;
                         const int st1 = min(nst, (ch + 1) * CHUNK);
-                        // the next block's A tiles (other modulus of this chunk, the next chunk,
-                        // or the first block of this CTA's next item)
-                        {
-                            int pch = slot == 0 ? ch : ch + 1, pm = I.m0 + (slot ^ 1);
-                            long long pbase = rbase;
-                            int prp = Pn.rows_pad;
-                            bool ptwo = two, pok = pch < nch;
-                            if (!pok && it + (int)gridDim.x < P.nitems) {
-                                const CItem J = decode_citem(P, it + gridDim.x);
-                                const PanelGPU &Qn = P.panels[J.panel];
-                                pch = 0;
-                                pm = J.m0;
-                                pbase = (P.kop ? Qn.offK : Qn.offV) / P.cols_pad + J.r0;
-                                prp = Qn.rows_pad;
-                                ptwo = J.r0 + 64 < Qn.nrows;
-                                pok = true;
-                            }
-                            if (pok)
-                                for (int st = pch * CHUNK; st < min(nst, (pch + 1) * CHUNK); ++st) {
-                                    const int d = st / P.nkb, kb = st % P.nkb;
-                                    const int blk = (int)((pbase + (long long)d * prp) >> 6) * P.nkb + kb;
-                                    tma_prefetch_4d(&mapA, 0, 0, blk, pm);
-                                    if (ptwo) tma_prefetch_4d(&mapA, 0, 0, blk + P.nkb, pm);
-                                }
-                        }
                         for (int st = ch * CHUNK; st < st1; ++st, ++g) {
                             const int s = g % NSTAGE;
                             if (!mbar_wait(&empty[s], ((g / NSTAGE) & 1) ^ 1, deadline)) {

@@ -60,16 +60,6 @@ __device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, int x,
         : "memory");
 }
 
-// L2 prefetch of a 3D tile of the panel parts (no shared memory, no barrier): the panel blocks are
-// streamed from HBM once, so requesting them several stages ahead hides their HBM latency
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, int y, int z)
-{
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map), "r"(x),
-                 "r"(y), "r"(z)
-                 : "memory");
-}
-constexpr int kPrefetchAhead = 8;  // stages
-
 __device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w, uint64_t *bar)
 {
     asm volatile(
@@ -167,20 +157,7 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
             for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
                 Item I = decode_item(P, it);
                 const PanelGPU &Pn = P.panels[I.panel];
-                const bool two_i = I.r0 + 64 < Pn.nrows;
-                const long long rbase = (P.kop ? Pn.offK : Pn.offV) / P.cols_pad + I.r0;
-                auto prefetch = [&](int st) {  // the A parts of stage st of this item into L2
-                    const int blk = (int)((rbase + (long long)(st / P.nkb) * Pn.rows_pad) >> 6) * P.nkb + st % P.nkb;
-                    tma_prefetch_3d(&mapAhi, 0, 0, blk);
-                    tma_prefetch_3d(&mapAlo, 0, 0, blk);
-                    if (two_i) {
-                        tma_prefetch_3d(&mapAhi, 0, 0, blk + P.nkb);
-                        tma_prefetch_3d(&mapAlo, 0, 0, blk + P.nkb);
-                    }
-                };
-                for (int st = I.st0; st < min(I.st1, I.st0 + kPrefetchAhead); ++st) prefetch(st);
                 for (int st = I.st0; st < I.st1; ++st, ++g) {
-                    if (st + kPrefetchAhead < I.st1) prefetch(st + kPrefetchAhead);
                     const int s = g % NSTAGE;
                     if (!mbar_wait(&empty[s], ((g / NSTAGE) & 1) ^ 1, deadline)) {
                         atomicExch(P.err, 1);
