@@ -323,8 +323,11 @@ int pfmm_autotune_params(const pfmm_mesh *mesh, const pfmm_params *base, double 
                          pfmm_params *out);
 
 /* Build n independent problems (one handle each, own tree, tables and nearfield).  With
- * tune_engines != 0 the tensor-core and CUDA-core nearfield applies of every problem that can
- * use tensor cores are timed and the faster engine is kept.  Synchronises `stream`. */
+ * tune_engines != 0, per problem and timed with CUDA events: the tensor-core and CUDA-core
+ * nearfield applies (where the panels allow the tensor cores), and the M2L kernel forms (the
+ * per-level default, the fused kernel, its sliced form, the three global passes, each where it can
+ * run the problem's levels) on the far field; the fastest of each is kept (pfmm_get_info reports
+ * the resulting M2L engine per level).  Synchronises `stream`. */
 int pfmm_build_trees_batched(int32_t n, const pfmm_mesh *meshes, const pfmm_params *params, int32_t tune_engines,
                              void *stream, pfmm_batch **out);
 

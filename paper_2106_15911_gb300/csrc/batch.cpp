@@ -9,12 +9,13 @@
 // |E_{k,l}(r, d_min)| with k + l in {m_x + 1, m_x + 2} and r in {0, 2} (coincident and
 // neighbouring boxes), relative to |E_{0,0}(0, d_min)|.  The smallest m_x in
 // [m_lo, m_hi] whose estimate is below tol is taken.
-// Engine selection (measured): for each problem whose nearfield can run on tensor cores, the
-// tensor-core and CUDA-core nearfield applies are timed after a warm-up and the faster one kept.
+// Engine selection (measured with CUDA events): for each problem the tensor-core and CUDA-core
+// nearfield applies (where the panels allow the tensor cores) and the M2L kernel forms (fused,
+// sliced fused, three global passes, where each can run the problem's levels) are timed after a
+// warm-up, and the fastest of each is kept.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -128,37 +129,73 @@ int pfmm_build_trees_batched(int32_t n, const pfmm_mesh *meshes, const pfmm_para
     B->join.resize(n);
     for (auto &e : B->join) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     if (tune_engines) {
-        // time both nearfield engines per tensor-core-capable problem and keep the faster
+        // per problem, timed with CUDA events on the build stream after a warm-up: the nearfield
+        // engine (tensor cores or CUDA cores) on the nearfield part, then the M2L kernel form
+        // (the per-level default, the fused kernel, its sliced form, the three global passes) on
+        // the far field; the fastest of each is kept
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        int rc_t = PFMM_OK;
         for (pfmm_handle *h : B->h) {
-            if (!h->tcV) continue;
             double *x = nullptr, *f = nullptr;
             size_t nn = (size_t)h->Et * h->nt;
             if (cudaMalloc(&x, nn * sizeof(double)) != cudaSuccess || cudaMalloc(&f, nn * sizeof(double)) != cudaSuccess) {
                 cudaFree(x);
-                delete B;
-                return set_error(PFMM_ERR_OOM, "autotune buffers");
+                rc_t = set_error(PFMM_ERR_OOM, "autotune buffers");
+                break;
             }
             cudaMemsetAsync(x, 0, nn * sizeof(double), st);
-            double best[2] = {1e300, 1e300};
-            for (int eng = 0; eng < 2; ++eng) {
-                h->nf_cuda_cores = eng == 1;
-                for (int r = 0; r < 4; ++r) {
-                    cudaStreamSynchronize(st);
-                    auto t0 = std::chrono::steady_clock::now();
-                    int rc = pfmm_apply_parts(h, 0, x, f, 1, PFMM_PART_NEAR, stream);
-                    cudaStreamSynchronize(st);
-                    if (rc) {
-                        cudaFree(x);
-                        cudaFree(f);
-                        delete B;
-                        return rc;
+            auto timed = [&](int parts, float &ms) {
+                int rc = pfmm_apply_parts(h, 0, x, f, 1, parts, stream);  // warm-up
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 3 && !rc; ++r) rc = pfmm_apply_parts(h, 0, x, f, 1, parts, stream);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                return rc;
+            };
+            float best = 1e30f, ms = 0.f;
+            if (h->tcV) {
+                bool cc = false;
+                for (int eng = 0; eng < 2 && !rc_t; ++eng) {
+                    h->nf_cuda_cores = eng == 1;
+                    if ((rc_t = timed(PFMM_PART_NEAR, ms))) break;
+                    if (ms < best) {
+                        best = ms;
+                        cc = eng == 1;
                     }
-                    if (r > 0) best[eng] = std::min(best[eng], std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+                }
+                h->nf_cuda_cores = cc;
+            }
+            const int cands[4] = {0, PFMM_M2L_FUSED, PFMM_M2L_FUSED_SLICED, PFMM_M2L_THREE_PASS};
+            int best_c = 0;
+            best = 1e30f;
+            for (int c : cands) {
+                if (rc_t || h->p < 2) break;
+                // skip a candidate that runs the same kernels as one already timed
+                bool differs = c == 0;
+                for (int l = 2; l <= h->p && !differs; ++l)
+                    differs = pfmm::m2l_engine_for(h->fprec, h->dl[l].G, h->nk, h->ne, h->mx, c) !=
+                              pfmm::m2l_engine(h->fprec, h->dl[l].G, h->nk, h->ne, h->mx);
+                if (!differs) continue;
+                h->m2l_force = c;
+                if ((rc_t = timed(PFMM_PART_FAR, ms))) break;
+                if (ms < best) {
+                    best = ms;
+                    best_c = c;
                 }
             }
-            h->nf_cuda_cores = best[1] < best[0];
+            h->m2l_force = best_c;
             cudaFree(x);
             cudaFree(f);
+            if (rc_t) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc_t) {
+            delete B;
+            return rc_t;
         }
     }
     *out = B;

@@ -394,6 +394,7 @@ int pfmm::apply_same_step(pfmm_handle *H, const double *x, double *f, int ns, vo
     g.ls = 1;
     g.perm = H->d_perm;
     g.nsm = H->nsm;
+    g.m2l_force = H->m2l_force;
     launch_permute_in(x, xint, H->mixed, 1, g, st);
     if (H->otf) {
         cudaMemsetAsync(fint, 0, sizeof(double) * ns * (size_t)H->nt, st);
@@ -941,6 +942,7 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     g.ne = H->ne;
     g.eoff = H->d_eoff;
     g.nsm = H->nsm;
+    g.m2l_force = H->m2l_force;
     if ((int)t.panels.size() == g.nbox_leaf) {  // one row panel per leaf box: its 64-row tiles
         g.tiles = H->d_tiles;
         g.ntiles = H->ntiles;
@@ -1154,7 +1156,7 @@ int pfmm_get_info(const pfmm_handle *h, pfmm_info *info)
         info->m2l_flops += 2.0 * pairs * na2 * R * (G3 * h->ne + G3 * c5 + (double)L.nbox * h->ne);
     }
     for (int l = 2; l <= h->p && l < 32 && l < (int)h->dl.size(); ++l) {
-        const int e = pfmm::m2l_engine(h->fprec, h->dl[l].G, h->nk, h->ne, h->mx);
+        const int e = pfmm::m2l_engine_for(h->fprec, h->dl[l].G, h->nk, h->ne, h->mx, h->m2l_force);
         info->m2l_engine[l] = e == pfmm::kM2LFused ? PFMM_M2L_FUSED
                               : e == pfmm::kM2LFusedSliced ? PFMM_M2L_FUSED_SLICED
                               : (e == pfmm::kM2LSlab ? PFMM_M2L_SLAB : PFMM_M2L_THREE_PASS);

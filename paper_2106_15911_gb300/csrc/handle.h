@@ -87,6 +87,7 @@ struct pfmm_handle {
     // tensor-core nearfield (mixed mode, untruncated panels of equal width, 2 steps per leaf)
     bool tcV = false, tcK = false;
     bool nf_cuda_cores = false;     // engine override chosen by the batch autotuner
+    int m2l_force = 0;              // M2L engine chosen by the batch autotuner (PFMM_M2L_* code, 0: per-level default)
     uint16_t *d_AVhi = nullptr, *d_AVlo = nullptr, *d_AKhi = nullptr, *d_AKlo = nullptr;  // FP16 parts
     int a_expV = 0, a_expK = 0;     // scale exponents of the panels' FP16 split
     CUtensorMap mapAVhi{}, mapAVlo{}, mapAKhi{}, mapAKlo{};

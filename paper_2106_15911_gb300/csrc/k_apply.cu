@@ -1210,6 +1210,24 @@ int m2l_engine(int prec, int G, int nk, int ne, int mx)
     return kM2LThreePass;
 }
 
+int m2l_engine_for(int prec, int G, int nk, int ne, int mx, int force)
+{
+    const int def = m2l_engine(prec, G, nk, ne, mx);
+    const int FG = m2l_fused_fg(G);
+    const size_t es = prec == 1 ? 4 : 8, cap = prec == 1 ? 200 * 1024 : 227 * 1024;
+    const bool fits_fused = prec != 0 && G <= FG && nk * FG <= 2 * kM2LThreads;
+    switch (force) {
+    case 1:  // PFMM_M2L_THREE_PASS
+        return kM2LThreePass;
+    case 2:  // PFMM_M2L_FUSED
+        return fits_fused && m2l_fused_smem(G, nk, ne, mx, es, false) <= cap ? kM2LFused : def;
+    case 4:  // PFMM_M2L_FUSED_SLICED
+        return fits_fused && m2l_fused_smem(G, nk, ne, mx, es, true) <= 227 * 1024 ? kM2LFusedSliced : def;
+    default:
+        return def;
+    }
+}
+
 // Runs the three passes over chunks of target intervals so that the intermediates fit the
 // workspace (ws_elems elements of R for each of T1 and T2).
 int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, int nrhs, const ApplyGeo &g,
@@ -1218,7 +1236,7 @@ int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, in
     (void)l;
     const size_t es = prec == 1 ? 4 : 8;
     const int G3 = L.G * L.G * L.G, na = g.na;
-    const int engine = m2l_engine(prec, L.G, g.nk, g.ne, g.mx);
+    const int engine = m2l_engine_for(prec, L.G, g.nk, g.ne, g.mx, g.m2l_force);
     const char *mb = (const char *)mu + L.mom_off * es * nrhs;
     char *lb = (char *)lam + L.mom_off * es * nrhs;
     int rc = 0;

@@ -82,6 +82,7 @@ struct ApplyGeo {
     int ntiles;
     const int *box_tiles;  // [nbox_p + 1] first tile of each leaf box (tiles are box-major)
     int nsm;               // streaming multiprocessors of the device (grid sizing)
+    int m2l_force;         // M2L engine asked for by the batch autotuner (PFMM_M2L_* code, 0: none)
 };
 
 // prec of the FMM launchers: 0 FP64, 1 FP32 (mixed mode), 2 double-FP32 (FP64 mode); every
@@ -120,6 +121,9 @@ int launch_m2l(int prec, const DevLevel &L, int l, const void *mu, void *lam, in
 // M2L kernel of a level with a G^3 grid (launch_m2l's choice): only kM2LThreePass uses T1 / T2
 enum { kM2LThreePass = 0, kM2LFused = 1, kM2LSlab = 2, kM2LFusedSliced = 3 };
 int m2l_engine(int prec, int G, int nk, int ne, int mx);
+// the engine of a level when an autotuner asks for `force` (a PFMM_M2L_* code; 0: none): the forced
+// engine where it can run that level, else m2l_engine's choice
+int m2l_engine_for(int prec, int G, int nk, int ne, int mx, int force);
 void launch_l2l(int prec, const DevLevel &par, const DevLevel &ch, int l, const void *qt, void *lam, int nrhs,
                 const ApplyGeo &g, int64_t mu_stride, cudaStream_t st);
 // ws: scratch (ws_elems elements of the arithmetic type) for the temporal factor of every (step,

@@ -81,7 +81,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     size_t need_T = 0;
     for (int l = 2; l <= H->p; ++l) {
         const DevLevel &L = H->dl[l];
-        if (m2l_engine(H->fprec, L.G, H->nk, H->ne, H->mx) != kM2LThreePass) continue;
+        if (m2l_engine_for(H->fprec, L.G, H->nk, H->ne, H->mx, H->m2l_force) != kM2LThreePass) continue;
         int maxpairs = 0;
         for (int k = 0; k < L.nint; ++k) maxpairs = std::max(maxpairs, L.kptr_host[k + 1] - L.kptr_host[k]);
         need_T = std::max(need_T, (size_t)nrhs * maxpairs * H->na * H->na * L.G * L.G * L.G * H->ne);
@@ -122,6 +122,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     g.ne = H->ne;
     g.eoff = H->d_eoff;
     g.nsm = H->nsm;
+    g.m2l_force = H->m2l_force;
     if ((int)H->tree.panels.size() == g.nbox_leaf) {  // one row panel per leaf box: its 64-row tiles
         g.tiles = H->d_tiles;
         g.ntiles = H->ntiles;

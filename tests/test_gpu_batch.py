@@ -68,3 +68,26 @@ def test_engine_autotune_keeps_oracle_parity():
         got = f.cpu().numpy()[0]
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-5
     B.close()
+
+
+def test_autotuner_picks_an_m2l_form_that_keeps_the_product():
+    """Degree 8 on 4^3 grids: the autotuner times the sliced fused M2L against the three global
+    passes (CUDA events) and keeps one; the tuned product equals that of an untuned handle of the
+    same problem within FP32 accuracy, and pfmm_get_info reports the engines in use."""
+    V, T = cube_mesh(8)
+    Et = 256
+    prm = P.pfmm_default_params()
+    prm.precision = P.PFMM_MIXED
+    prm.m_t, prm.m_x, prm.c_st = 4, 8, 1.0
+    B = P.Batch([(V, T, 1.0, Et, 1.0, prm)], tune_engines=True)
+    op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=8, c_st=1.0, precision=P.PFMM_MIXED)
+    eng = P.pfmm_get_info(B.handle(0))["m2l_engine"]
+    assert set(eng[6:]) <= {P.PFMM_M2L_FUSED_SLICED, P.PFMM_M2L_THREE_PASS}, eng
+    w = torch.tensor(random_density(Et, T.shape[0], 2, seed=77), device=DEV)
+    f = torch.empty_like(w)
+    P.pfmm_apply_V(B.handle(0), w, f, 2)
+    ref = op.V(w)
+    torch.cuda.synchronize()
+    assert float((f - ref).abs().max() / ref.abs().max()) <= 1e-5
+    op.close()
+    B.close()
