@@ -1032,7 +1032,23 @@ __global__ void k_m2l_sum_terms(const R *__restrict__ part, int na, size_t n, si
 // shared memory over the terms, so each is written once (no partials).  Same arithmetic as the
 // three-pass kernels; cells beyond G are empty.
 constexpr int SG = 8;  // padded grid extent per direction
-constexpr int kM2LSlabThreads = 256;
+constexpr int kM2LSlabThreads = 512;
+
+// asynchronous global -> shared copy of one element of B = 4 or 8 bytes (zero fill when !valid),
+// its commit and wait
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "n"(B), "r"(valid ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <typename R>
 __global__ void __launch_bounds__(kM2LSlabThreads, 1) k_m2l_slab(M2LArgs A, const R *__restrict__ mu,
@@ -1043,7 +1059,8 @@ __global__ void __launch_bounds__(kM2LSlabThreads, 1) k_m2l_slab(M2LArgs A, cons
     constexpr int SC = SG * SG, SCS = SC + 1, NO = 2 * SG - 1;
     const int G = A.G, nk = A.nk, ne = A.ne, mx = A.mx, m1 = mx + 1, na = A.na, esz = m1 * m1;
     R *Ms = reinterpret_cast<R *>(slab_raw);  // [nk][SCS]  moments of one source slab Y1, cells (Y2, Y3)
-    R *T1s = Ms + nk * SCS;                    // [ne][SCS]  cells (Y2, Y3) at X1
+    R *Ms2 = Ms + nk * SCS;                    // [nk][SCS]  the next source slab (double buffer)
+    R *T1s = Ms2 + nk * SCS;                   // [ne][SCS]  cells (Y2, Y3) at X1
     R *T2s = T1s + ne * SCS;                   // [ne][SCS]  cells (X2, Y3) at X1
     R *Ls = T2s + ne * SCS;                    // [nk][SCS]  locals, cells (X2, X3) at X1
     R *Es = Ls + nk * SCS;                     // [NO][m1][m1] offsets -(SG-1)..SG-1, zero outside the radius
@@ -1084,14 +1101,26 @@ __global__ void __launch_bounds__(kM2LSlabThreads, 1) k_m2l_slab(M2LArgs A, cons
             for (int i = threadIdx.x; i < ne * SCS; i += blockDim.x) T1s[i] = R(0);
             const R coef = pref[((D - 2) * na + a) * na + b];
             // pass 1 (direction x): unit = (triple (nu1, k2, k3), cell (Y2, Y3)); per source slab Y1
-            // the budget chain over B is added into T1 (the cumulative budget)
-            for (int Y1 = y_lo; Y1 <= y_hi; ++Y1) {
-                __syncthreads();  // Ms free, Es and T1s ready
-                for (int i = threadIdx.x; i < nk * SC; i += blockDim.x) {  // consecutive threads: consecutive kappa
+            // the budget chain over B is added into T1 (the cumulative budget).  The moments of slab
+            // Y1 + 1 are copied asynchronously into the other buffer while slab Y1 is used
+            auto load_slab = [&](int Y1, R *dst) {  // consecutive threads: consecutive kappa
+                for (int i = threadIdx.x; i < nk * SC; i += blockDim.x) {
                     const int c = i / nk, ik = i % nk, box = cbx[Y1 * SC + c];
-                    Ms[ik * SCS + c] = box >= 0 ? mJ[((size_t)box * na + a) * nk + ik] : R(0);
+                    cp_async_elem<sizeof(R)>(dst + ik * SCS + c, box >= 0 ? mJ + ((size_t)box * na + a) * nk + ik : mJ,
+                                             box >= 0);
                 }
-                __syncthreads();
+                cp_async_commit();
+            };
+            load_slab(y_lo, Ms);
+            for (int Y1 = y_lo; Y1 <= y_hi; ++Y1) {
+                R *Mc = ((Y1 - y_lo) & 1) ? Ms2 : Ms;
+                if (Y1 < y_hi) {
+                    load_slab(Y1 + 1, ((Y1 - y_lo) & 1) ? Ms : Ms2);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();  // slab Y1 in place for every thread; Es and T1s ready
                 const R *Eo = Es + (X1 - Y1 + SG - 1) * esz;
                 for (int u = threadIdx.x; u < nk * SC; u += blockDim.x) {
                     const int c = u % SC, t = u / SC, tk = kid[t];
@@ -1099,12 +1128,12 @@ __global__ void __launch_bounds__(kM2LSlabThreads, 1) k_m2l_slab(M2LArgs A, cons
                     R acc = R(0);
                     for (int B = s0; B <= mx; ++B) {
                         const int k1 = B - s0;
-                        acc += Eo[k1 * m1 + nu1] * Ms[kin[(k1 * m1 + k2) * m1 + k3] * SCS + c];
+                        acc += Eo[k1 * m1 + nu1] * Mc[kin[(k1 * m1 + k2) * m1 + k3] * SCS + c];
                         T1s[(eof[t] + k1) * SCS + c] += acc;
                     }
                 }
+                __syncthreads();  // done with Mc before its refill two slabs later
             }
-            __syncthreads();
             // pass 2 (direction y): unit = (triple (nu1, nu2, k3), Y3); registers: cells X2
             for (int u = threadIdx.x; u < nk * SG; u += blockDim.x) {
                 const int Y3 = u % SG, t = u / SG, tk = kid[t];
@@ -1172,7 +1201,7 @@ __global__ void __launch_bounds__(kM2LSlabThreads, 1) k_m2l_slab(M2LArgs A, cons
 size_t m2l_slab_smem(int nk, int ne, int mx, size_t es)
 {
     const int SCS = SG * SG + 1, m1 = mx + 1;
-    return es * ((size_t)(2 * nk + 2 * ne) * SCS + (size_t)(2 * SG - 1) * m1 * m1) +
+    return es * ((size_t)(3 * nk + 2 * ne) * SCS + (size_t)(2 * SG - 1) * m1 * m1) +
            4 * ((size_t)2 * nk + (size_t)m1 * m1 * m1 + SG * SG * SG);
 }
 
