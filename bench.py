@@ -529,7 +529,12 @@ def _profile_case(dev, case):
         run()
     e1.record()
     torch.cuda.synchronize()
-    return {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
+    out = {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
+    if case in ("crt", "m2l_slab", "otf"):
+        info = op.info()
+        out.update(nearfield_v_elements=info["nearfield_v_elements"], nf_form=info["nf_form"],
+                   m2l_engine=info["m2l_engine"])
+    return out
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
