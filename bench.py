@@ -40,18 +40,29 @@ def _set_size(n_a, et):
 
 
 def _clock_sampler(stop, out):
+    """nvidia-smi in its own loop mode (a sample every 50 ms) while the timed region runs."""
     cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
            "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-i",
+           "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50", "-i",
            os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"]
-    while not stop.is_set():
-        try:
-            r = subprocess.run(cmd, capture_output=True, text=True, timeout=5)
-            if r.returncode == 0:
-                out.append(r.stdout.strip().splitlines()[0])
-        except Exception:
-            pass
-        stop.wait(0.2)
+    try:
+        proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+
+    def reader():
+        for line in proc.stdout:
+            out.append(line.strip())
+
+    t = threading.Thread(target=reader, daemon=True)
+    t.start()
+    stop.wait()
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    t.join(timeout=2)
 
 
 def _clocks_summary(samples):
@@ -709,9 +720,13 @@ def main():
     stop, samples = threading.Event(), []
     th = threading.Thread(target=_clock_sampler, args=(stop, samples), daemon=True)
     th.start()
+    time.sleep(0.3)  # the sampler's first line comes before the timed region
+    n_before = len(samples)
     ms, phases = run_device_timed(args.steps, args.warmup, op, f)
+    time.sleep(0.1)
     stop.set()
-    th.join(timeout=5)
+    th.join(timeout=10)
+    samples = samples[max(0, n_before - 1):]  # the samples of (and bracketing) the timed region
     ms_step = max_over_ranks(statistics.mean(ms), world, dev)
     value = replicas_throughput(dof, ms_step, world)
     launches = P.pfmm_count_apply_kernels(op.h, 0, w, f, 1)
