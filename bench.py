@@ -31,6 +31,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "pFMM matvec space-time DOF/s"
+# DRAM bytes (read + write) per stored nearfield element of one FP64 residue-arithmetic nearfield
+# launch (k_nf_apply_crt, form 1), from an ncu capture of the 3072-triangle x 256-step case
+# (1.7167e9 B read + 1.18e7 B written over 50,331,648 stored elements); traffic grows with the
+# stored elements, so a full launch's traffic is this times its element count
+NF_CRT_DRAM_BYTES_PER_ELEMENT = (1.716715e9 + 1.1788e7) / 50331648
+NF_CRT_TRAFFIC_SOURCE = ("ncu capture of 3072 tri x 256 steps (profiles/nf_crt_3072x256_fp64.md), scaled by the "
+                         "stored elements")
 N_A, ET, M_X, M_T, C_ST = 32, 256, 6, 4, 1.0
 
 
@@ -767,7 +774,8 @@ def main():
         gbs = byts / (nf["ms"] * 1e-3) / 1e9
         executed = 16.0 * nf["flops"] / (nf["ms"] * 1e-3) / 1e12
         roofline = {"bound": "hbm", "kernel": "k_nf_apply_crt", "achieved": gbs, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                    "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                    "traffic": NF_CRT_DRAM_BYTES_PER_ELEMENT * nel, "traffic_source": NF_CRT_TRAFFIC_SOURCE,
                     "peak_source": "measured copy rate (of measured)", "bytes_per_launch": byts,
                     "ms_per_launch": nf["ms"],
                     "tensor": {"executed_fp16_tflops": executed, "frac_of_fp16_peak": executed / peaks["fp16_tflops"]},
