@@ -176,6 +176,13 @@ int pfmm_apply_parts(pfmm_handle *h, int32_t op, const double *x, double *f, int
  * 7 permute out) and the number of applies measured, then resets the accumulators. */
 int pfmm_set_profiling(pfmm_handle *h, int32_t on);
 int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies);
+/* The nearfield product kernel alone (the tensor-core kernel of the nearfield phase:
+ * k_nf_apply_tc in mixed precision, k_nf_apply_crt in FP64 mode), from CUDA events recorded on
+ * the apply's stream immediately before and after its launch while profiling is on: the
+ * accumulated milliseconds and the number of launches measured since the last call, then reset.
+ * Both are 0 when the nearfield ran on the CUDA cores.  Reads the events of the applies that
+ * pfmm_phase_times has not yet collected, so call it before pfmm_phase_times. */
+int pfmm_nf_kernel_time(pfmm_handle *h, double *ms, int32_t *n_launches);
 
 int pfmm_get_info(const pfmm_handle *h, pfmm_info *info);
 

@@ -265,6 +265,13 @@ void prof_collect(pfmm_handle *H, int upto_pending)
             cudaEventElapsedTime(&ms, e.ev[i], e.ev[i + 1]);
             H->acc_ms[i] += ms;
         }
+        if (e.nf) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e.ev[9], e.ev[10]);
+            H->acc_nf_ms += ms;
+            H->n_nf++;
+            e.nf = false;
+        }
         H->n_prof++;
         H->ev_pending--;
     }
@@ -313,9 +320,14 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
     P.wmax = wmax;
     P.f = fint;
     P.err = H->d_err;
+    if (H->cur_ev) cudaEventRecord(H->cur_ev->ev[9], st);
     if (launch_nf_apply_tc(op == 0 ? H->mapAVhi : H->mapAKhi, op == 0 ? H->mapAVlo : H->mapAKlo, mWhi, mWlo, P, H->nsm,
                            st))
         return fail(PFMM_ERR_CUDA, std::string("tensor-core nearfield launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (H->cur_ev) {
+        cudaEventRecord(H->cur_ev->ev[10], st);
+        H->cur_ev->nf = true;
+    }
     return PFMM_OK;
 }
 
@@ -349,9 +361,14 @@ int pfmm::run_nf_crt(pfmm_handle *H, int op, const double *x, int nrhs, double *
     P.nt = H->nt;
     P.res = H->d_res8;
     P.err = H->d_err;
+    if (H->cur_ev) cudaEventRecord(H->cur_ev->ev[9], st);
     if (launch_nf_apply_crt(op == 0 ? H->mapAVres : H->mapAKres, mW, P, H->nsm, st, H->crt_form))
         return fail(PFMM_ERR_CUDA, std::string("FP64 tensor-core nearfield launch: ") +
                                        cudaGetErrorString(cudaGetLastError()));
+    if (H->cur_ev) {
+        cudaEventRecord(H->cur_ev->ev[10], st);
+        H->cur_ev->nf = true;
+    }
     launch_crt_combine(H->d_res8, nrhs, H->Et, H->nt, op == 0 ? H->d_rexpV : H->d_rexpK, H->d_wmax, b, fint, st);
     return PFMM_OK;
 }
@@ -953,13 +970,19 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
         if (H->evs.empty()) {
             H->evs.resize(256);
             for (auto &e : H->evs)
-                for (int i = 0; i < 9; ++i) CK(cudaEventCreate(&e.ev[i]));
+                for (int i = 0; i < 11; ++i) CK(cudaEventCreate(&e.ev[i]));
         }
         if (H->ev_pending == (int)H->evs.size()) prof_collect(H, H->ev_pending - 1);
         ev = &H->evs[H->ev_head];
+        ev->nf = false;
         H->ev_head = (H->ev_head + 1) % (int)H->evs.size();
         H->ev_pending++;
     }
+    H->cur_ev = ev;
+    struct CurEvReset {
+        pfmm_handle *H;
+        ~CurEvReset() { H->cur_ev = nullptr; }
+    } cur_ev_reset{H};
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev->ev[i], st);
     };
@@ -1101,6 +1124,17 @@ int pfmm_phase_times(pfmm_handle *h, double *ms8, int32_t *n_applies)
     }
     if (n_applies) *n_applies = h->n_prof;
     h->n_prof = 0;
+    return PFMM_OK;
+}
+
+int pfmm_nf_kernel_time(pfmm_handle *h, double *ms, int32_t *n_launches)
+{
+    if (!h || !ms) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+    prof_collect(h, 0);
+    *ms = h->acc_nf_ms;
+    if (n_launches) *n_launches = h->n_nf;
+    h->acc_nf_ms = 0;
+    h->n_nf = 0;
     return PFMM_OK;
 }
 

@@ -39,7 +39,8 @@ void mpnn_dims(const pfmm_mpnn *net, int *nt, int *Et);
 }  // namespace pfmm
 
 struct EvSet {
-    cudaEvent_t ev[9];
+    cudaEvent_t ev[11];  // 0..8: phase boundaries; 9, 10: around the nearfield product kernel
+    bool nf = false;     // 9 and 10 were recorded
 };
 
 struct pfmm_handle {
@@ -114,6 +115,9 @@ struct pfmm_handle {
     int ev_head = 0, ev_pending = 0;
     double acc_ms[8] = {0};
     int n_prof = 0;
+    EvSet *cur_ev = nullptr;  // events of the apply in progress (profiling on)
+    double acc_nf_ms = 0;     // nearfield product kernel alone
+    int n_nf = 0;
 
     // stored nearfield blocks of op for the CUDA-core engine: the FP32/FP64 panels, or null once
     // only the tensor-core split exists (nf_split then describes it)
@@ -138,7 +142,7 @@ struct pfmm_handle {
     {
         for (void *p : allocs) cudaFree(p);
         for (auto &e : evs)
-            for (int i = 0; i < 9; ++i) cudaEventDestroy(e.ev[i]);
+            for (int i = 0; i < 11; ++i) cudaEventDestroy(e.ev[i]);
     }
 
     template <typename T_>

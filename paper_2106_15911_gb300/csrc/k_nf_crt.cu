@@ -15,8 +15,9 @@
 //     kind::f16 MMA chain accumulates them in FP32 exactly (integers below 2^24) over chunks of
 //     1024 columns; after each chunk the epilogue reduces the accumulator modulo p in place
 //     (tcgen05.ld / .st), so the next chunk adds onto a small residue;
-//   * the 16 residues of X are combined by Garner's mixed-radix algorithm (balanced digits) and
-//     X 2^-(e_r + s) is evaluated in FP64 from the leading digit down (relative error ~2^-48).
+//   * the 16 residues of X are combined by Garner's mixed-radix algorithm (balanced digits, exact
+//     FP32 arithmetic), X is assembled exactly in 128-bit integers and X 2^-(e_r + s) is rounded
+//     to FP64 (relative error ~2^-52).
 // The only rounding before the final FP64 result is that of A and W to b-bit fixed point per row /
 // per rhs (b = 52..53): the product is as accurate as an FP64 dot product of the same terms.
 //
@@ -48,9 +49,10 @@ using namespace tc;
 
 __constant__ int c_p[kCrtModuli];              // the moduli
 __constant__ float c_invp[kCrtModuli];         // 1 / p (FP32)
-__constant__ int c_pjmodpi[kCrtModuli][kCrtModuli];  // (p_0 ... p_{j-1}) mod p_i, j < i
-__constant__ int c_invPi[kCrtModuli];          // (p_0 ... p_{i-1})^-1 mod p_i
-__constant__ double c_Pj[kCrtModuli];          // p_0 ... p_{j-1} (FP64, rounded)
+__constant__ float c_pf[kCrtModuli];           // the moduli (FP32)
+__constant__ float c_pow11[kCrtModuli][5];     // 2^(11 k) mod p_i (FP32), k = 0 .. 4
+__constant__ float c_pjmodpif[kCrtModuli][kCrtModuli];  // (p_0 ... p_{j-1}) mod p_i, j < i (FP32)
+__constant__ float c_invPif[kCrtModuli];       // (p_0 ... p_{i-1})^-1 mod p_i (FP32)
 
 constexpr int BM = 128, BK = 64;
 constexpr int A_TILE = BM * BK * 2;      // 16 KB
@@ -582,13 +584,34 @@ __device__ __forceinline__ double pow2(int e)
     return ldexp(1.0, e);
 }
 
-// balanced residue of the integer a (|a| <= 2^53) modulo p, as FP16
-__device__ __forceinline__ __half residue16(long long a, int p)
+// balanced residue of an integer-valued x (|x| < 2^22) modulo p, in [-(p-1)/2, (p-1)/2]: the
+// FP32 quotient of mod_small is off by at most one, so one correction each way suffices
+__device__ __forceinline__ float mod_balanced(float x, float p, float invp)
 {
-    int r = (int)(a % p);  // C remainder: sign of a, |r| < p
-    if (r > (p - 1) / 2) r -= p;
-    if (r < -(p - 1) / 2) r += p;
-    return __int2half_rn(r);
+    float t = mod_small(x, p, invp);
+    const float hp = 0.5f * (p - 1.f);
+    t = t > hp ? t - p : t;
+    return t < -hp ? t + p : t;
+}
+
+// balanced residues of the integer a (|a| < 2^55) modulo the 16 primes, exactly in FP32: |a| is
+// cut into five 11-bit digits a_k and sum_k a_k (2^(11 k) mod p) < 5 * 2^11 * 2^8 < 2^22 is reduced
+// once; the residue of -a is minus that of a
+__device__ __forceinline__ void residues16(long long a, float (&r)[kCrtModuli])
+{
+    const bool neg = a < 0;
+    const unsigned long long u = neg ? 0ull - (unsigned long long)a : (unsigned long long)a;
+    float dg[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) dg[k] = (float)(unsigned)((u >> (11 * k)) & 0x7ffull);
+#pragma unroll
+    for (int m = 0; m < kCrtModuli; ++m) {
+        float x = dg[0];
+#pragma unroll
+        for (int k = 1; k < 5; ++k) x = fmaf(dg[k], c_pow11[m][k], x);
+        const float t = mod_balanced(x, c_pf[m], c_invp[m]);
+        r[m] = neg ? -t : t;
+    }
 }
 
 // FP64 panels -> residues of A' = rint(2^e_R A) for every modulus, [modulus][n] in the 64 x 64
@@ -601,9 +624,10 @@ __global__ void k_crt_split_panel(const double *__restrict__ A, const int *__res
     const size_t R = i / ncp;
     const int c = (int)(i - R * ncp);
     const size_t o = nf_tiled_index(R, c, ncp >> 6);
-    const long long ai = __double2ll_rn(A[i] * pow2(rowexp_R[R]));
-#pragma unroll 4
-    for (int m = 0; m < kCrtModuli; ++m) res[(size_t)m * n + o] = residue16(ai, c_p[m]);
+    float r[kCrtModuli];
+    residues16(__double2ll_rn(A[i] * pow2(rowexp_R[R])), r);
+#pragma unroll
+    for (int m = 0; m < kCrtModuli; ++m) res[(size_t)m * n + o] = __float2half_rn(r[m]);
 }
 
 // per-row exponents of global panel rows: rowexp_R[R] = e of the row's triangle
@@ -636,36 +660,42 @@ __global__ void k_crt_split_input(const double *__restrict__ x, const int *__res
         const double v = x[rt * ncol + (perm ? perm[c] : c)];
         wi = __double2ll_rn(v * pow2(crt_scale_exp(wmax[i / per_rhs], b)));
     }
-#pragma unroll 4
-    for (int m = 0; m < kCrtModuli; ++m) res[(size_t)m * total + i] = residue16(wi, c_p[m]);
+    float r[kCrtModuli];
+    residues16(wi, r);
+#pragma unroll
+    for (int m = 0; m < kCrtModuli; ++m) res[(size_t)m * total + i] = __float2half_rn(r[m]);
 }
 
-// f[rhs][t][row] = X 2^-(e_row + s_rhs), X from its residues by Garner's algorithm
+// f[rhs][t][row] = X 2^-(e_row + s_rhs), X from its residues by Garner's algorithm: the balanced
+// mixed-radix digits v_j = (r_j - sum_{k<j} v_k P_k) P_j^-1 mod p_j (P_j = p_0 ... p_{j-1}) in exact
+// FP32 arithmetic (every intermediate is an integer below 2^20), then X = sum_j v_j P_j by Horner's
+// rule in 128-bit integers (|X| < M / 2 < 2^123, exact) and one conversion to FP64
 __global__ void k_crt_combine(const unsigned char *__restrict__ res, size_t per_mod, size_t per_rhs, int nt,
                               const int *__restrict__ rowexp, const unsigned long long *__restrict__ wmax, int b,
                               double *__restrict__ f)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= per_mod) return;
-    int acc[kCrtModuli];
+    float acc[kCrtModuli], v[kCrtModuli];
 #pragma unroll
-    for (int k = 0; k < kCrtModuli; ++k) acc[k] = 0;
-    double x = 0.0;
-    int v[kCrtModuli];
+    for (int k = 0; k < kCrtModuli; ++k) acc[k] = 0.f;
 #pragma unroll
     for (int j = 0; j < kCrtModuli; ++j) {
-        const int p = c_p[j];
-        // v_j = (r_j - sum_{k<j} v_k P_k) P_j^-1 mod p_j, balanced
-        int t = ((int)res[(size_t)j * per_mod + i] - acc[j]) % p;
-        t = (t * c_invPi[j]) % p;
-        if (t < 0) t += p;
-        if (t > (p - 1) / 2) t -= p;
-        v[j] = t;
+        const float p = c_pf[j], invp = c_invp[j];
+        const float t = mod_small((float)res[(size_t)j * per_mod + i] - acc[j], p, invp);
+        v[j] = mod_balanced(t * c_invPif[j], p, invp);
 #pragma unroll
-        for (int k = j + 1; k < kCrtModuli; ++k) acc[k] += t * c_pjmodpi[j][k];
+        for (int k = j + 1; k < kCrtModuli; ++k) acc[k] = fmaf(v[j], c_pjmodpif[j][k], acc[k]);
     }
+    __int128 X = (__int128)(int)v[kCrtModuli - 1];
 #pragma unroll
-    for (int j = kCrtModuli - 1; j >= 0; --j) x += (double)v[j] * c_Pj[j];
+    for (int j = kCrtModuli - 2; j >= 0; --j) X = X * (__int128)c_p[j] + (__int128)(int)v[j];
+    // |X| = hi 2^64 + lo: both parts non-negative, so the two roundings cannot cancel
+    const bool neg = X < 0;
+    const unsigned __int128 U = neg ? (unsigned __int128)0 - (unsigned __int128)X : (unsigned __int128)X;
+    const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
+    const double ax = hi ? fma((double)hi, 18446744073709551616.0, (double)lo) : (double)lo;
+    const double x = neg ? -ax : ax;
     const int row = (int)(i % nt);
     const int e = rowexp[row] + crt_scale_exp(wmax[i / per_rhs], b);
     f[i] = x * pow2(-e);
@@ -696,28 +726,29 @@ int crt_upload_constants(cudaStream_t st)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
     if (done[dev]) return 0;
-    float invp[kCrtModuli];
-    int pj[kCrtModuli][kCrtModuli] = {{0}}, invPi[kCrtModuli];
-    double Pj[kCrtModuli];
+    float invp[kCrtModuli], pf[kCrtModuli], pow11[kCrtModuli][5];
+    float pj[kCrtModuli][kCrtModuli] = {{0.f}}, invPi[kCrtModuli];
     for (int i = 0; i < kCrtModuli; ++i) {
+        pf[i] = (float)g_moduli[i];
         invp[i] = 1.0f / (float)g_moduli[i];
         long long q = 1;  // p_0 ... p_{j-1} mod p_i, for j = 0 .. i
         for (int j = 0; j < i; ++j) {
-            pj[j][i] = (int)q;
+            pj[j][i] = (float)q;
             q = q * g_moduli[j] % g_moduli[i];
         }
-        invPi[i] = (int)modinv(q, g_moduli[i]);
-    }
-    double P = 1.0;
-    for (int j = 0; j < kCrtModuli; ++j) {
-        Pj[j] = P;
-        P *= (double)g_moduli[j];
+        invPi[i] = (float)modinv(q, g_moduli[i]);
+        long long w = 1;  // 2^(11 k) mod p_i
+        for (int k = 0; k < 5; ++k) {
+            pow11[i][k] = (float)w;
+            w = (w << 11) % g_moduli[i];
+        }
     }
     if (cudaMemcpyToSymbolAsync(c_p, g_moduli, sizeof(g_moduli), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_pf, pf, sizeof(pf), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyToSymbolAsync(c_invp, invp, sizeof(invp), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyToSymbolAsync(c_pjmodpi, pj, sizeof(pj), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyToSymbolAsync(c_invPi, invPi, sizeof(invPi), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyToSymbolAsync(c_Pj, Pj, sizeof(Pj), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_pow11, pow11, sizeof(pow11), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_pjmodpif, pj, sizeof(pj), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(c_invPif, invPi, sizeof(invPi), 0, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return -1;
     done[dev] = true;

@@ -79,6 +79,7 @@ SIGNATURES = {
     "pfmm_apply_V_noalloc": (ctypes.c_int, [_VP, _DP, _DP, _I, _VP]),
     "pfmm_set_profiling": (ctypes.c_int, [_VP, _I]),
     "pfmm_phase_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    "pfmm_nf_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
     "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
@@ -276,6 +277,14 @@ def pfmm_phase_times(h):
     n = ctypes.c_int32()
     _check(lib().pfmm_phase_times(h, ms, ctypes.byref(n)))
     return dict(zip(PHASES, list(ms))), n.value
+
+
+def pfmm_nf_kernel_time(h):
+    """(milliseconds, launches) of the nearfield product kernel alone since the last call."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int32()
+    _check(lib().pfmm_nf_kernel_time(h, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def pfmm_get_info(h) -> dict:
