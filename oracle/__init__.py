@@ -84,6 +84,13 @@ def lib():
             L.orc_cheb_node.argtypes = [i, i]
             L.orc_interaction_list.argtypes = [i, pi]
             L.orc_nearfield_list.argtypes = [i, pi]
+            L.orc_time_V_steps.restype = d
+            L.orc_time_V_steps.argtypes = [d, d, d, d, d, d]
+            L.orc_gen_tree_info.argtypes = [ctypes.POINTER(Problem), pd, i, pi, pi, pi, pi, pi, pi, pi, pi, pd, pi, i]
+            L.orc_gen_interval.argtypes = [ctypes.POINTER(Problem), pd, i, i, i, pi, pi]
+            L.orc_gen_coverage.argtypes = [ctypes.POINTER(Problem), pd, i, pi]
+            L.orc_gen_pfmm_apply.argtypes = [ctypes.POINTER(Problem), pd, i, pd, pd, pi, i, i, i]
+            L.orc_gen_dense_apply.argtypes = [ctypes.POINTER(Problem), pd, pd, pi, i, pd, i]
             L.orc_sizeof_problem.restype = i
             assert L.orc_sizeof_problem() == ctypes.sizeof(Problem)
             _lib = L
@@ -320,3 +327,83 @@ def lagrange(b, m, lo, hi, t):
 
 def cheb_node(k, m):
     return lib().orc_cheb_node(k, m)
+
+
+# ---- general time steps (Section 3.2 with Alg. 1 in full, Section 3.3, Alg. 2) ---------------
+def make_general_problem(V, T, ts, alpha=1.0, m_t=4, m_x=4, c_st=1.0, n_tr=-1, eps_tr=1e-12, n_r=3, n_s=6):
+    """Problem for the time steps ts[0] = 0 < ts[1] < ... < ts[Et] = T (single layer)."""
+    ts = np.ascontiguousarray(ts, dtype=np.float64)
+    P = make_problem(V, T, float(ts[-1]), ts.shape[0] - 1, alpha=alpha, m_t=m_t, m_x=m_x, c_st=c_st, n_tr=n_tr,
+                     eps_tr=eps_tr, n_r=n_r, n_s=n_s)
+    P._ts = ts
+    return P
+
+
+def time_V_steps(r, tk0, tk1, tj0, tj1, alpha=1.0):
+    """int over the target step (tk0, tk1] and the source step (tj0, tj1] of the heat kernel."""
+    return lib().orc_time_V_steps(r, tk0, tk1, tj0, tj1, alpha)
+
+
+def gen_tree_info(P, n_max, boxes=False):
+    """The general tree: per level lx, boxes, leaves, intervals present, radii, refinement kind,
+    padding; with boxes=True also [nbox_total][6] rows (level, cell x y z, k, leaf)."""
+    nlev = ctypes.c_int()
+    a = {k: np.zeros(32, np.int32) for k in ("lx", "nbox", "nleaf", "nint", "ntr_far", "ntr_near", "st")}
+    pad = np.zeros(32)
+    cap = 1 << 20 if boxes else 0
+    bx = np.zeros((max(cap, 1), 6), np.int32)
+    rc = lib().orc_gen_tree_info(ctypes.byref(P), _pd(P._ts), n_max, ctypes.byref(nlev), _pi(a["lx"]),
+                                 _pi(a["nbox"]), _pi(a["nleaf"]), _pi(a["nint"]), _pi(a["ntr_far"]),
+                                 _pi(a["ntr_near"]), _pi(a["st"]), _pd(pad), _pi(bx) if boxes else None, cap)
+    if rc:
+        raise ValueError("general tree build failed")
+    n = nlev.value
+    out = {k: v[:n].tolist() for k, v in a.items()}
+    out["nlev"] = n
+    out["pad"] = pad[:n].tolist()
+    if boxes:
+        out["boxes"] = bx[:sum(out["nbox"])]
+    return out
+
+
+def gen_interval(P, n_max, l, k):
+    """Steps [ia, ib) of interval k of level l of the general tree ((-1, -1) when absent)."""
+    ia, ib = ctypes.c_int(), ctypes.c_int()
+    if lib().orc_gen_interval(ctypes.byref(P), _pd(P._ts), n_max, l, k, ctypes.byref(ia), ctypes.byref(ib)):
+        raise ValueError("general tree build failed")
+    return ia.value, ib.value
+
+
+def gen_coverage(P, n_max):
+    """cover[e, e'] (e = k nt + x target, e' = j nt + y source): how often the nearfield blocks and
+    the admissible blocks of the general tree cover the pair (tiny problems only)."""
+    ne = P.Et * P.nt
+    cov = np.zeros((ne, ne), np.int32)
+    if lib().orc_gen_coverage(ctypes.byref(P), _pd(P._ts), n_max, _pi(cov)):
+        raise ValueError("general tree build failed")
+    return cov
+
+
+def gen_pfmm_apply(P, n_max, w, targets=None, parts=3, nthreads=0):
+    """Oracle pFMM (Alg. 2) on the general tree: f = V_h w, w and f [Et, nt]."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    f = np.zeros((P.Et, P.nt))
+    if targets is None:
+        tg, n = None, -1
+    else:
+        tg = np.ascontiguousarray(targets, dtype=np.int32)
+        n = tg.shape[0]
+    rc = lib().orc_gen_pfmm_apply(ctypes.byref(P), _pd(P._ts), n_max, _pd(w), _pd(f),
+                                  _pi(tg) if tg is not None else None, n, parts, nthreads)
+    if rc:
+        raise ValueError("oracle general pfmm failed")
+    return f
+
+
+def gen_dense_apply(P, w, targets, nthreads=0):
+    """Dense Galerkin product V_h w on the rows of the listed triangles (all steps), general steps."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    f = np.zeros((P.Et, P.nt))
+    lib().orc_gen_dense_apply(ctypes.byref(P), _pd(P._ts), _pd(w), _pi(tg), tg.shape[0], _pd(f), nthreads)
+    return f

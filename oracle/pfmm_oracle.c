@@ -244,20 +244,24 @@ static void or_tri_normal(const double *P0, const double *P1, const double *P2, 
  *    ORIGINAL vertex order (needed for the p1 trial functions of K_h).
  * ====================================================================================== */
 
-enum { ORK_V = 0, ORK_K = 1, ORK_LAPSL = 2, ORK_LAPDL = 3, ORK_POLY = 4 };
+enum { ORK_V = 0, ORK_K = 1, ORK_LAPSL = 2, ORK_LAPDL = 3, ORK_POLY = 4, ORK_VSTEPS = 5 };
 
 typedef struct {
     int kind;
-    int d0, nd;        /* time offsets d0 .. d0 + nd - 1 (kinds V, K) */
+    int d0, nd;        /* time offsets d0 .. d0 + nd - 1 (kinds V, K); step pairs (kind VSTEPS) */
     double h, alpha;
     double ny[3];      /* outward unit normal of the source triangle */
     double poly[4];    /* coefficients of the smooth test kernel */
+    const double *tb;  /* kind VSTEPS: [nd][4] target step (t0, t1] and source step (t0, t1] */
 } or_kernel;
+
+double orc_time_V_steps(double r, double tk0, double tk1, double tj0, double tj1, double alpha);
 
 static int or_ncomp(const or_kernel *k)
 {
     switch (k->kind) {
     case ORK_V: return k->nd;
+    case ORK_VSTEPS: return k->nd;
     case ORK_K: return 3 * k->nd;
     default: return 1;
     }
@@ -281,6 +285,10 @@ static void or_eval(const or_kernel *k, const double *x, const double *y, const 
         }
         break;
     }
+    case ORK_VSTEPS:
+        for (int i = 0; i < k->nd; ++i)
+            out[i] = orc_time_V_steps(r, k->tb[4 * i], k->tb[4 * i + 1], k->tb[4 * i + 2], k->tb[4 * i + 3], k->alpha);
+        break;
     case ORK_LAPSL: out[0] = 1.0 / (4.0 * OR_PI * r); break;
     case ORK_LAPDL: {
         double dn = dx * k->ny[0] + dy * k->ny[1] + dz * k->ny[2];
@@ -1375,5 +1383,783 @@ int orc_repr_eval(const orc_problem *P, const double *w, const double *g, const 
         u[p] = acc;
     }
     free(R);
+    return 0;
+}
+
+/* ======================================================================================
+ * 10. General time steps t_0 = 0 < t_1 < ... < t_Et = T (Section 3.2 with Alg. 1 in full,
+ *     Section 3.3, Alg. 2; the adaptive direction of Section 6).  Single layer V_h only.
+ *     Step j is (t_j, t_{j+1}] (0-based).  No Toeplitz structure: every target / source step
+ *     pair is integrated on its own.
+ *     Readings (where Section 3.2 leaves the rule open):
+ *      - levels: level 0 holds the cells of the grid 2^lx0 (the root refined in space until it
+ *        satisfies Eq. rel_h_t_h_x, as for uniform steps) with the interval (0, T]; the refinement
+ *        of level l into level l+1 is temporal iff hx_l^2 <= c_st 4 alpha T / 2^(l+2) (the nominal
+ *        half-size h_t^(l+1) of Alg. 1), the same for every box of the level;
+ *      - RefineCluster: a box Z = X x I is refined iff it holds at least n_max elements, unless
+ *        an element is oversized (the early stop of Section 3.2): I holds a single step, a step
+ *        of I is longer than the nominal interval length T / 2^l of the level, or a triangle of
+ *        X extends over more than the box width 2 hx_l in some direction;
+ *      - the temporal split of (t_a, t_b] is at the step t_s (a < s < b) nearest to
+ *        (t_a + t_b) / 2, the smaller s on a tie; children without elements are not added;
+ *      - padding per level as for uniform steps; the interaction-area radii of level l from the
+ *        longest interval L_l of the level (separation 4 L_l for M2L, 2 L_l for the nearfield).
+ * ====================================================================================== */
+
+/* int over the target step (tk0, tk1] and the source step (tj0, tj1] of the heat kernel (Section
+ * 2): the second difference of G2 at the four time differences, 0 for a later source step; the
+ * bounded form G2t for small u as for uniform steps (the parts linear in s cancel when the source
+ * step precedes the target step; the same step keeps G2 alone). */
+double orc_time_V_steps(double r, double tk0, double tk1, double tj0, double tj1, double alpha)
+{
+    if (tj0 >= tk1) return 0.0;
+    if (tj0 == tk0 && tj1 == tk1) return orc_G2(r, tk1 - tk0, alpha);
+    const double s1 = tk1 - tj0, s2 = tk1 - tj1, s3 = tk0 - tj0, s4 = tk0 - tj1;
+    const double u = r / (2.0 * sqrt(alpha * s1));
+    if (u < 1.0)
+        return orc_G2t(r, s1, alpha) - orc_G2t(r, s2, alpha) - orc_G2t(r, s3, alpha) + orc_G2t(r, s4, alpha);
+    return orc_G2(r, s1, alpha) - orc_G2(r, s2, alpha) - orc_G2(r, s3, alpha) + orc_G2(r, s4, alpha);
+}
+
+/* V_h entries of the triangle pair (x, y) for n step pairs pr[i] = (k, j): out[i] = V[(k,x),(j,y)].
+ * Touching triangles use the Sauter-Schwab rule when the source step is the target step or the
+ * one before it (the time integral is singular in r there), the regular rule otherwise. */
+static void og_pair_steps(const orc_problem *P, const double *ts, int x, int y, const int (*pr)[2], int n,
+                          double *out)
+{
+    const int *tx = P->T + 3 * x, *ty = P->T + 3 * y;
+    const double *X[3] = {P->V + 3 * tx[0], P->V + 3 * tx[1], P->V + 3 * tx[2]};
+    const double *Y[3] = {P->V + 3 * ty[0], P->V + 3 * ty[1], P->V + 3 * ty[2]};
+    const int cls = or_shared(tx, ty);
+    double tb[4 * 64], acc[64];
+    int sel[64];
+    for (int pass = 0; pass < 2; ++pass) { /* pass 0: regular pairs, pass 1: Sauter-Schwab pairs */
+        int m = 0;
+        for (int i = 0; i <= n; ++i) {
+            if (i < n) {
+                const int k = pr[i][0], j = pr[i][1];
+                const int ss = cls > 0 && k - j <= 1;
+                if (j > k) { out[i] = 0.0; continue; }
+                if (ss != pass) continue;
+                tb[4 * m] = ts[k];
+                tb[4 * m + 1] = ts[k + 1];
+                tb[4 * m + 2] = ts[j];
+                tb[4 * m + 3] = ts[j + 1];
+                sel[m++] = i;
+            }
+            if (m == 64 || (i == n && m > 0)) {
+                or_kernel kr;
+                memset(&kr, 0, sizeof(kr));
+                kr.kind = ORK_VSTEPS;
+                kr.nd = m;
+                kr.alpha = P->alpha;
+                kr.tb = tb;
+                if (pass) {
+                    const double *PX[3], *PY[3];
+                    int perm[3];
+                    or_ss_order(P->V, tx, ty, PX, PY, perm);
+                    or_pair_ss(cls, PX, PY, perm, &kr, P->n_s, acc);
+                } else {
+                    or_pair_regular(X, Y, &kr, P->n_r, acc);
+                }
+                for (int q = 0; q < m; ++q) out[sel[q]] = acc[q];
+                m = 0;
+            }
+        }
+    }
+}
+
+typedef struct {
+    int nlev;
+    int lx[OR_MAXL], st[OR_MAXL];   /* st[l]: level l -> l+1 is a space-time refinement */
+    double H, corner[3], pad[OR_MAXL];
+    int ntr_far[OR_MAXL], ntr_near[OR_MAXL];
+    int nb[OR_MAXL];
+    int *cell[OR_MAXL];             /* [nb][3] grid multi-index of the spatial part */
+    int *kk[OR_MAXL];               /* [nb] index k of the temporal part I_k^(l) */
+    int *leaf[OR_MAXL];             /* [nb] */
+    int *par[OR_MAXL];              /* [nb] parent box (-1 at level 0) */
+    int *ia[OR_MAXL], *ib[OR_MAXL]; /* [2^l] steps [ia, ib) of interval k, -1 when absent */
+    int *cstart[OR_MAXL];           /* [G^3 + 1] triangles of each cell: ctri[cstart[c] .. cstart[c+1]) */
+    int *ctri[OR_MAXL];
+    long long *key[OR_MAXL];        /* [nb] sorted k G^3 + cell */
+    int *kbox[OR_MAXL];             /* [nb] the box of key[i] */
+} og_tree;
+
+static int og_G(const og_tree *t, int l) { return 1 << t->lx[l]; }
+static int og_lin(const int *c, int G) { return (c[0] * G + c[1]) * G + c[2]; }
+
+static void og_tree_free(og_tree *t)
+{
+    for (int l = 0; l < OR_MAXL; ++l) {
+        free(t->cell[l]); free(t->kk[l]); free(t->leaf[l]); free(t->par[l]);
+        free(t->ia[l]); free(t->ib[l]); free(t->cstart[l]); free(t->ctri[l]);
+        free(t->key[l]); free(t->kbox[l]);
+    }
+    memset(t, 0, sizeof(*t));
+}
+
+static int og_find(const og_tree *t, int l, int k, const int *c)
+{
+    const int G = og_G(t, l);
+    for (int d = 0; d < 3; ++d)
+        if (c[d] < 0 || c[d] >= G) return -1;
+    const long long q = (long long)k * G * G * G + og_lin(c, G);
+    int lo = 0, hi = t->nb[l] - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) / 2;
+        if (t->key[l][mid] == q) return t->kbox[l][mid];
+        if (t->key[l][mid] < q) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+typedef struct { long long k; int b; } og_kb;
+static int og_kb_cmp(const void *a, const void *b)
+{
+    const long long x = ((const og_kb *)a)->k, y = ((const og_kb *)b)->k;
+    return x < y ? -1 : x > y;
+}
+
+/* cells of the triangles at level l (CSR by cell) */
+static void og_cells(const orc_problem *P, const double *cent, og_tree *t, int l)
+{
+    const int G = og_G(t, l), nc = G * G * G;
+    const double w = 2.0 * t->H / G;
+    t->cstart[l] = (int *)calloc((size_t)nc + 1, sizeof(int));
+    t->ctri[l] = (int *)malloc(sizeof(int) * (P->nt > 0 ? P->nt : 1));
+    int *lin = (int *)malloc(sizeof(int) * P->nt);
+    for (int x = 0; x < P->nt; ++x) {
+        int c[3];
+        for (int d = 0; d < 3; ++d) c[d] = or_cell(cent[3 * x + d], t->corner[d], w, G);
+        lin[x] = og_lin(c, G);
+        t->cstart[l][lin[x] + 1]++;
+    }
+    for (int c = 0; c < nc; ++c) t->cstart[l][c + 1] += t->cstart[l][c];
+    int *fill = (int *)malloc(sizeof(int) * nc);
+    memcpy(fill, t->cstart[l], sizeof(int) * nc);
+    for (int x = 0; x < P->nt; ++x) t->ctri[l][fill[lin[x]]++] = x;
+    free(fill);
+    free(lin);
+}
+
+static int og_tree_build(const orc_problem *P, const double *ts, int n_max, og_tree *t)
+{
+    memset(t, 0, sizeof(*t));
+    const int nt = P->nt, E = P->Et;
+    if (nt < 1 || E < 1 || n_max < 1) return -1;
+    for (int j = 0; j < E; ++j)
+        if (!(ts[j + 1] > ts[j])) return -1;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < P->nv; ++i)
+        for (int c = 0; c < 3; ++c) {
+            if (P->V[3 * i + c] < lo[c]) lo[c] = P->V[3 * i + c];
+            if (P->V[3 * i + c] > hi[c]) hi[c] = P->V[3 * i + c];
+        }
+    for (int c = 0; c < 3; ++c)
+        if (0.5 * (hi[c] - lo[c]) > t->H) t->H = 0.5 * (hi[c] - lo[c]);
+    for (int c = 0; c < 3; ++c) t->corner[c] = 0.5 * (lo[c] + hi[c]) - t->H;
+    double *cent = (double *)malloc(sizeof(double) * 3 * nt), *ext = (double *)malloc(sizeof(double) * nt);
+    for (int x = 0; x < nt; ++x) {
+        ext[x] = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double a = P->V[3 * P->T[3 * x] + c], b = P->V[3 * P->T[3 * x + 1] + c], d = P->V[3 * P->T[3 * x + 2] + c];
+            cent[3 * x + c] = ((a + b) + d) / 3.0;
+            const double mx_ = fmax(a, fmax(b, d)), mn = fmin(a, fmin(b, d));
+            if (mx_ - mn > ext[x]) ext[x] = mx_ - mn;
+        }
+    }
+    const double T = ts[E];
+    int lx0 = 0;
+    while (1) {
+        const double hx = t->H / (double)(1 << lx0);
+        if (hx * hx <= P->c_st * 4.0 * P->alpha * (T / 2.0) || lx0 > 20) break;
+        lx0++;
+    }
+    /* level 0: every non-empty cell with the interval (0, T] */
+    t->lx[0] = lx0;
+    og_cells(P, cent, t, 0);
+    {
+        const int G = og_G(t, 0), nc = G * G * G;
+        int nb = 0;
+        for (int c = 0; c < nc; ++c) nb += t->cstart[0][c + 1] > t->cstart[0][c];
+        t->nb[0] = nb;
+        t->cell[0] = (int *)malloc(sizeof(int) * 3 * nb);
+        t->kk[0] = (int *)calloc(nb, sizeof(int));
+        t->par[0] = (int *)malloc(sizeof(int) * nb);
+        nb = 0;
+        for (int c = 0; c < nc; ++c)
+            if (t->cstart[0][c + 1] > t->cstart[0][c]) {
+                t->cell[0][3 * nb] = c / (G * G);
+                t->cell[0][3 * nb + 1] = (c / G) % G;
+                t->cell[0][3 * nb + 2] = c % G;
+                t->par[0][nb++] = -1;
+            }
+        t->ia[0] = (int *)malloc(sizeof(int));
+        t->ib[0] = (int *)malloc(sizeof(int));
+        t->ia[0][0] = 0;
+        t->ib[0][0] = E;
+    }
+    int l = 0, rc = 0;
+    while (1) {
+        const int G = og_G(t, l), nb = t->nb[l];
+        const double hx = t->H / G;
+        t->leaf[l] = (int *)malloc(sizeof(int) * (nb > 0 ? nb : 1));
+        int nref = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int *c = t->cell[l] + 3 * b, k = t->kk[l][b], a = t->ia[l][k], e = t->ib[l][k];
+            const int cl = og_lin(c, G), ntri = t->cstart[l][cl + 1] - t->cstart[l][cl];
+            double maxstep = 0.0, maxext = 0.0;
+            for (int j = a; j < e; ++j)
+                if (ts[j + 1] - ts[j] > maxstep) maxstep = ts[j + 1] - ts[j];
+            for (int q = t->cstart[l][cl]; q < t->cstart[l][cl + 1]; ++q)
+                if (ext[t->ctri[l][q]] > maxext) maxext = ext[t->ctri[l][q]];
+            const int refine = (long long)ntri * (e - a) >= n_max && e - a >= 2 && maxstep <= T / (double)(1 << l) &&
+                               maxext <= 2.0 * hx;
+            t->leaf[l][b] = !refine;
+            nref += refine;
+        }
+        if (nref == 0) break;
+        if (l + 1 >= OR_MAXL) { rc = -1; break; }
+        const double ht1 = T / (double)(1 << (l + 2));
+        t->st[l] = !(hx * hx <= P->c_st * 4.0 * P->alpha * ht1);
+        t->lx[l + 1] = t->lx[l] + t->st[l];
+        og_cells(P, cent, t, l + 1);
+        const int G1 = og_G(t, l + 1), n1 = 1 << (l + 1);
+        t->ia[l + 1] = (int *)malloc(sizeof(int) * n1);
+        t->ib[l + 1] = (int *)malloc(sizeof(int) * n1);
+        for (int k = 0; k < n1; ++k) t->ia[l + 1][k] = t->ib[l + 1][k] = -1;
+        int cap = 16 * nref + 16, nb1 = 0;
+        t->cell[l + 1] = (int *)malloc(sizeof(int) * 3 * cap);
+        t->kk[l + 1] = (int *)malloc(sizeof(int) * cap);
+        t->par[l + 1] = (int *)malloc(sizeof(int) * cap);
+        for (int b = 0; b < nb; ++b) {
+            if (t->leaf[l][b]) continue;
+            const int *c = t->cell[l] + 3 * b, k = t->kk[l][b], a = t->ia[l][k], e = t->ib[l][k];
+            /* split at the step nearest the centre (smaller index on a tie) */
+            const double mid = 0.5 * (ts[a] + ts[e]);
+            int s = a + 1;
+            for (int q = a + 2; q < e; ++q)
+                if (fabs(ts[q] - mid) < fabs(ts[s] - mid)) s = q;
+            t->ia[l + 1][2 * k] = a;
+            t->ib[l + 1][2 * k] = s;
+            t->ia[l + 1][2 * k + 1] = s;
+            t->ib[l + 1][2 * k + 1] = e;
+            for (int ci = 0; ci < 2; ++ci)
+                for (int o = 0; o < (t->st[l] ? 8 : 1); ++o) {
+                    int cc[3];
+                    for (int d = 0; d < 3; ++d) cc[d] = t->st[l] ? 2 * c[d] + ((o >> (2 - d)) & 1) : c[d];
+                    const int cl = og_lin(cc, G1);
+                    if (t->cstart[l + 1][cl + 1] == t->cstart[l + 1][cl]) continue;
+                    memcpy(t->cell[l + 1] + 3 * nb1, cc, sizeof(cc));
+                    t->kk[l + 1][nb1] = 2 * k + ci;
+                    t->par[l + 1][nb1++] = b;
+                }
+        }
+        t->nb[l + 1] = nb1;
+        l++;
+    }
+    t->nlev = l + 1;
+    /* padding: largest overshoot of a triangle over its unpadded cell, monotone in the level */
+    for (int q = 0; q < t->nlev; ++q) {
+        const int G = og_G(t, q);
+        const double w = 2.0 * t->H / G;
+        double ov = 0.0;
+        for (int x = 0; x < nt; ++x) {
+            int c[3];
+            for (int d = 0; d < 3; ++d) c[d] = or_cell(cent[3 * x + d], t->corner[d], w, G);
+            for (int v = 0; v < 3; ++v)
+                for (int d = 0; d < 3; ++d) {
+                    const double z = P->V[3 * P->T[3 * x + v] + d], blo = t->corner[d] + c[d] * w, bhi = blo + w;
+                    if (blo - z > ov) ov = blo - z;
+                    if (z - bhi > ov) ov = z - bhi;
+                }
+        }
+        t->pad[q] = ov;
+    }
+    for (int q = t->nlev - 2; q >= 0; --q)
+        if (t->pad[q + 1] > t->pad[q]) t->pad[q] = t->pad[q + 1];
+    for (int q = 0; q < t->nlev; ++q) {
+        const int G = og_G(t, q);
+        double L = 0.0;
+        for (int k = 0; k < (1 << q); ++k)
+            if (t->ia[q][k] >= 0 && ts[t->ib[q][k]] - ts[t->ia[q][k]] > L) L = ts[t->ib[q][k]] - ts[t->ia[q][k]];
+        t->ntr_far[q] = or_ntr(P, t->H / G, t->pad[q], 4.0 * L, G);
+        t->ntr_near[q] = or_ntr(P, t->H / G, t->pad[q], 2.0 * L, G);
+        og_kb *kb = (og_kb *)malloc(sizeof(og_kb) * (t->nb[q] > 0 ? t->nb[q] : 1));
+        for (int b = 0; b < t->nb[q]; ++b) {
+            kb[b].k = (long long)t->kk[q][b] * G * G * G + og_lin(t->cell[q] + 3 * b, G);
+            kb[b].b = b;
+        }
+        qsort(kb, t->nb[q], sizeof(og_kb), og_kb_cmp);
+        t->key[q] = (long long *)malloc(sizeof(long long) * (t->nb[q] > 0 ? t->nb[q] : 1));
+        t->kbox[q] = (int *)malloc(sizeof(int) * (t->nb[q] > 0 ? t->nb[q] : 1));
+        for (int b = 0; b < t->nb[q]; ++b) {
+            t->key[q][b] = kb[b].k;
+            t->kbox[q][b] = kb[b].b;
+        }
+        free(kb);
+    }
+    free(cent);
+    free(ext);
+    if (rc) og_tree_free(t);
+    return rc;
+}
+
+/* the same-level nearfield of box b of level l (Eq. def_st_nearfield, first set): boxes Y x J of
+ * level l with J in {I_{k-1}, I_k} and Y in the interaction area of X; returns their count */
+static int og_near_same(const og_tree *t, int l, int b, int *out, int cap)
+{
+    const int *c = t->cell[l] + 3 * b, k = t->kk[l][b], r = t->ntr_near[l], G = og_G(t, l);
+    int n = 0, lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = c[d] - r < 0 ? 0 : c[d] - r;
+        hi[d] = c[d] + r > G - 1 ? G - 1 : c[d] + r;
+    }
+    for (int j = k - 1; j <= k; ++j) {
+        if (j < 0) continue;
+        for (int a0 = lo[0]; a0 <= hi[0]; ++a0)
+            for (int a1 = lo[1]; a1 <= hi[1]; ++a1)
+                for (int a2 = lo[2]; a2 <= hi[2]; ++a2) {
+                    const int cc[3] = {a0, a1, a2};
+                    const int s = og_find(t, l, j, cc);
+                    if (s >= 0 && n < cap) out[n++] = s;
+                }
+    }
+    return n;
+}
+
+/* an upper bound of the nearfield list length of any leaf */
+static int og_nf_cap(const og_tree *t)
+{
+    int c = 0;
+    for (int l = 0; l < t->nlev; ++l) c += 2 * og_G(t, l) * og_G(t, l) * og_G(t, l);
+    return c;
+}
+
+/* the nearfield N(Z) of a leaf box (Eq. def_st_nearfield): its same-level nearfield and the
+ * leaves in the same-level nearfields of all its ancestors (N(parent(Z)) /\ L_Sigma, recursively);
+ * entries (level, box); returns the count */
+static int og_nearfield(const og_tree *t, int l, int b, int (*out)[2], int cap)
+{
+    const int tcap = og_nf_cap(t);
+    int *tmp = (int *)malloc(sizeof(int) * tcap), n = 0;
+    int m = og_near_same(t, l, b, tmp, tcap);
+    for (int i = 0; i < m && n < cap; ++i) { out[n][0] = l; out[n][1] = tmp[i]; n++; }
+    for (int q = l - 1, a = t->par[l][b]; q >= 0 && a >= 0; a = t->par[q][a], --q) {
+        m = og_near_same(t, q, a, tmp, tcap);
+        for (int i = 0; i < m && n < cap; ++i)
+            if (t->leaf[q][tmp[i]]) { out[n][0] = q; out[n][1] = tmp[i]; n++; }
+    }
+    free(tmp);
+    return n;
+}
+
+/* the interaction list I(Z) of box b of level l >= 2 (Eq. def_st_interaction_list) */
+static int og_interaction(const og_tree *t, int l, int b, int *out, int cap)
+{
+    const int *c = t->cell[l] + 3 * b, k = t->kk[l][b], r = t->ntr_far[l], G = og_G(t, l);
+    int js[2], nj = or_interaction_list(k, js), n = 0, lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = c[d] - r < 0 ? 0 : c[d] - r;
+        hi[d] = c[d] + r > G - 1 ? G - 1 : c[d] + r;
+    }
+    for (int q = 0; q < nj; ++q)
+        for (int a0 = lo[0]; a0 <= hi[0]; ++a0)
+            for (int a1 = lo[1]; a1 <= hi[1]; ++a1)
+                for (int a2 = lo[2]; a2 <= hi[2]; ++a2) {
+                    const int cc[3] = {a0, a1, a2};
+                    const int s = og_find(t, l, js[q], cc);
+                    if (s >= 0 && n < cap) out[n++] = s;
+                }
+    return n;
+}
+
+/* spatial part of box b of level l: padded centre and half-size */
+static void og_box_geom(const og_tree *t, int l, int b, double *cen, double *hp)
+{
+    const int G = og_G(t, l);
+    const double hx = t->H / G;
+    for (int c = 0; c < 3; ++c) cen[c] = t->corner[c] + (2.0 * t->cell[l][3 * b + c] + 1.0) * hx;
+    *hp = hx + t->pad[l];
+}
+
+/* tree summary for the pins and the GPU comparison: nlev; per level l: lx, boxes, leaves,
+ * intervals present, ntr_far, ntr_near, st (levels [0, OR_MAXL)); boxes_out (optional, cap
+ * entries of 6 ints: level, cell x y z, k, leaf) */
+int orc_gen_tree_info(const orc_problem *P, const double *ts, int n_max, int *nlev, int *lx, int *nbox, int *nleaf,
+                      int *nint, int *ntr_far, int *ntr_near, int *st, double *pad, int *boxes_out, int cap)
+{
+    og_tree t;
+    if (og_tree_build(P, ts, n_max, &t)) return -1;
+    *nlev = t.nlev;
+    int w = 0;
+    for (int l = 0; l < t.nlev; ++l) {
+        lx[l] = t.lx[l];
+        nbox[l] = t.nb[l];
+        nleaf[l] = 0;
+        for (int b = 0; b < t.nb[l]; ++b) {
+            nleaf[l] += t.leaf[l][b];
+            if (boxes_out && w < cap) {
+                int *o = boxes_out + 6 * w++;
+                o[0] = l; o[1] = t.cell[l][3 * b]; o[2] = t.cell[l][3 * b + 1]; o[3] = t.cell[l][3 * b + 2];
+                o[4] = t.kk[l][b]; o[5] = t.leaf[l][b];
+            }
+        }
+        nint[l] = 0;
+        for (int k = 0; k < (1 << l); ++k) nint[l] += t.ia[l][k] >= 0;
+        ntr_far[l] = t.ntr_far[l];
+        ntr_near[l] = t.ntr_near[l];
+        st[l] = t.st[l];
+        pad[l] = t.pad[l];
+    }
+    og_tree_free(&t);
+    return 0;
+}
+
+/* interval bounds of interval k of level l: [ia, ib) steps, or -1 when absent (for the pins) */
+int orc_gen_interval(const orc_problem *P, const double *ts, int n_max, int l, int k, int *ia, int *ib)
+{
+    og_tree t;
+    if (og_tree_build(P, ts, n_max, &t)) return -1;
+    *ia = *ib = -1;
+    if (l < t.nlev && k >= 0 && k < (1 << l)) {
+        *ia = t.ia[l][k];
+        *ib = t.ib[l][k];
+    }
+    og_tree_free(&t);
+    return 0;
+}
+
+/* How often the FMM partition of Alg. 2 covers every element pair: cover[e][e'] for target
+ * element e = k nt + x and source element e' = j nt + y, over the nearfield blocks of the leaves
+ * (causal pairs j <= k only: the other entries of a block vanish) and the admissible blocks of
+ * all M2L pairs (their pairs are all causal).  For tiny problems: (Et nt)^2 ints. */
+int orc_gen_coverage(const orc_problem *P, const double *ts, int n_max, int *cover)
+{
+    og_tree t;
+    if (og_tree_build(P, ts, n_max, &t)) return -1;
+    const int nt = P->nt;
+    const size_t ne = (size_t)P->Et * nt;
+    memset(cover, 0, sizeof(int) * ne * ne);
+    const int cap = og_nf_cap(&t);
+    int (*nf)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)cap);
+    int *il = (int *)malloc(sizeof(int) * (size_t)cap);
+    for (int l = 0; l < t.nlev; ++l) {
+        const int G = og_G(&t, l);
+        for (int b = 0; b < t.nb[l]; ++b) {
+            const int ct = og_lin(t.cell[l] + 3 * b, G), kt = t.kk[l][b];
+            /* nearfield of a leaf */
+            int nn = t.leaf[l][b] ? og_nearfield(&t, l, b, nf, cap) : 0;
+            for (int q = 0; q < nn; ++q) {
+                const int ls = nf[q][0], s = nf[q][1], Gs = og_G(&t, ls), cs = og_lin(t.cell[ls] + 3 * s, Gs);
+                const int ks = t.kk[ls][s];
+                for (int i = t.cstart[l][ct]; i < t.cstart[l][ct + 1]; ++i)
+                    for (int k = t.ia[l][kt]; k < t.ib[l][kt]; ++k)
+                        for (int i2 = t.cstart[ls][cs]; i2 < t.cstart[ls][cs + 1]; ++i2)
+                            for (int j = t.ia[ls][ks]; j < t.ib[ls][ks] && j <= k; ++j)
+                                cover[((size_t)k * nt + t.ctri[l][i]) * ne + (size_t)j * nt + t.ctri[ls][i2]]++;
+            }
+            /* admissible blocks */
+            const int ni = l >= 2 ? og_interaction(&t, l, b, il, cap) : 0;
+            for (int q = 0; q < ni; ++q) {
+                const int s = il[q], cs = og_lin(t.cell[l] + 3 * s, G), ks = t.kk[l][s];
+                for (int i = t.cstart[l][ct]; i < t.cstart[l][ct + 1]; ++i)
+                    for (int k = t.ia[l][kt]; k < t.ib[l][kt]; ++k)
+                        for (int i2 = t.cstart[l][cs]; i2 < t.cstart[l][cs + 1]; ++i2)
+                            for (int j = t.ia[l][ks]; j < t.ib[l][ks]; ++j)
+                                cover[((size_t)k * nt + t.ctri[l][i]) * ne + (size_t)j * nt + t.ctri[l][i2]]++;
+            }
+        }
+    }
+    free(nf);
+    free(il);
+    og_tree_free(&t);
+    return 0;
+}
+
+/* f = V_h w by the pFMM (Alg. 2) on the general tree; w, f: [Et][nt].  parts: bit 0 nearfield,
+ * bit 1 far field; targets: triangles whose rows are computed (NULL: all), the other rows are 0. */
+int orc_gen_pfmm_apply(const orc_problem *P, const double *ts, int n_max, const double *w, double *f,
+                       const int *targets, int ntargets, int parts, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    og_tree t;
+    if (og_tree_build(P, ts, n_max, &t)) return -1;
+    or_fmm F;
+    memset(&F, 0, sizeof(F));
+    F.P = P;
+    or_mi_make(P->m_x, &F.mi);
+    const int na = P->m_t + 1, nk = F.mi.nk, mt = P->m_t, mx = P->m_x, nt = P->nt, L = t.nlev;
+    memset(f, 0, sizeof(double) * (size_t)P->Et * nt);
+    unsigned char *is_tgt = (unsigned char *)calloc(nt, 1);
+    if (targets && ntargets >= 0)
+        for (int i = 0; i < ntargets; ++i) is_tgt[targets[i]] = 1;
+    else
+        memset(is_tgt, 1, nt);
+
+    if ((parts & 2) && L >= 3) {
+        double *mu[OR_MAXL] = {0}, *lam[OR_MAXL] = {0};
+        for (int l = 0; l < L; ++l) {
+            mu[l] = (double *)calloc((size_t)t.nb[l] * na * nk + 1, sizeof(double));
+            lam[l] = (double *)calloc((size_t)t.nb[l] * na * nk + 1, sizeof(double));
+        }
+        /* S2M at every leaf of a level >= 2 (Eq. s2m); leaves above level 2 have no far field */
+        for (int l = 2; l < L; ++l) {
+            const int G = og_G(&t, l);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+            for (int b = 0; b < t.nb[l]; ++b) {
+                if (!t.leaf[l][b]) continue;
+                const int cl = og_lin(t.cell[l] + 3 * b, G), k = t.kk[l][b], a0 = t.ia[l][k], a1 = t.ib[l][k];
+                double cen[3], hp, *sm = (double *)malloc(sizeof(double) * nk), tm[OR_MAXQ];
+                og_box_geom(&t, l, b, cen, &hp);
+                double *m = mu[l] + (size_t)b * na * nk;
+                for (int q = t.cstart[l][cl]; q < t.cstart[l][cl + 1]; ++q) {
+                    const int x = t.ctri[l][q];
+                    or_space_moments(&F, x, cen, hp, 0, sm);
+                    for (int j = a0; j < a1; ++j) {
+                        for (int a = 0; a < na; ++a) tm[a] = or_time_moment(a, mt, ts[a0], ts[a1], ts[j], ts[j + 1] - ts[j]);
+                        const double wv = w[(size_t)j * nt + x];
+                        for (int a = 0; a < na; ++a)
+                            for (int i = 0; i < nk; ++i) m[a * nk + i] += wv * tm[a] * sm[i];
+                    }
+                }
+                free(sm);
+            }
+        }
+        /* M2M (Eq. temp_m2m, st_m2m): parents of levels L-2 .. 2 */
+        for (int l = L - 2; l >= 2; --l) {
+            for (int bc = 0; bc < t.nb[l + 1]; ++bc) { /* serial: children of one parent add into it */
+                const int bp = t.par[l + 1][bc], kc = t.kk[l + 1][bc], kp = t.kk[l][bp];
+                double cc[3], hc, cp[3], hp, q1[3][OR_MAXQ][OR_MAXQ], qt[OR_MAXQ][OR_MAXQ];
+                og_box_geom(&t, l + 1, bc, cc, &hc);
+                og_box_geom(&t, l, bp, cp, &hp);
+                const double clo = ts[t.ia[l + 1][kc]], chi = ts[t.ib[l + 1][kc]];
+                for (int ac = 0; ac < na; ++ac) {
+                    const double xi = 0.5 * (clo + chi) + 0.5 * (chi - clo) * or_cheb_node(ac, mt);
+                    for (int ap = 0; ap < na; ++ap) qt[ac][ap] = or_lagrange(ap, mt, ts[t.ia[l][kp]], ts[t.ib[l][kp]], xi);
+                }
+                if (t.st[l])
+                    for (int d = 0; d < 3; ++d)
+                        for (int a1 = 0; a1 <= mx; ++a1)
+                            for (int n1 = 0; n1 <= mx; ++n1) q1[d][a1][n1] = or_qx(a1, n1, cc[d], hc, cp[d], hp, mx);
+                const double *mc = mu[l + 1] + (size_t)bc * na * nk;
+                double *mp = mu[l] + (size_t)bp * na * nk;
+                for (int ap = 0; ap < na; ++ap)
+                    for (int ac = 0; ac < na; ++ac)
+                        for (int iv = 0; iv < nk; ++iv) {
+                            const int *nu = F.mi.k[iv];
+                            double acc = 0.0;
+                            if (!t.st[l]) {
+                                acc = mc[ac * nk + iv];
+                            } else {
+                                for (int k0 = 0; k0 <= nu[0]; ++k0)
+                                    for (int k1 = 0; k1 <= nu[1]; ++k1)
+                                        for (int k2 = 0; k2 <= nu[2]; ++k2) {
+                                            const int ik = F.mi.lookup[(k0 * (mx + 1) + k1) * (mx + 1) + k2];
+                                            acc += q1[0][k0][nu[0]] * q1[1][k1][nu[1]] * q1[2][k2][nu[2]] * mc[ac * nk + ik];
+                                        }
+                            }
+                            mp[ap * nk + iv] += qt[ac][ap] * acc;
+                        }
+            }
+        }
+        /* M2L (Eq. m2l with Eq. exp_coeffs_3d / exp_coeffs_1d) at every level >= 2 */
+        for (int l = 2; l < L; ++l) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+            for (int bt = 0; bt < t.nb[l]; ++bt) {
+                const int cap = og_nf_cap(&t);
+                int *il = (int *)malloc(sizeof(int) * (size_t)cap);
+                const int ni = og_interaction(&t, l, bt, il, cap), kt = t.kk[l][bt];
+                double ct[3], hpx, *E1 = (double *)malloc(sizeof(double) * 3 * OR_MAXQ * OR_MAXQ);
+                og_box_geom(&t, l, bt, ct, &hpx);
+                const double tlo = ts[t.ia[l][kt]], thi = ts[t.ib[l][kt]];
+                double *lt = lam[l] + (size_t)bt * na * nk;
+                for (int q = 0; q < ni; ++q) {
+                    const int bs = il[q], ks = t.kk[l][bs];
+                    double cs[3], hs;
+                    og_box_geom(&t, l, bs, cs, &hs);
+                    const double slo = ts[t.ia[l][ks]], shi = ts[t.ib[l][ks]];
+                    const double *ms = mu[l] + (size_t)bs * na * nk;
+                    for (int a = 0; a < na; ++a)
+                        for (int b = 0; b < na; ++b) {
+                            /* xi_{I,b} - xi_{J,a} */
+                            const double dt = (0.5 * (tlo + thi) + 0.5 * (thi - tlo) * or_cheb_node(b, mt)) -
+                                              (0.5 * (slo + shi) + 0.5 * (shi - slo) * or_cheb_node(a, mt));
+                            const double dab = 4.0 * P->alpha * dt / (hpx * hpx), pf = pow(4.0 * OR_PI * P->alpha * dt, -1.5);
+                            for (int d = 0; d < 3; ++d)
+                                for (int kk = 0; kk <= mx; ++kk)
+                                    for (int ll = 0; ll + kk <= mx; ++ll)
+                                        E1[(d * OR_MAXQ + kk) * OR_MAXQ + ll] = or_E1(kk, ll, (ct[d] - cs[d]) / hpx, dab, mx);
+                            for (int iv = 0; iv < nk; ++iv) {
+                                const int *nu = F.mi.k[iv];
+                                double acc = 0.0;
+                                for (int ik = 0; ik < nk; ++ik) {
+                                    const int *ka = F.mi.k[ik];
+                                    if (ka[0] + ka[1] + ka[2] + nu[0] + nu[1] + nu[2] > mx) continue;
+                                    double E = pf;
+                                    for (int d = 0; d < 3; ++d) E *= E1[(d * OR_MAXQ + ka[d]) * OR_MAXQ + nu[d]];
+                                    acc += E * ms[a * nk + ik];
+                                }
+                                lt[b * nk + iv] += acc;
+                            }
+                        }
+                }
+                free(E1);
+                free(il);
+            }
+        }
+        /* L2L (transposed M2M) for levels 3 .. L-1 */
+        for (int l = 3; l < L; ++l) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+            for (int bc = 0; bc < t.nb[l]; ++bc) {
+                const int bp = t.par[l][bc], kc = t.kk[l][bc], kp = t.kk[l - 1][bp];
+                double cc[3], hc, cp[3], hp, q1[3][OR_MAXQ][OR_MAXQ], qt[OR_MAXQ][OR_MAXQ];
+                og_box_geom(&t, l, bc, cc, &hc);
+                og_box_geom(&t, l - 1, bp, cp, &hp);
+                const double clo = ts[t.ia[l][kc]], chi = ts[t.ib[l][kc]];
+                for (int bcI = 0; bcI < na; ++bcI) {
+                    const double xi = 0.5 * (clo + chi) + 0.5 * (chi - clo) * or_cheb_node(bcI, mt);
+                    for (int bpI = 0; bpI < na; ++bpI)
+                        qt[bcI][bpI] = or_lagrange(bpI, mt, ts[t.ia[l - 1][kp]], ts[t.ib[l - 1][kp]], xi);
+                }
+                if (t.st[l - 1])
+                    for (int d = 0; d < 3; ++d)
+                        for (int a1 = 0; a1 <= mx; ++a1)
+                            for (int n1 = 0; n1 <= mx; ++n1) q1[d][a1][n1] = or_qx(a1, n1, cc[d], hc, cp[d], hp, mx);
+                const double *lp = lam[l - 1] + (size_t)bp * na * nk;
+                double *lc = lam[l] + (size_t)bc * na * nk;
+                for (int bcI = 0; bcI < na; ++bcI)
+                    for (int ik = 0; ik < nk; ++ik) {
+                        const int *ka = F.mi.k[ik];
+                        double acc = 0.0;
+                        for (int bpI = 0; bpI < na; ++bpI) {
+                            if (!t.st[l - 1]) {
+                                acc += qt[bcI][bpI] * lp[bpI * nk + ik];
+                                continue;
+                            }
+                            for (int n0 = ka[0]; n0 <= mx; ++n0)
+                                for (int n1 = ka[1]; n0 + n1 <= mx; ++n1)
+                                    for (int n2 = ka[2]; n0 + n1 + n2 <= mx; ++n2) {
+                                        const int iv = F.mi.lookup[(n0 * (mx + 1) + n1) * (mx + 1) + n2];
+                                        acc += qt[bcI][bpI] * q1[0][ka[0]][n0] * q1[1][ka[1]][n1] * q1[2][ka[2]][n2] *
+                                               lp[bpI * nk + iv];
+                                    }
+                        }
+                        lc[bcI * nk + ik] += acc;
+                    }
+            }
+        }
+        /* L2T at every leaf of a level >= 2 (Eq. l2t) */
+        for (int l = 2; l < L; ++l) {
+            const int G = og_G(&t, l);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+            for (int b = 0; b < t.nb[l]; ++b) {
+                if (!t.leaf[l][b]) continue;
+                const int cl = og_lin(t.cell[l] + 3 * b, G), k = t.kk[l][b], a0 = t.ia[l][k], a1 = t.ib[l][k];
+                double cen[3], hp, *sm = (double *)malloc(sizeof(double) * nk), tm[OR_MAXQ];
+                og_box_geom(&t, l, b, cen, &hp);
+                const double *lb = lam[l] + (size_t)b * na * nk;
+                for (int q = t.cstart[l][cl]; q < t.cstart[l][cl + 1]; ++q) {
+                    const int x = t.ctri[l][q];
+                    if (!is_tgt[x]) continue;
+                    or_space_moments(&F, x, cen, hp, 0, sm);
+                    for (int kt = a0; kt < a1; ++kt) {
+                        for (int bb = 0; bb < na; ++bb) tm[bb] = or_time_moment(bb, mt, ts[a0], ts[a1], ts[kt], ts[kt + 1] - ts[kt]);
+                        double acc = 0.0;
+                        for (int bb = 0; bb < na; ++bb)
+                            for (int i = 0; i < nk; ++i) acc += lb[bb * nk + i] * tm[bb] * sm[i];
+                        f[(size_t)kt * nt + x] += acc;
+                    }
+                }
+                free(sm);
+            }
+        }
+        for (int l = 0; l < L; ++l) { free(mu[l]); free(lam[l]); }
+    }
+
+    if (parts & 1) {
+        /* nearfield of every leaf (Eq. eval_sl_nf_block over N(Z) of Eq. def_st_nearfield) */
+        for (int l = 0; l < L; ++l) {
+            const int G = og_G(&t, l);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+            for (int b = 0; b < t.nb[l]; ++b) {
+                if (!t.leaf[l][b]) continue;
+                const int cap = og_nf_cap(&t);
+                int (*nf)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)cap);
+                const int nn = og_nearfield(&t, l, b, nf, cap);
+                const int cl = og_lin(t.cell[l] + 3 * b, G), kt = t.kk[l][b];
+                const int k0 = t.ia[l][kt], k1 = t.ib[l][kt];
+                int (*pr)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)P->Et * P->Et);
+                double *ent = (double *)malloc(sizeof(double) * (size_t)P->Et * P->Et);
+                for (int q = t.cstart[l][cl]; q < t.cstart[l][cl + 1]; ++q) {
+                    const int x = t.ctri[l][q];
+                    if (!is_tgt[x]) continue;
+                    for (int s = 0; s < nn; ++s) {
+                        const int ls = nf[s][0], bs = nf[s][1], cs = og_lin(t.cell[ls] + 3 * bs, og_G(&t, ls));
+                        const int ks = t.kk[ls][bs], j0 = t.ia[ls][ks], j1 = t.ib[ls][ks];
+                        int np = 0;
+                        for (int k = k0; k < k1; ++k)
+                            for (int j = j0; j < j1 && j <= k; ++j) { pr[np][0] = k; pr[np][1] = j; np++; }
+                        if (!np) continue;
+                        for (int q2 = t.cstart[ls][cs]; q2 < t.cstart[ls][cs + 1]; ++q2) {
+                            const int y = t.ctri[ls][q2];
+                            og_pair_steps(P, ts, x, y, (const int(*)[2])pr, np, ent);
+                            for (int i = 0; i < np; ++i) f[(size_t)pr[i][0] * nt + x] += ent[i] * w[(size_t)pr[i][1] * nt + y];
+                        }
+                    }
+                }
+                free(pr);
+                free(ent);
+                free(nf);
+            }
+        }
+    }
+    free(is_tgt);
+    free(F.mi.k);
+    free(F.mi.lookup);
+    og_tree_free(&t);
+    return 0;
+}
+
+/* The dense Galerkin product of Section 2 on the listed target rows: f[k][x] = sum over all
+ * source steps j <= k and all triangles y of V[(k,x),(j,y)] w[j][y] (no FMM, no truncation). */
+int orc_gen_dense_apply(const orc_problem *P, const double *ts, const double *w, const int *targets, int ntargets,
+                        double *f, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    const int nt = P->nt, E = P->Et;
+    memset(f, 0, sizeof(double) * (size_t)E * nt);
+    int (*pr)[2] = (int(*)[2])malloc(sizeof(int) * 2 * (size_t)E * (E + 1) / 2);
+    int np = 0;
+    for (int k = 0; k < E; ++k)
+        for (int j = 0; j <= k; ++j) { pr[np][0] = k; pr[np][1] = j; np++; }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < ntargets; ++i) {
+        const int x = targets[i];
+        double *ent = (double *)malloc(sizeof(double) * np);
+        for (int y = 0; y < nt; ++y) {
+            og_pair_steps(P, ts, x, y, (const int(*)[2])pr, np, ent);
+            for (int q = 0; q < np; ++q) f[(size_t)pr[q][0] * nt + x] += ent[q] * w[(size_t)pr[q][1] * nt + y];
+        }
+        free(ent);
+    }
+    free(pr);
     return 0;
 }
