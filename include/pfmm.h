@@ -267,6 +267,53 @@ int pfmm_shard_owners(int32_t levels, int32_t nranks, int32_t *owner);
  * the total (call with cap = 0 to size the array). */
 int pfmm_shard_messages(int32_t levels, int32_t nranks, int32_t *msgs, int64_t cap, int64_t *count);
 
+/* ---- general (non-uniform) time steps -----------------------------------------------------
+ * The space-time FMM of Alg. 2 on the general box cluster tree of Alg. 1 (Section 3.2 in full;
+ * the adaptive direction of Section 6): time steps t_0 = 0 < t_1 < ... < t_Et = T of any lengths,
+ * boxes refined while they hold at least n_max space-time elements (early leaves on any level),
+ * temporal splits at the step nearest an interval's centre, refinement stopped early for oversized
+ * elements (an interval of a single step, a step longer than the level's nominal interval length
+ * T / 2^l, a triangle wider than its cell), and the nearfield of Eq. def_st_nearfield including
+ * the leaves of the ancestors' nearfields (N(parent(Z)) /\ L_Sigma).  No block-Toeplitz
+ * structure: the nearfield blocks hold the entries of every (target step, source step) pair.
+ * Single layer V_h, FP64.  Vector layouts as above ([nrhs][E_t][E_x], device pointers). */
+typedef struct pfmm_gen pfmm_gen;
+
+typedef struct pfmm_gen_info {
+    int32_t nlev;            /* levels 0 .. nlev - 1 */
+    int32_t lx[32];          /* spatial refinements of level l */
+    int32_t nbox[32];        /* boxes of level l */
+    int32_t nleaf[32];       /* leaves of level l */
+    int32_t nint[32];        /* temporal intervals present on level l */
+    int32_t ntr_far[32];     /* interaction-area radius of level l for M2L (Eq. 03:Iarea) */
+    int32_t ntr_near[32];    /* ... and for the nearfield */
+    int32_t st[32];          /* 1: level l is refined into level l+1 in space and time, 0: in time */
+    double pad[32];          /* padding of level l */
+    int64_t n_m2l_pairs;     /* box pairs of all interaction lists */
+    int64_t n_near_blocks;   /* (leaf, nearfield box) blocks */
+    int64_t nearfield_entries; /* stored nearfield entries */
+    int64_t device_bytes;    /* device memory held by the handle */
+} pfmm_gen_info;
+
+/* Build the general tree, lists, tables and stored nearfield.  mesh: as for pfmm_build_trees with
+ * n_steps = E_t and T = t_steps[E_t]; t_steps: HOST array of E_t + 1 times, t_steps[0] = 0,
+ * strictly increasing (copied).  params: m_t, m_x, c_st, n_tr, eps_tr, quad_regular and
+ * quad_singular are used (leaf_steps, leaf_tris, nearfield, nf_engine, fp64_native and nf_form
+ * are ignored; precision must be PFMM_FP64, else PFMM_ERR_UNSUPPORTED).  n_max >= 1: the element
+ * bound of Alg. 1.  Returns PFMM_ERR_OOM when the stored nearfield exceeds 60 % of the free device
+ * memory.  Synchronises `stream`. */
+int pfmm_gen_create(const pfmm_mesh *mesh, const double *t_steps, const pfmm_params *params, int32_t n_max,
+                    void *stream, pfmm_gen **out);
+/* f = V_h w (Alg. 2, parts as for pfmm_apply_parts), f overwritten; w, f device [nrhs][E_t][E_x]
+ * FP64, must not overlap.  Enqueued on `stream`; may allocate workspaces on first use or a larger
+ * nrhs. */
+int pfmm_gen_apply_V(pfmm_gen *h, const double *w, double *f, int32_t nrhs, int32_t parts, void *stream);
+int pfmm_gen_get_info(const pfmm_gen *h, pfmm_gen_info *info);
+/* The boxes as rows (level, cell x, cell y, cell z, interval k, leaf, first step, end step), level
+ * by level; at most cap rows into rows [cap][8], *count gets the total. */
+int pfmm_gen_boxes(const pfmm_gen *h, int32_t *rows, int64_t cap, int64_t *count);
+void pfmm_gen_destroy(pfmm_gen *h);
+
 /* ---- solver ------------------------------------------------------------------------------ */
 #define PFMM_DIRECT 0    /* V_h w = (1/2 M_h + K_h) g  (Section 2, Eq. 02:linear:system) */
 #define PFMM_INDIRECT 1  /* V_h w = M_h g              (single-layer ansatz) */

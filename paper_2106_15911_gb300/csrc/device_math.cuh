@@ -106,6 +106,42 @@ __device__ __forceinline__ void time_V_all(R r, R h, R alpha, int nd, R *out)
     }
 }
 
+// G2 and its bounded form G2t (above) at one time difference s (both 0 for s <= 0)
+__device__ __forceinline__ void g2_and_g2t(double r, double s, double alpha, double &g2, double &g2t)
+{
+    if (!(s > 0.0)) {
+        g2 = g2t = 0.0;
+        return;
+    }
+    const double ss = sqrt(s), a32 = alpha * sqrt(alpha), u = r / (2.0 * sqrt(alpha) * ss);
+    double ef, efc;
+    erf_pair(u, ef, efc);
+    const double ex = exp(-u * u);
+    g2t = r * efc / (8.0 * kPi * alpha * alpha) - ss * erf_over_u(u, ef) / (8.0 * kPi * a32) -
+          ss * ex / (4.0 * kPi * kSqrtPi * a32);
+    g2 = r > 0.0 ? ((s + r * r / (2.0 * alpha)) * efc - r * ss / sqrt(kPi * alpha) * ex) / (4.0 * kPi * alpha * r) : 0.0;
+}
+
+// Single-layer entry factor for a target step (tk0, tk1] and a source step (tj0, tj1] of any
+// lengths (general time steps): the second difference of G2 over the four time differences;
+// 0 for a later source step, G2(tk1 - tk0) alone for the same step (r > 0 then).  As for uniform
+// steps the bounded form is taken when u at the largest difference is below 1 (the linear parts
+// cancel when the source step precedes the target step).
+__device__ __forceinline__ double time_V_steps(double r, double tk0, double tk1, double tj0, double tj1,
+                                               double alpha)
+{
+    if (tj0 >= tk1) return 0.0;
+    double g[4], gt[4];
+    if (tj0 == tk0 && tj1 == tk1) {
+        g2_and_g2t(r, tk1 - tk0, alpha, g[0], gt[0]);
+        return g[0];
+    }
+    const double s[4] = {tk1 - tj0, tk1 - tj1, tk0 - tj0, tk0 - tj1};
+    for (int i = 0; i < 4; ++i) g2_and_g2t(r, s[i], alpha, g[i], gt[i]);
+    const double u = r / (2.0 * sqrt(alpha * s[0]));
+    return u < 1.0 ? (gt[0] - gt[1]) - (gt[2] - gt[3]) : (g[0] - g[1]) - (g[2] - g[3]);
+}
+
 // Double-layer time factors for d = 0 .. nd-1 (multiply by (x - y).n_y); 0 at r = 0.
 template <typename R>
 __device__ __forceinline__ void time_K_all(R r, R h, R alpha, int nd, R *out)

@@ -1,0 +1,419 @@
+// k_gen.cu -- kernels of the space-time FMM for general time steps (Alg. 2 on the general tree of
+// Alg. 1; single layer V_h, FP64):
+//   nearfield entries  Eq. eval_sl_nf_block with the entries of Section 2 for arbitrary target and
+//                      source steps (collapsed Gauss rule for regular pairs, Sauter-Schwab for
+//                      touching triangles on the same or the previous step);
+//   nearfield apply    one CTA per leaf box over the blocks of its nearfield N(Z) (Eq.
+//                      def_st_nearfield), each target element written once (no atomics);
+//   S2M                Eq. s2m at every leaf of a level >= 2;
+//   M2M / L2L          Eq. temp_m2m / st_m2m and their transposes, one CTA per parent / child, with
+//                      q^(t) of the actual (unequal) intervals;
+//   M2L                Eq. m2l with Eq. exp_coeffs_3d: one CTA per target box over its interaction
+//                      list, E as prefactor x three 1D factors tabulated per interval pair (the time
+//                      nodes of unequal intervals differ pair by pair);
+//   L2T                Eq. l2t at every leaf of a level >= 2.
+// Every kernel is a plain grid over the boxes of one phase; phases that depend on coarser or finer
+// levels are launched level by level.
+#include "device_math.cuh"
+#include "gtree.h"
+#include "nf_geom.cuh"
+#include "pfmm_internal.h"
+
+namespace pfmm {
+
+using namespace dev;
+
+namespace {
+
+constexpr int kGenRhs = 8;  // right-hand sides per pass of the nearfield apply
+
+__device__ __forceinline__ void load_tri_v(const double *verts, const int *tv, double P[3][3])
+{
+    for (int v = 0; v < 3; ++v)
+        for (int c = 0; c < 3; ++c) P[v][c] = verts[3 * tv[v] + c];
+}
+
+// regular pair (x, y): collapsed Gauss rule on both triangles
+__device__ double gen_regular(const GenQuad &q, int x, int y, double tk0, double tk1, double tj0, double tj1)
+{
+    double PX[3][3], PY[3][3], n[3];
+    load_tri_v(q.verts, q.tri + 3 * x, PX);
+    load_tri_v(q.verts, q.tri + 3 * y, PY);
+    const double Jx = tri_jac(PX, n), Jy = tri_jac(PY, n);
+    const int nq = q.nq_reg;
+    double acc = 0.0;
+    for (int i = 0; i < nq; ++i) {
+        const double s1 = q.rule_reg[i], s2 = q.rule_reg[nq + i], wi = q.rule_reg[2 * nq + i];
+        double xp[3];
+        for (int c = 0; c < 3; ++c) xp[c] = PX[0][c] + s1 * (PX[1][c] - PX[0][c]) + s2 * (PX[2][c] - PX[1][c]);
+        for (int j = 0; j < nq; ++j) {
+            const double t1 = q.rule_reg[j], t2 = q.rule_reg[nq + j], wj = q.rule_reg[2 * nq + j];
+            double d2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double d = xp[c] - (PY[0][c] + t1 * (PY[1][c] - PY[0][c]) + t2 * (PY[2][c] - PY[1][c]));
+                d2 += d * d;
+            }
+            acc += wi * wj * time_V_steps(sqrt(d2), tk0, tk1, tj0, tj1, q.alpha);
+        }
+    }
+    return acc * Jx * Jy;
+}
+
+// touching pair (x, y) with Sauter-Schwab class and vertex order `code` (see ss_code)
+__device__ double gen_singular(const GenQuad &q, int x, int y, int code, double tk0, double tk1, double tj0,
+                               double tj1)
+{
+    const int cls = code & 3;
+    const int ox[3] = {(code >> 2) & 3, (code >> 4) & 3, (code >> 6) & 3};
+    const int oy[3] = {(code >> 8) & 3, (code >> 10) & 3, (code >> 12) & 3};
+    double PXo[3][3], PYo[3][3], PX[3][3], PY[3][3], n[3];
+    load_tri_v(q.verts, q.tri + 3 * x, PXo);
+    load_tri_v(q.verts, q.tri + 3 * y, PYo);
+    for (int v = 0; v < 3; ++v)
+        for (int c = 0; c < 3; ++c) {
+            PX[v][c] = PXo[ox[v]][c];
+            PY[v][c] = PYo[oy[v]][c];
+        }
+    const double Jx = tri_jac(PX, n), Jy = tri_jac(PY, n);
+    const int ns = q.nq_sing;
+    const double *gx = q.gl_sing, *gw = q.gl_sing + ns;
+    double acc = 0.0;
+    for (int i0 = 0; i0 < ns; ++i0)
+        for (int i1 = 0; i1 < ns; ++i1)
+            for (int i2 = 0; i2 < ns; ++i2)
+                for (int i3 = 0; i3 < ns; ++i3) {
+                    double pts[6][4], jac[6];
+                    const int np = ss_points(cls, gx[i0], gx[i1], gx[i2], gx[i3], pts, jac);
+                    const double w4 = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                    for (int u = 0; u < np; ++u) {
+                        double d2 = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            const double xp = PX[0][c] + pts[u][0] * (PX[1][c] - PX[0][c]) + pts[u][1] * (PX[2][c] - PX[1][c]);
+                            const double yp = PY[0][c] + pts[u][2] * (PY[1][c] - PY[0][c]) + pts[u][3] * (PY[2][c] - PY[1][c]);
+                            d2 += (xp - yp) * (xp - yp);
+                        }
+                        acc += w4 * jac[u] * time_V_steps(sqrt(d2), tk0, tk1, tj0, tj1, q.alpha);
+                    }
+                }
+    return acc * Jx * Jy;
+}
+
+// index of (rhs r, box b, time index a, multi-index i) in mu / lam
+__device__ __forceinline__ size_t gidx(const GenDev &g, int r, int b, int a, int i)
+{
+    return (((size_t)r * g.nbox + b) * g.na + a) * g.nk + i;
+}
+
+}  // namespace
+
+// one CTA per nearfield block, thread per entry [jj][y][kk][x]
+__global__ void __launch_bounds__(128) k_gen_nf_entries(GenQuad q, const GBox *__restrict__ box,
+                                                          const GNear *__restrict__ blocks, double *__restrict__ A)
+{
+    const GNear B = blocks[blockIdx.x];
+    const GBox T = box[B.tgt], S = box[B.src];
+    const int ntx = T.t1 - T.t0, nkt = T.a1 - T.a0, nys = S.t1 - S.t0, nks = S.a1 - S.a0;
+    const int64_t n = (int64_t)ntx * nkt * nys * nks;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const int x = (int)(e % ntx), kk = (int)((e / ntx) % nkt), y = (int)((e / ((int64_t)ntx * nkt)) % nys);
+        const int jj = (int)(e / ((int64_t)ntx * nkt * nys));
+        const int k = T.a0 + kk, j = S.a0 + jj, xi = T.t0 + x, yi = S.t0 + y;
+        double v = 0.0;
+        if (j <= k) {
+            const double tk0 = q.ts[k], tk1 = q.ts[k + 1], tj0 = q.ts[j], tj1 = q.ts[j + 1];
+            const int code = ss_code(q.tri + 3 * xi, q.tri + 3 * yi);
+            v = (code && k - j <= 1) ? gen_singular(q, xi, yi, code, tk0, tk1, tj0, tj1)
+                                     : gen_regular(q, xi, yi, tk0, tk1, tj0, tj1);
+        }
+        A[B.off + e] = v;
+    }
+}
+
+void launch_gen_nf_entries(const GenQuad &q, const GBox *box, const GNear *blocks, int nblocks, double *A,
+                           cudaStream_t st)
+{
+    if (nblocks > 0) k_gen_nf_entries<<<nblocks, 128, 0, st>>>(q, box, blocks, A);
+}
+
+// E1[p][a][b][o][kappa][nu] of Eq. exp_coeffs_1d and pref[p][a][b] = (4 pi alpha dt)^{-3/2} for the
+// interval pairs p of one level: dt = xi_{I,b} - xi_{J,a} from dts[p][a][b]; thread per entry
+__global__ void k_gen_e1(int npairs, const double *__restrict__ dts, int na, int mx, int G, double hx, double hxp,
+                         double alpha, double *__restrict__ E1, double *__restrict__ pref)
+{
+    const int m1 = mx + 1, no = 2 * G - 1;
+    const int64_t total = (int64_t)npairs * na * na * no * m1 * m1;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int nu = (int)(gid % m1), ka = (int)((gid / m1) % m1), o = (int)((gid / (m1 * m1)) % no);
+    const int64_t pab = gid / ((int64_t)m1 * m1 * no);  // (p, a, b)
+    const double dt = dts[pab];
+    if (o == 0 && ka == 0 && nu == 0) pref[pab] = pow(4.0 * kPi * alpha * dt, -1.5);
+    double val = 0.0;
+    if (ka + nu <= mx) {
+        const double r = 2.0 * hx * (o - (G - 1)) / hxp, dab = 4.0 * alpha * dt / (hxp * hxp);
+        double s = 0.0;
+        for (int n = 0; n <= mx; ++n) {
+            const double xn = cos((2.0 * n + 1.0) * kPi / (2.0 * mx + 2.0)), Tn = cos(nu * acos(xn));
+            for (int m = 0; m <= mx; ++m) {
+                const double xm = cos((2.0 * m + 1.0) * kPi / (2.0 * mx + 2.0)), z = r + xn - xm;
+                s += exp(-z * z / dab) * Tn * cos(ka * acos(xm));
+            }
+        }
+        val = (ka == 0 ? 1.0 : 2.0) * (nu == 0 ? 1.0 : 2.0) / ((mx + 1.0) * (mx + 1.0)) * s;
+    }
+    E1[gid] = val;
+}
+
+void launch_gen_e1(int npairs, const double *dts, int na, int mx, int G, double hx, double hxp, double alpha,
+                   double *E1, double *pref, cudaStream_t st)
+{
+    const int64_t total = (int64_t)npairs * na * na * (2 * G - 1) * (mx + 1) * (mx + 1);
+    if (total > 0)
+        k_gen_e1<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(npairs, dts, na, mx, G, hx, hxp, alpha, E1, pref);
+}
+
+// w_int[row][i] = w[row][perm[i]], f[row][perm[i]] = f_int[row][i]
+__global__ void k_gen_permute_in(const double *__restrict__ w, double *__restrict__ w_int, const int *__restrict__ perm,
+                                 int nt, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w_int[i] = w[i - i % nt + perm[i % nt]];
+}
+__global__ void k_gen_permute_out(const double *__restrict__ f_int, double *__restrict__ f, const int *__restrict__ perm,
+                                  int nt, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i - i % nt + perm[i % nt]] = f_int[i];
+}
+void launch_gen_permute_in(const double *w, double *w_int, const int *perm, int nt, int rows, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nt * rows;
+    if (n > 0) k_gen_permute_in<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w, w_int, perm, nt, n);
+}
+void launch_gen_permute_out(const double *f_int, double *f, const int *perm, int nt, int rows, cudaStream_t st)
+{
+    const int64_t n = (int64_t)nt * rows;
+    if (n > 0) k_gen_permute_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f_int, f, perm, nt, n);
+}
+
+// f_int[r][k][x] = sum over the blocks of the leaf of A[jj][y][kk][x] w_int[r][j][y] (j <= k)
+__global__ void __launch_bounds__(128) k_gen_nf_apply(const GBox *__restrict__ box, const int *__restrict__ leaves,
+                                                        const int *__restrict__ nptr, const GNear *__restrict__ blocks,
+                                                        const double *__restrict__ A, const double *__restrict__ w_int,
+                                                        double *__restrict__ f_int, int nt, int Et, int nrhs)
+{
+    const int b = leaves[blockIdx.x];
+    const GBox T = box[b];
+    const int ntx = T.t1 - T.t0, nkt = T.a1 - T.a0;
+    const size_t per_rhs = (size_t)Et * nt;
+    for (int r0 = 0; r0 < nrhs; r0 += kGenRhs) {
+        const int nr = min(kGenRhs, nrhs - r0);
+        for (int e = threadIdx.x; e < ntx * nkt; e += blockDim.x) {
+            const int x = e % ntx, kk = e / ntx, k = T.a0 + kk;
+            double acc[kGenRhs];
+#pragma unroll
+            for (int r = 0; r < kGenRhs; ++r) acc[r] = 0.0;
+            for (int q = nptr[b]; q < nptr[b + 1]; ++q) {
+                const GNear B = blocks[q];
+                const GBox S = box[B.src];
+                const int nys = S.t1 - S.t0;
+                const double *Ab = A + B.off + (size_t)kk * ntx + x;
+                for (int jj = 0; jj < S.a1 - S.a0 && S.a0 + jj <= k; ++jj) {
+                    const double *wj = w_int + (size_t)r0 * per_rhs + (size_t)(S.a0 + jj) * nt + S.t0;
+                    for (int y = 0; y < nys; ++y) {
+                        const double a = Ab[((size_t)jj * nys + y) * nkt * ntx];
+#pragma unroll
+                        for (int r = 0; r < kGenRhs; ++r)
+                            if (r < nr) acc[r] += a * wj[(size_t)r * per_rhs + y];
+                    }
+                }
+            }
+            for (int r = 0; r < nr; ++r) f_int[(size_t)(r0 + r) * per_rhs + (size_t)k * nt + T.t0 + x] = acc[r];
+        }
+    }
+}
+
+void launch_gen_nf_apply(const GBox *box, const int *leaves, int nleaves, const int *nptr, const GNear *blocks,
+                         const double *A, const double *w_int, double *f_int, int nt, int Et, int nrhs,
+                         cudaStream_t st)
+{
+    if (nleaves > 0) k_gen_nf_apply<<<nleaves, 128, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, nrhs);
+}
+
+// mu[r][b][a][kappa] = sum_j St[l][j][a] sum_x Sx[slot][x][kappa] w_int[r][j][x]  (Eq. s2m)
+__global__ void __launch_bounds__(128) k_gen_s2m(GenDev g, const int *__restrict__ leaves,
+                                                   const double *__restrict__ w_int)
+{
+    const int b = leaves[blockIdx.x];
+    const GBox B = g.box[b];
+    const double *Sx = g.Sx + (size_t)B.sx * g.nt * g.nk, *St = g.St + (size_t)B.level * g.Et * g.na;
+    const size_t per_rhs = (size_t)g.Et * g.nt;
+    for (int r = 0; r < g.nrhs; ++r)
+        for (int ik = threadIdx.x; ik < g.nk; ik += blockDim.x) {
+            double acc[kMaxNa];
+            for (int a = 0; a < g.na; ++a) acc[a] = 0.0;
+            for (int j = B.a0; j < B.a1; ++j) {
+                const double *w = w_int + r * per_rhs + (size_t)j * g.nt;
+                double Q = 0.0;
+                for (int x = B.t0; x < B.t1; ++x) Q += Sx[(size_t)x * g.nk + ik] * w[x];
+                for (int a = 0; a < g.na; ++a) acc[a] += St[(size_t)j * g.na + a] * Q;
+            }
+            for (int a = 0; a < g.na; ++a) g.mu[gidx(g, r, b, a, ik)] = acc[a];
+        }
+}
+
+void launch_gen_s2m(const GenDev &g, const int *leaves, int n, const double *w_int, cudaStream_t st)
+{
+    if (n > 0) k_gen_s2m<<<n, 128, 0, st>>>(g, leaves, w_int);
+}
+
+// mu(Z_p)[ap][nu] = sum_children sum_ac q^(t)_{ac,ap} (sum_{kappa <= nu} q^(x)_{kappa,nu} mu(Z_c)[ac][kappa])
+// (Eq. st_m2m; Eq. temp_m2m when the children were refined in time only: kappa = nu)
+__global__ void __launch_bounds__(128) k_gen_m2m(GenDev g, const int *__restrict__ parents)
+{
+    const int bp = parents[blockIdx.x];
+    const GBox P = g.box[bp];
+    const int m1 = g.mx + 1, lc = P.level + 1, st = g.lvst[lc];
+    const double *q1 = g.q1 + (size_t)lc * 2 * m1 * m1;
+    for (int r = 0; r < g.nrhs; ++r)
+        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
+            const int ap = t / g.nk, iv = t % g.nk;
+            const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
+            double acc = 0.0;
+            for (int c = P.c0; c < P.c1; ++c) {
+                const GBox C = g.box[c];
+                const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
+                             *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
+                for (int ac = 0; ac < g.na; ++ac) {
+                    double v;
+                    if (!st) {
+                        v = g.mu[gidx(g, r, c, ac, iv)];
+                    } else {
+                        v = 0.0;
+                        for (int k0 = 0; k0 <= n0; ++k0)
+                            for (int k1 = 0; k1 <= n1; ++k1)
+                                for (int k2 = 0; k2 <= n2; ++k2)
+                                    v += qa[k0 * m1 + n0] * qb[k1 * m1 + n1] * qc[k2 * m1 + n2] *
+                                         g.mu[gidx(g, r, c, ac, g.kinv[(k0 * m1 + k1) * m1 + k2])];
+                    }
+                    acc += g.qt[((size_t)c * g.na + ac) * g.na + ap] * v;
+                }
+            }
+            g.mu[gidx(g, r, bp, ap, iv)] = acc;
+        }
+}
+
+void launch_gen_m2m(const GenDev &g, const int *parents, int n, cudaStream_t st)
+{
+    if (n > 0) k_gen_m2m<<<n, 128, 0, st>>>(g, parents);
+}
+
+// lam(Z)[b][nu] = sum over I(Z) of sum_a pref[a][b] sum_{|kappa + nu| <= m_x} prod_d E1_d mu(Z_s)[a][kappa]
+// (Eq. m2l with Eq. exp_coeffs_3d; E1 of the pair's intervals, offsets of the cells per direction)
+__global__ void __launch_bounds__(128) k_gen_m2l(GenDev g, const int *__restrict__ targets, const int *__restrict__ mptr,
+                                                   const GPair *__restrict__ pairs, const double *__restrict__ E1,
+                                                   const int64_t *__restrict__ e1off, const double *__restrict__ pref)
+{
+    const int bt = targets[blockIdx.x];
+    const GBox T = g.box[bt];
+    const int m1 = g.mx + 1, G = g.lvG[T.level], no = 2 * G - 1;
+    for (int r = 0; r < g.nrhs; ++r)
+        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
+            const int b = t / g.nk, iv = t % g.nk;
+            const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
+            double acc = 0.0;
+            for (int q = mptr[bt]; q < mptr[bt + 1]; ++q) {
+                const GPair pr = pairs[q];
+                const GBox S = g.box[pr.src];
+                const int o0 = T.cell[0] - S.cell[0] + G - 1, o1 = T.cell[1] - S.cell[1] + G - 1,
+                          o2 = T.cell[2] - S.cell[2] + G - 1;
+                for (int a = 0; a < g.na; ++a) {
+                    const double *E = E1 + e1off[pr.e] + (size_t)(a * g.na + b) * no * m1 * m1;
+                    const double *E0 = E + (size_t)o0 * m1 * m1, *Ea = E + (size_t)o1 * m1 * m1,
+                                 *Eb = E + (size_t)o2 * m1 * m1;
+                    double s = 0.0;
+                    for (int ik = 0; ik < g.nk; ++ik) {
+                        const int k0 = g.kidx[3 * ik], k1 = g.kidx[3 * ik + 1], k2 = g.kidx[3 * ik + 2];
+                        if (k0 + k1 + k2 + n0 + n1 + n2 > g.mx) continue;
+                        s += E0[k0 * m1 + n0] * Ea[k1 * m1 + n1] * Eb[k2 * m1 + n2] * g.mu[gidx(g, r, pr.src, a, ik)];
+                    }
+                    acc += pref[((size_t)pr.e * g.na + a) * g.na + b] * s;
+                }
+            }
+            g.lam[gidx(g, r, bt, b, iv)] = acc;
+        }
+}
+
+void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
+                    const double *E1, const int64_t *e1off, const double *pref, cudaStream_t st)
+{
+    if (n > 0) k_gen_m2l<<<n, 128, 0, st>>>(g, targets, mptr, pairs, E1, e1off, pref);
+}
+
+// lam(Z_c)[bc][kappa] += sum_bp q^(t)_{bc,bp} sum_{nu >= kappa, |nu| <= m_x} q^(x)_{kappa,nu} lam(Z_p)[bp][nu]
+// (the transposes of Eq. temp_m2m / st_m2m)
+__global__ void __launch_bounds__(128) k_gen_l2l(GenDev g, const int *__restrict__ children)
+{
+    const int bc = children[blockIdx.x];
+    const GBox C = g.box[bc];
+    const int m1 = g.mx + 1, st = g.lvst[C.level], bp = C.par;
+    const double *q1 = g.q1 + (size_t)C.level * 2 * m1 * m1;
+    const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
+                 *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
+    for (int r = 0; r < g.nrhs; ++r)
+        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
+            const int bcI = t / g.nk, ik = t % g.nk;
+            const int k0 = g.kidx[3 * ik], k1 = g.kidx[3 * ik + 1], k2 = g.kidx[3 * ik + 2];
+            double acc = 0.0;
+            for (int bpI = 0; bpI < g.na; ++bpI) {
+                double v;
+                if (!st) {
+                    v = g.lam[gidx(g, r, bp, bpI, ik)];
+                } else {
+                    v = 0.0;
+                    for (int n0 = k0; n0 <= g.mx; ++n0)
+                        for (int n1 = k1; n0 + n1 <= g.mx; ++n1)
+                            for (int n2 = k2; n0 + n1 + n2 <= g.mx; ++n2)
+                                v += qa[k0 * m1 + n0] * qb[k1 * m1 + n1] * qc[k2 * m1 + n2] *
+                                     g.lam[gidx(g, r, bp, bpI, g.kinv[(n0 * m1 + n1) * m1 + n2])];
+                }
+                acc += g.qt[((size_t)bc * g.na + bcI) * g.na + bpI] * v;
+            }
+            g.lam[gidx(g, r, bc, bcI, ik)] += acc;
+        }
+}
+
+void launch_gen_l2l(const GenDev &g, const int *children, int n, cudaStream_t st)
+{
+    if (n > 0) k_gen_l2l<<<n, 128, 0, st>>>(g, children);
+}
+
+// f_int[r][k][x] += sum_b St[l][k][b] sum_nu lam(Z)[b][nu] Sx[slot][x][nu]  (Eq. l2t)
+__global__ void __launch_bounds__(128) k_gen_l2t(GenDev g, const int *__restrict__ leaves, double *__restrict__ f_int)
+{
+    const int b = leaves[blockIdx.x];
+    const GBox B = g.box[b];
+    const double *Sx = g.Sx + (size_t)B.sx * g.nt * g.nk, *St = g.St + (size_t)B.level * g.Et * g.na;
+    const size_t per_rhs = (size_t)g.Et * g.nt;
+    for (int r = 0; r < g.nrhs; ++r)
+        for (int x = B.t0 + threadIdx.x; x < B.t1; x += blockDim.x) {
+            double P[kMaxNa];
+            for (int bb = 0; bb < g.na; ++bb) {
+                double s = 0.0;
+                for (int iv = 0; iv < g.nk; ++iv) s += g.lam[gidx(g, r, b, bb, iv)] * Sx[(size_t)x * g.nk + iv];
+                P[bb] = s;
+            }
+            for (int k = B.a0; k < B.a1; ++k) {
+                double v = 0.0;
+                for (int bb = 0; bb < g.na; ++bb) v += St[(size_t)k * g.na + bb] * P[bb];
+                f_int[r * per_rhs + (size_t)k * g.nt + x] += v;
+            }
+        }
+}
+
+void launch_gen_l2t(const GenDev &g, const int *leaves, int n, double *f_int, cudaStream_t st)
+{
+    if (n > 0) k_gen_l2t<<<n, 128, 0, st>>>(g, leaves, f_int);
+}
+
+}  // namespace pfmm

@@ -208,41 +208,7 @@ __global__ void __launch_bounds__(128) k_nf_singular(NfQuadArgs a, const int *__
         double xi = gx[i0], e1 = gx[i1], e2 = gx[i2], e3 = gx[i3];
         double w4 = gw[i0] * gw[i1] * gw[i2] * gw[i3];
         double pts[6][4], jac[6];
-        int np;
-        if (cls == 3) {
-            double j = xi * xi * xi * e1 * e1 * e2;
-            double A_[6][4] = {{xi, xi * (1 - e1 + e1 * e2), xi * (1 - e1 * e2 * e3), xi * (1 - e1)},
-                               {xi * (1 - e1 * e2 * e3), xi * (1 - e1), xi, xi * (1 - e1 + e1 * e2)},
-                               {xi, xi * e1 * (1 - e2 + e2 * e3), xi * (1 - e1 * e2), xi * e1 * (1 - e2)},
-                               {xi * (1 - e1 * e2), xi * e1 * (1 - e2), xi, xi * e1 * (1 - e2 + e2 * e3)},
-                               {xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3), xi, xi * e1 * (1 - e2)},
-                               {xi, xi * e1 * (1 - e2), xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3)}};
-            for (int u = 0; u < 6; ++u) {
-                for (int c = 0; c < 4; ++c) pts[u][c] = A_[u][c];
-                jac[u] = j;
-            }
-            np = 6;
-        } else if (cls == 2) {
-            double j0 = xi * xi * xi * e1 * e1, j1 = j0 * e2;
-            double A_[5][4] = {{xi, xi * e1 * e3, xi * (1 - e1 * e2), xi * e1 * (1 - e2)},
-                               {xi, xi * e1, xi * (1 - e1 * e2 * e3), xi * e1 * e2 * (1 - e3)},
-                               {xi * (1 - e1 * e2), xi * e1 * (1 - e2), xi, xi * e1 * e2 * e3},
-                               {xi * (1 - e1 * e2 * e3), xi * e1 * e2 * (1 - e3), xi, xi * e1},
-                               {xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3), xi, xi * e1 * e2}};
-            for (int u = 0; u < 5; ++u) {
-                for (int c = 0; c < 4; ++c) pts[u][c] = A_[u][c];
-                jac[u] = u == 0 ? j0 : j1;
-            }
-            np = 5;
-        } else {
-            double j = xi * xi * xi * e2;
-            double A_[2][4] = {{xi, xi * e1, xi * e2, xi * e2 * e3}, {xi * e2, xi * e2 * e3, xi, xi * e1}};
-            for (int u = 0; u < 2; ++u) {
-                for (int c = 0; c < 4; ++c) pts[u][c] = A_[u][c];
-                jac[u] = j;
-            }
-            np = 2;
-        }
+        const int np = ss_points(cls, xi, e1, e2, e3, pts, jac);
         for (int u = 0; u < np; ++u) {
             double xp[3], yp[3], dx[3];
             for (int c = 0; c < 3; ++c) {

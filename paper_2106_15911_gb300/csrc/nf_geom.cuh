@@ -45,6 +45,49 @@ __device__ __forceinline__ int shared_count(const int *tri, int x, int y)
     return s;
 }
 
+// The Sauter-Schwab regularising substitutions (Sauter & Schwab, Boundary Element Methods,
+// Sec. 5.2) at the point (xi, e1, e2, e3) of [0,1]^4: the pairs (s1, s2) on x's and (t1, t2) on
+// y's reference triangle, pts[u] = {s1, s2, t1, t2}, with their Jacobians; cls 3 identical, 2
+// common edge, 1 common vertex (vertices in the rule's local order).  Returns the count.
+__device__ __forceinline__ int ss_points(int cls, double xi, double e1, double e2, double e3, double pts[6][4],
+                                         double jac[6])
+{
+    if (cls == 3) {
+        const double j = xi * xi * xi * e1 * e1 * e2;
+        const double A_[6][4] = {{xi, xi * (1 - e1 + e1 * e2), xi * (1 - e1 * e2 * e3), xi * (1 - e1)},
+                                 {xi * (1 - e1 * e2 * e3), xi * (1 - e1), xi, xi * (1 - e1 + e1 * e2)},
+                                 {xi, xi * e1 * (1 - e2 + e2 * e3), xi * (1 - e1 * e2), xi * e1 * (1 - e2)},
+                                 {xi * (1 - e1 * e2), xi * e1 * (1 - e2), xi, xi * e1 * (1 - e2 + e2 * e3)},
+                                 {xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3), xi, xi * e1 * (1 - e2)},
+                                 {xi, xi * e1 * (1 - e2), xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3)}};
+        for (int u = 0; u < 6; ++u) {
+            for (int c = 0; c < 4; ++c) pts[u][c] = A_[u][c];
+            jac[u] = j;
+        }
+        return 6;
+    }
+    if (cls == 2) {
+        const double j0 = xi * xi * xi * e1 * e1, j1 = j0 * e2;
+        const double A_[5][4] = {{xi, xi * e1 * e3, xi * (1 - e1 * e2), xi * e1 * (1 - e2)},
+                                 {xi, xi * e1, xi * (1 - e1 * e2 * e3), xi * e1 * e2 * (1 - e3)},
+                                 {xi * (1 - e1 * e2), xi * e1 * (1 - e2), xi, xi * e1 * e2 * e3},
+                                 {xi * (1 - e1 * e2 * e3), xi * e1 * e2 * (1 - e3), xi, xi * e1},
+                                 {xi * (1 - e1 * e2 * e3), xi * e1 * (1 - e2 * e3), xi, xi * e1 * e2}};
+        for (int u = 0; u < 5; ++u) {
+            for (int c = 0; c < 4; ++c) pts[u][c] = A_[u][c];
+            jac[u] = u == 0 ? j0 : j1;
+        }
+        return 5;
+    }
+    const double j = xi * xi * xi * e2;
+    const double A_[2][4] = {{xi, xi * e1, xi * e2, xi * e2 * e3}, {xi * e2, xi * e2 * e3, xi, xi * e1}};
+    for (int u = 0; u < 2; ++u) {
+        for (int c = 0; c < 4; ++c) pts[u][c] = A_[u][c];
+        jac[u] = j;
+    }
+    return 2;
+}
+
 // Regular quadrature of the pair (x, y) (internal triangles) for the step offsets d0 .. nd-1 of
 // Eq. eval_sl_nf_block: acc[d] (V) or acc[3 d + v] (K, v: y's vertices in mesh order) are
 // accumulated (the caller zeroes them).  Touching pairs start at d0 = 2: their d = 0, 1 entries

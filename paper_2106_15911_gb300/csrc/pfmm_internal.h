@@ -81,6 +81,38 @@ struct Tree {
 
 int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string &err);
 
+// Sauter-Schwab class and vertex order of a triangle pair (vertex ids tx, ty): 0 when the
+// triangles share no vertex, else shared | ox[0..2] << 2, 4, 6 | oy[0..2] << 8, 10, 12 (the
+// rule's local vertex order: shared vertices first, in matching order)
+__host__ __device__ inline int ss_code(const int *tx, const int *ty)
+{
+    int shared = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) shared += tx[i] == ty[j];
+    int ox[3] = {0, 1, 2}, oy[3] = {0, 1, 2};
+    if (shared == 3) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (ty[j] == tx[i]) oy[i] = j;
+    } else if (shared == 2) {
+        int n = 0;
+        for (int i = 0; i < 3 && n < 2; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (tx[i] == ty[j]) { ox[n] = i; oy[n] = j; n++; }
+        ox[2] = 3 - ox[0] - ox[1];
+        oy[2] = 3 - oy[0] - oy[1];
+    } else if (shared == 1) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (tx[i] == ty[j]) { ox[0] = i; oy[0] = j; }
+        ox[1] = (ox[0] + 1) % 3; ox[2] = (ox[0] + 2) % 3;
+        oy[1] = (oy[0] + 1) % 3; oy[2] = (oy[0] + 2) % 3;
+    } else {
+        return 0;
+    }
+    return shared | (ox[0] << 2) | (ox[1] << 4) | (ox[2] << 6) | (oy[0] << 8) | (oy[1] << 10) | (oy[2] << 12);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Device-side descriptors.
 struct DevLevel {

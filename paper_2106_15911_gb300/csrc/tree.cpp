@@ -340,30 +340,8 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
             int Y = t.tri_leaf[y];
             if (gdist(&Lp.grid[3 * X], &Lp.grid[3 * Y]) > t.ntr_near) continue;
             const int *ty = &T[3 * t.perm[y]];
-            int shared = 0;
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j) shared += tx[i] == ty[j];
-            int ox[3] = {0, 1, 2}, oy[3] = {0, 1, 2};
-            if (shared == 3) {
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j)
-                        if (ty[j] == tx[i]) oy[i] = j;
-            } else if (shared == 2) {
-                int n = 0;
-                for (int i = 0; i < 3 && n < 2; ++i)
-                    for (int j = 0; j < 3; ++j)
-                        if (tx[i] == ty[j]) { ox[n] = i; oy[n] = j; n++; }
-                ox[2] = 3 - ox[0] - ox[1];
-                oy[2] = 3 - oy[0] - oy[1];
-            } else if (shared == 1) {
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j)
-                        if (tx[i] == ty[j]) { ox[0] = i; oy[0] = j; }
-                ox[1] = (ox[0] + 1) % 3; ox[2] = (ox[0] + 2) % 3;
-                oy[1] = (oy[0] + 1) % 3; oy[2] = (oy[0] + 2) % 3;
-            } else {
-                continue;
-            }
+            const int code = ss_code(tx, ty);
+            if (!code) continue;
             SingularPair s;
             s.x = x;
             s.y = y;
@@ -380,7 +358,7 @@ int build_tree(const pfmm_mesh &m, const pfmm_params &prm, Tree &t, std::string 
             }
             s.colV = colv;
             for (int v = 0; v < 3; ++v) s.colK[v] = t.kmap[(size_t)X * nv + ty[v]];
-            s.code = shared | (ox[0] << 2) | (ox[1] << 4) | (ox[2] << 6) | (oy[0] << 8) | (oy[1] << 10) | (oy[2] << 12);
+            s.code = code;
             t.sing.push_back(s);
         }
     }

@@ -40,6 +40,14 @@ class pfmm_params(ctypes.Structure):
                 ("fp64_native", ctypes.c_int32), ("nf_form", ctypes.c_int32)]
 
 
+class pfmm_gen_info(ctypes.Structure):
+    _fields_ = [("nlev", ctypes.c_int32), ("lx", ctypes.c_int32 * 32), ("nbox", ctypes.c_int32 * 32),
+                ("nleaf", ctypes.c_int32 * 32), ("nint", ctypes.c_int32 * 32), ("ntr_far", ctypes.c_int32 * 32),
+                ("ntr_near", ctypes.c_int32 * 32), ("st", ctypes.c_int32 * 32), ("pad", ctypes.c_double * 32),
+                ("n_m2l_pairs", ctypes.c_int64), ("n_near_blocks", ctypes.c_int64),
+                ("nearfield_entries", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
 class pfmm_info(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("lx", ctypes.c_int32 * 32), ("nbox", ctypes.c_int32 * 32),
                 ("pad", ctypes.c_double * 32), ("n_m2l_pairs", ctypes.c_int32), ("nearfield_bytes", ctypes.c_int64),
@@ -81,6 +89,13 @@ SIGNATURES = {
     "pfmm_phase_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "pfmm_nf_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "pfmm_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_info)]),
+    "pfmm_gen_create": (ctypes.c_int, [ctypes.POINTER(pfmm_mesh), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(pfmm_params), _I, _VP, ctypes.POINTER(ctypes.c_void_p)]),
+    "pfmm_gen_apply_V": (ctypes.c_int, [_VP, _DP, _DP, _I, _I, _VP]),
+    "pfmm_gen_get_info": (ctypes.c_int, [_VP, ctypes.POINTER(pfmm_gen_info)]),
+    "pfmm_gen_boxes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "pfmm_gen_destroy": (None, [_VP]),
     "pfmm_check": (ctypes.c_int, [_VP]),
     "pfmm_probe_fma_rate": (ctypes.c_int, [_I, ctypes.POINTER(ctypes.c_double), _VP]),
     "pfmm_eval_repr": (ctypes.c_int, [_VP, _DP, _DP, _DP, _I, _DP, _I, _VP]),
@@ -443,6 +458,68 @@ class Operator:
     def close(self):
         if self.h:
             pfmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GeneralOperator:
+    """V_h on general (non-uniform) time steps t_steps[0] = 0 < ... < t_steps[E_t] = T (pfmm_gen_*):
+    the FMM on the general tree of Alg. 1 with early leaves; n_max is Alg. 1's element bound."""
+
+    def __init__(self, vertices, triangles, t_steps, n_max, alpha=1.0, stream=None, **params):
+        p = pfmm_default_params()
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        self.h = None
+        ts = np.ascontiguousarray(t_steps, dtype=np.float64)
+        self.nt = int(np.asarray(triangles).shape[0])
+        self.n_steps = ts.shape[0] - 1
+        m = _mesh_struct(vertices, triangles, float(ts[-1]), self.n_steps, alpha)
+        out = ctypes.c_void_p()
+        _check(lib().pfmm_gen_create(ctypes.byref(m), ts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     ctypes.byref(p), int(n_max), _stream(stream), ctypes.byref(out)))
+        self.h = out.value
+
+    def V(self, w, parts=PFMM_PART_ALL, stream=None):
+        import torch
+
+        ww = (w if w.dim() == 3 else w.unsqueeze(0)).contiguous()
+        if ww.shape[1] != self.n_steps or ww.shape[2] != self.nt:
+            raise ValueError(f"expected [nrhs, {self.n_steps}, {self.nt}], got {tuple(w.shape)}")
+        f = torch.empty_like(ww)
+        _check(lib().pfmm_gen_apply_V(self.h, _ptr(ww), _ptr(f), int(ww.shape[0]), int(parts), _stream(stream)))
+        return f if w.dim() == 3 else f[0]
+
+    def info(self) -> dict:
+        i = pfmm_gen_info()
+        _check(lib().pfmm_gen_get_info(self.h, ctypes.byref(i)))
+        n = i.nlev
+        out = {k: list(getattr(i, k)[:n]) for k in ("lx", "nbox", "nleaf", "nint", "ntr_far", "ntr_near", "st",
+                                                     "pad")}
+        out.update(nlev=n, n_m2l_pairs=i.n_m2l_pairs, n_near_blocks=i.n_near_blocks,
+                   nearfield_entries=i.nearfield_entries, device_bytes=i.device_bytes)
+        return out
+
+    def boxes(self):
+        """[nbox][8] rows (level, cell x, y, z, interval k, leaf, first step, end step)."""
+        n = ctypes.c_int64()
+        _check(lib().pfmm_gen_boxes(self.h, None, 0, ctypes.byref(n)))
+        rows = np.zeros((max(n.value, 1), 8), np.int32)
+        _check(lib().pfmm_gen_boxes(self.h, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
+                                    ctypes.byref(n)))
+        return rows[:n.value]
+
+    def close(self):
+        if self.h:
+            lib().pfmm_gen_destroy(self.h)
             self.h = None
 
     def __del__(self):
