@@ -500,6 +500,67 @@ def _paper_scale(dev, steps=5, dense_rows=4):
             "paper": "1.5 s per GMRES iteration on 256 Salomon nodes (Tab. mpi), CPU cluster, context only"}
 
 
+def _general_steps(dev, n_a=8, Et=64, n_max=200, steps=10, oracle_rows=6):
+    """General (non-uniform) time steps (pfmm_gen_*: the tree of Alg. 1 with early leaves, no
+    Toeplitz structure): cube with n_a x n_a squares per face, Et graded steps t_j = (j / Et)^1.5 on
+    [0, 1], n_max = 200, m_t 4, m_x 6.  V_h matvec throughput (CUDA events, the stored step-pair
+    nearfield of several GB is larger than L2), the nearfield and far-field parts alone, the
+    nearfield apply's HBM roofline (8 bytes per stored entry), and parity with the oracle's pFMM on
+    the same tree: far field on every row, nearfield on `oracle_rows` sampled triangles."""
+    import torch
+
+    import oracle as O
+    from paper_2106_15911_gb300 import pfmm as P
+    from paper_2106_15911_gb300.inputs import cube_mesh, random_density
+
+    V, T = cube_mesh(n_a)
+    nt = T.shape[0]
+    ts = np.linspace(0.0, 1.0, Et + 1) ** 1.5
+    kw = dict(m_t=4, m_x=6)
+    t0 = time.perf_counter()
+    op = P.GeneralOperator(V, T, ts, n_max, **kw)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    info = op.info()
+    w = torch.tensor(random_density(Et, nt, 1, seed=2106)[0], device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = {}
+    for name, parts in (("all", P.PFMM_PART_ALL), ("near", P.PFMM_PART_NEAR), ("far", P.PFMM_PART_FAR)):
+        for _ in range(3):
+            f = op.V(w, parts=parts)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            f = op.V(w, parts=parts)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[name] = e0.elapsed_time(e1) / steps
+    f = op.V(w).cpu().numpy()
+    near = op.V(w, parts=P.PFMM_PART_NEAR).cpu().numpy()
+    peaks = _peaks(P, torch.cuda.current_stream())
+    nf_bytes = 8.0 * info["nearfield_entries"] + 16.0 * nt * Et
+    gbs = nf_bytes / (ms["near"] * 1e-3) / 1e9
+    Pr = O.make_general_problem(V, T, ts, **kw)
+    wn = w.cpu().numpy()
+    far_ref = O.gen_pfmm_apply(Pr, n_max, wn, parts=P.PFMM_PART_FAR)
+    rows = np.linspace(0, nt - 1, oracle_rows).astype(np.int32)
+    near_ref = O.gen_pfmm_apply(Pr, n_max, wn, targets=rows, parts=P.PFMM_PART_NEAR)[:, rows]
+    rel_far = float(np.max(np.abs((f - near) - far_ref)) / np.max(np.abs(far_ref)))
+    rel_near = float(np.max(np.abs(near[:, rows] - near_ref)) / np.max(np.abs(near_ref)))
+    op.close()
+    return {"workload": f"cube {n_a}x{n_a} faces ({nt} tri) x {Et} graded steps t_j = (j/{Et})^1.5, n_max {n_max}, "
+                        f"m_t 4, m_x 6, FP64", "dof": nt * Et, "build_s": build_s,
+            "ms_per_matvec": ms["all"], "dofs_per_s": nt * Et / (ms["all"] * 1e-3),
+            "ms_nearfield_only": ms["near"], "ms_farfield_only": ms["far"],
+            "tree": {k: info[k] for k in ("nlev", "lx", "nbox", "nleaf", "nint")},
+            "n_m2l_pairs": info["n_m2l_pairs"], "nearfield_entries": info["nearfield_entries"],
+            "nearfield_GB": 8e-9 * info["nearfield_entries"],
+            "roofline_nearfield": {"kernel": "k_gen_nf_apply", "bound": "hbm", "achieved": gbs,
+                                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                                   "bytes_per_launch": nf_bytes, "timing": "nearfield-only apply (permutes included)"},
+            "parity_vs_oracle": {"far_all_rows": rel_far, "near_rows": int(rows.shape[0]), "near": rel_near}}
+
+
 def _profile_case(dev, case):
     """Small cases for ncu captures: the learned preconditioner's layers (`mpnn`), its compiled
     form (`mpnn_compiled`), the on-the-fly nearfield (`otf`), the slab M2L of 8^3 grids
@@ -640,6 +701,8 @@ def main():
     ap.add_argument("--config5", action="store_true", help="run only the 50M-DOF combined workload")
     ap.add_argument("--paper-scale", action="store_true",
                     help="run only the paper's large-run parameters (m_x 12, c_st 4.1, n_tr 2) on 12288 x 1024")
+    ap.add_argument("--general", action="store_true",
+                    help="run only the general (non-uniform) time-step FMM on 768 tri x 64 graded steps")
     ap.add_argument("--config5-matvec", action="store_true",
                     help="with --config5: the build and matvecs only (no recording, training or solves)")
     ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt"], default=None,
@@ -676,6 +739,10 @@ def main():
     if args.paper_scale:
         if rank == 0:
             print(json.dumps({"paper_scale": _paper_scale(dev)}), flush=True)
+        return 0
+    if args.general:
+        if rank == 0:
+            print(json.dumps({"general_steps": _general_steps(dev)}), flush=True)
         return 0
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)

@@ -30,18 +30,19 @@ def _rel(a, b):
     return np.max(np.abs(a - b)) / np.max(np.abs(b))
 
 
-# mesh, squares per face edge, steps, n_max, parameters, stride of the sampled nearfield rows
+# mesh, squares per face edge, steps, n_max, parameters, stride of the sampled nearfield rows,
+# leaves on several levels (not with uniform steps on a uniform mesh)
 CASES = [
-    (cube_mesh, 4, _graded(32, 1.5), 60, dict(m_t=4, m_x=4), 4),
-    (cube_mesh, 4, _random_steps(24, 5), 40, dict(m_t=3, m_x=5), 4),
-    (cube_mesh, 8, _graded(16, 2.0), 200, dict(m_t=4, m_x=6), 16),
-    (cube_mesh, 4, np.linspace(0.0, 1.0, 33), 100, dict(m_t=4, m_x=4, c_st=0.25), 4),
-    (cube_sphere_mesh, 4, _graded(24, 2.5), 48, dict(m_t=4, m_x=4, c_st=0.5), 4),
+    (cube_mesh, 4, _graded(32, 1.5), 60, dict(m_t=4, m_x=4), 4, True),
+    (cube_mesh, 4, _random_steps(24, 5), 40, dict(m_t=3, m_x=5), 4, True),
+    (cube_mesh, 8, _graded(16, 2.0), 200, dict(m_t=4, m_x=6), 16, True),
+    (cube_mesh, 4, np.linspace(0.0, 1.0, 33), 100, dict(m_t=4, m_x=4, c_st=0.25), 4, False),
+    (cube_sphere_mesh, 4, _graded(24, 2.5), 48, dict(m_t=4, m_x=4, c_st=0.5), 4, True),
 ]
 
 
-@pytest.mark.parametrize("mesh,n_a,ts,n_max,kw,stride", CASES)
-def test_general_tree_matches_oracle(mesh, n_a, ts, n_max, kw, stride):
+@pytest.mark.parametrize("mesh,n_a,ts,n_max,kw,stride,early", CASES)
+def test_general_tree_matches_oracle(mesh, n_a, ts, n_max, kw, stride, early):
     V, T = mesh(n_a)
     op = P.GeneralOperator(V, T, ts, n_max, **kw)
     Pr = O.make_general_problem(V, T, ts, **kw)
@@ -57,13 +58,14 @@ def test_general_tree_matches_oracle(mesh, n_a, ts, n_max, kw, stride):
     op.close()
 
 
-@pytest.mark.parametrize("mesh,n_a,ts,n_max,kw,stride", CASES)
-def test_general_apply_matches_oracle(mesh, n_a, ts, n_max, kw, stride):
+@pytest.mark.parametrize("mesh,n_a,ts,n_max,kw,stride,early", CASES)
+def test_general_apply_matches_oracle(mesh, n_a, ts, n_max, kw, stride, early):
     V, T = mesh(n_a)
     E = len(ts) - 1
     op = P.GeneralOperator(V, T, ts, n_max, **kw)
     info = op.info()
-    assert info["nlev"] >= 3 and sum(1 for n in info["nleaf"] if n > 0) >= 2  # leaves on several levels
+    assert info["nlev"] >= 3
+    assert (sum(1 for n in info["nleaf"] if n > 0) >= 2) == early  # leaves on several levels
     Pr = O.make_general_problem(V, T, ts, **kw)
     w = random_density(E, T.shape[0], 2, seed=91)
     wt = torch.tensor(w, device=DEV)
