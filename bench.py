@@ -564,7 +564,8 @@ def _general_steps(dev, n_a=8, Et=64, n_max=200, steps=10, oracle_rows=6):
 def _profile_case(dev, case):
     """Small cases for ncu captures: the learned preconditioner's layers (`mpnn`), its compiled
     form (`mpnn_compiled`), the on-the-fly nearfield (`otf`), the slab M2L of 8^3 grids
-    (`m2l_slab`), the FP64 residue-arithmetic nearfield (`crt`, 3072 triangles x 256 steps).  3072-triangle cube; 128 steps
+    (`m2l_slab`), the FP64 residue-arithmetic nearfield (`crt`, 3072 triangles x 256 steps), the
+    general-step product (`general`, 768 triangles x 64 graded steps, as bench --general).  3072-triangle cube; 128 steps
     (network) or 32 steps (on-the-fly); 1728-triangle cube x 32 steps with an 8^3 leaf grid
     (c_st 0.1, interaction radius 7) for the slab M2L, far field only."""
     import numpy as np
@@ -590,6 +591,12 @@ def _profile_case(dev, case):
         op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_FP64)
         w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
         run = lambda: op.V(w, parts=P.PFMM_PART_NEAR)  # noqa: E731
+    elif case == "general":
+        V, T = cube_mesh(8)
+        Et = 64
+        op = P.GeneralOperator(V, T, np.linspace(0.0, 1.0, Et + 1) ** 1.5, 200, m_t=4, m_x=6)
+        w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
+        run = lambda: op.V(w)  # noqa: E731
     elif case == "m2l_slab":
         V, T = cube_mesh(12)
         Et = 32
@@ -705,7 +712,7 @@ def main():
                     help="run only the general (non-uniform) time-step FMM on 768 tri x 64 graded steps")
     ap.add_argument("--config5-matvec", action="store_true",
                     help="with --config5: the build and matvecs only (no recording, training or solves)")
-    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt"], default=None,
+    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt", "general"], default=None,
                     help="profiling only: run one small case of a kernel outside the matvec and exit")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")

@@ -505,10 +505,13 @@ int build_impl(pfmm_gen *h, const pfmm_mesh &m, const double *ts_host, cudaStrea
         lvG[l] = lv[l].G;
         lvst[l] = l ? lv[l - 1].st_next : 0;
     }
+    // multi-indices |kappa| <= m_x graded by total degree: those with |kappa| <= d are a prefix of
+    // C(d + 3, 3) entries (the M2L kernel sums over such prefixes)
     std::vector<int> kidx, kinv((size_t)m1 * m1 * m1, -1);
-    for (int a = 0; a <= mx; ++a)
-        for (int b = 0; a + b <= mx; ++b)
-            for (int c = 0; a + b + c <= mx; ++c) {
+    for (int deg = 0; deg <= mx; ++deg)
+        for (int a = deg; a >= 0; --a)
+            for (int b = deg - a; b >= 0; --b) {
+                const int c = deg - a - b;
                 kinv[((size_t)a * m1 + b) * m1 + c] = (int)kidx.size() / 3;
                 kidx.insert(kidx.end(), {a, b, c});
             }
@@ -695,6 +698,11 @@ int pfmm_gen_create(const pfmm_mesh *mesh, const double *t_steps, const pfmm_par
         p.quad_regular > 16 || p.quad_singular < 1 || p.quad_singular > 16)
         return fail(PFMM_ERR_INVALID_ARG, "invalid parameters (m_t, m_x, c_st or quadrature orders)");
     if (p.precision != PFMM_FP64) return fail(PFMM_ERR_UNSUPPORTED, "general time steps: FP64 only");
+    {
+        const int m1 = p.m_x + 1, nk = m1 * (m1 + 1) * (m1 + 2) / 6;
+        if (gen_m2l_smem(p.m_t + 1, nk, p.m_x) > 227 * 1024)
+            return fail(PFMM_ERR_UNSUPPORTED, "general time steps: (m_t + 1)^2 (m_x + 1)^2 too large for the M2L kernel");
+    }
     if (t_steps[0] != 0.0) return fail(PFMM_ERR_INVALID_ARG, "t_steps[0] must be 0");
     for (int j = 0; j < m.n_steps; ++j)
         if (!(t_steps[j + 1] > t_steps[j]) || !std::isfinite(t_steps[j + 1]))

@@ -76,6 +76,8 @@ void launch_gen_s2m(const GenDev &g, const int *leaves, int n, const double *w_i
 void launch_gen_m2m(const GenDev &g, const int *parents, int n, cudaStream_t st);
 void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
                     const double *E1, const int64_t *e1off, const double *pref, cudaStream_t st);
+// dynamic shared memory of the M2L kernel (the create call refuses parameters beyond 227 KB)
+size_t gen_m2l_smem(int na, int nk, int mx);
 void launch_gen_l2l(const GenDev &g, const int *children, int n, cudaStream_t st);
 void launch_gen_l2t(const GenDev &g, const int *leaves, int n, double *f_int, cudaStream_t st);
 

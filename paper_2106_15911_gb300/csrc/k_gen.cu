@@ -196,39 +196,61 @@ void launch_gen_permute_out(const double *f_int, double *f, const int *perm, int
     if (n > 0) k_gen_permute_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f_int, f, perm, nt, n);
 }
 
-// f_int[r][k][x] = sum over the blocks of the leaf of A[jj][y][kk][x] w_int[r][j][y] (j <= k)
-__global__ void __launch_bounds__(128) k_gen_nf_apply(const GBox *__restrict__ box, const int *__restrict__ leaves,
-                                                        const int *__restrict__ nptr, const GNear *__restrict__ blocks,
-                                                        const double *__restrict__ A, const double *__restrict__ w_int,
-                                                        double *__restrict__ f_int, int nt, int Et, int nrhs)
+// f_int[r][k][x] = sum over the blocks of the leaf of A[jj][y][kk][x] w_int[r][j][y] (entries with
+// j > k are stored as zeros).  The target elements e = kk ntx + x of the leaf go 32 at a time to the
+// lanes; the 8 warps of the CTA take every 8th source column (jj, y) of the leaf's blocks (the
+// column's 32 entries are one coalesced load) and their partial sums are added in warp order.
+constexpr int kGenNfWarps = 8;
+__global__ void __launch_bounds__(32 * kGenNfWarps) k_gen_nf_apply(const GBox *__restrict__ box,
+                                                                    const int *__restrict__ leaves,
+                                                                    const int *__restrict__ nptr,
+                                                                    const GNear *__restrict__ blocks,
+                                                                    const double *__restrict__ A,
+                                                                    const double *__restrict__ w_int,
+                                                                    double *__restrict__ f_int, int nt, int Et, int nrhs)
 {
+    __shared__ double red[kGenNfWarps][kGenRhs][32];
     const int b = leaves[blockIdx.x];
     const GBox T = box[b];
-    const int ntx = T.t1 - T.t0, nkt = T.a1 - T.a0;
+    const int ntx = T.t1 - T.t0, ne = ntx * (T.a1 - T.a0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t per_rhs = (size_t)Et * nt;
     for (int r0 = 0; r0 < nrhs; r0 += kGenRhs) {
         const int nr = min(kGenRhs, nrhs - r0);
-        for (int e = threadIdx.x; e < ntx * nkt; e += blockDim.x) {
-            const int x = e % ntx, kk = e / ntx, k = T.a0 + kk;
+        for (int e0 = 0; e0 < ne; e0 += 32) {
+            const int e = e0 + lane;
+            const bool valid = e < ne;
             double acc[kGenRhs];
 #pragma unroll
             for (int r = 0; r < kGenRhs; ++r) acc[r] = 0.0;
             for (int q = nptr[b]; q < nptr[b + 1]; ++q) {
                 const GNear B = blocks[q];
                 const GBox S = box[B.src];
-                const int nys = S.t1 - S.t0;
-                const double *Ab = A + B.off + (size_t)kk * ntx + x;
-                for (int jj = 0; jj < S.a1 - S.a0 && S.a0 + jj <= k; ++jj) {
-                    const double *wj = w_int + (size_t)r0 * per_rhs + (size_t)(S.a0 + jj) * nt + S.t0;
-                    for (int y = 0; y < nys; ++y) {
-                        const double a = Ab[((size_t)jj * nys + y) * nkt * ntx];
+                const int nys = S.t1 - S.t0, ncol = nys * (S.a1 - S.a0);
+                const double *Ab = A + B.off + (valid ? e : 0);
+                const double *w0 = w_int + (size_t)r0 * per_rhs + (size_t)S.a0 * nt + S.t0;
+#pragma unroll 4
+                for (int c = warp; c < ncol; c += kGenNfWarps) {
+                    const int jj = c / nys, y = c - jj * nys;
+                    const double a = valid ? Ab[(size_t)c * ne] : 0.0;
+                    const double *wj = w0 + (size_t)jj * nt + y;
 #pragma unroll
-                        for (int r = 0; r < kGenRhs; ++r)
-                            if (r < nr) acc[r] += a * wj[(size_t)r * per_rhs + y];
-                    }
+                    for (int r = 0; r < kGenRhs; ++r)
+                        if (r < nr) acc[r] += a * wj[(size_t)r * per_rhs];
                 }
             }
-            for (int r = 0; r < nr; ++r) f_int[(size_t)(r0 + r) * per_rhs + (size_t)k * nt + T.t0 + x] = acc[r];
+#pragma unroll
+            for (int r = 0; r < kGenRhs; ++r) red[warp][r][lane] = acc[r];
+            __syncthreads();
+            if (warp == 0 && valid) {
+                const int kk = e / ntx, x = e - kk * ntx;
+                for (int r = 0; r < nr; ++r) {
+                    double s = 0.0;
+                    for (int w = 0; w < kGenNfWarps; ++w) s += red[w][r][lane];
+                    f_int[(size_t)(r0 + r) * per_rhs + (size_t)(T.a0 + kk) * nt + T.t0 + x] = s;
+                }
+            }
+            __syncthreads();
         }
     }
 }
@@ -237,7 +259,8 @@ void launch_gen_nf_apply(const GBox *box, const int *leaves, int nleaves, const 
                          const double *A, const double *w_int, double *f_int, int nt, int Et, int nrhs,
                          cudaStream_t st)
 {
-    if (nleaves > 0) k_gen_nf_apply<<<nleaves, 128, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, nrhs);
+    if (nleaves > 0)
+        k_gen_nf_apply<<<nleaves, 32 * kGenNfWarps, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, nrhs);
 }
 
 // mu[r][b][a][kappa] = sum_j St[l][j][a] sum_x Sx[slot][x][kappa] w_int[r][j][x]  (Eq. s2m)
@@ -268,124 +291,220 @@ void launch_gen_s2m(const GenDev &g, const int *leaves, int n, const double *w_i
 }
 
 // mu(Z_p)[ap][nu] = sum_children sum_ac q^(t)_{ac,ap} (sum_{kappa <= nu} q^(x)_{kappa,nu} mu(Z_c)[ac][kappa])
-// (Eq. st_m2m; Eq. temp_m2m when the children were refined in time only: kappa = nu)
-__global__ void __launch_bounds__(128) k_gen_m2m(GenDev g, const int *__restrict__ parents)
+// (Eq. st_m2m; Eq. temp_m2m when the children were refined in time only: kappa = nu).  One CTA per
+// parent; each child's moments are staged in shared memory as dense cubes [ac][m1^3] and the
+// product of the three 1D factors is summed one direction at a time (innermost kappa2).
+constexpr int kGenPassThreads = 256;
+__global__ void __launch_bounds__(kGenPassThreads) k_gen_m2m(GenDev g, const int *__restrict__ parents)
 {
+    extern __shared__ double sm[];
+    const int na = g.na, nk = g.nk, m1 = g.mx + 1, m3 = m1 * m1 * m1;
+    double *sc = sm;  // [na][m1^3]
     const int bp = parents[blockIdx.x];
     const GBox P = g.box[bp];
-    const int m1 = g.mx + 1, lc = P.level + 1, st = g.lvst[lc];
+    const int lc = P.level + 1, st = g.lvst[lc];
     const double *q1 = g.q1 + (size_t)lc * 2 * m1 * m1;
-    for (int r = 0; r < g.nrhs; ++r)
-        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
-            const int ap = t / g.nk, iv = t % g.nk;
-            const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
-            double acc = 0.0;
-            for (int c = P.c0; c < P.c1; ++c) {
-                const GBox C = g.box[c];
-                const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
-                             *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
-                for (int ac = 0; ac < g.na; ++ac) {
+    for (int r = 0; r < g.nrhs; ++r) {
+        double acc[(kMaxNa * 455 + kGenPassThreads - 1) / kGenPassThreads];
+        const int nmine = (na * nk - (int)threadIdx.x + kGenPassThreads - 1) / kGenPassThreads;
+        for (int u = 0; u < nmine; ++u) acc[u] = 0.0;
+        for (int c = P.c0; c < P.c1; ++c) {
+            const GBox C = g.box[c];
+            __syncthreads();
+            for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
+                const int a = i / nk, ik = i - a * nk;
+                sc[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
+                    g.mu[gidx(g, r, c, 0, 0) + i];
+            }
+            __syncthreads();
+            const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
+                         *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
+            const double *qtc = g.qt + (size_t)c * na * na;
+            for (int u = 0; u < nmine; ++u) {
+                const int t = threadIdx.x + u * kGenPassThreads, ap = t / nk, iv = t - ap * nk;
+                const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
+                double sum = 0.0;
+                for (int ac = 0; ac < na; ++ac) {
+                    const double *cube = sc + ac * m3;
                     double v;
                     if (!st) {
-                        v = g.mu[gidx(g, r, c, ac, iv)];
+                        v = cube[(n0 * m1 + n1) * m1 + n2];
                     } else {
                         v = 0.0;
-                        for (int k0 = 0; k0 <= n0; ++k0)
-                            for (int k1 = 0; k1 <= n1; ++k1)
-                                for (int k2 = 0; k2 <= n2; ++k2)
-                                    v += qa[k0 * m1 + n0] * qb[k1 * m1 + n1] * qc[k2 * m1 + n2] *
-                                         g.mu[gidx(g, r, c, ac, g.kinv[(k0 * m1 + k1) * m1 + k2])];
+                        for (int k0 = 0; k0 <= n0; ++k0) {
+                            double v1 = 0.0;
+                            for (int k1 = 0; k1 <= n1; ++k1) {
+                                const double *row = cube + (k0 * m1 + k1) * m1;
+                                double v2 = 0.0;
+                                for (int k2 = 0; k2 <= n2; ++k2) v2 += qc[k2 * m1 + n2] * row[k2];
+                                v1 += qb[k1 * m1 + n1] * v2;
+                            }
+                            v += qa[k0 * m1 + n0] * v1;
+                        }
                     }
-                    acc += g.qt[((size_t)c * g.na + ac) * g.na + ap] * v;
+                    sum += qtc[ac * na + ap] * v;
                 }
+                acc[u] += sum;
             }
-            g.mu[gidx(g, r, bp, ap, iv)] = acc;
         }
+        for (int u = 0; u < nmine; ++u) g.mu[gidx(g, r, bp, 0, 0) + threadIdx.x + u * kGenPassThreads] = acc[u];
+    }
 }
+
+size_t gen_pass_smem(int na, int mx) { return sizeof(double) * (size_t)na * (mx + 1) * (mx + 1) * (mx + 1); }
 
 void launch_gen_m2m(const GenDev &g, const int *parents, int n, cudaStream_t st)
 {
-    if (n > 0) k_gen_m2m<<<n, 128, 0, st>>>(g, parents);
+    if (n <= 0) return;
+    const size_t smem = gen_pass_smem(g.na, g.mx);
+    cudaFuncSetAttribute(k_gen_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gen_m2m<<<n, kGenPassThreads, smem, st>>>(g, parents);
 }
 
 // lam(Z)[b][nu] = sum over I(Z) of sum_a pref[a][b] sum_{|kappa + nu| <= m_x} prod_d E1_d mu(Z_s)[a][kappa]
-// (Eq. m2l with Eq. exp_coeffs_3d; E1 of the pair's intervals, offsets of the cells per direction)
-__global__ void __launch_bounds__(128) k_gen_m2l(GenDev g, const int *__restrict__ targets, const int *__restrict__ mptr,
-                                                   const GPair *__restrict__ pairs, const double *__restrict__ E1,
-                                                   const int64_t *__restrict__ e1off, const double *__restrict__ pref)
+// (Eq. m2l with Eq. exp_coeffs_3d; E1 of the pair's intervals, offsets of the cells per direction).
+// One CTA per target box; per source the moments mu(Z_s) (as dense cubes [a][m1^3]) and the three
+// 1D factor slices of every (a, b) are staged in shared memory, then thread (b, nu) sums over the
+// simplex |kappa| <= m_x - |nu| one direction at a time (innermost kappa2).
+constexpr int kGenM2lThreads = 256;
+__global__ void __launch_bounds__(kGenM2lThreads) k_gen_m2l(GenDev g, const int *__restrict__ targets,
+                                                             const int *__restrict__ mptr,
+                                                             const GPair *__restrict__ pairs,
+                                                             const double *__restrict__ E1,
+                                                             const int64_t *__restrict__ e1off,
+                                                             const double *__restrict__ pref)
 {
+    extern __shared__ double sm[];
+    const int na = g.na, nk = g.nk, m1 = g.mx + 1, mm = m1 * m1, m3 = mm * m1;
+    double *smu = sm;               // [na][m1^3]
+    double *sE = smu + na * m3;     // [3][na][na][m1][m1]
     const int bt = targets[blockIdx.x];
     const GBox T = g.box[bt];
-    const int m1 = g.mx + 1, G = g.lvG[T.level], no = 2 * G - 1;
-    for (int r = 0; r < g.nrhs; ++r)
-        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
-            const int b = t / g.nk, iv = t % g.nk;
-            const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
-            double acc = 0.0;
-            for (int q = mptr[bt]; q < mptr[bt + 1]; ++q) {
-                const GPair pr = pairs[q];
-                const GBox S = g.box[pr.src];
-                const int o0 = T.cell[0] - S.cell[0] + G - 1, o1 = T.cell[1] - S.cell[1] + G - 1,
-                          o2 = T.cell[2] - S.cell[2] + G - 1;
-                for (int a = 0; a < g.na; ++a) {
-                    const double *E = E1 + e1off[pr.e] + (size_t)(a * g.na + b) * no * m1 * m1;
-                    const double *E0 = E + (size_t)o0 * m1 * m1, *Ea = E + (size_t)o1 * m1 * m1,
-                                 *Eb = E + (size_t)o2 * m1 * m1;
-                    double s = 0.0;
-                    for (int ik = 0; ik < g.nk; ++ik) {
-                        const int k0 = g.kidx[3 * ik], k1 = g.kidx[3 * ik + 1], k2 = g.kidx[3 * ik + 2];
-                        if (k0 + k1 + k2 + n0 + n1 + n2 > g.mx) continue;
-                        s += E0[k0 * m1 + n0] * Ea[k1 * m1 + n1] * Eb[k2 * m1 + n2] * g.mu[gidx(g, r, pr.src, a, ik)];
-                    }
-                    acc += pref[((size_t)pr.e * g.na + a) * g.na + b] * s;
-                }
+    const int G = g.lvG[T.level], no = 2 * G - 1;
+    for (int r = 0; r < g.nrhs; ++r) {
+        double acc[(kMaxNa * 455 + kGenM2lThreads - 1) / kGenM2lThreads];
+        const int nmine = (na * nk - (int)threadIdx.x + kGenM2lThreads - 1) / kGenM2lThreads;
+        for (int u = 0; u < nmine; ++u) acc[u] = 0.0;
+        for (int q = mptr[bt]; q < mptr[bt + 1]; ++q) {
+            const GPair pr = pairs[q];
+            const GBox S = g.box[pr.src];
+            const int o[3] = {T.cell[0] - S.cell[0] + G - 1, T.cell[1] - S.cell[1] + G - 1, T.cell[2] - S.cell[2] + G - 1};
+            __syncthreads();
+            for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
+                const int a = i / nk, ik = i - a * nk;
+                smu[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
+                    g.mu[gidx(g, r, pr.src, 0, 0) + i];
             }
-            g.lam[gidx(g, r, bt, b, iv)] = acc;
+            const double *Ep = E1 + e1off[pr.e];
+            for (int i = threadIdx.x; i < 3 * na * na * mm; i += blockDim.x) {
+                const int kv = i % mm, ab = (i / mm) % (na * na), d = i / (mm * na * na);
+                sE[i] = Ep[((size_t)ab * no + o[d]) * mm + kv];
+            }
+            __syncthreads();
+            const double *pf = pref + (size_t)pr.e * na * na;
+            for (int u = 0; u < nmine; ++u) {
+                const int t = threadIdx.x + u * kGenM2lThreads, b = t / nk, iv = t - b * nk;
+                const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
+                const int dd = g.mx - (n0 + n1 + n2);
+                double sum = 0.0;
+                for (int a = 0; a < na; ++a) {
+                    const double *E0 = sE + (size_t)(a * na + b) * mm, *Ea = E0 + (size_t)na * na * mm,
+                                 *Eb = Ea + (size_t)na * na * mm;
+                    const double *cube = smu + a * m3;
+                    double v0 = 0.0;
+                    for (int k0 = 0; k0 <= dd; ++k0) {
+                        double v1 = 0.0;
+                        for (int k1 = 0; k1 <= dd - k0; ++k1) {
+                            const double *row = cube + (k0 * m1 + k1) * m1;
+                            double v2 = 0.0;
+                            for (int k2 = 0; k2 <= dd - k0 - k1; ++k2) v2 += Eb[k2 * m1 + n2] * row[k2];
+                            v1 += Ea[k1 * m1 + n1] * v2;
+                        }
+                        v0 += E0[k0 * m1 + n0] * v1;
+                    }
+                    sum += pf[a * na + b] * v0;
+                }
+                acc[u] += sum;
+            }
         }
+        for (int u = 0; u < nmine; ++u) g.lam[gidx(g, r, bt, 0, 0) + threadIdx.x + u * kGenM2lThreads] = acc[u];
+    }
+}
+
+size_t gen_m2l_smem(int na, int nk, int mx)
+{
+    (void)nk;
+    const size_t m1 = mx + 1;
+    return sizeof(double) * ((size_t)na * m1 * m1 * m1 + 3 * (size_t)na * na * m1 * m1);
 }
 
 void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
                     const double *E1, const int64_t *e1off, const double *pref, cudaStream_t st)
 {
-    if (n > 0) k_gen_m2l<<<n, 128, 0, st>>>(g, targets, mptr, pairs, E1, e1off, pref);
+    if (n <= 0) return;
+    const size_t smem = gen_m2l_smem(g.na, g.nk, g.mx);
+    cudaFuncSetAttribute(k_gen_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gen_m2l<<<n, kGenM2lThreads, smem, st>>>(g, targets, mptr, pairs, E1, e1off, pref);
 }
 
 // lam(Z_c)[bc][kappa] += sum_bp q^(t)_{bc,bp} sum_{nu >= kappa, |nu| <= m_x} q^(x)_{kappa,nu} lam(Z_p)[bp][nu]
-// (the transposes of Eq. temp_m2m / st_m2m)
-__global__ void __launch_bounds__(128) k_gen_l2l(GenDev g, const int *__restrict__ children)
+// (the transposes of Eq. temp_m2m / st_m2m).  One CTA per child; the parent's local contributions
+// are staged as dense cubes and summed one direction at a time.
+__global__ void __launch_bounds__(kGenPassThreads) k_gen_l2l(GenDev g, const int *__restrict__ children)
 {
+    extern __shared__ double sm[];
+    const int na = g.na, nk = g.nk, m1 = g.mx + 1, m3 = m1 * m1 * m1;
+    double *sp = sm;  // [na][m1^3]
     const int bc = children[blockIdx.x];
     const GBox C = g.box[bc];
-    const int m1 = g.mx + 1, st = g.lvst[C.level], bp = C.par;
+    const int st = g.lvst[C.level], bp = C.par;
     const double *q1 = g.q1 + (size_t)C.level * 2 * m1 * m1;
     const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
                  *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
-    for (int r = 0; r < g.nrhs; ++r)
-        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
-            const int bcI = t / g.nk, ik = t % g.nk;
+    const double *qtc = g.qt + (size_t)bc * na * na;
+    for (int r = 0; r < g.nrhs; ++r) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
+            const int a = i / nk, ik = i - a * nk;
+            sp[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
+                g.lam[gidx(g, r, bp, 0, 0) + i];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < na * nk; t += blockDim.x) {
+            const int bcI = t / nk, ik = t - bcI * nk;
             const int k0 = g.kidx[3 * ik], k1 = g.kidx[3 * ik + 1], k2 = g.kidx[3 * ik + 2];
             double acc = 0.0;
-            for (int bpI = 0; bpI < g.na; ++bpI) {
+            for (int bpI = 0; bpI < na; ++bpI) {
+                const double *cube = sp + bpI * m3;
                 double v;
                 if (!st) {
-                    v = g.lam[gidx(g, r, bp, bpI, ik)];
+                    v = cube[(k0 * m1 + k1) * m1 + k2];
                 } else {
                     v = 0.0;
-                    for (int n0 = k0; n0 <= g.mx; ++n0)
-                        for (int n1 = k1; n0 + n1 <= g.mx; ++n1)
-                            for (int n2 = k2; n0 + n1 + n2 <= g.mx; ++n2)
-                                v += qa[k0 * m1 + n0] * qb[k1 * m1 + n1] * qc[k2 * m1 + n2] *
-                                     g.lam[gidx(g, r, bp, bpI, g.kinv[(n0 * m1 + n1) * m1 + n2])];
+                    for (int n0 = k0; n0 <= g.mx; ++n0) {
+                        double v1 = 0.0;
+                        for (int n1 = k1; n0 + n1 <= g.mx; ++n1) {
+                            const double *row = cube + (n0 * m1 + n1) * m1;
+                            double v2 = 0.0;
+                            for (int n2 = k2; n0 + n1 + n2 <= g.mx; ++n2) v2 += qc[k2 * m1 + n2] * row[n2];
+                            v1 += qb[k1 * m1 + n1] * v2;
+                        }
+                        v += qa[k0 * m1 + n0] * v1;
+                    }
                 }
-                acc += g.qt[((size_t)bc * g.na + bcI) * g.na + bpI] * v;
+                acc += qtc[bcI * na + bpI] * v;
             }
             g.lam[gidx(g, r, bc, bcI, ik)] += acc;
         }
+    }
 }
 
 void launch_gen_l2l(const GenDev &g, const int *children, int n, cudaStream_t st)
 {
-    if (n > 0) k_gen_l2l<<<n, 128, 0, st>>>(g, children);
+    if (n <= 0) return;
+    const size_t smem = gen_pass_smem(g.na, g.mx);
+    cudaFuncSetAttribute(k_gen_l2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gen_l2l<<<n, kGenPassThreads, smem, st>>>(g, children);
 }
 
 // f_int[r][k][x] += sum_b St[l][k][b] sum_nu lam(Z)[b][nu] Sx[slot][x][nu]  (Eq. l2t)
