@@ -122,7 +122,7 @@ struct pfmm_gen {
     double *d_A = nullptr;
     std::vector<int *> d_parents_lv, d_all_lv;
     int ws_nrhs = 0;
-    double *d_wint = nullptr, *d_fint = nullptr, *d_mu = nullptr, *d_lam = nullptr;
+    double *d_wint = nullptr, *d_fint = nullptr, *d_mu = nullptr, *d_lam = nullptr, *d_contrib = nullptr;
 
     ~pfmm_gen()
     {
@@ -674,7 +674,7 @@ int ensure_ws(pfmm_gen *h, int nrhs)
     int rc;
     const size_t n = (size_t)nrhs * h->Et * h->nt, nm = (size_t)nrhs * h->nbox * h->na * h->nk;
     if ((rc = h->alloc(&h->d_wint, n)) || (rc = h->alloc(&h->d_fint, n)) || (rc = h->alloc(&h->d_mu, nm)) ||
-        (rc = h->alloc(&h->d_lam, nm)))
+        (rc = h->alloc(&h->d_lam, nm)) || (rc = h->alloc(&h->d_contrib, nm)))
         return rc;
     h->ws_nrhs = nrhs;
     return PFMM_OK;
@@ -772,7 +772,9 @@ int pfmm_gen_apply_V(pfmm_gen *h, const double *w, double *f, int32_t nrhs, int3
         g.mu = h->d_mu;
         g.lam = h->d_lam;
         launch_gen_s2m(g, h->d_leaves_far, (int)h->leaves_far.size(), h->d_wint, st);
-        for (int l = h->nlev - 2; l >= 2; --l) launch_gen_m2m(g, h->d_parents_lv[l], (int)h->parents_lv[l].size(), st);
+        for (int l = h->nlev - 2; l >= 2; --l)
+            launch_gen_m2m(g, h->d_parents_lv[l], (int)h->parents_lv[l].size(), h->d_all_lv[l + 1],
+                           (int)h->all_lv[l + 1].size(), h->d_contrib, st);
         if (cudaMemsetAsync(h->d_lam, 0, sizeof(double) * (size_t)nrhs * h->nbox * h->na * h->nk, st) != cudaSuccess)
             return fail(PFMM_ERR_CUDA, "cudaMemsetAsync failed");
         launch_gen_m2l(g, h->d_m2l_targets, (int)h->m2l_targets.size(), h->d_mptr, h->d_pairs, h->d_E1, h->d_e1off,

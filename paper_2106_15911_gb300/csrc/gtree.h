@@ -73,7 +73,10 @@ void launch_gen_nf_apply(const GBox *box, const int *leaves, int nleaves, const 
                          const double *A, const double *w_int, double *f_int, int nt, int Et, int nrhs,
                          cudaStream_t st);
 void launch_gen_s2m(const GenDev &g, const int *leaves, int n, const double *w_int, cudaStream_t st);
-void launch_gen_m2m(const GenDev &g, const int *parents, int n, cudaStream_t st);
+// M2M of the parents of one level: the children (all boxes of the next level) write their
+// contributions into contrib ([nrhs][boxes][na][nk]), the parents add them in child order
+void launch_gen_m2m(const GenDev &g, const int *parents, int n, const int *children, int nc, double *contrib,
+                    cudaStream_t st);
 void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
                     const double *E1, const int64_t *e1off, const double *pref, cudaStream_t st);
 // dynamic shared memory of the M2L kernel (the create call refuses parameters beyond 227 KB)

@@ -14,6 +14,7 @@
 //   L2T                Eq. l2t at every leaf of a level >= 2.
 // Every kernel is a plain grid over the boxes of one phase; phases that depend on coarser or finer
 // levels are launched level by level.
+#include "df64.cuh"
 #include "device_math.cuh"
 #include "gtree.h"
 #include "nf_geom.cuh"
@@ -201,57 +202,59 @@ void launch_gen_permute_out(const double *f_int, double *f, const int *perm, int
 // lanes; the 8 warps of the CTA take every 8th source column (jj, y) of the leaf's blocks (the
 // column's 32 entries are one coalesced load) and their partial sums are added in warp order.
 constexpr int kGenNfWarps = 8;
+template <int R>
 __global__ void __launch_bounds__(32 * kGenNfWarps) k_gen_nf_apply(const GBox *__restrict__ box,
                                                                     const int *__restrict__ leaves,
                                                                     const int *__restrict__ nptr,
                                                                     const GNear *__restrict__ blocks,
                                                                     const double *__restrict__ A,
                                                                     const double *__restrict__ w_int,
-                                                                    double *__restrict__ f_int, int nt, int Et, int nrhs)
+                                                                    double *__restrict__ f_int, int nt, int Et, int r0)
 {
-    __shared__ double red[kGenNfWarps][kGenRhs][32];
+    __shared__ double red[kGenNfWarps][R][32];
     const int b = leaves[blockIdx.x];
     const GBox T = box[b];
     const int ntx = T.t1 - T.t0, ne = ntx * (T.a1 - T.a0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t per_rhs = (size_t)Et * nt;
-    for (int r0 = 0; r0 < nrhs; r0 += kGenRhs) {
-        const int nr = min(kGenRhs, nrhs - r0);
-        for (int e0 = 0; e0 < ne; e0 += 32) {
-            const int e = e0 + lane;
-            const bool valid = e < ne;
-            double acc[kGenRhs];
+    for (int e0 = 0; e0 < ne; e0 += 32) {
+        const int e = e0 + lane;
+        const bool valid = e < ne;
+        double acc[R];
 #pragma unroll
-            for (int r = 0; r < kGenRhs; ++r) acc[r] = 0.0;
-            for (int q = nptr[b]; q < nptr[b + 1]; ++q) {
-                const GNear B = blocks[q];
-                const GBox S = box[B.src];
-                const int nys = S.t1 - S.t0, ncol = nys * (S.a1 - S.a0);
-                const double *Ab = A + B.off + (valid ? e : 0);
-                const double *w0 = w_int + (size_t)r0 * per_rhs + (size_t)S.a0 * nt + S.t0;
+        for (int r = 0; r < R; ++r) acc[r] = 0.0;
+        for (int q = nptr[b]; q < nptr[b + 1]; ++q) {
+            const GNear B = blocks[q];
+            const GBox S = box[B.src];
+            const int nys = S.t1 - S.t0, ncol = nys * (S.a1 - S.a0);
+            const double *Ab = A + B.off + (valid ? e : 0);
+            const double *w0 = w_int + (size_t)r0 * per_rhs + (size_t)S.a0 * nt + S.t0;
+            int jj = warp / nys, y = warp - jj * nys;  // column c = jj nys + y, advanced by kGenNfWarps
 #pragma unroll 4
-                for (int c = warp; c < ncol; c += kGenNfWarps) {
-                    const int jj = c / nys, y = c - jj * nys;
-                    const double a = valid ? Ab[(size_t)c * ne] : 0.0;
-                    const double *wj = w0 + (size_t)jj * nt + y;
+            for (int c = warp; c < ncol; c += kGenNfWarps) {
+                const double a = valid ? Ab[(size_t)c * ne] : 0.0;
+                const double *wj = w0 + (size_t)jj * nt + y;
 #pragma unroll
-                    for (int r = 0; r < kGenRhs; ++r)
-                        if (r < nr) acc[r] += a * wj[(size_t)r * per_rhs];
+                for (int r = 0; r < R; ++r) acc[r] = fma(a, wj[(size_t)r * per_rhs], acc[r]);
+                y += kGenNfWarps;
+                while (y >= nys) {
+                    y -= nys;
+                    ++jj;
                 }
             }
-#pragma unroll
-            for (int r = 0; r < kGenRhs; ++r) red[warp][r][lane] = acc[r];
-            __syncthreads();
-            if (warp == 0 && valid) {
-                const int kk = e / ntx, x = e - kk * ntx;
-                for (int r = 0; r < nr; ++r) {
-                    double s = 0.0;
-                    for (int w = 0; w < kGenNfWarps; ++w) s += red[w][r][lane];
-                    f_int[(size_t)(r0 + r) * per_rhs + (size_t)(T.a0 + kk) * nt + T.t0 + x] = s;
-                }
-            }
-            __syncthreads();
         }
+#pragma unroll
+        for (int r = 0; r < R; ++r) red[warp][r][lane] = acc[r];
+        __syncthreads();
+        if (warp == 0 && valid) {
+            const int kk = e / ntx, x = e - kk * ntx;
+            for (int r = 0; r < R; ++r) {
+                double s = 0.0;
+                for (int w = 0; w < kGenNfWarps; ++w) s += red[w][r][lane];
+                f_int[(size_t)(r0 + r) * per_rhs + (size_t)(T.a0 + kk) * nt + T.t0 + x] = s;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -259,8 +262,21 @@ void launch_gen_nf_apply(const GBox *box, const int *leaves, int nleaves, const 
                          const double *A, const double *w_int, double *f_int, int nt, int Et, int nrhs,
                          cudaStream_t st)
 {
-    if (nleaves > 0)
-        k_gen_nf_apply<<<nleaves, 32 * kGenNfWarps, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, nrhs);
+    if (nleaves <= 0) return;
+    const dim3 grid(nleaves), blk(32 * kGenNfWarps);
+    for (int r0 = 0; r0 < nrhs;) {
+        const int n = nrhs - r0;
+        if (n >= 4) {
+            k_gen_nf_apply<4><<<grid, blk, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, r0);
+            r0 += 4;
+        } else if (n >= 2) {
+            k_gen_nf_apply<2><<<grid, blk, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, r0);
+            r0 += 2;
+        } else {
+            k_gen_nf_apply<1><<<grid, blk, 0, st>>>(box, leaves, nptr, blocks, A, w_int, f_int, nt, Et, r0);
+            r0 += 1;
+        }
+    }
 }
 
 // mu[r][b][a][kappa] = sum_j St[l][j][a] sum_x Sx[slot][x][kappa] w_int[r][j][x]  (Eq. s2m)
@@ -290,83 +306,95 @@ void launch_gen_s2m(const GenDev &g, const int *leaves, int n, const double *w_i
     if (n > 0) k_gen_s2m<<<n, 128, 0, st>>>(g, leaves, w_int);
 }
 
-// mu(Z_p)[ap][nu] = sum_children sum_ac q^(t)_{ac,ap} (sum_{kappa <= nu} q^(x)_{kappa,nu} mu(Z_c)[ac][kappa])
-// (Eq. st_m2m; Eq. temp_m2m when the children were refined in time only: kappa = nu).  One CTA per
-// parent; each child's moments are staged in shared memory as dense cubes [ac][m1^3] and the
-// product of the three 1D factors is summed one direction at a time (innermost kappa2).
+// M2M in two launches per level, deterministic: each child Z_c writes its contribution
+//   contrib(Z_c)[ap][nu] = sum_ac q^(t)_{ac,ap} (sum_{kappa <= nu} q^(x)_{kappa,nu} mu(Z_c)[ac][kappa])
+// (Eq. st_m2m; Eq. temp_m2m when refined in time only: kappa = nu), one CTA per child with its moments
+// staged as dense cubes [ac][m1^3] and the 1D factors applied one direction at a time; then every
+// parent adds its children's contributions in child order.
 constexpr int kGenPassThreads = 256;
-__global__ void __launch_bounds__(kGenPassThreads) k_gen_m2m(GenDev g, const int *__restrict__ parents)
+__global__ void __launch_bounds__(kGenPassThreads) k_gen_m2m_child(GenDev g, const int *__restrict__ children,
+                                                                    double *__restrict__ contrib)
 {
     extern __shared__ double sm[];
     const int na = g.na, nk = g.nk, m1 = g.mx + 1, m3 = m1 * m1 * m1;
     double *sc = sm;  // [na][m1^3]
+    const int c = children[blockIdx.x];
+    const GBox C = g.box[c];
+    const int st = g.lvst[C.level];
+    const double *q1 = g.q1 + (size_t)C.level * 2 * m1 * m1;
+    const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
+                 *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
+    const double *qtc = g.qt + (size_t)c * na * na;
+    for (int r = 0; r < g.nrhs; ++r) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
+            const int a = i / nk, ik = i - a * nk;
+            sc[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
+                g.mu[gidx(g, r, c, 0, 0) + i];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < na * nk; t += blockDim.x) {
+            const int ap = t / nk, iv = t - ap * nk;
+            const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
+            double sum = 0.0;
+            for (int ac = 0; ac < na; ++ac) {
+                const double *cube = sc + ac * m3;
+                double v;
+                if (!st) {
+                    v = cube[(n0 * m1 + n1) * m1 + n2];
+                } else {
+                    v = 0.0;
+                    for (int k0 = 0; k0 <= n0; ++k0) {
+                        double v1 = 0.0;
+                        for (int k1 = 0; k1 <= n1; ++k1) {
+                            const double *row = cube + (k0 * m1 + k1) * m1;
+                            double v2 = 0.0;
+                            for (int k2 = 0; k2 <= n2; ++k2) v2 += qc[k2 * m1 + n2] * row[k2];
+                            v1 += qb[k1 * m1 + n1] * v2;
+                        }
+                        v += qa[k0 * m1 + n0] * v1;
+                    }
+                }
+                sum += qtc[ac * na + ap] * v;
+            }
+            contrib[gidx(g, r, c, 0, 0) + t] = sum;
+        }
+    }
+}
+
+__global__ void k_gen_m2m_sum(GenDev g, const int *__restrict__ parents, const double *__restrict__ contrib)
+{
     const int bp = parents[blockIdx.x];
     const GBox P = g.box[bp];
-    const int lc = P.level + 1, st = g.lvst[lc];
-    const double *q1 = g.q1 + (size_t)lc * 2 * m1 * m1;
-    for (int r = 0; r < g.nrhs; ++r) {
-        double acc[(kMaxNa * 455 + kGenPassThreads - 1) / kGenPassThreads];
-        const int nmine = (na * nk - (int)threadIdx.x + kGenPassThreads - 1) / kGenPassThreads;
-        for (int u = 0; u < nmine; ++u) acc[u] = 0.0;
-        for (int c = P.c0; c < P.c1; ++c) {
-            const GBox C = g.box[c];
-            __syncthreads();
-            for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
-                const int a = i / nk, ik = i - a * nk;
-                sc[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
-                    g.mu[gidx(g, r, c, 0, 0) + i];
-            }
-            __syncthreads();
-            const double *qa = q1 + (size_t)(C.bits & 1) * m1 * m1, *qb = q1 + (size_t)((C.bits >> 1) & 1) * m1 * m1,
-                         *qc = q1 + (size_t)((C.bits >> 2) & 1) * m1 * m1;
-            const double *qtc = g.qt + (size_t)c * na * na;
-            for (int u = 0; u < nmine; ++u) {
-                const int t = threadIdx.x + u * kGenPassThreads, ap = t / nk, iv = t - ap * nk;
-                const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
-                double sum = 0.0;
-                for (int ac = 0; ac < na; ++ac) {
-                    const double *cube = sc + ac * m3;
-                    double v;
-                    if (!st) {
-                        v = cube[(n0 * m1 + n1) * m1 + n2];
-                    } else {
-                        v = 0.0;
-                        for (int k0 = 0; k0 <= n0; ++k0) {
-                            double v1 = 0.0;
-                            for (int k1 = 0; k1 <= n1; ++k1) {
-                                const double *row = cube + (k0 * m1 + k1) * m1;
-                                double v2 = 0.0;
-                                for (int k2 = 0; k2 <= n2; ++k2) v2 += qc[k2 * m1 + n2] * row[k2];
-                                v1 += qb[k1 * m1 + n1] * v2;
-                            }
-                            v += qa[k0 * m1 + n0] * v1;
-                        }
-                    }
-                    sum += qtc[ac * na + ap] * v;
-                }
-                acc[u] += sum;
-            }
+    for (int r = 0; r < g.nrhs; ++r)
+        for (int t = threadIdx.x; t < g.na * g.nk; t += blockDim.x) {
+            double s = 0.0;
+            for (int c = P.c0; c < P.c1; ++c) s += contrib[gidx(g, r, c, 0, 0) + t];
+            g.mu[gidx(g, r, bp, 0, 0) + t] = s;
         }
-        for (int u = 0; u < nmine; ++u) g.mu[gidx(g, r, bp, 0, 0) + threadIdx.x + u * kGenPassThreads] = acc[u];
-    }
 }
 
 size_t gen_pass_smem(int na, int mx) { return sizeof(double) * (size_t)na * (mx + 1) * (mx + 1) * (mx + 1); }
 
-void launch_gen_m2m(const GenDev &g, const int *parents, int n, cudaStream_t st)
+void launch_gen_m2m(const GenDev &g, const int *parents, int n, const int *children, int nc, double *contrib,
+                    cudaStream_t st)
 {
-    if (n <= 0) return;
+    if (n <= 0 || nc <= 0) return;
     const size_t smem = gen_pass_smem(g.na, g.mx);
-    cudaFuncSetAttribute(k_gen_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gen_m2m<<<n, kGenPassThreads, smem, st>>>(g, parents);
+    cudaFuncSetAttribute(k_gen_m2m_child, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_gen_m2m_child<<<nc, kGenPassThreads, smem, st>>>(g, children, contrib);
+    k_gen_m2m_sum<<<n, 128, 0, st>>>(g, parents, contrib);
 }
 
 // lam(Z)[b][nu] = sum over I(Z) of sum_a pref[a][b] sum_{|kappa + nu| <= m_x} prod_d E1_d mu(Z_s)[a][kappa]
 // (Eq. m2l with Eq. exp_coeffs_3d; E1 of the pair's intervals, offsets of the cells per direction).
-// One CTA per target box; per source the moments mu(Z_s) (as dense cubes [a][m1^3]) and the three
-// 1D factor slices of every (a, b) are staged in shared memory, then thread (b, nu) sums over the
-// simplex |kappa| <= m_x - |nu| one direction at a time (innermost kappa2).
+// One CTA per target box; per source the moments mu(Z_s) (dense cubes [a][m1^3]) and the three 1D
+// factor slices of every (a, b) are staged in shared memory in double-FP32 (pairs of floats, about
+// 48 significant bits: the FP32 pipe issues such operations several times faster than GB300's
+// FP64 pipe), and item (b, nu) sums over the simplex |kappa| <= m_x - |nu| one direction at a time.
+// Items are ordered by |nu| so the lanes of a warp run loops of equal length.
 constexpr int kGenM2lThreads = 256;
+constexpr int kGenM2lItems = (kMaxNa * 455 + kGenM2lThreads - 1) / kGenM2lThreads;
 __global__ void __launch_bounds__(kGenM2lThreads) k_gen_m2l(GenDev g, const int *__restrict__ targets,
                                                              const int *__restrict__ mptr,
                                                              const GPair *__restrict__ pairs,
@@ -374,17 +402,32 @@ __global__ void __launch_bounds__(kGenM2lThreads) k_gen_m2l(GenDev g, const int 
                                                              const int64_t *__restrict__ e1off,
                                                              const double *__restrict__ pref)
 {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const int na = g.na, nk = g.nk, m1 = g.mx + 1, mm = m1 * m1, m3 = mm * m1;
-    double *smu = sm;               // [na][m1^3]
-    double *sE = smu + na * m3;     // [3][na][na][m1][m1]
+    df64 *smu = (df64 *)smraw;      // [na][m1^3]
+    df64 *sE = smu + na * m3;       // [3][na][na][m1][m1]
     const int bt = targets[blockIdx.x];
     const GBox T = g.box[bt];
     const int G = g.lvG[T.level], no = 2 * G - 1;
+    // this thread's items: t -> (degree s, b, nu of degree s), degree-major
+    int item_b[kGenM2lItems], item_iv[kGenM2lItems];
+    const int nmine = (na * nk - (int)threadIdx.x + kGenM2lThreads - 1) / kGenM2lThreads;
+    for (int u = 0; u < nmine; ++u) {
+        int t = threadIdx.x + u * kGenM2lThreads, sdeg = 0;
+        while (true) {
+            const int grp = (sdeg + 1) * (sdeg + 2) / 2;  // multi-indices of degree sdeg
+            if (t < na * grp) {
+                item_b[u] = t / grp;
+                item_iv[u] = sdeg * (sdeg + 1) * (sdeg + 2) / 6 + t % grp;  // degree-graded index
+                break;
+            }
+            t -= na * grp;
+            ++sdeg;
+        }
+    }
     for (int r = 0; r < g.nrhs; ++r) {
-        double acc[(kMaxNa * 455 + kGenM2lThreads - 1) / kGenM2lThreads];
-        const int nmine = (na * nk - (int)threadIdx.x + kGenM2lThreads - 1) / kGenM2lThreads;
-        for (int u = 0; u < nmine; ++u) acc[u] = 0.0;
+        df64 acc[kGenM2lItems];
+        for (int u = 0; u < nmine; ++u) acc[u] = df64(0);
         for (int q = mptr[bt]; q < mptr[bt + 1]; ++q) {
             const GPair pr = pairs[q];
             const GBox S = g.box[pr.src];
@@ -393,41 +436,39 @@ __global__ void __launch_bounds__(kGenM2lThreads) k_gen_m2l(GenDev g, const int 
             for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
                 const int a = i / nk, ik = i - a * nk;
                 smu[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
-                    g.mu[gidx(g, r, pr.src, 0, 0) + i];
+                    df64(g.mu[gidx(g, r, pr.src, 0, 0) + i]);
             }
             const double *Ep = E1 + e1off[pr.e];
             for (int i = threadIdx.x; i < 3 * na * na * mm; i += blockDim.x) {
                 const int kv = i % mm, ab = (i / mm) % (na * na), d = i / (mm * na * na);
-                sE[i] = Ep[((size_t)ab * no + o[d]) * mm + kv];
+                sE[i] = df64(Ep[((size_t)ab * no + o[d]) * mm + kv]);
             }
             __syncthreads();
             const double *pf = pref + (size_t)pr.e * na * na;
             for (int u = 0; u < nmine; ++u) {
-                const int t = threadIdx.x + u * kGenM2lThreads, b = t / nk, iv = t - b * nk;
+                const int b = item_b[u], iv = item_iv[u];
                 const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
                 const int dd = g.mx - (n0 + n1 + n2);
-                double sum = 0.0;
                 for (int a = 0; a < na; ++a) {
-                    const double *E0 = sE + (size_t)(a * na + b) * mm, *Ea = E0 + (size_t)na * na * mm,
-                                 *Eb = Ea + (size_t)na * na * mm;
-                    const double *cube = smu + a * m3;
-                    double v0 = 0.0;
+                    const df64 *E0 = sE + (size_t)(a * na + b) * mm, *Ea = E0 + (size_t)na * na * mm,
+                               *Eb = Ea + (size_t)na * na * mm;
+                    const df64 *cube = smu + a * m3;
+                    df64 v0(0);
                     for (int k0 = 0; k0 <= dd; ++k0) {
-                        double v1 = 0.0;
+                        df64 v1(0);
                         for (int k1 = 0; k1 <= dd - k0; ++k1) {
-                            const double *row = cube + (k0 * m1 + k1) * m1;
-                            double v2 = 0.0;
-                            for (int k2 = 0; k2 <= dd - k0 - k1; ++k2) v2 += Eb[k2 * m1 + n2] * row[k2];
-                            v1 += Ea[k1 * m1 + n1] * v2;
+                            const df64 *row = cube + (k0 * m1 + k1) * m1;
+                            df64 v2(0);
+                            for (int k2 = 0; k2 <= dd - k0 - k1; ++k2) mac(v2, Eb[k2 * m1 + n2], row[k2]);
+                            mac(v1, Ea[k1 * m1 + n1], v2);
                         }
-                        v0 += E0[k0 * m1 + n0] * v1;
+                        mac(v0, E0[k0 * m1 + n0], v1);
                     }
-                    sum += pf[a * na + b] * v0;
+                    mac(acc[u], df64(pf[a * na + b]), v0);
                 }
-                acc[u] += sum;
             }
         }
-        for (int u = 0; u < nmine; ++u) g.lam[gidx(g, r, bt, 0, 0) + threadIdx.x + u * kGenM2lThreads] = acc[u];
+        for (int u = 0; u < nmine; ++u) g.lam[gidx(g, r, bt, item_b[u], item_iv[u])] = as_double(acc[u]);
     }
 }
 
@@ -435,7 +476,7 @@ size_t gen_m2l_smem(int na, int nk, int mx)
 {
     (void)nk;
     const size_t m1 = mx + 1;
-    return sizeof(double) * ((size_t)na * m1 * m1 * m1 + 3 * (size_t)na * na * m1 * m1);
+    return sizeof(df64) * ((size_t)na * m1 * m1 * m1 + 3 * (size_t)na * na * m1 * m1);
 }
 
 void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
