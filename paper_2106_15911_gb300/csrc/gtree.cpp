@@ -116,6 +116,7 @@ struct pfmm_gen {
     int *d_leaves_all = nullptr, *d_leaves_far = nullptr, *d_m2l_targets = nullptr, *d_mptr = nullptr;
     GPair *d_pairs = nullptr;
     double *d_E1 = nullptr, *d_pref = nullptr;
+    void *d_E1df = nullptr, *d_prefdf = nullptr;  // double-FP32 copies for the M2L kernel
     int64_t *d_e1off = nullptr;
     int *d_nptr = nullptr;
     GNear *d_blocks = nullptr;
@@ -642,6 +643,14 @@ int build_impl(pfmm_gen *h, const pfmm_mesh &m, const double *ts_host, cudaStrea
                           h->d_E1 + e1off[e0], h->d_pref + (size_t)e0 * na * na, st);
             e0 = e1;
         }
+        double *e1df = nullptr, *prefdf = nullptr;  // 8 bytes per value either way
+        if ((rc = h->alloc(&e1df, (size_t)std::max<int64_t>(e1off[npairs], 1))) ||
+            (rc = h->alloc(&prefdf, (size_t)std::max(npairs, 1) * na * na)))
+            return rc;
+        launch_gen_to_df64(h->d_E1, e1df, e1off[npairs], st);
+        launch_gen_to_df64(h->d_pref, prefdf, (int64_t)npairs * na * na, st);
+        h->d_E1df = e1df;
+        h->d_prefdf = prefdf;
     }
     // ---- the nearfield entries (Eq. eval_sl_nf_block with the entries of Section 2)
     {
@@ -777,8 +786,10 @@ int pfmm_gen_apply_V(pfmm_gen *h, const double *w, double *f, int32_t nrhs, int3
                            (int)h->all_lv[l + 1].size(), h->d_contrib, st);
         if (cudaMemsetAsync(h->d_lam, 0, sizeof(double) * (size_t)nrhs * h->nbox * h->na * h->nk, st) != cudaSuccess)
             return fail(PFMM_ERR_CUDA, "cudaMemsetAsync failed");
-        launch_gen_m2l(g, h->d_m2l_targets, (int)h->m2l_targets.size(), h->d_mptr, h->d_pairs, h->d_E1, h->d_e1off,
-                       h->d_pref, st);
+        // the moments as double-FP32 pairs (into the M2M contribution buffer, free by now)
+        launch_gen_to_df64(h->d_mu, h->d_contrib, (int64_t)nrhs * h->nbox * h->na * h->nk, st);
+        launch_gen_m2l(g, h->d_m2l_targets, (int)h->m2l_targets.size(), h->d_mptr, h->d_pairs, h->d_E1df, h->d_e1off,
+                       h->d_prefdf, h->d_contrib, st);
         for (int l = 3; l < h->nlev; ++l) launch_gen_l2l(g, h->d_all_lv[l], (int)h->all_lv[l].size(), st);
         launch_gen_l2t(g, h->d_leaves_far, (int)h->leaves_far.size(), h->d_fint, st);
     }

@@ -77,8 +77,12 @@ void launch_gen_s2m(const GenDev &g, const int *leaves, int n, const double *w_i
 // contributions into contrib ([nrhs][boxes][na][nk]), the parents add them in child order
 void launch_gen_m2m(const GenDev &g, const int *parents, int n, const int *children, int nc, double *contrib,
                     cudaStream_t st);
+// M2L of all target boxes in double-FP32: Edf, prefdf, mudf are double-FP32 copies (pairs of
+// floats) of the E1 tables, the prefactors and the moments
 void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
-                    const double *E1, const int64_t *e1off, const double *pref, cudaStream_t st);
+                    const void *Edf, const int64_t *e1off, const void *prefdf, const void *mudf, cudaStream_t st);
+// y = x as double-FP32 pairs (8 bytes per value)
+void launch_gen_to_df64(const double *x, void *y, int64_t n, cudaStream_t st);
 // dynamic shared memory of the M2L kernel (the create call refuses parameters beyond 227 KB)
 size_t gen_m2l_smem(int na, int nk, int mx);
 void launch_gen_l2l(const GenDev &g, const int *children, int n, cudaStream_t st);

@@ -387,72 +387,62 @@ void launch_gen_m2m(const GenDev &g, const int *parents, int n, const int *child
 }
 
 // lam(Z)[b][nu] = sum over I(Z) of sum_a pref[a][b] sum_{|kappa + nu| <= m_x} prod_d E1_d mu(Z_s)[a][kappa]
-// (Eq. m2l with Eq. exp_coeffs_3d; E1 of the pair's intervals, offsets of the cells per direction).
-// One CTA per target box; per source the moments mu(Z_s) (dense cubes [a][m1^3]) and the three 1D
-// factor slices of every (a, b) are staged in shared memory in double-FP32 (pairs of floats, about
-// 48 significant bits: the FP32 pipe issues such operations several times faster than GB300's
-// FP64 pipe), and item (b, nu) sums over the simplex |kappa| <= m_x - |nu| one direction at a time.
-// Items are ordered by |nu| so the lanes of a warp run loops of equal length.
-constexpr int kGenM2lThreads = 256;
-constexpr int kGenM2lItems = (kMaxNa * 455 + kGenM2lThreads - 1) / kGenM2lThreads;
-__global__ void __launch_bounds__(kGenM2lThreads) k_gen_m2l(GenDev g, const int *__restrict__ targets,
-                                                             const int *__restrict__ mptr,
-                                                             const GPair *__restrict__ pairs,
-                                                             const double *__restrict__ E1,
-                                                             const int64_t *__restrict__ e1off,
-                                                             const double *__restrict__ pref)
+// (Eq. m2l with Eq. exp_coeffs_3d; E1 of the pair's intervals, offsets of the cells per direction),
+// in double-FP32 (pairs of floats, about 48 significant bits: the FP32 pipe issues such operations
+// several times faster than GB300's FP64 pipe) from tables converted once (Edf, prefdf, mudf).
+// One CTA per target box, 8 warps working independently: a warp takes the tasks (source, a) in
+// turn, stages the source's moment cube mu(Z_s)[a] and the 1D factor slices of all b in its own
+// shared memory, and its lanes sum for nu = lane, lane + 32, ... over the simplex |kappa| <= m_x -
+// |nu| one direction at a time; the warps' partial sums are added in warp order at the end.
+constexpr int kGenM2lWarps = 8;
+constexpr int kGenM2lSlots = (455 + 31) / 32;  // nu per lane (m_x <= 12)
+__global__ void __launch_bounds__(32 * kGenM2lWarps) k_gen_m2l(GenDev g, const int *__restrict__ targets,
+                                                                const int *__restrict__ mptr,
+                                                                const GPair *__restrict__ pairs,
+                                                                const df64 *__restrict__ Edf,
+                                                                const int64_t *__restrict__ e1off,
+                                                                const df64 *__restrict__ prefdf,
+                                                                const df64 *__restrict__ mudf)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int na = g.na, nk = g.nk, m1 = g.mx + 1, mm = m1 * m1, m3 = mm * m1;
-    df64 *smu = (df64 *)smraw;      // [na][m1^3]
-    df64 *sE = smu + na * m3;       // [3][na][na][m1][m1]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_warp = m3 + 3 * na * mm;  // cube + slices of all b
+    df64 *cube = (df64 *)smraw + (size_t)warp * per_warp, *sE = cube + m3;  // sE [b][d][m1][m1]
     const int bt = targets[blockIdx.x];
     const GBox T = g.box[bt];
     const int G = g.lvG[T.level], no = 2 * G - 1;
-    // this thread's items: t -> (degree s, b, nu of degree s), degree-major
-    int item_b[kGenM2lItems], item_iv[kGenM2lItems];
-    const int nmine = (na * nk - (int)threadIdx.x + kGenM2lThreads - 1) / kGenM2lThreads;
-    for (int u = 0; u < nmine; ++u) {
-        int t = threadIdx.x + u * kGenM2lThreads, sdeg = 0;
-        while (true) {
-            const int grp = (sdeg + 1) * (sdeg + 2) / 2;  // multi-indices of degree sdeg
-            if (t < na * grp) {
-                item_b[u] = t / grp;
-                item_iv[u] = sdeg * (sdeg + 1) * (sdeg + 2) / 6 + t % grp;  // degree-graded index
-                break;
-            }
-            t -= na * grp;
-            ++sdeg;
-        }
-    }
+    const int nsrc = mptr[bt + 1] - mptr[bt];
+    const int nslot = (nk + 31) / 32;
     for (int r = 0; r < g.nrhs; ++r) {
-        df64 acc[kGenM2lItems];
-        for (int u = 0; u < nmine; ++u) acc[u] = df64(0);
-        for (int q = mptr[bt]; q < mptr[bt + 1]; ++q) {
+        df64 acc[kMaxNa][kGenM2lSlots];
+        for (int b = 0; b < na; ++b)
+            for (int sl = 0; sl < nslot; ++sl) acc[b][sl] = df64(0);
+        for (int task = warp; task < nsrc * na; task += kGenM2lWarps) {
+            const int q = mptr[bt] + task / na, a = task % na;
             const GPair pr = pairs[q];
             const GBox S = g.box[pr.src];
             const int o[3] = {T.cell[0] - S.cell[0] + G - 1, T.cell[1] - S.cell[1] + G - 1, T.cell[2] - S.cell[2] + G - 1};
-            __syncthreads();
-            for (int i = threadIdx.x; i < na * nk; i += blockDim.x) {
-                const int a = i / nk, ik = i - a * nk;
-                smu[a * m3 + (g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] =
-                    df64(g.mu[gidx(g, r, pr.src, 0, 0) + i]);
-            }
-            const double *Ep = E1 + e1off[pr.e];
-            for (int i = threadIdx.x; i < 3 * na * na * mm; i += blockDim.x) {
-                const int kv = i % mm, ab = (i / mm) % (na * na), d = i / (mm * na * na);
-                sE[i] = df64(Ep[((size_t)ab * no + o[d]) * mm + kv]);
-            }
-            __syncthreads();
-            const double *pf = pref + (size_t)pr.e * na * na;
-            for (int u = 0; u < nmine; ++u) {
-                const int b = item_b[u], iv = item_iv[u];
+            __syncwarp();
+            const df64 *ms = mudf + gidx(g, r, pr.src, a, 0);
+            for (int ik = lane; ik < nk; ik += 32)
+                cube[(g.kidx[3 * ik] * m1 + g.kidx[3 * ik + 1]) * m1 + g.kidx[3 * ik + 2]] = ms[ik];
+            const df64 *Ep = Edf + e1off[pr.e];
+            for (int b = 0; b < na; ++b)
+                for (int d = 0; d < 3; ++d) {
+                    const df64 *src = Ep + ((size_t)(a * na + b) * no + o[d]) * mm;
+                    df64 *dst = sE + (size_t)(b * 3 + d) * mm;
+                    for (int kv = lane; kv < mm; kv += 32) dst[kv] = src[kv];
+                }
+            __syncwarp();
+            const df64 *pf = prefdf + (size_t)pr.e * na * na + a * na;
+            for (int sl = 0; sl < nslot; ++sl) {
+                const int iv = lane + 32 * sl;
+                if (iv >= nk) break;
                 const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
                 const int dd = g.mx - (n0 + n1 + n2);
-                for (int a = 0; a < na; ++a) {
-                    const df64 *E0 = sE + (size_t)(a * na + b) * mm, *Ea = E0 + (size_t)na * na * mm,
-                               *Eb = Ea + (size_t)na * na * mm;
-                    const df64 *cube = smu + a * m3;
+                for (int b = 0; b < na; ++b) {
+                    const df64 *E0 = sE + (size_t)(b * 3) * mm, *Ea = E0 + mm, *Eb = Ea + mm;
                     df64 v0(0);
                     for (int k0 = 0; k0 <= dd; ++k0) {
                         df64 v1(0);
@@ -464,28 +454,55 @@ __global__ void __launch_bounds__(kGenM2lThreads) k_gen_m2l(GenDev g, const int 
                         }
                         mac(v0, E0[k0 * m1 + n0], v1);
                     }
-                    mac(acc[u], df64(pf[a * na + b]), v0);
+                    mac(acc[b][sl], pf[b], v0);
                 }
             }
         }
-        for (int u = 0; u < nmine; ++u) g.lam[gidx(g, r, bt, item_b[u], item_iv[u])] = as_double(acc[u]);
+        // the warps' partial sums, added in warp order (the staging area is reused)
+        __syncthreads();
+        df64 *red = (df64 *)smraw;  // [warps][na][nk]
+        for (int b = 0; b < na; ++b)
+            for (int sl = 0; sl < nslot; ++sl) {
+                const int iv = lane + 32 * sl;
+                if (iv < nk) red[((size_t)warp * na + b) * nk + iv] = acc[b][sl];
+            }
+        __syncthreads();
+        for (int t = threadIdx.x; t < na * nk; t += blockDim.x) {
+            df64 s = red[t];
+            for (int w = 1; w < kGenM2lWarps; ++w) s += red[(size_t)w * na * nk + t];
+            g.lam[gidx(g, r, bt, 0, 0) + t] = as_double(s);
+        }
+        __syncthreads();
     }
+}
+
+// double -> double-FP32 copies of the M2L operands
+__global__ void k_gen_to_df64(const double *__restrict__ x, df64 *__restrict__ y, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = df64(x[i]);
+}
+
+void launch_gen_to_df64(const double *x, void *y, int64_t n, cudaStream_t st)
+{
+    if (n > 0) k_gen_to_df64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, (df64 *)y, n);
 }
 
 size_t gen_m2l_smem(int na, int nk, int mx)
 {
-    (void)nk;
-    const size_t m1 = mx + 1;
-    return sizeof(df64) * ((size_t)na * m1 * m1 * m1 + 3 * (size_t)na * na * m1 * m1);
+    const size_t m1 = mx + 1, stage = (size_t)kGenM2lWarps * (m1 * m1 * m1 + 3 * (size_t)na * m1 * m1),
+                 red = (size_t)kGenM2lWarps * na * nk;
+    return sizeof(df64) * (stage > red ? stage : red);
 }
 
 void launch_gen_m2l(const GenDev &g, const int *targets, int n, const int *mptr, const GPair *pairs,
-                    const double *E1, const int64_t *e1off, const double *pref, cudaStream_t st)
+                    const void *Edf, const int64_t *e1off, const void *prefdf, const void *mudf, cudaStream_t st)
 {
     if (n <= 0) return;
     const size_t smem = gen_m2l_smem(g.na, g.nk, g.mx);
     cudaFuncSetAttribute(k_gen_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_gen_m2l<<<n, kGenM2lThreads, smem, st>>>(g, targets, mptr, pairs, E1, e1off, pref);
+    k_gen_m2l<<<n, 32 * kGenM2lWarps, smem, st>>>(g, targets, mptr, pairs, (const df64 *)Edf, e1off,
+                                                   (const df64 *)prefdf, (const df64 *)mudf);
 }
 
 // lam(Z_c)[bc][kappa] += sum_bp q^(t)_{bc,bp} sum_{nu >= kappa, |nu| <= m_x} q^(x)_{kappa,nu} lam(Z_p)[bp][nu]
