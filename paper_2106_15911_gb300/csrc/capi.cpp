@@ -168,12 +168,15 @@ int ensure_workspace(pfmm_handle *H, int nrhs)
     H->release(H->d_Whi);
     H->release(H->d_Wlo);
     H->release(H->d_wmax);
+    H->release(H->d_nfpart);
     H->d_Whi = H->d_Wlo = nullptr;
     H->d_wmax = nullptr;
+    H->d_nfpart = nullptr;
     if (H->tcV || H->tcK) {
         H->w_elems = (size_t)nrhs * H->Et * std::max(H->colsV_u, H->colsK_u);
+        const int planes = std::max(H->tcV ? pfmm::nf_tc_planes(H, 0, nrhs) : 1, H->tcK ? pfmm::nf_tc_planes(H, 1, nrhs) : 1);
         if ((rc = H->alloc(&H->d_Whi, H->w_elems)) || (rc = H->alloc(&H->d_Wlo, H->w_elems)) ||
-            (rc = H->alloc(&H->d_wmax, (size_t)nrhs)))
+            (rc = H->alloc(&H->d_wmax, (size_t)nrhs)) || (rc = H->alloc(&H->d_nfpart, (size_t)planes * n_in)))
             return rc;
     }
     H->release(H->d_Wres);
@@ -220,8 +223,14 @@ int pfmm::ensure_ws(pfmm_handle *H, int nrhs) { return ensure_workspace(H, nrhs)
 // Tensor-core nearfield of op (0: V, 1: K) into fint (zeroed here): splits the FP64 input into
 // scaled FP16 hi/lo parts in whi/wlo ([nrhs][E_t][cols] each; per-rhs scale from max |x| in
 // wmax), encodes their TMA views and launches.
+int pfmm::nf_tc_planes(const pfmm_handle *H, int op, int nrhs)
+{
+    const int cols = op == 0 ? H->colsV_u : H->colsK_u, nint = H->Et / 2;
+    return nf_tc_ksplit(nrhs * H->ntiles128 * ((nint + 127) / 128), cols / 64, H->nsm);
+}
+
 int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo,
-                    unsigned long long *wmax, double *fint, cudaStream_t st)
+                    unsigned long long *wmax, double *fint, double *part, cudaStream_t st)
 {
     int rc;
     const int cols = op == 0 ? H->colsV_u : H->colsK_u;
@@ -233,7 +242,6 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
     uint32_t box[4] = {64, 1, 128, 1};
     CUtensorMap mWhi, mWlo;
     if ((rc = encode_map(&mWhi, whi, 4, dims, str, box)) || (rc = encode_map(&mWlo, wlo, 4, dims, str, box))) return rc;
-    CK(cudaMemsetAsync(fint, 0, sizeof(double) * nrhs * (size_t)H->Et * H->nt, st));
     NfTcParams P{};
     P.panels = H->d_panels;
     P.tiles = H->d_tiles128;
@@ -241,10 +249,9 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
     P.nib = (nint + 127) / 128;
     P.nkb = cols / 64;
     const int tiles = nrhs * P.ntiles * P.nib;
-    // split K into chunks of at most 32 stages (2048 columns): shorter FP32 accumulation in TMEM
-    // and at least three work items per SM; the FP64 atomics of the partials are cheap
-    int ks = std::max((3 * H->nsm + tiles - 1) / tiles, (4 * P.nkb + 31) / 32);
-    ks = std::max(1, std::min(ks, 4 * P.nkb / 8));
+    // split K into a few chunks for SM balance (each chunk accumulates 32-stage sub-chunks into its
+    // own FP64 partial plane; the planes are summed in order afterwards)
+    const int ks = nf_tc_ksplit(tiles, P.nkb, H->nsm);
     P.ksplit = ks;
     P.nitems = tiles * ks;
     P.cols_pad = cols;
@@ -254,7 +261,8 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
     P.nt = H->nt;
     P.a_exp = op == 0 ? H->a_expV : H->a_expK;
     P.wmax = wmax;
-    P.f = fint;
+    P.part = part;
+    P.nrhs = nrhs;
     P.err = H->d_err;
     if (H->cur_ev) cudaEventRecord(H->cur_ev->ev[9], st);
     if (launch_nf_apply_tc(op == 0 ? H->mapAVhi : H->mapAKhi, op == 0 ? H->mapAVlo : H->mapAKlo, mWhi, mWlo, P, H->nsm,
@@ -264,6 +272,7 @@ int pfmm::run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi
         cudaEventRecord(H->cur_ev->ev[10], st);
         H->cur_ev->nf = true;
     }
+    launch_nf_tc_reduce(part, ks, (size_t)nrhs * H->Et * H->nt, fint, st);
     return PFMM_OK;
 }
 
@@ -941,7 +950,8 @@ static int apply_impl(pfmm_handle *H, int op, const double *x, double *f, int nr
     const bool tc = (parts & PFMM_PART_NEAR) && (op == 0 ? H->tcV : H->tcK) && !H->nf_cuda_cores;
     const bool crt = (parts & PFMM_PART_NEAR) && (op == 0 ? H->crtV : H->crtK) && !H->nf_cuda_cores;
     if (tc) {
-        if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_wmax, H->d_fint, st))) return rc;
+        if ((rc = pfmm::run_nf_tc(H, op, x, nrhs, H->d_Whi, H->d_Wlo, H->d_wmax, H->d_fint, H->d_nfpart, st)))
+            return rc;
     } else if (crt) {
         if ((rc = pfmm::run_nf_crt(H, op, x, nrhs, H->d_fint, st))) return rc;
     } else if ((parts & PFMM_PART_NEAR) && H->otf) {

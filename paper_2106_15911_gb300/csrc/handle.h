@@ -22,8 +22,11 @@ struct pfmm_handle;
 namespace pfmm {
 // tensor-core nearfield of op (0: V, 1: K) into fint; whi/wlo: [nrhs][E_t][cols] FP32 workspaces
 // whi, wlo: FP16 input parts ([nrhs][E_t][cols] each); wmax: nrhs words of scratch
+// part: FP64 partial planes, nf_tc_planes(H, op, nrhs) x nrhs x E_t x E_x doubles
 int run_nf_tc(pfmm_handle *H, int op, const double *x, int nrhs, void *whi, void *wlo, unsigned long long *wmax,
-              double *fint, cudaStream_t st);
+              double *fint, double *part, cudaStream_t st);
+// K-chunk partial planes of the tensor-core nearfield of op for nrhs right-hand sides
+int nf_tc_planes(const pfmm_handle *H, int op, int nrhs);
 // FP64 mode: exact residue-arithmetic nearfield of op on the tensor cores into fint (overwritten)
 int run_nf_crt(pfmm_handle *H, int op, const double *x, int nrhs, double *fint, cudaStream_t st);
 // size the per-call workspaces of a handle for nrhs right-hand sides (may allocate)
@@ -108,6 +111,7 @@ struct pfmm_handle {
     unsigned char *d_res8 = nullptr;                  // output residues [16][nrhs][E_t][E_x]
     uint16_t *d_Whi = nullptr, *d_Wlo = nullptr;  // FP16 input parts
     unsigned long long *d_wmax = nullptr;          // [ws_nrhs] max |input| per rhs (FP64 bits)
+    double *d_nfpart = nullptr;                    // partial planes of the tensor-core nearfield
     size_t w_elems = 0;
 
     bool prof = false;

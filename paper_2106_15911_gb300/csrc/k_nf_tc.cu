@@ -18,8 +18,10 @@
 // where s_A (per operator, at build) and s_W (per rhs and apply, from max |W|) bring the largest
 // magnitude into [2^14, 2^15): the parts are normal FP16 down to 2^-29 of the maximum, and
 // |A - (A_hi + A_lo) / s_A| <= 2^-22 |A| above that.  The products are accumulated in FP32 in
-// TMEM over a chunk of the column loop (split K), unscaled exactly (powers of two) in FP64 and
-// added to the FP64 output with FP64 atomics.
+// TMEM over sub-chunks of 32 stages (2048 columns) of the column loop, unscaled exactly (powers of
+// two) in FP64 and added, sub-chunk by sub-chunk and by the one CTA that owns the work item, into
+// the item's FP64 partial plane; the ksplit planes of a tile (split K, for SM balance) are then
+// summed in plane order by k_nf_tc_reduce: no atomics, bitwise reproducible.
 // Warp roles (192 threads): warp 0 issues TMA, warp 1 allocates TMEM and issues the MMAs,
 // warps 2-5 drain TMEM (each warp reads its 32-lane quadrant).  Two smem stages, two TMEM
 // accumulators (512 columns), persistent CTAs over (tile, K chunk) work items.  Every mbarrier
@@ -49,6 +51,7 @@ constexpr int B_HALF = 128 * BK * 2;               // 16 KB (one phase)
 constexpr int STAGE_BYTES = 2 * A_TILE + 4 * B_HALF;  // A_hi, A_lo, B_hi (2 halves), B_lo (2 halves)
 constexpr int NSTAGE = 2;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // 2 s per wait
+constexpr int kSub = 32;                            // stages per FP32 accumulation in TMEM
 
 // 3D tile: the FP16 panel parts seen as [block][64 rows][64 columns]
 __device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
@@ -88,7 +91,7 @@ __device__ __forceinline__ void mma_f16(uint32_t dt, uint64_t a, uint64_t b, uin
 }
 
 struct Item {
-    int panel, r0, ib, rhs, st0, st1;  // tile and its stage range [st0, st1)
+    int panel, r0, ib, rhs, st0, st1, kc;  // tile, its stage range [st0, st1), K chunk (partial plane)
 };
 
 __device__ __forceinline__ Item decode_item(const NfTcParams &P, int it)
@@ -105,6 +108,7 @@ __device__ __forceinline__ Item decode_item(const NfTcParams &P, int it)
     int nst = 4 * P.nkb;  // stage list: d = 0..3, then column blocks
     I.st0 = (int)((long long)nst * kc / P.ksplit);
     I.st1 = (int)((long long)nst * (kc + 1) / P.ksplit);
+    I.kc = kc;
     return I;
 }
 
@@ -197,10 +201,12 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int g = 0, n = 0;
+            int g = 0, n = 0;  // n: sub-chunks issued (the TMEM accumulators alternate per sub-chunk)
             const uint32_t id256 = idesc_f16(BM, 256), id128 = idesc_f16(BM, 128);
-            for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x, ++n) {
-                Item I = decode_item(P, it);
+            for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
+              Item I = decode_item(P, it);
+              for (int sc0 = I.st0; sc0 < I.st1 && !s_abort; sc0 += kSub, ++n) {
+                const int sc1 = min(I.st1, sc0 + kSub);
                 const int acc = n & 1;
                 if (!mbar_wait(&tempty[acc], ((n >> 1) & 1) ^ 1, deadline)) {
                     atomicExch(P.err, 2);
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dcol = tmem + acc * 256;
                 uint32_t first = 1;
-                for (int st = I.st0; st < I.st1; ++st, ++g) {
+                for (int st = sc0; st < sc1; ++st, ++g) {
                     const int s = g % NSTAGE;
                     if (!mbar_wait(&full[s], (g / NSTAGE) & 1, deadline)) {
                         atomicExch(P.err, 3);
@@ -243,7 +249,8 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
                     }
                     mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
                 }
-                mma_commit(&tfull[acc]);  // an empty chunk accumulated nothing: the epilogue skips it
+                mma_commit(&tfull[acc]);
+              }
             }
         }
     } else {
@@ -251,37 +258,42 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
         const int quad = warp & 3;
         const int row_l = quad * 32 + lane;
         int n = 0;
-        for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x, ++n) {
+        for (int it = blockIdx.x; it < nitems && !s_abort; it += gridDim.x) {
             Item I = decode_item(P, it);
-            const int acc = n & 1;
-            if (!mbar_wait(&tfull[acc], (n >> 1) & 1, deadline)) {
-                atomicExch(P.err, 4);
-                s_abort = 1;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const PanelGPU &Pn = P.panels[I.panel];
             const int row = I.r0 + row_l;
             const bool row_ok = row < Pn.nrows;
-            // the phase-1 half is written by any stage, the phase-0 half only by stages with d < 3
-            const bool has_any = I.st1 > I.st0;
-            const bool has_ph0 = has_any && I.st0 < 3 * P.nkb;
-            double *fr = P.f + (size_t)I.rhs * P.Et * P.nt + Pn.row0 + row;
+            double *fr = P.part + ((size_t)I.kc * P.nrhs + I.rhs) * P.Et * P.nt + Pn.row0 + row;
             // 2^-(a_exp + E_W) (|exponent| <= 200) built from its bits
             const double unscale = __longlong_as_double((long long)(1023 - P.a_exp - f64_scale_exp(P.wmax[I.rhs])) << 52);
-#pragma unroll 1
-            for (int c0 = 0; c0 < 256; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + acc * 256 + c0, v);
-                if (!row_ok || !has_any || (c0 < 128 && !has_ph0)) continue;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int c = c0 + j, ph = c >> 7, iv = I.ib * 128 + (c & 127);
-                    if (iv < P.nint) atomicAdd(fr + (size_t)(2 * iv + ph) * P.nt, (double)__uint_as_float(v[j]) * unscale);
+            for (int sc0 = I.st0; sc0 < I.st1 && !s_abort; sc0 += kSub, ++n) {
+                const int acc = n & 1;
+                if (!mbar_wait(&tfull[acc], (n >> 1) & 1, deadline)) {
+                    atomicExch(P.err, 4);
+                    s_abort = 1;
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // the phase-1 half is written by any stage, the phase-0 half only by stages with
+                // d < 3 (stages ascend in d, so a sub-chunk starting at d = 3 has none)
+                const bool first = sc0 == I.st0, has_ph0 = sc0 < 3 * P.nkb;
+#pragma unroll 1
+                for (int c0 = 0; c0 < 256; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + acc * 256 + c0, v);
+                    if (!row_ok || (c0 < 128 && !has_ph0 && !first)) continue;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int c = c0 + j, ph = c >> 7, iv = I.ib * 128 + (c & 127);
+                        if (iv >= P.nint) continue;
+                        double *a = fr + (size_t)(2 * iv + ph) * P.nt;
+                        const double x = (ph == 0 && !has_ph0) ? 0.0 : (double)__uint_as_float(v[j]) * unscale;
+                        *a = first ? x : *a + x;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&tempty[acc]);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&tempty[acc]);
         }
     }
     __syncthreads();
@@ -391,6 +403,28 @@ void launch_absmax_input(const double *x, size_t per_rhs, int nrhs, unsigned gri
                          cudaStream_t st)
 {
     k_absmax_input<<<dim3(grid_x, nrhs), 256, 0, st>>>(x, per_rhs, wmax);
+}
+
+// f[i] = sum over the K-chunk planes of part[kc][i], in plane order
+__global__ void k_nf_tc_reduce(const double *__restrict__ part, int ks, size_t n, double *__restrict__ f)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = part[i];
+    for (int kc = 1; kc < ks; ++kc) s += part[(size_t)kc * n + i];
+    f[i] = s;
+}
+
+void launch_nf_tc_reduce(const double *part, int ks, size_t n, double *f, cudaStream_t st)
+{
+    if (n > 0) k_nf_tc_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, ks, n, f);
+}
+
+int nf_tc_ksplit(int tiles, int nkb, int nsm)
+{
+    const int nsub = (4 * nkb + kSub - 1) / kSub;  // sub-chunks of a tile
+    int ks = (2 * nsm + tiles - 1) / tiles;
+    return std::max(1, std::min(ks, std::min(8, nsub)));
 }
 
 size_t nf_tc_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + 1024 + 256; }

@@ -40,7 +40,8 @@ struct NfTcParams {
     int nint, Et, nt;
     int a_exp;              // scale exponent of the panels' FP16 split
     const unsigned long long *wmax;  // [nrhs] FP64 bits of max |W| per rhs (scale of the input split)
-    double *f;          // FP64 output [rhs][Et][nt] (internal order), accumulated with atomics
+    double *part;       // FP64 partial planes [ksplit][nrhs][Et][nt] (internal order), every element written
+    int nrhs;
     int *err;           // set non-zero when a bounded wait gave up
 };
 
@@ -48,6 +49,11 @@ struct NfTcParams {
 void launch_absmax_input(const double *x, size_t per_rhs, int nrhs, unsigned grid_x, unsigned long long *wmax,
                          cudaStream_t st);
 size_t nf_tc_smem_bytes();
+// K chunks (partial planes) of the tensor-core nearfield for `tiles` output tiles of nkb column
+// blocks: enough work items for two per SM, at most 8 and at most the tile's 32-stage sub-chunks
+int nf_tc_ksplit(int tiles, int nkb, int nsm);
+// f[i] = sum_kc part[kc][i] (n elements per plane, plane order)
+void launch_nf_tc_reduce(const double *part, int ks, size_t n, double *f, cudaStream_t st);
 int launch_nf_apply_tc(const CUtensorMap &Ahi, const CUtensorMap &Alo, const CUtensorMap &Whi, const CUtensorMap &Wlo,
                        const NfTcParams &P, int nsm, cudaStream_t st);
 // scale exponent of n stored FP32 panel values (synchronises st; scratch: one device word);

@@ -65,7 +65,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     if (!H || !w || !f || nrhs < 1) return set_error(PFMM_ERR_INVALID_ARG, "invalid pfmm_apply_V_noalloc arguments");
     cudaStream_t st = (cudaStream_t)stream;
     // carve the static array: permuted input | FP64 output | moments | locals |
-    // [tensor-core input split hi | lo | max |w| per rhs] | M2L T1 | M2L T2
+    // [tensor-core input split hi | lo | max |w| per rhs | partial planes] | M2L T1 | M2L T2
     const size_t n_in = (size_t)nrhs * H->Et * H->nt;
     const size_t b_x = up256(n_in * H->es), b_f = up256(n_in * sizeof(double));
     const size_t n_mom = (size_t)nrhs * (H->mom_per_rhs > 0 ? H->mom_per_rhs : 1);
@@ -73,7 +73,8 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     const bool tc = H->tcV && !H->nf_cuda_cores;
     const size_t b_w = tc ? up256((size_t)nrhs * H->Et * H->colsV_u * sizeof(uint16_t)) : 0;
     const size_t b_m = tc ? up256((size_t)nrhs * sizeof(unsigned long long)) : 0;
-    const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w + b_m;
+    const size_t b_p = tc ? up256((size_t)nf_tc_planes(H, 0, nrhs) * n_in * sizeof(double)) : 0;
+    const size_t fixed = b_x + b_f + 2 * b_mu + 2 * b_w + b_m + b_p;
     // elements of T1 (and of T2) for the largest single-interval chunk of the levels whose M2L
     // takes the three separable passes (the fused and slab kernels keep their intermediates in
     // shared memory; the fused kernel's split mode and the two-stage S2M / L2T use T1 only when
@@ -99,6 +100,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     char *lam = mu + b_mu;
     void *whi = lam + b_mu, *wlo = lam + b_mu + b_w;
     unsigned long long *wmax = (unsigned long long *)(lam + b_mu + 2 * b_w);
+    double *part = (double *)(lam + b_mu + 2 * b_w + b_m);
     const size_t t_bytes = (kScratchBytes - fixed) / 2 / 256 * 256;
     void *T1 = base + fixed, *T2 = base + fixed + t_bytes;
     const size_t ws_elems = t_bytes / H->es;
@@ -132,7 +134,7 @@ extern "C" int pfmm_apply_V_noalloc(pfmm_handle *H, const double *w, double *f, 
     // intervals of each level, which launch_m2l clears; nothing depends on the previous call
     launch_permute_in(w, xint, H->mixed, nrhs, g, st);
     if (tc) {  // the same nearfield engine as pfmm_apply_V
-        if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, wmax, fint, st))) return rc;
+        if ((rc = run_nf_tc(H, 0, w, nrhs, whi, wlo, wmax, fint, part, st))) return rc;
     } else if (H->otf) {
         cudaMemsetAsync(fint, 0, n_in * sizeof(double), st);
         if ((rc = run_nf_otf(H, 0, xint, H->nt, H->Et, H->ls, nrhs, 1 << 30, fint, st))) return rc;
