@@ -282,13 +282,22 @@ __global__ void __launch_bounds__(192, 1) k_nf_apply_tc(const __grid_constant__ 
                     uint32_t v[32];
                     tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + acc * 256 + c0, v);
                     if (!row_ok || (c0 < 128 && !has_ph0 && !first)) continue;
+                    // the group's 32 partial values are read together (one latency per group), then
+                    // updated: the plane is private to this work item, so no atomics are needed
+                    const int ph = c0 >> 7, iv0 = I.ib * 128 + (c0 & 127);
+                    double *a0 = fr + (size_t)(2 * iv0 + ph) * P.nt;
+                    const size_t step = 2 * (size_t)P.nt;
+                    const int nj = min(32, P.nint - iv0);
+                    double old[32];
+                    if (!first) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) old[j] = j < nj ? a0[j * step] : 0.0;
+                    }
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int c = c0 + j, ph = c >> 7, iv = I.ib * 128 + (c & 127);
-                        if (iv >= P.nint) continue;
-                        double *a = fr + (size_t)(2 * iv + ph) * P.nt;
+                        if (j >= nj) continue;
                         const double x = (ph == 0 && !has_ph0) ? 0.0 : (double)__uint_as_float(v[j]) * unscale;
-                        *a = first ? x : *a + x;
+                        a0[j * step] = first ? x : old[j] + x;
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -422,9 +431,20 @@ void launch_nf_tc_reduce(const double *part, int ks, size_t n, double *f, cudaSt
 
 int nf_tc_ksplit(int tiles, int nkb, int nsm)
 {
-    const int nsub = (4 * nkb + kSub - 1) / kSub;  // sub-chunks of a tile
-    int ks = (2 * nsm + tiles - 1) / tiles;
-    return std::max(1, std::min(ks, std::min(8, nsub)));
+    // the number of K chunks (1 .. 8, at most the tile's 32-stage sub-chunks) whose work items fill
+    // the rounds of the persistent grid best (items / (nsm x rounds)); the smallest on a tie
+    const int nsub = (4 * nkb + kSub - 1) / kSub;
+    int best = 1;
+    double best_eff = -1.0;
+    for (int ks = 1; ks <= std::min(8, nsub); ++ks) {
+        const long long items = (long long)tiles * ks, rounds = (items + nsm - 1) / nsm;
+        const double eff = (double)items / ((double)nsm * rounds);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = ks;
+        }
+    }
+    return best;
 }
 
 size_t nf_tc_smem_bytes() { return (size_t)NSTAGE * STAGE_BYTES + 1024 + 256; }

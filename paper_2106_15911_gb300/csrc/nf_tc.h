@@ -50,7 +50,8 @@ void launch_absmax_input(const double *x, size_t per_rhs, int nrhs, unsigned gri
                          cudaStream_t st);
 size_t nf_tc_smem_bytes();
 // K chunks (partial planes) of the tensor-core nearfield for `tiles` output tiles of nkb column
-// blocks: enough work items for two per SM, at most 8 and at most the tile's 32-stage sub-chunks
+// blocks: 1 .. 8 (at most the tile's 32-stage sub-chunks), chosen so the work items fill the
+// rounds of the persistent grid of nsm CTAs best
 int nf_tc_ksplit(int tiles, int nkb, int nsm);
 // f[i] = sum_kc part[kc][i] (n elements per plane, plane order)
 void launch_nf_tc_reduce(const double *part, int ks, size_t n, double *f, cudaStream_t st);
