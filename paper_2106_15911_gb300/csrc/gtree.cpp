@@ -709,8 +709,8 @@ int pfmm_gen_create(const pfmm_mesh *mesh, const double *t_steps, const pfmm_par
     if (p.precision != PFMM_FP64) return fail(PFMM_ERR_UNSUPPORTED, "general time steps: FP64 only");
     {
         const int m1 = p.m_x + 1, nk = m1 * (m1 + 1) * (m1 + 2) / 6;
-        if (gen_m2l_smem(p.m_t + 1, nk, p.m_x) > 227 * 1024)
-            return fail(PFMM_ERR_UNSUPPORTED, "general time steps: (m_t + 1)^2 (m_x + 1)^2 too large for the M2L kernel");
+        if (gen_m2l_smem(p.m_t + 1, nk, p.m_x) > 227 * 1024 || (p.m_t + 1) * nk > 2048)
+            return fail(PFMM_ERR_UNSUPPORTED, "general time steps: m_t and m_x too large for the M2L kernel (shared memory, or (m_t + 1) x multi-indices > 2048)");
     }
     if (t_steps[0] != 0.0) return fail(PFMM_ERR_INVALID_ARG, "t_steps[0] must be 0");
     for (int j = 0; j < m.n_steps; ++j)

@@ -395,7 +395,25 @@ void launch_gen_m2m(const GenDev &g, const int *parents, int n, const int *child
 // shared memory, and its lanes sum for nu = lane, lane + 32, ... over the simplex |kappa| <= m_x -
 // |nu| one direction at a time; the warps' partial sums are added in warp order at the end.
 constexpr int kGenM2lWarps = 8;
-constexpr int kGenM2lSlots = (455 + 31) / 32;  // nu per lane (m_x <= 12)
+constexpr int kGenM2lSlots = 64;  // items (b, nu) per lane: na nk <= 2048 (checked at creation)
+
+// item t of the (b, nu) list in degree-major order: all (b, nu) with |nu| = 0, then |nu| = 1, ...
+// (so the 32 lanes of a slot mostly share |nu| and run loops of one length)
+__device__ __forceinline__ void m2l_item(int t, int na, int &b, int &iv)
+{
+    int sdeg = 0;
+    while (true) {
+        const int grp = (sdeg + 1) * (sdeg + 2) / 2;  // multi-indices of degree sdeg
+        if (t < na * grp) {
+            b = t / grp;
+            iv = sdeg * (sdeg + 1) * (sdeg + 2) / 6 + t % grp;  // its place in the degree-graded order
+            return;
+        }
+        t -= na * grp;
+        ++sdeg;
+    }
+}
+
 __global__ void __launch_bounds__(32 * kGenM2lWarps) k_gen_m2l(GenDev g, const int *__restrict__ targets,
                                                                 const int *__restrict__ mptr,
                                                                 const GPair *__restrict__ pairs,
@@ -413,11 +431,10 @@ __global__ void __launch_bounds__(32 * kGenM2lWarps) k_gen_m2l(GenDev g, const i
     const GBox T = g.box[bt];
     const int G = g.lvG[T.level], no = 2 * G - 1;
     const int nsrc = mptr[bt + 1] - mptr[bt];
-    const int nslot = (nk + 31) / 32;
+    const int nitem = na * nk, nslot = (nitem + 31) / 32;
     for (int r = 0; r < g.nrhs; ++r) {
-        df64 acc[kMaxNa][kGenM2lSlots];
-        for (int b = 0; b < na; ++b)
-            for (int sl = 0; sl < nslot; ++sl) acc[b][sl] = df64(0);
+        df64 acc[kGenM2lSlots];
+        for (int sl = 0; sl < nslot; ++sl) acc[sl] = df64(0);
         for (int task = warp; task < nsrc * na; task += kGenM2lWarps) {
             const int q = mptr[bt] + task / na, a = task % na;
             const GPair pr = pairs[q];
@@ -437,40 +454,41 @@ __global__ void __launch_bounds__(32 * kGenM2lWarps) k_gen_m2l(GenDev g, const i
             __syncwarp();
             const df64 *pf = prefdf + (size_t)pr.e * na * na + a * na;
             for (int sl = 0; sl < nslot; ++sl) {
-                const int iv = lane + 32 * sl;
-                if (iv >= nk) break;
+                const int t = lane + 32 * sl;
+                if (t >= nitem) break;
+                int b, iv;
+                m2l_item(t, na, b, iv);
                 const int n0 = g.kidx[3 * iv], n1 = g.kidx[3 * iv + 1], n2 = g.kidx[3 * iv + 2];
                 const int dd = g.mx - (n0 + n1 + n2);
-                for (int b = 0; b < na; ++b) {
-                    const df64 *E0 = sE + (size_t)(b * 3) * mm, *Ea = E0 + mm, *Eb = Ea + mm;
-                    df64 v0(0);
-                    for (int k0 = 0; k0 <= dd; ++k0) {
-                        df64 v1(0);
-                        for (int k1 = 0; k1 <= dd - k0; ++k1) {
-                            const df64 *row = cube + (k0 * m1 + k1) * m1;
-                            df64 v2(0);
-                            for (int k2 = 0; k2 <= dd - k0 - k1; ++k2) mac(v2, Eb[k2 * m1 + n2], row[k2]);
-                            mac(v1, Ea[k1 * m1 + n1], v2);
-                        }
-                        mac(v0, E0[k0 * m1 + n0], v1);
+                const df64 *E0 = sE + (size_t)(b * 3) * mm, *Ea = E0 + mm, *Eb = Ea + mm;
+                df64 v0(0);
+                for (int k0 = 0; k0 <= dd; ++k0) {
+                    df64 v1(0);
+                    for (int k1 = 0; k1 <= dd - k0; ++k1) {
+                        const df64 *row = cube + (k0 * m1 + k1) * m1;
+                        df64 v2(0);
+                        for (int k2 = 0; k2 <= dd - k0 - k1; ++k2) mac(v2, Eb[k2 * m1 + n2], row[k2]);
+                        mac(v1, Ea[k1 * m1 + n1], v2);
                     }
-                    mac(acc[b][sl], pf[b], v0);
+                    mac(v0, E0[k0 * m1 + n0], v1);
                 }
+                mac(acc[sl], pf[b], v0);
             }
         }
         // the warps' partial sums, added in warp order (the staging area is reused)
         __syncthreads();
-        df64 *red = (df64 *)smraw;  // [warps][na][nk]
-        for (int b = 0; b < na; ++b)
-            for (int sl = 0; sl < nslot; ++sl) {
-                const int iv = lane + 32 * sl;
-                if (iv < nk) red[((size_t)warp * na + b) * nk + iv] = acc[b][sl];
-            }
+        df64 *red = (df64 *)smraw;  // [warps][items]
+        for (int sl = 0; sl < nslot; ++sl) {
+            const int t = lane + 32 * sl;
+            if (t < nitem) red[(size_t)warp * nitem + t] = acc[sl];
+        }
         __syncthreads();
-        for (int t = threadIdx.x; t < na * nk; t += blockDim.x) {
-            df64 s = red[t];
-            for (int w = 1; w < kGenM2lWarps; ++w) s += red[(size_t)w * na * nk + t];
-            g.lam[gidx(g, r, bt, 0, 0) + t] = as_double(s);
+        for (int t = threadIdx.x; t < nitem; t += blockDim.x) {
+            df64 sum = red[t];
+            for (int w = 1; w < kGenM2lWarps; ++w) sum += red[(size_t)w * nitem + t];
+            int b, iv;
+            m2l_item(t, na, b, iv);
+            g.lam[gidx(g, r, bt, b, iv)] = as_double(sum);
         }
         __syncthreads();
     }
