@@ -6,14 +6,17 @@
 //   nearfield apply    one CTA per leaf box over the blocks of its nearfield N(Z) (Eq.
 //                      def_st_nearfield), each target element written once (no atomics);
 //   S2M                Eq. s2m at every leaf of a level >= 2;
-//   M2M / L2L          Eq. temp_m2m / st_m2m and their transposes, one CTA per parent / child, with
-//                      q^(t) of the actual (unequal) intervals;
-//   M2L                Eq. m2l with Eq. exp_coeffs_3d: one CTA per target box over its interaction
-//                      list, E as prefactor x three 1D factors tabulated per interval pair (the time
-//                      nodes of unequal intervals differ pair by pair);
+//   M2M / L2L          Eq. temp_m2m / st_m2m and their transposes with q^(t) of the actual
+//                      (unequal) intervals: M2M as one CTA per child (its contribution) plus a
+//                      per-parent sum in child order, L2L as one CTA per child;
+//   M2L                Eq. m2l with Eq. exp_coeffs_3d in double-FP32: one CTA per target box, its
+//                      warps taking (source, a) tasks over the interaction list; E as prefactor x
+//                      three 1D factors tabulated per interval pair (the time nodes of unequal
+//                      intervals differ pair by pair);
 //   L2T                Eq. l2t at every leaf of a level >= 2.
 // Every kernel is a plain grid over the boxes of one phase; phases that depend on coarser or finer
-// levels are launched level by level.
+// levels are launched level by level.  Moments are staged in shared memory as dense cubes and the
+// tensor-product factors are applied one direction at a time.
 #include "df64.cuh"
 #include "device_math.cuh"
 #include "gtree.h"
