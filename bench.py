@@ -565,7 +565,8 @@ def _profile_case(dev, case):
     """Small cases for ncu captures: the learned preconditioner's layers (`mpnn`), its compiled
     form (`mpnn_compiled`), the on-the-fly nearfield (`otf`), the slab M2L of 8^3 grids
     (`m2l_slab`), the FP64 residue-arithmetic nearfield (`crt`, 3072 triangles x 256 steps), the
-    general-step product (`general`, 768 triangles x 64 graded steps, as bench --general).  3072-triangle cube; 128 steps
+    general-step product (`general`, 768 triangles x 64 graded steps, as bench --general), the FP64
+    far field (`passes`: S2M, M2M, M2L, L2L, L2T in double-FP32, 3072 triangles x 256 steps).  3072-triangle cube; 128 steps
     (network) or 32 steps (on-the-fly); 1728-triangle cube x 32 steps with an 8^3 leaf grid
     (c_st 0.1, interaction radius 7) for the slab M2L, far field only."""
     import numpy as np
@@ -591,6 +592,11 @@ def _profile_case(dev, case):
         op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_FP64)
         w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
         run = lambda: op.V(w, parts=P.PFMM_PART_NEAR)  # noqa: E731
+    elif case == "passes":
+        Et = 256
+        op = P.Operator(V, T, 1.0, Et, m_t=4, m_x=6, c_st=1.0, precision=P.PFMM_FP64)
+        w = torch.randn((1, Et, len(T)), dtype=torch.float64, device=dev)
+        run = lambda: op.V(w, parts=P.PFMM_PART_FAR)  # noqa: E731
     elif case == "general":
         V, T = cube_mesh(8)
         Et = 64
@@ -616,7 +622,7 @@ def _profile_case(dev, case):
     e1.record()
     torch.cuda.synchronize()
     out = {"profile_case": case, "ms_per_call": e0.elapsed_time(e1) / 2}
-    if case in ("crt", "m2l_slab", "otf"):
+    if case in ("crt", "m2l_slab", "otf", "passes"):
         info = op.info()
         out.update(nearfield_v_elements=info["nearfield_v_elements"], nf_form=info["nf_form"],
                    m2l_engine=info["m2l_engine"])
@@ -712,7 +718,7 @@ def main():
                     help="run only the general (non-uniform) time-step FMM on 768 tri x 64 graded steps")
     ap.add_argument("--config5-matvec", action="store_true",
                     help="with --config5: the build and matvecs only (no recording, training or solves)")
-    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt", "general"], default=None,
+    ap.add_argument("--profile-case", choices=["mpnn", "mpnn_compiled", "otf", "m2l_slab", "crt", "passes", "general"], default=None,
                     help="profiling only: run one small case of a kernel outside the matvec and exit")
     ap.add_argument("--batch", type=int, default=64, help="problems in the batch measurement (0: skip)")
     ap.add_argument("--n-a", type=int, default=N_A, help="profiling only: squares per cube face edge")
