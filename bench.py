@@ -336,14 +336,39 @@ def _batch_comparison(dev, n_problems, seed=3, tol=3e-3):
             P.pfmm_apply_V(h, w, f, w.shape[0], stream)
 
     t_seq = timed(seq)
+
+    # where the batch's time goes: every problem's apply alone, with its phases (CUDA events
+    # between the phases), summed by phase and by degree
+    by_phase = dict.fromkeys(P.PHASES, 0.0)
+    by_mx, per_problem = {}, []
+    for i, (h, w, f) in enumerate(zip(hs, ws, fs)):
+        P.pfmm_apply_V(h, w, f, w.shape[0], stream)
+        P.pfmm_phase_times(h)
+        P.pfmm_set_profiling(h, True)
+        for _ in range(3):
+            P.pfmm_apply_V(h, w, f, w.shape[0], stream)
+        torch.cuda.synchronize()
+        ph, n = P.pfmm_phase_times(h)
+        P.pfmm_set_profiling(h, False)
+        ms = sum(ph.values()) / max(n, 1)
+        for k in by_phase:
+            by_phase[k] += ph[k] / max(n, 1)
+        m = str(int(probs[i][5].m_x))
+        by_mx[m] = by_mx.get(m, 0.0) + ms
+        per_problem.append((ms, probs[i][1].shape[0], probs[i][3], probs[i][6], int(probs[i][5].m_x)))
     B.close()
     best = min(graph_ms.values())
     mx = [int(p[5].m_x) for p in probs]
+    per_problem.sort(reverse=True)
     return {"workload": f"{n_problems} problems, 768..12288 triangles, 32..256 steps, 1..8 rhs, mixed, "
                         f"autotuned m_x (truncation estimate {tol:g})",
             "space_time_dofs": dofs, "graph_ms_by_streams": graph_ms, "sequential_ms": t_seq,
             "dofs_per_s": dofs / (best * 1e-3), "build_s": t_build,
-            "m_x_histogram": {str(m): mx.count(m) for m in sorted(set(mx))}}
+            "m_x_histogram": {str(m): mx.count(m) for m in sorted(set(mx))},
+            "alone_ms_sum": sum(p[0] for p in per_problem), "alone_ms_by_phase": by_phase,
+            "alone_ms_by_m_x": by_mx,
+            "alone_top8": [{"ms": p[0], "triangles": p[1], "steps": p[2], "rhs": p[3], "m_x": p[4]}
+                           for p in per_problem[:8]]}
 
 
 def _config5(dev, n_rhs=4, n_record=2, tol=1e-6, solve=True):

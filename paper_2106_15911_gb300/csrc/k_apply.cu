@@ -798,16 +798,22 @@ __global__ void k_m2l_s3(M2LArgs A, const R *__restrict__ E1, const R *__restric
 // Fused M2L for grids of at most 4^3 cells: one CTA per (target interval k, time node b, rhs)
 // keeps the source moments of all cells, the intermediates T1, T2 of all cells and the target
 // locals in shared memory.  The grid is padded to FG^3 cells (FG = 4, or 2 for levels with G <= 2,
-// whose CTAs then need an eighth of the shared memory and work).  Every thread owns one
-// multi-index triple and one grid coordinate and keeps an FG x FG block of cells in registers, so
-// each step of its list does FG^3 FMAs from FG^2 moment / intermediate loads and 7 coefficient
-// loads.  Coefficients beyond the
+// whose CTAs then need an eighth of the shared memory and work).  A unit of passes 1 and 2 is a
+// multi-index triple, one budget chain (pass 1: the whole prefix chain; pass 2: one budget value)
+// and two grid coordinates, with the FG cells of the third in registers; an item of pass 3 is a
+// target multi-index and two target coordinates, whose FG locals stay in registers over all
+// terms.  Each step does FG^2 FMAs from FG loads of moments or intermediates and 7 coefficient
+// loads.  Units and items are short chains dealt round-robin over the CTA, so the passes end
+// together.  Coefficients beyond the
 // interaction radius are zeroed once per (J, a), which applies Eq. 03:Iarea without branches.
 // Same arithmetic as the three-pass kernels (cells with G < 4 are padded with empty cells).
 // Split mode (levels with too few intervals to fill the GPU): one CTA per (k, b, source term)
 // with source term = (J, a) of the interaction list; each term's locals go to its own slice of a
 // workspace and k_m2l_sum_terms adds the slices in a fixed order (deterministic).
 constexpr int FGMax = 4;  // padded grid extent per direction: 4, or 2 for the coarse levels (G <= 2)
+
+// C(n, 4), 0 for n < 4: the budget rows of all triples with |t| <= n - 4 (slice offsets of T2)
+__host__ __device__ inline int binom4(int n) { return n < 4 ? 0 : n * (n - 1) * (n - 2) * (n - 3) / 24; }
 
 constexpr int kM2LThreads = 384;
 // split mode below this many (interval, node, rhs) CTAs per SM: eight.  At two resident CTAs per
@@ -836,6 +842,7 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 && 
     int *eof = kin + m1 * m1 * m1;
     int *cbx = eof + nk;                       // [C3] padded cell -> box or -1
     int *eofs = cbx + C3;                      // SL: offset of a triple's budget range within its nu1 slice
+    int *rs = eofs + nk;                       // [ne] pass-2 rows: triple | budget index << 16, per slice
     const int nterm = split ? 2 * na : 1;  // source terms per CTA group: (J index, a)
     const int kb = blockIdx.x / nterm, term = blockIdx.x % nterm;
     const int k = kb / na, b = kb % na, rhs = blockIdx.y;
@@ -857,14 +864,23 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 && 
             off[n1] += mx - s0 + 1;
         }
     }
-    // target locals of this thread's pass-3 items (nu, X1), cells (X1, X2, X3), kept in registers
-    R lamr[2][FG][FG];
+    __syncthreads();
+    // rows of T2 (triple t, budget index j = B' - |t|) in the order pass 2 writes them: T1's order,
+    // or slice by slice (slice nu1 = v holds C(m_x - v + 3, 3) rows, after C(m_x + 4, 4) -
+    // C(m_x - v + 4, 4) rows of the slices before it)
+    for (int t = threadIdx.x; t < nk; t += blockDim.x) {
+        const int tk = kid[t], n1 = tk & 255, s0 = n1 + ((tk >> 8) & 255) + (tk >> 16);
+        const int base = SL ? ne - binom4(mx - n1 + 4) + eofs[t] : eof[t];
+        for (int j = 0; j <= mx - s0; ++j) rs[base + j] = t | (j << 16);
+    }
+    // target locals of this thread's pass-3 items (nu, X1, X2), cells X3, kept in registers
+    constexpr int Q3 = 2 * FG;  // items per thread: nk * FG <= 2 * blockDim.x
+    const int nit3 = nk * FG * FG;
+    R lamr[Q3][FG];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < Q3; ++q)
 #pragma unroll
-        for (int y = 0; y < FG; ++y)
-#pragma unroll
-            for (int z = 0; z < FG; ++z) lamr[q][y][z] = R(0);
+        for (int z = 0; z < FG; ++z) lamr[q][z] = R(0);
     int js[2], nj = 0;
     if (k >= 2) {
         if (k % 2 == 0) { js[0] = k - 2; nj = 1; }
@@ -920,69 +936,64 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 && 
             __syncthreads();
             for (int sl = 0; sl < (SL ? m1 : 1); ++sl) {
             if (SL && sl > 0) __syncthreads();  // the previous slice's pass 3 is done with U
-            // pass 2 (direction y): unit = (triple (nu1, nu2, k3), X1, Y3); registers: cells X2; T2 -> U
-            for (int u = threadIdx.x; u < nitems * FG; u += blockDim.x) {
-                const int z = u % FG, X1 = (u / FG) % FG, t = u / (FG * FG), tk = kid[t];
-                const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16, s0 = nu1 + nu2 + k3;
-                if (SL && nu1 != sl) continue;
-                for (int Bp = s0; Bp <= mx; ++Bp) {
-                    R acc[FG];
+            // pass 2 (direction y): unit = (row (triple (nu1, nu2, k3), budget B'), X1, Y3); registers:
+            // cells X2; T2 -> U.  One budget value per unit keeps the chains short (at most m_x + 1
+            // steps) and spreads a slice's rows over all threads
+            const int r0 = SL ? ne - binom4(mx - sl + 4) : 0;
+            const int r1 = SL ? ne - binom4(mx - sl + 3) : ne;
+            for (int u = r0 * FG * FG + threadIdx.x; u < r1 * FG * FG; u += blockDim.x) {
+                const int z = u % FG, X1 = (u / FG) % FG, rw = rs[u / (FG * FG)];
+                const int t = rw & 0xffff, j = rw >> 16, tk = kid[t];
+                const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, k3 = tk >> 16;
+                R acc[FG];
 #pragma unroll
-                    for (int y = 0; y < FG; ++y) acc[y] = R(0);
-                    for (int k2 = 0; k2 <= Bp - s0; ++k2) {
-                        const int row = eof[kin[(nu1 * m1 + k2) * m1 + k3]] + (Bp - nu2 - nu1 - k2 - k3);
-                        const R *trow = T1s + row * CS + X1 * FG * FG + z;
-                        R e[7];
+                for (int y = 0; y < FG; ++y) acc[y] = R(0);
+                for (int k2 = 0; k2 <= j; ++k2) {
+                    const int row = eof[kin[(nu1 * m1 + k2) * m1 + k3]] + (j - k2);
+                    const R *trow = T1s + row * CS + X1 * FG * FG + z;
+                    R e[7];
 #pragma unroll
-                        for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k2 * m1 + nu2];
+                    for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k2 * m1 + nu2];
 #pragma unroll
-                        for (int Y2 = 0; Y2 < FG; ++Y2) {
-                            const R tv = trow[Y2 * FG];
+                    for (int Y2 = 0; Y2 < FG; ++Y2) {
+                        const R tv = trow[Y2 * FG];
 #pragma unroll
-                            for (int X2 = 0; X2 < FG; ++X2) acc[X2] += e[X2 - Y2 + 3] * tv;
-                        }
+                        for (int X2 = 0; X2 < FG; ++X2) acc[X2] += e[X2 - Y2 + 3] * tv;
                     }
-                    R *out = U + ((SL ? eofs[t] : eof[t]) + Bp - s0) * CS + X1 * FG * FG + z;
-#pragma unroll
-                    for (int X2 = 0; X2 < FG; ++X2) out[X2 * FG] = acc[X2];
                 }
+                R *out = U + (u / (FG * FG) - r0) * CS + X1 * FG * FG + z;
+#pragma unroll
+                for (int X2 = 0; X2 < FG; ++X2) out[X2 * FG] = acc[X2];
             }
             __syncthreads();
-            // pass 3 (direction z): item = (nu, X1), fixed per thread; registers: cells (X2, X3)
+            // pass 3 (direction z): item = (nu, X1, X2), fixed per thread; registers: cells X3
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < Q3; ++q) {
                 const int it = threadIdx.x + q * blockDim.x;
-                if (it >= nitems) break;
-                const int iv = it / FG, X1 = it % FG, tk = kid[iv];
+                if (it >= nit3) break;
+                const int iv = it / (FG * FG), X1 = (it / FG) % FG, X2 = it % FG, tk = kid[iv];
                 const int nu1 = tk & 255, nu2 = (tk >> 8) & 255, nu3 = tk >> 16, smax = mx - nu1 - nu2 - nu3;
                 if (SL && nu1 != sl) continue;
-                R acc[FG][FG];
+                R acc[FG];
 #pragma unroll
-                for (int y = 0; y < FG; ++y)
-#pragma unroll
-                    for (int z = 0; z < FG; ++z) acc[y][z] = R(0);
+                for (int z = 0; z < FG; ++z) acc[z] = R(0);
                 for (int k3 = 0; k3 <= smax; ++k3) {
                     const int t2 = kin[(nu1 * m1 + nu2) * m1 + k3];
                     const int row = (SL ? eofs[t2] : eof[t2]) + (mx - nu3 - nu1 - nu2 - k3);
-                    const R *trow = U + row * CS + X1 * FG * FG;
+                    const R *trow = U + row * CS + X1 * FG * FG + X2 * FG;
                     R e[7];
 #pragma unroll
                     for (int o = 0; o < 7; ++o) e[o] = Es[o * esz + k3 * m1 + nu3];
+                    R tv[FG];
 #pragma unroll
-                    for (int X2 = 0; X2 < FG; ++X2) {
-                        R tv[FG];
+                    for (int Y3 = 0; Y3 < FG; ++Y3) tv[Y3] = trow[Y3];
 #pragma unroll
-                        for (int Y3 = 0; Y3 < FG; ++Y3) tv[Y3] = trow[X2 * FG + Y3];
+                    for (int X3 = 0; X3 < FG; ++X3)
 #pragma unroll
-                        for (int X3 = 0; X3 < FG; ++X3)
-#pragma unroll
-                            for (int Y3 = 0; Y3 < FG; ++Y3) acc[X2][X3] += e[X3 - Y3 + 3] * tv[Y3];
-                    }
+                        for (int Y3 = 0; Y3 < FG; ++Y3) acc[X3] += e[X3 - Y3 + 3] * tv[Y3];
                 }
 #pragma unroll
-                for (int X2 = 0; X2 < FG; ++X2)
-#pragma unroll
-                    for (int X3 = 0; X3 < FG; ++X3) lamr[q][X2][X3] += coef * acc[X2][X3];
+                for (int X3 = 0; X3 < FG; ++X3) lamr[q][X3] += coef * acc[X3];
             }
             }  // slices
         }
@@ -992,19 +1003,17 @@ __global__ void __launch_bounds__(kM2LThreads, FG == 2 ? 2 : (sizeof(R) == 4 && 
     R *lk = (split ? part + (size_t)term * nrhs * A.nint * A.nbox * na * nk : lam) +
             ((size_t)rhs * A.nint + k) * A.nbox * na * nk;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < Q3; ++q) {
         const int it = threadIdx.x + q * blockDim.x;
-        if (it >= nitems) break;
-        const int iv = it / FG, X1 = it % FG;
-        if (X1 >= G) continue;
+        if (it >= nit3) break;
+        const int iv = it / (FG * FG), X1 = (it / FG) % FG, X2 = it % FG;
+        if (X1 >= G || X2 >= G) continue;
 #pragma unroll
-        for (int X2 = 0; X2 < FG; ++X2)
-#pragma unroll
-            for (int X3 = 0; X3 < FG; ++X3) {
-                if (X2 >= G || X3 >= G) continue;
-                const int box = A.cellbox[(X1 * G + X2) * G + X3];
-                if (box >= 0) lk[((size_t)box * na + b) * nk + iv] = lamr[q][X2][X3];
-            }
+        for (int X3 = 0; X3 < FG; ++X3) {
+            if (X3 >= G) continue;
+            const int box = A.cellbox[(X1 * G + X2) * G + X3];
+            if (box >= 0) lk[((size_t)box * na + b) * nk + iv] = lamr[q][X3];
+        }
     }
 }
 
@@ -1213,7 +1222,7 @@ size_t m2l_fused_smem(int G, int nk, int ne, int mx, size_t es, bool sliced)
     const int FG = m2l_fused_fg(G), CS = FG * FG * FG + 1, m1 = mx + 1;
     const size_t urows = sliced ? (size_t)nk : (size_t)std::max(ne, nk);
     return es * (((size_t)ne + urows) * CS + (size_t)7 * m1 * m1) +
-           4 * ((size_t)3 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG);
+           4 * ((size_t)3 * nk + (size_t)m1 * m1 * m1 + FG * FG * FG + ne);
 }
 
 // Which M2L kernel a level takes (prec: 0 FP64, 1 FP32, 2 double-FP32): the fused kernel for FP32
