@@ -74,6 +74,10 @@ def lib():
             L.orc_repr_eval.argtypes = [ctypes.POINTER(Problem), pd, pd, pd, i, pd, i]
             L.orc_E1.restype = d
             L.orc_E1.argtypes = [i, i, d, d, i]
+            L.orc_space_moments.restype = i
+            L.orc_space_moments.argtypes = [ctypes.POINTER(Problem), i, pd, d, i, pd]
+            L.orc_time_moment.restype = d
+            L.orc_time_moment.argtypes = [i, i, d, d, d, d]
             L.orc_qt.restype = d
             L.orc_qt.argtypes = [i, i, i, i]
             L.orc_qx.restype = d
@@ -311,6 +315,29 @@ def nearfield_list(k):
 
 def E1(k, l, r, dab, mx):
     return lib().orc_E1(k, l, r, dab, mx)
+
+
+def space_moments(P, x, cen, hp, op=0):
+    """Spatial moments of triangle x about the padded box (cen, hp) used by S2M / L2T (Eq. s2m,
+    l2t): op 0 -> [n_kappa] values int_x T_{Y,kappa}; op 1 -> [n_kappa, 3] values
+    int_x alpha n.grad T_{Y,kappa} phi_v.  Multi-indices with |kappa| <= m_x, kappa_1 slowest
+    (``multi_indices``)."""
+    nk = len(multi_indices(P.m_x))
+    out = np.zeros(nk * (3 if op else 1))
+    c = np.ascontiguousarray(cen, dtype=np.float64)
+    n = lib().orc_space_moments(ctypes.byref(P), int(x), _pd(c), float(hp), int(op), _pd(out))
+    assert n == nk
+    return out.reshape(nk, 3) if op else out
+
+
+def multi_indices(m):
+    """The oracle's multi-index order: kappa with |kappa| <= m, kappa_1 slowest."""
+    return [(a, b, c) for a in range(m + 1) for b in range(m + 1 - a) for c in range(m + 1 - a - b)]
+
+
+def time_moment(a, m, jlo, jhi, lo, h):
+    """int over (lo, lo + h] of the Lagrange polynomial L_{J,a} of the interval J = (jlo, jhi]."""
+    return lib().orc_time_moment(a, m, jlo, jhi, lo, h)
 
 
 def qt(c, ac, ap, m):

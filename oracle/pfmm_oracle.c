@@ -1311,6 +1311,27 @@ int orc_sizeof_problem(void) { return (int)sizeof(orc_problem); }
 int orc_interaction_list(int k, int *js) { return or_interaction_list(k, js); }
 int orc_nearfield_list(int k, int *js) { return or_nearfield_list(k, js); }
 
+/* Exposed for the S2M / L2T moment pins (Eq. s2m, l2t): the spatial moments of triangle x about
+ * the padded box (cen, hp) -- op 0: int_x T_{Y,kappa}; op 1: int_x alpha n.grad T_{Y,kappa} phi_v,
+ * three per multi-index -- in the oracle's multi-index order (kappa_1 slowest); returns their
+ * count n_kappa.  And the time moment int_(lo, lo+h] L_{J,a} of the interval J = (jlo, jhi]. */
+int orc_space_moments(const orc_problem *P, int x, const double *cen, double hp, int op, double *out)
+{
+    or_fmm F;
+    memset(&F, 0, sizeof F);
+    F.P = P;
+    or_mi_make(P->m_x, &F.mi);
+    or_space_moments(&F, x, cen, hp, op, out);
+    const int nk = F.mi.nk;
+    free(F.mi.k);
+    free(F.mi.lookup);
+    return nk;
+}
+double orc_time_moment(int a, int m, double jlo, double jhi, double lo, double h)
+{
+    return or_time_moment(a, m, jlo, jhi, lo, h);
+}
+
 /* ======================================================================================
  * 9. Representation formula (Section 2): for (x, t) in Omega x (0, T)
  *      u(x, t) = (V~ w)(x, t) - (W u)(x, t),
