@@ -155,22 +155,36 @@ def _dense_rows_error(V, T, Et, w, outs, n_rows=8, nthreads=0):
     return {k: float(np.max(np.abs(v[:, rows] - ref)) / den) for k, v in outs.items()}, len(rows)
 
 
-def phase_rooflines(phases, info, es, nt, Et, mx, mt, peaks):
+# FP32 operations of one double-FP32 multiply-add (FMA two-product, two-sum, renormalisation):
+# the FP64 mode's FMM passes reach at most the FP32 rate divided by this
+DF64_FP32_OPS_PER_MAC = 15
+
+
+def phase_rooflines(phases, info, es, nt, Et, mx, mt, peaks, arith=None):
     """Algorithmic work per apply of every phase, the rate it achieved in its measured phase time
-    and the fraction of the relevant peak.  S2M / L2T: 2 E_t E_x n_kappa + 4 (leaves) n_a n_kappa
-    flops; M2L: the separable passes' flops reported by the library (info m2l_flops); nearfield:
-    2 sum_t |D(t)| nnz(A_d) flops on the stored elements.  peaks: hbm_gbs, fp64_tflops,
-    fp32_tflops (and fp16_tflops for a tensor-core nearfield)."""
+    and the fraction of the peak of the unit it runs on.  S2M / L2T: 2 E_t E_x n_kappa + 4 (leaves)
+    n_a n_kappa flops; M2L: the separable passes' flops reported by the library (info m2l_flops);
+    nearfield: 2 sum_t |D(t)| nnz(A_d) flops on the stored elements.  arith: "fp32" (mixed mode),
+    "df64" (FP64 mode: passes in double-FP32 on the FP32 pipe, peak = FP32 rate /
+    DF64_FP32_OPS_PER_MAC; nearfield as residue products on the tensor cores where the handle
+    has them, 32 B per stored element) or "fp64" (native FP64 on the FP64 pipe); default from es.
+    peaks: hbm_gbs, fp64_tflops, fp32_tflops, fp16_tflops."""
     from math import comb
 
+    arith = arith or ("fp64" if es == 8 else "fp32")
     nk, na = comb(mx + 3, 3), mt + 1
     p = info["p"]
     nleaf = info["nbox"][p] * (Et // 2)
     dof = nt * Et
-    fma = peaks["fp64_tflops"] if es == 8 else peaks["fp32_tflops"]
+    if arith == "df64":
+        fma, fsrc = peaks["fp32_tflops"] / DF64_FP32_OPS_PER_MAC, "FP32 FMA rate / %d (double-FP32)" % DF64_FP32_OPS_PER_MAC
+    elif arith == "fp64":
+        fma, fsrc = peaks["fp64_tflops"], "FP64 FMA rate"
+    else:
+        fma, fsrc = peaks["fp32_tflops"], "FP32 FMA rate"
     out = {}
 
-    def put(name, flops, byts, ms, fpeak):
+    def put(name, flops, byts, ms, fpeak, src):
         if not ms or ms <= 0:
             return
         d = {"ms": ms, "flops": flops, "bytes": byts, "tflops": flops / (ms * 1e-3) / 1e12,
@@ -178,19 +192,27 @@ def phase_rooflines(phases, info, es, nt, Et, mx, mt, peaks):
         d["frac_fp"] = d["tflops"] / fpeak
         d["frac_hbm"] = d["gbs"] / peaks["hbm_gbs"]
         d["bound"] = "fp" if d["frac_fp"] >= d["frac_hbm"] else "hbm"
+        d["fp_peak_tflops"], d["fp_peak"] = fpeak, src
         out[name] = d
 
     s2m_f = 2.0 * Et * nt * nk + 2.0 * nleaf * 2 * na * nk
-    put("s2m", s2m_f, es * dof + es * nt * nk + es * nleaf * na * nk, phases.get("s2m"), fma)
-    put("l2t", s2m_f, 16.0 * dof + es * nt * nk + es * nleaf * na * nk, phases.get("l2t"), fma)
+    put("s2m", s2m_f, es * dof + es * nt * nk + es * nleaf * na * nk, phases.get("s2m"), fma, fsrc)
+    put("l2t", s2m_f, 16.0 * dof + es * nt * nk + es * nleaf * na * nk, phases.get("l2t"), fma, fsrc)
     if p >= 2:
         put("m2l", info["m2l_flops"],
-            2.0 * es * sum(info["nbox"][l] * 2 ** l for l in range(2, p + 1)) * na * nk, phases.get("m2l"), fma)
+            2.0 * es * sum(info["nbox"][l] * 2 ** l for l in range(2, p + 1)) * na * nk, phases.get("m2l"), fma, fsrc)
     nel = info["nearfield_v_elements"]
     nf_flops = 2.0 * (nel / 4) * (Et // 2) * 7  # 2 sum_t |D(t)| nnz(A_d): |D| = 3, 4 on the two steps
-    tc = bool(info.get("nf_tensor_cores", 0) & 1) and es == 4
-    put("nearfield", nf_flops, nel * (4 if tc else es) + 16.0 * dof, phases.get("nearfield"),
-        peaks.get("fp16_tflops", fma) if tc else fma)
+    tc = bool(info.get("nf_tensor_cores", 0) & 1)
+    if tc and arith == "fp32":  # scaled FP16 hi / lo parts: 4 B per element, 3 FP16 products
+        put("nearfield", nf_flops, nel * 4 + 16.0 * dof, phases.get("nearfield"), peaks["fp16_tflops"] / 3,
+            "FP16 tensor peak / 3 (hi / lo products)")
+    elif tc and arith == "df64":  # residues modulo 16 primes: 32 B per element, 16 FP16 products
+        put("nearfield", nf_flops, nel * 32 + 48.0 * dof, phases.get("nearfield"), peaks["fp16_tflops"] / 16,
+            "FP16 tensor peak / 16 (residue products)")
+    else:
+        put("nearfield", nf_flops, nel * es + 16.0 * dof, phases.get("nearfield"), peaks["fp64_tflops"] if es == 8
+            else peaks["fp32_tflops"], "FP64 FMA rate" if es == 8 else "FP32 FMA rate")
     return out
 
 
@@ -871,7 +893,7 @@ def main():
     # ---- rooflines: every phase from its algorithmic work; the dominant kernel is the nearfield
     peaks = _peaks(P, stream)
     es = 8 if head == P.PFMM_FP64 else 4
-    rl = phase_rooflines(phases, info, es, nt, ET, M_X, M_T, peaks)
+    rl = phase_rooflines(phases, info, es, nt, ET, M_X, M_T, peaks, arith="df64" if head == P.PFMM_FP64 else "fp32")
     nf = rl["nearfield"]
     tc = head == P.PFMM_MIXED and bool(info["nf_tensor_cores"] & 1)
     crt = head == P.PFMM_FP64 and bool(info["nf_tensor_cores"] & 1)
@@ -928,7 +950,7 @@ def main():
                       "value": dof / (statistics.mean(ms2) * 1e-3), "ms_per_step": statistics.mean(ms2),
                       "phases_ms": ph2, "build_s": t_build2, "mixed_vs_fp64_rel_maxnorm": rel,
                       "rooflines": phase_rooflines(ph2, info2, 8 if other == P.PFMM_FP64 else 4, nt, ET, M_X, M_T,
-                                                   peaks),
+                                                   peaks, arith="df64" if other == P.PFMM_FP64 else "fp32"),
                       "nf_tensor_cores": info2["nf_tensor_cores"]}
         op2.close()
 
