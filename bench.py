@@ -982,7 +982,13 @@ def main():
         cfg = _config_dict(nt, world)
         cfg.update({"precision": args.precision, "build_s": t_build,
                     "nearfield_GB": info["nearfield_bytes"] / 1e9, "nf_form": info["nf_form"],
-                    "nf_form_ms_at_build": info["nf_form_ms"], "m2l_engine": info["m2l_engine"]})
+                    "nf_form_ms_at_build": info["nf_form_ms"], "m2l_engine": info["m2l_engine"],
+                    "arithmetic": ("FP64-accurate: nearfield as exact integer products of residues modulo 16 primes "
+                                   "(FP16 tcgen05 MMAs, exact FP32 accumulation, Garner's combination to FP64); FMM "
+                                   "passes in double-FP32 (two FP32 words, about 48 significant bits); FP64 in / out"
+                                   if head == P.PFMM_FP64 else
+                                   "mixed: nearfield as three FP16 products of scaled hi / lo parts on tcgen05 with "
+                                   "FP32 accumulation; FMM passes in FP32; FP64 in / out")})
         line = {"metric": METRIC, "value": value, "unit": "space-time DOF/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if head == P.PFMM_FP64 else "f32", "data": "synthetic",
